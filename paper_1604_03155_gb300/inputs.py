@@ -1,0 +1,182 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests, the bench and the oracle.
+
+This module holds no arithmetic of the volume-potential method: it only draws
+random numbers and samples the test densities on the grid.  Both sides of every
+parity check read the arrays produced here, so the CUDA library and the CPU
+oracle always see bit-identical inputs.
+
+Random numbers come from one counter-based generator, splitmix64 (Steele, Lea &
+Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014): the i-th
+draw of stream ``seed`` is ``mix(seed + (i + 1) * 0x9E3779B97F4A7C15)``.  Uniform
+doubles take the top 53 bits; normal draws use the Box-Muller transform.
+
+Grid convention (paper Section 4): N even, h = 1/N, storage index p in [0, N)
+maps to grid index i = p - N/2 + 1 and coordinate x = i * h, so the origin is a
+grid node and the box is [-1/2 + h, 1/2] per axis.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+# Base seed of the workload recipes; workload c uses BASE_SEED + c.
+BASE_SEED = 1604031550
+
+
+def splitmix64(seed: int, count: int, offset: int = 0) -> np.ndarray:
+    """Draws ``offset .. offset+count-1`` of the splitmix64 stream ``seed`` (uint64)."""
+    with np.errstate(over="ignore"):
+        ctr = np.arange(offset + 1, offset + count + 1, dtype=np.uint64)
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + ctr * _GAMMA
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform(seed: int, count: int, offset: int = 0) -> np.ndarray:
+    """Uniform doubles in [0, 1) from the top 53 bits of each draw."""
+    return (splitmix64(seed, count, offset) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+def normal(seed: int, count: int, offset: int = 0) -> np.ndarray:
+    """Standard normal doubles by Box-Muller on pairs of uniforms."""
+    npair = (count + 1) // 2
+    u = uniform(seed, 2 * npair, 2 * offset)
+    u1 = 1.0 - u[0::2]  # (0, 1]
+    u2 = u[1::2]
+    r = np.sqrt(-2.0 * np.log(u1))
+    z = np.empty(2 * npair)
+    z[0::2] = r * np.cos(2.0 * np.pi * u2)
+    z[1::2] = r * np.sin(2.0 * np.pi * u2)
+    return z[:count]
+
+
+def grid_coords(N: int) -> np.ndarray:
+    """Coordinates x_p = (p - N/2 + 1)/N of one grid axis (paper Section 4)."""
+    if N <= 0 or N % 2:
+        raise ValueError("N must be a positive even integer")
+    p = np.arange(N, dtype=np.float64)
+    return (p - N // 2 + 1) / N
+
+
+@dataclass
+class GaussianSources:
+    """f(x) = sum_q a_q exp(-|x - c_q|^2 / sigma_q^2)."""
+
+    centres: np.ndarray  # (Q, d)
+    sigmas: np.ndarray  # (Q,)
+    amps: np.ndarray  # (Q,) complex
+
+    @property
+    def d(self) -> int:
+        return self.centres.shape[1]
+
+
+def random_gaussians(seed: int, count: int, d: int, centre_half_width: float = 0.3,
+                     sigma_range=(0.03, 0.08), complex_amps: bool = True) -> GaussianSources:
+    """Gaussian sources with centres U[-w, w]^d, widths U[sigma_range] and
+    amplitudes whose real and imaginary parts are independent N(0, 1)."""
+    u = uniform(seed, count * (d + 1))
+    centres = (2.0 * u[: count * d].reshape(count, d) - 1.0) * centre_half_width
+    lo, hi = sigma_range
+    sigmas = lo + (hi - lo) * u[count * d:]
+    z = normal(seed ^ 0x5DEECE66D, 2 * count)
+    amps = z[:count] + (1j * z[count:] if complex_amps else 0.0)
+    return GaussianSources(centres, sigmas, amps.astype(np.complex128))
+
+
+def sample_gaussians(src: GaussianSources, N: int) -> np.ndarray:
+    """Samples the sources on the N^d grid, C order, last axis fastest (complex128)."""
+    x = grid_coords(N)
+    d = src.d
+    f = np.zeros((N,) * d, dtype=np.complex128)
+    for c, s, a in zip(src.centres, src.sigmas, src.amps):
+        # separable: exp(-sum_j (x_j - c_j)^2 / s^2) = prod_j exp(-(x_j - c_j)^2 / s^2)
+        term = np.array(a, dtype=np.complex128)
+        for j in range(d):
+            e = np.exp(-((x - c[j]) ** 2) / (s * s))
+            shape = [1] * d
+            shape[j] = N
+            term = term * e.reshape(shape)
+        f += term
+    return f
+
+
+def random_complex_field(seed: int, shape) -> np.ndarray:
+    """Unstructured complex N(0,1) field, for linearity and edge-case checks."""
+    n = int(np.prod(shape))
+    z = normal(seed, 2 * n)
+    return (z[:n] + 1j * z[n:]).reshape(shape)
+
+
+# ---------------------------------------------------------------------------
+# Workload recipes (the five configurations of the benchmark suite)
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Workload:
+    name: str
+    d: int
+    N: int
+    kernel: str  # "laplace" | "helmholtz"
+    k: float
+    L: float  # <= 0 selects the paper's default (1.8 in 3D, 1.5 in 2D)
+    seed: int
+    n_gauss: int
+    precision: str  # "fp64" | "fp32"
+    grad: bool = False
+    extra: dict = field(default_factory=dict)
+
+    def density(self, N: int | None = None) -> np.ndarray:
+        """The workload's density, optionally sampled on another grid size."""
+        N = self.N if N is None else N
+        if self.name == "laplace3d_single_gaussian":
+            src = GaussianSources(np.zeros((1, 3)), np.array([0.08]), np.array([1.0 + 0j]))
+        else:
+            src = random_gaussians(self.seed, self.n_gauss, self.d)
+        return sample_gaussians(src, N)
+
+
+def workload(name: str) -> Workload:
+    """The five benchmark workloads by name."""
+    if name == "laplace3d_single_gaussian":  # 3D Laplace, N=32, one Gaussian sigma=0.08, FP64
+        return Workload(name, 3, 32, "laplace", 0.0, 1.8, BASE_SEED + 1, 1, "fp64")
+    if name == "helmholtz2d_k40_n1024_grad":  # 2D Helmholtz k=40, N=1024, 8 Gaussians, FP32 + grad
+        return Workload(name, 2, 1024, "helmholtz", 40.0, 1.5, BASE_SEED + 2, 8, "fp32", grad=True)
+    if name == "helmholtz3d_k60_n256":  # 3D Helmholtz k=60, N=256, 16 Gaussians, FP32
+        return Workload(name, 3, 256, "helmholtz", 60.0, 1.8, BASE_SEED + 3, 16, "fp32")
+    raise KeyError(name)
+
+
+def batch_recipe(seed: int = BASE_SEED + 4, count: int = 64):
+    """64 densities: N uniform in {48, 64, 96, 128}, half Laplace and half
+    Helmholtz with k ~ U[5, 40], four Gaussians each (3D, FP32)."""
+    u = uniform(seed, 2 * count)
+    sizes = np.array([48, 64, 96, 128])
+    out = []
+    for i in range(count):
+        N = int(sizes[min(3, int(u[i] * 4))])
+        helm = i >= count // 2
+        k = 5.0 + 35.0 * u[count + i] if helm else 0.0
+        w = Workload(f"batch{i}", 3, N, "helmholtz" if helm else "laplace", k, 1.8,
+                     seed * 1000 + i, 4, "fp32")
+        out.append(w)
+    return out
+
+
+def to_device_dtype(f: np.ndarray, precision: str) -> np.ndarray:
+    """The array both sides consume: complex64 for the FP32 path, complex128 for FP64."""
+    return f.astype(np.complex64 if precision == "fp32" else np.complex128)
+
+
+def gaussian_amplitude(sigma_cfg: float, d: int) -> float:
+    """exp(-r^2/sigma^2) = Q * rho(r) with rho the unit-mass Gaussian of standard
+    deviation sigma/sqrt(2); returns Q = (pi sigma^2)^(d/2)."""
+    return (math.pi * sigma_cfg * sigma_cfg) ** (d / 2)

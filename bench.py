@@ -1,0 +1,401 @@
+"""Benchmark of the volume-potential apply on GB300.
+
+Default workload: 2D Helmholtz, k = 40, N = 1024 (2N = 2048 FFTs), eight random
+Gaussian sources, FP32 complex apply with exact gradients (phi + 2 gradient
+fields from one forward transform), FP64 precompute done once before timing.
+
+One step = one vp_apply_grad on inputs resident in HBM; L2 (129 MB) is flushed
+by writing a 256 MB buffer before every timed step, outside the timed events.
+The metric is grid points per second per potential, N^d / t_step (a gradient
+call counts once).  Printed as one JSON line on rank 0.
+
+--impl reference times the CPU oracle (float64, its own FFT) on the same
+workload instead; it is a deliberately slow correctness reference.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOADS = {
+    "helmholtz2d_k40_n1024_grad": dict(d=2, N=1024, kernel="helmholtz", k=40.0, L=1.5, grad=True),
+    "helmholtz3d_k60_n256": dict(d=3, N=256, kernel="helmholtz", k=60.0, L=1.8, grad=False),
+    "laplace3d_single_gaussian": dict(d=3, N=32, kernel="laplace", k=0.0, L=1.8, grad=False),
+}
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="helmholtz2d_k40_n1024_grad", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1604_03155_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, fn), "rb") as fh:
+                h.update(fn.encode())
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(pass_name: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.md")
+    if not os.path.exists(path):
+        return None
+    want = kernel_source_hash()
+    for ln in open(path):
+        parts = [p.strip() for p in ln.strip().strip("|").split("|")]
+        if len(parts) >= 4 and parts[0] == pass_name and parts[1] == workload and parts[3] == want:
+            try:
+                return float(parts[2])
+            except ValueError:
+                return None
+    return None
+
+
+def pass_bytes(d: int, N: int, F: int, csize: int) -> dict:
+    """Algorithmic bytes per launch of each pass (pruned schedule, U = N^d complex
+    elements): reads of the nonzero half only, writes of the kept half only."""
+    U = N ** d * csize
+    oct_b = (N + 1) ** d * csize
+    if d == 3:
+        return {"fwd_rows": 3 * U, "fwd_axis1": 6 * U, "fused_axis0": 4 * U + F * oct_b + F * 4 * U,
+                "inv_axis1": F * 6 * U, "inv_rows": 3 * U}
+    return {"fwd_rows": 3 * U, "fused_axis0": 2 * U + F * oct_b + F * 2 * U, "inv_rows": 3 * U}
+
+
+# ---------------------------------------------------------------------------
+# oracle (CPU) timing: the cpu_baseline leg and the reference arm
+# ---------------------------------------------------------------------------
+
+def oracle_step(wl: dict, f: np.ndarray, Gf, Gjf):
+    from oracle import apply as A
+    phi = A.apply_fft2n(Gf, f)
+    grads = [A.apply_fft2n(g, f) for g in Gjf] if wl["grad"] else []
+    return phi, grads
+
+
+def oracle_setup(wl: dict):
+    from oracle import kernel as K
+    d, N = wl["d"], wl["N"]
+    T = K.T_octant_by_sums(d, N, wl["kernel"], wl["k"], wl["L"])
+    Gf = K.ghat_full_from_octant(K.ghat_octant_by_sums(T, N))
+    Gjf = []
+    if wl["grad"]:
+        for j in range(d):
+            Tj = K.T_octant_by_sums(d, N, wl["kernel"], wl["k"], wl["L"], deriv_axis=j)
+            Gjf.append(K.ghat_full_from_octant(K.ghat_octant_by_sums(Tj, N, odd_axis=j), odd_axis=j))
+    return Gf, Gjf
+
+
+def time_oracle(wl: dict, f: np.ndarray, steps: int, Gf=None, Gjf=None):
+    if Gf is None:
+        Gf, Gjf = oracle_setup(wl)
+    f = np.asarray(f, dtype=np.complex128)
+    wall, cpu = 0.0, 0.0
+    out = None
+    for _ in range(steps):
+        t0, c0 = time.perf_counter(), time.process_time()
+        out = oracle_step(wl, f, Gf, Gjf)
+        wall += time.perf_counter() - t0
+        cpu += time.process_time() - c0
+    pts = wl["N"] ** wl["d"] * steps
+    return {"value": pts / wall, "seconds": wall, "cores": round(cpu / wall, 2), "out": out}
+
+
+def density_for(name: str, wl: dict, rank: int = 0):
+    from paper_1604_03155_gb300 import inputs as I
+    if name == "laplace3d_single_gaussian":
+        return I.workload(name).density()
+    base = I.workload(name)
+    src = I.random_gaussians(base.seed + 7919 * rank, base.n_gauss, base.d)
+    return I.sample_gaussians(src, base.N)
+
+
+def run_reference(args, wl):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    steps = max(1, args.steps)
+    f = density_for(args.workload, wl).astype(np.complex64)
+    Gf, Gjf = oracle_setup(wl)
+    for _ in range(min(args.warmup, 1)):
+        oracle_step(wl, f.astype(np.complex128), Gf, Gjf)
+    r = time_oracle(wl, f, steps, Gf, Gjf)
+    unit = "grid pts/s"
+    line = {
+        "impl": "reference",
+        "metric": "grid pts/s per potential (N^d/s), % HBM roofline, vs plain FP64 at stated rel err",
+        "value": r["value"], "unit": unit, "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * r["seconds"] / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, **{k: v for k, v in wl.items()}},
+        "cpu_baseline": {"value": r["value"], "unit": unit, "cores": r["cores"], "kind": "oracle",
+                         "sample": f"full {args.workload} apply per step (phi + gradients), FP64 oracle, own FFT"},
+        "e2e": {"value": r["value"], "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the CUDA path
+# ---------------------------------------------------------------------------
+
+def run_ours(args, wl):
+    import torch
+    import torch.distributed as dist
+
+    from oracle import apply as OA  # noqa: F401  (cpu_baseline leg only)
+    from paper_1604_03155_gb300.vp import Plan
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    d, N, F = wl["d"], wl["N"], (1 + wl["d"]) if wl["grad"] else 1
+    prec = args.precision
+    cdt = torch.complex64 if prec == "fp32" else torch.complex128
+    npdt = np.complex64 if prec == "fp32" else np.complex128
+
+    stream = torch.cuda.Stream(device=dev)
+    t0 = time.perf_counter()
+    plan = Plan(d, N, wl["kernel"], wl["k"], wl["L"], precision=prec, grad_mode="exact")
+    if wl["grad"]:
+        plan.get_array("ghatj", 0)  # builds the derivative multipliers (precompute)
+    precompute_s = time.perf_counter() - t0
+    plan.set_stream(stream)
+
+    f_host = density_for(args.workload, wl, rank).astype(npdt)
+    f = torch.from_numpy(f_host).to(dev)
+    phi = torch.empty_like(f)
+    grad = torch.empty((d,) + f.shape, dtype=cdt, device=dev) if wl["grad"] else None
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        if wl["grad"]:
+            plan.apply_grad(f, phi, grad)
+        else:
+            plan.apply(f, phi)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            step()
+    torch.cuda.synchronize(dev)
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    clocks = ClockSampler(vis.split(",")[local] if vis else local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    plan.get_timing()  # reset the per-pass counters
+    plan.set_timing(True)
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.fill_(float(i))  # evict L2 (256 MB > 129 MB), outside the timed events
+            starts[i].record(stream)
+            step()
+            stops[i].record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    plan.set_timing(False)
+    passes = plan.get_timing()
+    clk = clocks.stop()
+    total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, stops))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = (N ** d) * world / (ms_per_step / 1000.0)
+
+    # roofline of the dominant pass (per launch, events on the plan's stream)
+    csize = 8 if prec == "fp32" else 16
+    pb = pass_bytes(d, N, F, csize)
+    dom = max((k for k in passes if passes[k][0] > 0), key=lambda k: passes[k][1])
+    dom_launches, dom_ms = passes[dom]
+    dom_avg_s = dom_ms / dom_launches / 1000.0
+    peak, peak_kind = measured_peak_hbm()
+    achieved = pb[dom] / dom_avg_s / 1e9
+    traffic = ncu_traffic(dom, args.workload)
+    launches_per_step = plan.launch_count(wl["grad"])
+
+    # end to end through the C ABI with host buffers (pinned), copies inside
+    f_pin = torch.from_numpy(f_host).pin_memory()
+    phi_pin = torch.empty_like(f_pin).pin_memory()
+    grad_pin = torch.empty((d,) + f_pin.shape, dtype=cdt).pin_memory() if wl["grad"] else None
+    e2e_steps = max(3, min(args.steps, 20))
+    plan.set_stream(stream)
+    for _ in range(2):
+        plan.apply_grad(f_pin, phi_pin, grad_pin) if wl["grad"] else plan.apply(f_pin, phi_pin)
+    te = time.perf_counter()
+    for _ in range(e2e_steps):
+        plan.apply_grad(f_pin, phi_pin, grad_pin) if wl["grad"] else plan.apply(f_pin, phi_pin)
+    e2e_s = (time.perf_counter() - te) / e2e_steps
+    U_b = (N ** d) * csize
+
+    # FP64 form on the same grid (same kernels in double), for "vs plain FP64"
+    fp64 = None
+    if prec == "fp32":
+        plan.set_precision("fp64")
+        f64 = f.to(torch.complex128)
+        phi64 = torch.empty_like(f64)
+        grad64 = torch.empty((d,) + f64.shape, dtype=torch.complex128, device=dev) if wl["grad"] else None
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                plan.apply_grad(f64, phi64, grad64) if wl["grad"] else plan.apply(f64, phi64)
+            s64 = [torch.cuda.Event(enable_timing=True) for _ in range(10)]
+            e64 = [torch.cuda.Event(enable_timing=True) for _ in range(10)]
+            for i in range(10):
+                flush.fill_(float(i))
+                s64[i].record(stream)
+                plan.apply_grad(f64, phi64, grad64) if wl["grad"] else plan.apply(f64, phi64)
+                e64[i].record(stream)
+        torch.cuda.synchronize(dev)
+        ms64 = sum(a.elapsed_time(b) for a, b in zip(s64, e64)) / 10
+        fp64 = {"value": (N ** d) / (ms64 / 1000.0), "ms_per_step": ms64, "speedup_of_fp32": ms64 / ms_per_step}
+        plan.set_precision("fp32")
+
+    line = None
+    if rank == 0:
+        line = {
+            "metric": "grid pts/s per potential (N^d/s), % HBM roofline, vs plain FP64 at stated rel err",
+            "value": value, "unit": "grid pts/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "d": d, "N": N, "kernel": wl["kernel"], "k": wl["k"],
+                       "L": wl["L"], "fields": F, "grad_mode": "exact" if wl["grad"] else None,
+                       "l2": "flushed before every timed step (256 MB write)", "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic,
+                         "algorithmic_bytes_per_launch": pb[dom], "avg_launch_ms": dom_avg_s * 1000.0},
+            "passes": {k: {"launches": v[0], "avg_ms": (v[1] / v[0] if v[0] else None)} for k, v in passes.items()},
+            "clocks": clk,
+            "e2e": {"value": (N ** d) / e2e_s, "unit": "grid pts/s", "h2d_bytes_per_step": U_b,
+                    "d2h_bytes_per_step": U_b * F},
+            "gpu_launches": launches_per_step * args.steps,
+            "precompute_s": precompute_s,
+            "fp64_form": fp64,
+        }
+        if not args.no_cpu_baseline and world == 1:
+            r = time_oracle(wl, f_host.astype(np.complex128), 1)
+            phi_o, grads_o = r["out"]
+            from oracle import apply as A
+            errs = {"phi": A.rel_l2(phi.cpu().numpy(), phi_o)}
+            if wl["grad"]:
+                errs["grad"] = A.rel_l2(grad.cpu().numpy(), np.stack(grads_o))
+            line["cpu_baseline"] = {"value": r["value"], "unit": "grid pts/s", "cores": r["cores"], "kind": "oracle",
+                                    "sample": f"one full {args.workload} apply (phi + gradients), FP64 oracle, own FFT"}
+            line["rel_l2_vs_oracle"] = errs
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,155 @@
+/*
+ * vp.h -- C ABI of the GB300 volume-potential library.
+ *
+ * The library computes volume potentials phi = g_k * f on a uniform N^d grid
+ * with the truncated-Green's-function method of Vico, Greengard & Ferrando,
+ * "Fast convolution with free-space Green's functions" (arXiv:1604.03155):
+ *
+ *   phi(x) = int_D g_k(x - y) f(y) dy,  D = [-1/2, 1/2]^d        (Section 1, eq. volint)
+ *
+ * where g_k is the free-space Green's function of -(Delta + k^2): e^{ikr}/(4 pi r)
+ * in 3D, (i/4) H_0^(1)(kr) in 2D, 1/(4 pi r) and -log(r)/(2 pi) for k = 0
+ * (Tables 1-2).  The kernel is cut off at r = L (Section 1, g^L) so that its
+ * Fourier transform G^L is smooth; G^L is sampled on the 4N-oversampled grid
+ * and inverse transformed once to the discrete kernel T (Section 4, the
+ * "precomputation step"); every apply is then a zero-padded (2N)^d FFT
+ * convolution (Section 4), optionally with gradients by spectral
+ * differentiation (Section 3).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid (Section 4): N even, h = 1/N; storage index p_j in [0, N) on each axis
+ *   maps to grid index i_j = p_j - N/2 + 1 and coordinate x_j = i_j h, so the
+ *   origin is a node.  Arrays are C order (last axis fastest), N^d elements.
+ * Result: phi_p = sum_{p'} T(p - p') f_{p'}, the quadrature weight h^d included,
+ *   so phi approximates the integral above to spectral accuracy for smooth f.
+ * Pointers: f, phi and grad may be device pointers (asynchronous on the
+ *   plan's stream) or host pointers (the call stages through device memory
+ *   and returns when the host result is written).  phi may not alias f.
+ * Complex data is interleaved (re, im).  grad holds d contiguous N^d blocks,
+ *   block j = d phi / d x_j.
+ * Errors: every call returns a vp_status and never aborts; argument errors are
+ *   reported before any device work.  vp_last_error() gives a message.
+ */
+#ifndef VP_H
+#define VP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vp_plan_s* vp_plan; /* opaque; owned by the library */
+
+typedef enum {
+  VP_OK = 0,
+  VP_ERR_INVALID_ARG = 1, /* bad argument (NULL, out of range, wrong dtype) */
+  VP_ERR_UNSUPPORTED = 2, /* valid but not built (grid size without an FFT plan) */
+  VP_ERR_OOM = 3,         /* device allocation failed */
+  VP_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+  VP_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
+  VP_ERR_NUMERICAL = 6    /* non-finite value where a finite one is required */
+} vp_status;
+
+typedef enum { VP_LAPLACE = 0, VP_HELMHOLTZ = 1 } vp_kernel;
+
+/* Arithmetic of the apply.  The precompute is always FP64. */
+typedef enum { VP_FP32 = 0, VP_FP64 = 1 } vp_precision;
+
+/* Gradient definition (Section 3, spectral differentiation):
+ *  VP_GRAD_EXACT      derivative kernels T_j = inverse 4N transform of i s_j G^L
+ *                     (the Nyquist sample zeroed), cropped and transformed like
+ *                     T; the exact derivative of the discretised integral.
+ *  VP_GRAD_SPECTRAL2N multiply the (2N)^d product by i pi m_j (the 2N grid's own
+ *                     frequencies, Nyquist zeroed); agrees with EXACT to
+ *                     spectral accuracy when f is negligible at the box edge. */
+typedef enum { VP_GRAD_EXACT = 0, VP_GRAD_SPECTRAL2N = 1 } vp_grad_mode;
+
+/* Element type of f, phi and grad.  Complex types work for every kernel; real
+ * types only for VP_LAPLACE (real kernel, real potential).  The type must
+ * match the plan's precision: R32/C64 for FP32, R64/C128 for FP64. */
+typedef enum { VP_R32 = 0, VP_C64 = 1, VP_R64 = 2, VP_C128 = 3 } vp_dtype;
+
+/* Precomputed arrays that can be read back (FP64, complex128 octants). */
+typedef enum {
+  VP_ARRAY_T = 0,     /* T(n), n in [0, N]^d                      (Section 4) */
+  VP_ARRAY_GHAT = 1,  /* multiplier at m in [0, N]^d, unscaled       (Section 4) */
+  VP_ARRAY_TJ = 2,    /* T_j(n), n in [0, N]^d, axis j = `axis`      (Section 3) */
+  VP_ARRAY_GHATJ = 3  /* gradient multiplier octant, axis j          (Section 3) */
+} vp_array;
+
+/* Creates a plan and runs the FP64 precompute on the device (Sections 2 and 4):
+ * samples G^L(|s_m|) for s_m = (pi/2) m, m in [0, 2N]^d (the octant of the
+ * 4N grid; G^L is radial), reduces it to T by separable cosine sums (the
+ * inverse 4N DFT of an even array), crops to (-N, N]^d and transforms to the
+ * (2N)^d multiplier, stored as its [0, N]^d octant in FP64 and FP32.
+ *   d       2 or 3
+ *   N       even, >= 4; 2N must be a supported FFT length (VP_ERR_UNSUPPORTED)
+ *   kernel  VP_LAPLACE (k must be 0) or VP_HELMHOLTZ (k > 0)
+ *   L       truncation radius; L <= 0 selects 1.8 (3D) / 1.5 (2D) (Section 2);
+ *           otherwise sqrt(d) < L <= 3 (3 keeps the 4N grid alias-free).
+ * The plan owns all device memory it allocates; workspace for applies is
+ * allocated on first use.  Synchronous: returns after the precompute. */
+vp_status vp_plan_create(vp_plan* out, int d, int N, vp_kernel kernel, double k, double L);
+
+/* Stream for subsequent calls (cudaStream_t as void*; NULL = legacy default).
+ * One plan serves one stream at a time. */
+vp_status vp_plan_set_stream(vp_plan plan, void* stream);
+
+/* Apply arithmetic (default VP_FP32). */
+vp_status vp_plan_set_precision(vp_plan plan, vp_precision precision);
+
+/* Gradient definition (default VP_GRAD_EXACT).  EXACT builds the derivative
+ * multipliers on the first gradient apply (FP64 precompute, synchronous). */
+vp_status vp_plan_set_grad_mode(vp_plan plan, vp_grad_mode mode);
+
+/* phi = T * f (Section 4): zero-pad to (2N)^d, forward FFT, multiply, inverse
+ * FFT, crop.  f, phi: N^d elements of `dtype`. */
+vp_status vp_apply(vp_plan plan, const void* f, void* phi, vp_dtype dtype);
+
+/* phi = T * f (phi may be NULL) and grad_j = T_j * f (or the 2N-mode
+ * derivative), all from one forward transform (Section 3: "any derivative
+ * ... at the cost of an additional FFT").  grad: d * N^d elements. */
+vp_status vp_apply_grad(vp_plan plan, const void* f, void* phi, void* grad, vp_dtype dtype);
+
+/* Copies a precomputed FP64 octant ((N+1)^d complex128 = 2 (N+1)^d doubles) to
+ * host memory.  `axis` selects j for the gradient arrays (ignored otherwise);
+ * `count` is the number of doubles available at host_dst. */
+vp_status vp_plan_get_array(vp_plan plan, vp_array which, int axis, double* host_dst, size_t count);
+
+/* Plan parameters and the device bytes it currently holds. */
+vp_status vp_plan_info(vp_plan plan, int* d, int* N, double* k, double* L, size_t* device_bytes);
+
+/* Per-pass device timing with CUDA events recorded on the plan's stream
+ * around every kernel launch (off by default).  vp_plan_get_timing
+ * synchronises the stream, returns for each pass its name, launch count and
+ * summed milliseconds since the last read, and resets the counters.
+ * Up to `cap` passes are written; *npass receives the number of passes. */
+vp_status vp_plan_set_timing(vp_plan plan, int enable);
+vp_status vp_plan_get_timing(vp_plan plan, int cap, int* npass, const char** names, int* launches,
+                             double* total_ms);
+
+/* Number of kernel launches one vp_apply / vp_apply_grad issues. */
+vp_status vp_plan_launch_count(vp_plan plan, int grad, int* launches);
+
+/* Synchronises the plan's stream and reports the first device-side error. */
+vp_status vp_plan_status(vp_plan plan);
+
+/* Message of the last failing call on this plan (plan may be NULL for
+ * vp_plan_create failures; the message is then per thread). */
+const char* vp_last_error(vp_plan plan);
+
+const char* vp_status_string(vp_status status);
+
+/* Frees every device allocation of the plan.  NULL-safe. */
+vp_status vp_destroy(vp_plan plan);
+
+/* Whether 2N is a built FFT length (1) or not (0). */
+int vp_fft_length_supported(int n2);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VP_H */

@@ -1,0 +1,710 @@
+// vp_capi.cu -- the C ABI declared in include/vp.h: plan lifecycle, the FP64
+// precompute driver (Sections 2 and 4) and the pass sequence of the apply
+// (Section 4: pad, FFT, multiply, inverse FFT, crop; Section 3 gradients).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/vp.h"
+#include "vp_internal.cuh"
+
+using namespace vp;
+
+namespace {
+
+thread_local std::string g_thread_error;
+
+struct TimedLaunch {
+  int pass;
+  cudaEvent_t start, stop;
+};
+
+const char* kPassNames[5] = {"fwd_rows", "fwd_axis1", "fused_axis0", "inv_axis1", "inv_rows"};
+enum { P_FWD_ROWS = 0, P_FWD_AX1 = 1, P_FUSED = 2, P_INV_AX1 = 3, P_INV_ROWS = 4, NPASS = 5 };
+
+}  // namespace
+
+struct vp_plan_s {
+  int d = 0, N = 0, kernel = 0;
+  double k = 0.0, L = 0.0;
+  int n2 = 0;  // FFT length 2N
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  vp_precision prec = VP_FP32;
+  vp_grad_mode gmode = VP_GRAD_EXACT;
+
+  long long oct = 0;  // (N+1)^d
+  // FP64 precompute results (octants, complex128)
+  double2* T64 = nullptr;
+  double2* G64u = nullptr;  // unscaled multiplier
+  double2* G64 = nullptr;   // scaled by 1/(2N)^d
+  float2* G32 = nullptr;
+  double2* Tj64[3] = {nullptr, nullptr, nullptr};
+  double2* Gj64u[3] = {nullptr, nullptr, nullptr};
+  double2* Gj64[3] = {nullptr, nullptr, nullptr};
+  float2* Gj32[3] = {nullptr, nullptr, nullptr};
+  bool grad_built = false;
+  double2* tw64 = nullptr;
+  float2* tw32 = nullptr;
+
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  void* stage = nullptr;
+  size_t stage_bytes = 0;
+  size_t device_bytes = 0;
+
+  bool timing = false;
+  std::vector<TimedLaunch> timed;
+  std::vector<cudaEvent_t> event_pool;
+
+  std::string last_error;
+};
+
+namespace {
+
+vp_status fail(vp_plan p, vp_status st, const std::string& msg) {
+  if (p)
+    p->last_error = msg;
+  else
+    g_thread_error = msg;
+  return st;
+}
+
+vp_status cuda_fail(vp_plan p, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(p, e == cudaErrorMemoryAllocation ? VP_ERR_OOM : VP_ERR_CUDA, m);
+}
+
+#define VP_CUDA(p, call)                                   \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail(p, e_, #call); \
+  } while (0)
+
+template <typename T> cudaError_t dalloc(vp_plan p, T** ptr, size_t count) {
+  cudaError_t e = cudaMalloc((void**)ptr, count * sizeof(T));
+  if (e == cudaSuccess) p->device_bytes += count * sizeof(T);
+  return e;
+}
+
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on the
+// three-term recurrence of P_n (host, FP64).
+void gauss_legendre(int n, double* x, double* w) {
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < n; ++i) {
+    double z = cos(pi * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int kk = 2; kk <= n; ++kk) {
+        const double p2 = ((2.0 * kk - 1.0) * z * p1 - (kk - 1.0) * p0) / kk;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// Separable transform chain: applies mats[a] (Q_a x P_a) along each axis a.
+cudaError_t run_chain(const double2* src, double2* dst, double2* t0, double2* t1, int d, const int* dims_in,
+                      double* const* mats, const int* qs, cudaStream_t s) {
+  long long dims[3] = {dims_in[0], dims_in[1], d == 3 ? dims_in[2] : 1};
+  const double2* cur = src;
+  for (int a = 0; a < d; ++a) {
+    long long O = 1, I = 1;
+    for (int j = 0; j < a; ++j) O *= dims[j];
+    for (int j = a + 1; j < d; ++j) I *= dims[j];
+    double2* out = (a == d - 1) ? dst : ((a % 2 == 0) ? t0 : t1);
+    cudaError_t e = launch_axis_transform(cur, out, mats[a], O, (int)dims[a], qs[a], I, s);
+    if (e != cudaSuccess) return e;
+    dims[a] = qs[a];
+    cur = out;
+  }
+  return cudaSuccess;
+}
+
+struct Scratch {
+  double2* G = nullptr;
+  double2* t0 = nullptr;
+  double2* t1 = nullptr;
+  double2* Traw = nullptr;
+  double* C4 = nullptr;
+  double* S4 = nullptr;
+  double* C2 = nullptr;
+  double* S2 = nullptr;
+  void release() {
+    cudaFree(G);
+    cudaFree(t0);
+    cudaFree(t1);
+    cudaFree(Traw);
+    cudaFree(C4);
+    cudaFree(S4);
+    cudaFree(C2);
+    cudaFree(S2);
+    *this = Scratch();
+  }
+};
+
+cudaError_t scratch_alloc(vp_plan p, Scratch& sc) {
+  const long long M1 = 2LL * p->N + 1, Np1 = p->N + 1;
+  const long long gsz = p->d == 3 ? M1 * M1 * M1 : M1 * M1;
+  const long long tsz = p->d == 3 ? Np1 * M1 * M1 : Np1 * M1;
+  cudaError_t e;
+  if ((e = cudaMalloc(&sc.G, gsz * sizeof(double2))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&sc.t0, tsz * sizeof(double2))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&sc.t1, tsz * sizeof(double2))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&sc.Traw, p->oct * sizeof(double2))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&sc.C4, Np1 * M1 * sizeof(double))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&sc.S4, Np1 * M1 * sizeof(double))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&sc.C2, Np1 * Np1 * sizeof(double))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&sc.S2, Np1 * Np1 * sizeof(double))) != cudaSuccess) return e;
+  if ((e = launch_matrix(sc.C4, p->N, 0, 0)) != cudaSuccess) return e;
+  if ((e = launch_matrix(sc.S4, p->N, 1, 0)) != cudaSuccess) return e;
+  if ((e = launch_matrix(sc.C2, p->N, 2, 0)) != cudaSuccess) return e;
+  if ((e = launch_matrix(sc.S2, p->N, 3, 0)) != cudaSuccess) return e;
+  return launch_spectrum(sc.G, p->d, p->N, p->kernel, p->k, p->L, 0);
+}
+
+// T (odd_axis < 0) or T_j, then the multiplier, into the plan's arrays.
+cudaError_t build_kernel(vp_plan p, Scratch& sc, int odd_axis, double2* Tout, double2* Gu, double2* G64, float2* G32) {
+  const int M1 = 2 * p->N + 1, Np1 = p->N + 1;
+  int dims4[3] = {M1, M1, M1};
+  int qs[3] = {Np1, Np1, Np1};
+  double* m4[3];
+  double* m2[3];
+  for (int a = 0; a < 3; ++a) {
+    m4[a] = (a == odd_axis) ? sc.S4 : sc.C4;
+    m2[a] = (a == odd_axis) ? sc.S2 : sc.C2;
+  }
+  cudaError_t e = run_chain(sc.G, Tout, sc.t0, sc.t1, p->d, dims4, m4, qs, 0);
+  if (e != cudaSuccess) return e;
+  int dims2[3] = {Np1, Np1, Np1};
+  e = run_chain(Tout, sc.Traw, sc.t0, sc.t1, p->d, dims2, m2, qs, 0);
+  if (e != cudaSuccess) return e;
+  const double scale = 1.0 / pow(2.0 * p->N, p->d);
+  return launch_finalize(sc.Traw, Gu, G64, G32, p->oct, scale, odd_axis >= 0 ? 1 : 0, 0);
+}
+
+vp_status build_grad(vp_plan p) {
+  if (p->grad_built) return VP_OK;
+  VP_CUDA(p, cudaStreamSynchronize(p->stream));
+  for (int j = 0; j < p->d; ++j) {
+    VP_CUDA(p, dalloc(p, &p->Tj64[j], p->oct));
+    VP_CUDA(p, dalloc(p, &p->Gj64u[j], p->oct));
+    VP_CUDA(p, dalloc(p, &p->Gj64[j], p->oct));
+    VP_CUDA(p, dalloc(p, &p->Gj32[j], p->oct));
+  }
+  Scratch sc;
+  cudaError_t e = scratch_alloc(p, sc);
+  for (int j = 0; j < p->d && e == cudaSuccess; ++j) e = build_kernel(p, sc, j, p->Tj64[j], p->Gj64u[j], p->Gj64[j], p->Gj32[j]);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+  sc.release();
+  if (e != cudaSuccess) return cuda_fail(p, e, "gradient precompute");
+  p->grad_built = true;
+  return VP_OK;
+}
+
+size_t elem_bytes(vp_dtype t) {
+  switch (t) {
+    case VP_R32: return 4;
+    case VP_C64: return 8;
+    case VP_R64: return 8;
+    case VP_C128: return 16;
+  }
+  return 0;
+}
+
+bool is_device_ptr(const void* ptr) {
+  cudaPointerAttributes attr;
+  cudaError_t e = cudaPointerGetAttributes(&attr, ptr);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+cudaEvent_t pool_event(vp_plan p) {
+  if (!p->event_pool.empty()) {
+    cudaEvent_t e = p->event_pool.back();
+    p->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+template <typename Real>
+cudaError_t launch_pass(vp_plan p, int pass, PassKind kind, const PassArgs<Real>& a) {
+  TimedLaunch tl{pass, nullptr, nullptr};
+  if (p->timing && p->timed.size() < 100000) {
+    tl.start = pool_event(p);
+    tl.stop = pool_event(p);
+    cudaEventRecord(tl.start, p->stream);
+  }
+  cudaError_t e;
+  if (sizeof(Real) == 4)
+    e = launch_pass_f32(kind, p->n2, reinterpret_cast<const PassArgs<float>&>(a), p->stream);
+  else
+    e = launch_pass_f64(kind, p->n2, reinterpret_cast<const PassArgs<double>&>(a), p->stream);
+  if (tl.start) {
+    cudaEventRecord(tl.stop, p->stream);
+    p->timed.push_back(tl);
+  }
+  return e;
+}
+
+// Workspace (complex Real elements, U = N^d): 3D: F x 2U (rows) + F x 4U
+// (two-axis spectra); 2D: F x 2U.
+size_t workspace_bytes(int d, int N, int F, size_t csize) {
+  const size_t U = (size_t)N * N * (d == 3 ? N : 1);
+  return (d == 3 ? (size_t)F * 6 * U : (size_t)F * 2 * U) * csize;
+}
+
+vp_status ensure_workspace(vp_plan p, size_t bytes) {
+  if (p->ws_bytes >= bytes) return VP_OK;
+  if (p->ws) {
+    VP_CUDA(p, cudaStreamSynchronize(p->stream));
+    cudaFree(p->ws);
+    p->device_bytes -= p->ws_bytes;
+    p->ws = nullptr;
+    p->ws_bytes = 0;
+  }
+  VP_CUDA(p, cudaMalloc(&p->ws, bytes));
+  p->ws_bytes = bytes;
+  p->device_bytes += bytes;
+  return VP_OK;
+}
+
+// The apply on device pointers: F fields (phi and/or gradient components).
+template <typename Real>
+vp_status run_apply(vp_plan p, const void* f, void* const* outs, const FieldDesc* fields, int F, bool real_io) {
+  using C = typename CxT<Real>::T;
+  const int N = p->N, n = p->n2, d = p->d;
+  const long long U = (long long)N * N * (d == 3 ? N : 1);
+  vp_status st = ensure_workspace(p, workspace_bytes(d, N, F, sizeof(C)));
+  if (st != VP_OK) return st;
+  C* wsA = reinterpret_cast<C*>(p->ws);  // rows: F x 2U
+  C* wsB = wsA + (long long)F * 2 * U;   // 3D spectra: F x 4U
+  const C* tw = sizeof(Real) == 4 ? reinterpret_cast<const C*>(p->tw32) : reinterpret_cast<const C*>(p->tw64);
+
+  PassArgs<Real> a;
+  memset(&a, 0, sizeof(a));
+  a.tw = tw;
+  a.d = d;
+  a.Nh = N;
+  cudaError_t e;
+  if (d == 3) {
+    // P1: rows along axis 2, N -> 2N
+    a.in = f;
+    a.out = wsA;
+    a.O = N * N;
+    a.I = 1;
+    a.in_pitch_o = N;
+    a.in_pitch_pos = 1;
+    a.out_pitch_o = n;
+    a.out_pitch_pos = 1;
+    a.in_real = real_io;
+    a.out_real = 0;
+    if ((e = launch_pass<Real>(p, P_FWD_ROWS, FWD_CONTIG, a)) != cudaSuccess) return cuda_fail(p, e, "pass fwd_rows");
+    // P2: axis 1, N -> 2N, slabs i0
+    a.in = wsA;
+    a.out = wsB;
+    a.O = N;
+    a.I = n;
+    a.in_pitch_o = (long long)N * n;
+    a.in_pitch_pos = n;
+    a.out_pitch_o = (long long)n * n;
+    a.out_pitch_pos = n;
+    a.in_real = 0;
+    if ((e = launch_pass<Real>(p, P_FWD_AX1, FWD_STRIDED, a)) != cudaSuccess) return cuda_fail(p, e, "pass fwd_axis1");
+    // P3: axis 0 fused, N -> N per field (field 0 in place)
+    a.in = wsB;
+    a.out = wsB;
+    a.O = 1;
+    a.I = n * n;
+    a.in_pitch_o = 0;
+    a.in_pitch_pos = (long long)n * n;
+    a.out_pitch_o = 0;
+    a.out_pitch_pos = (long long)n * n;
+    a.out_field_stride = 4 * U;
+    a.nfields = F;
+    for (int i = 0; i < F; ++i) a.fields[i] = fields[i];
+    if ((e = launch_pass<Real>(p, P_FUSED, FUSED_STRIDED, a)) != cudaSuccess) return cuda_fail(p, e, "pass fused_axis0");
+    a.nfields = 0;
+    // P4: axis 1 inverse, 2N -> N, all fields as slabs
+    a.in = wsB;
+    a.out = wsA;
+    a.O = F * N;
+    a.I = n;
+    a.in_pitch_o = (long long)n * n;
+    a.in_pitch_pos = n;
+    a.out_pitch_o = (long long)N * n;
+    a.out_pitch_pos = n;
+    if ((e = launch_pass<Real>(p, P_INV_AX1, INV_STRIDED, a)) != cudaSuccess) return cuda_fail(p, e, "pass inv_axis1");
+    // P5: rows inverse, 2N -> N, one launch per field
+    for (int i = 0; i < F; ++i) {
+      a.in = wsA + (long long)i * 2 * U;
+      a.out = outs[i];
+      a.O = N * N;
+      a.I = 1;
+      a.in_pitch_o = n;
+      a.in_pitch_pos = 1;
+      a.out_pitch_o = N;
+      a.out_pitch_pos = 1;
+      a.out_real = real_io;
+      if ((e = launch_pass<Real>(p, P_INV_ROWS, INV_CONTIG, a)) != cudaSuccess) return cuda_fail(p, e, "pass inv_rows");
+    }
+  } else {
+    // P1: rows along axis 1, N -> 2N
+    a.in = f;
+    a.out = wsA;
+    a.O = N;
+    a.I = 1;
+    a.in_pitch_o = N;
+    a.in_pitch_pos = 1;
+    a.out_pitch_o = n;
+    a.out_pitch_pos = 1;
+    a.in_real = real_io;
+    if ((e = launch_pass<Real>(p, P_FWD_ROWS, FWD_CONTIG, a)) != cudaSuccess) return cuda_fail(p, e, "pass fwd_rows");
+    // P2: axis 0 fused
+    a.in = wsA;
+    a.out = wsA;
+    a.O = 1;
+    a.I = n;
+    a.in_pitch_o = 0;
+    a.in_pitch_pos = n;
+    a.out_pitch_o = 0;
+    a.out_pitch_pos = n;
+    a.out_field_stride = 2 * U;
+    a.in_real = 0;
+    a.nfields = F;
+    for (int i = 0; i < F; ++i) a.fields[i] = fields[i];
+    if ((e = launch_pass<Real>(p, P_FUSED, FUSED_STRIDED, a)) != cudaSuccess) return cuda_fail(p, e, "pass fused_axis0");
+    a.nfields = 0;
+    for (int i = 0; i < F; ++i) {
+      a.in = wsA + (long long)i * 2 * U;
+      a.out = outs[i];
+      a.O = N;
+      a.I = 1;
+      a.in_pitch_o = n;
+      a.in_pitch_pos = 1;
+      a.out_pitch_o = N;
+      a.out_pitch_pos = 1;
+      a.out_real = real_io;
+      if ((e = launch_pass<Real>(p, P_INV_ROWS, INV_CONTIG, a)) != cudaSuccess) return cuda_fail(p, e, "pass inv_rows");
+    }
+  }
+  return VP_OK;
+}
+
+vp_status check_dtype(vp_plan p, vp_dtype dtype, bool* real_io) {
+  const bool fp64 = p->prec == VP_FP64;
+  if (dtype == VP_R32 || dtype == VP_R64) {
+    if (p->kernel != VP_LAPLACE)
+      return fail(p, VP_ERR_INVALID_ARG, "real data types need the Laplace kernel (a real multiplier)");
+    *real_io = true;
+  } else if (dtype == VP_C64 || dtype == VP_C128) {
+    *real_io = false;
+  } else {
+    return fail(p, VP_ERR_INVALID_ARG, "unknown dtype");
+  }
+  const bool dt64 = (dtype == VP_R64 || dtype == VP_C128);
+  if (dt64 != fp64) return fail(p, VP_ERR_INVALID_ARG, "dtype does not match the plan's precision");
+  return VP_OK;
+}
+
+vp_status apply_common(vp_plan p, const void* f, void* phi, void* grad, vp_dtype dtype, bool want_grad) {
+  if (!p) return fail(nullptr, VP_ERR_INVALID_ARG, "plan is NULL");
+  if (!f) return fail(p, VP_ERR_INVALID_ARG, "f is NULL");
+  if (!want_grad && !phi) return fail(p, VP_ERR_INVALID_ARG, "phi is NULL");
+  if (want_grad && !grad) return fail(p, VP_ERR_INVALID_ARG, "grad is NULL");
+  if (phi && phi == f) return fail(p, VP_ERR_INVALID_ARG, "phi may not alias f");
+  bool real_io = false;
+  vp_status st = check_dtype(p, dtype, &real_io);
+  if (st != VP_OK) return st;
+  VP_CUDA(p, cudaSetDevice(p->device));
+  if (want_grad && p->gmode == VP_GRAD_EXACT) {
+    st = build_grad(p);
+    if (st != VP_OK) return st;
+  }
+  const bool fp64 = p->prec == VP_FP64;
+  const size_t eb = elem_bytes(dtype);
+  const size_t U = (size_t)p->N * p->N * (p->d == 3 ? p->N : 1);
+
+  FieldDesc fields[4];
+  int F = 0;
+  if (phi) fields[F++] = FieldDesc{fp64 ? (const void*)p->G64 : (const void*)p->G32, -1, -1};
+  if (want_grad) {
+    for (int j = 0; j < p->d; ++j) {
+      if (p->gmode == VP_GRAD_EXACT)
+        fields[F++] = FieldDesc{fp64 ? (const void*)p->Gj64[j] : (const void*)p->Gj32[j], j, -1};
+      else
+        fields[F++] = FieldDesc{fp64 ? (const void*)p->G64 : (const void*)p->G32, -1, j};
+    }
+  }
+
+  // host pointers are staged through device memory
+  const bool host_io = !is_device_ptr(f);
+  const void* fd = f;
+  void* outs[4];
+  char* out_base = nullptr;
+  if (host_io) {
+    const size_t need = (1 + (size_t)F) * U * eb;
+    if (p->stage_bytes < need) {
+      if (p->stage) {
+        cudaStreamSynchronize(p->stream);
+        cudaFree(p->stage);
+        p->device_bytes -= p->stage_bytes;
+        p->stage = nullptr;
+        p->stage_bytes = 0;
+      }
+      VP_CUDA(p, cudaMalloc(&p->stage, need));
+      p->stage_bytes = need;
+      p->device_bytes += need;
+    }
+    char* sbase = reinterpret_cast<char*>(p->stage);
+    VP_CUDA(p, cudaMemcpyAsync(sbase, f, U * eb, cudaMemcpyHostToDevice, p->stream));
+    fd = sbase;
+    out_base = sbase + U * eb;
+    for (int i = 0; i < F; ++i) outs[i] = out_base + (size_t)i * U * eb;
+  } else {
+    int i = 0;
+    if (phi) outs[i++] = phi;
+    if (want_grad)
+      for (int j = 0; j < p->d; ++j) outs[i++] = reinterpret_cast<char*>(grad) + (size_t)j * U * eb;
+  }
+  st = fp64 ? run_apply<double>(p, fd, outs, fields, F, real_io) : run_apply<float>(p, fd, outs, fields, F, real_io);
+  if (st != VP_OK) return st;
+  if (host_io) {
+    int i = 0;
+    if (phi) {
+      VP_CUDA(p, cudaMemcpyAsync(phi, outs[i], U * eb, cudaMemcpyDeviceToHost, p->stream));
+      ++i;
+    }
+    if (want_grad)
+      VP_CUDA(p, cudaMemcpyAsync(grad, outs[i], (size_t)p->d * U * eb, cudaMemcpyDeviceToHost, p->stream));
+    VP_CUDA(p, cudaStreamSynchronize(p->stream));
+  }
+  return VP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int vp_fft_length_supported(int n2) { return fft_length_built(n2) ? 1 : 0; }
+
+vp_status vp_plan_create(vp_plan* out, int d, int N, vp_kernel kernel, double k, double L) {
+  if (!out) return fail(nullptr, VP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (d != 2 && d != 3) return fail(nullptr, VP_ERR_INVALID_ARG, "d must be 2 or 3");
+  if (N < 4 || N % 2) return fail(nullptr, VP_ERR_INVALID_ARG, "N must be even and >= 4");
+  if (kernel != VP_LAPLACE && kernel != VP_HELMHOLTZ) return fail(nullptr, VP_ERR_INVALID_ARG, "unknown kernel");
+  if (!isfinite(k) || (kernel == VP_LAPLACE && k != 0.0) || (kernel == VP_HELMHOLTZ && !(k > 0.0)))
+    return fail(nullptr, VP_ERR_INVALID_ARG, "k must be 0 for Laplace and > 0 for Helmholtz");
+  if (!isfinite(L)) return fail(nullptr, VP_ERR_INVALID_ARG, "L must be finite");
+  if (L <= 0.0) L = (d == 3) ? 1.8 : 1.5;
+  if (!(L > sqrt((double)d)) || L > 3.0) return fail(nullptr, VP_ERR_INVALID_ARG, "L must satisfy sqrt(d) < L <= 3");
+  if (!fft_length_built(2 * N)) return fail(nullptr, VP_ERR_UNSUPPORTED, "2N is not a built FFT length");
+  const long long oct = d == 3 ? (long long)(N + 1) * (N + 1) * (N + 1) : (long long)(N + 1) * (N + 1);
+
+  vp_plan p = new vp_plan_s();
+  p->d = d;
+  p->N = N;
+  p->kernel = kernel;
+  p->k = k;
+  p->L = L;
+  p->n2 = 2 * N;
+  p->oct = oct;
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e == cudaSuccess) {
+    double x[GL_NODES], w[GL_NODES];
+    gauss_legendre(GL_NODES, x, w);
+    e = set_gauss_legendre(x, w);
+  }
+  if (e == cudaSuccess) e = dalloc(p, &p->T64, oct);
+  if (e == cudaSuccess) e = dalloc(p, &p->G64u, oct);
+  if (e == cudaSuccess) e = dalloc(p, &p->G64, oct);
+  if (e == cudaSuccess) e = dalloc(p, &p->G32, oct);
+  if (e == cudaSuccess) e = dalloc(p, &p->tw64, 2 * N);
+  if (e == cudaSuccess) e = dalloc(p, &p->tw32, 2 * N);
+  if (e == cudaSuccess) e = launch_twiddles(p->tw64, p->tw32, 2 * N, 0);
+  Scratch sc;
+  if (e == cudaSuccess) e = scratch_alloc(p, sc);
+  if (e == cudaSuccess) e = build_kernel(p, sc, -1, p->T64, p->G64u, p->G64, p->G32);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+  sc.release();
+  if (e != cudaSuccess) {
+    std::string msg = std::string("precompute: ") + cudaGetErrorString(e);
+    vp_status st = (e == cudaErrorMemoryAllocation) ? VP_ERR_OOM : VP_ERR_CUDA;
+    vp_destroy(p);
+    return fail(nullptr, st, msg);
+  }
+  *out = p;
+  return VP_OK;
+}
+
+vp_status vp_plan_set_stream(vp_plan p, void* stream) {
+  if (!p) return fail(nullptr, VP_ERR_INVALID_ARG, "plan is NULL");
+  p->stream = reinterpret_cast<cudaStream_t>(stream);
+  return VP_OK;
+}
+
+vp_status vp_plan_set_precision(vp_plan p, vp_precision precision) {
+  if (!p) return fail(nullptr, VP_ERR_INVALID_ARG, "plan is NULL");
+  if (precision != VP_FP32 && precision != VP_FP64) return fail(p, VP_ERR_INVALID_ARG, "unknown precision");
+  p->prec = precision;
+  return VP_OK;
+}
+
+vp_status vp_plan_set_grad_mode(vp_plan p, vp_grad_mode mode) {
+  if (!p) return fail(nullptr, VP_ERR_INVALID_ARG, "plan is NULL");
+  if (mode != VP_GRAD_EXACT && mode != VP_GRAD_SPECTRAL2N) return fail(p, VP_ERR_INVALID_ARG, "unknown gradient mode");
+  p->gmode = mode;
+  return VP_OK;
+}
+
+vp_status vp_apply(vp_plan p, const void* f, void* phi, vp_dtype dtype) {
+  return apply_common(p, f, phi, nullptr, dtype, false);
+}
+
+vp_status vp_apply_grad(vp_plan p, const void* f, void* phi, void* grad, vp_dtype dtype) {
+  return apply_common(p, f, phi, grad, dtype, true);
+}
+
+vp_status vp_plan_get_array(vp_plan p, vp_array which, int axis, double* host_dst, size_t count) {
+  if (!p) return fail(nullptr, VP_ERR_INVALID_ARG, "plan is NULL");
+  if (!host_dst) return fail(p, VP_ERR_INVALID_ARG, "host_dst is NULL");
+  if (count < (size_t)(2 * p->oct)) return fail(p, VP_ERR_INVALID_ARG, "host buffer too small");
+  const double2* src = nullptr;
+  if (which == VP_ARRAY_T) {
+    src = p->T64;
+  } else if (which == VP_ARRAY_GHAT) {
+    src = p->G64u;
+  } else if (which == VP_ARRAY_TJ || which == VP_ARRAY_GHATJ) {
+    if (axis < 0 || axis >= p->d) return fail(p, VP_ERR_INVALID_ARG, "axis out of range");
+    VP_CUDA(p, cudaSetDevice(p->device));
+    vp_status st = build_grad(p);
+    if (st != VP_OK) return st;
+    src = which == VP_ARRAY_TJ ? p->Tj64[axis] : p->Gj64u[axis];
+  } else {
+    return fail(p, VP_ERR_INVALID_ARG, "unknown array");
+  }
+  VP_CUDA(p, cudaSetDevice(p->device));
+  VP_CUDA(p, cudaStreamSynchronize(p->stream));
+  VP_CUDA(p, cudaMemcpy(host_dst, src, p->oct * sizeof(double2), cudaMemcpyDeviceToHost));
+  return VP_OK;
+}
+
+vp_status vp_plan_info(vp_plan p, int* d, int* N, double* k, double* L, size_t* device_bytes) {
+  if (!p) return fail(nullptr, VP_ERR_INVALID_ARG, "plan is NULL");
+  if (d) *d = p->d;
+  if (N) *N = p->N;
+  if (k) *k = p->k;
+  if (L) *L = p->L;
+  if (device_bytes) *device_bytes = p->device_bytes;
+  return VP_OK;
+}
+
+vp_status vp_plan_set_timing(vp_plan p, int enable) {
+  if (!p) return fail(nullptr, VP_ERR_INVALID_ARG, "plan is NULL");
+  p->timing = enable != 0;
+  return VP_OK;
+}
+
+vp_status vp_plan_get_timing(vp_plan p, int cap, int* npass, const char** names, int* launches, double* total_ms) {
+  if (!p) return fail(nullptr, VP_ERR_INVALID_ARG, "plan is NULL");
+  if (cap < 0) return fail(p, VP_ERR_INVALID_ARG, "cap < 0");
+  VP_CUDA(p, cudaSetDevice(p->device));
+  VP_CUDA(p, cudaStreamSynchronize(p->stream));
+  double sums[NPASS] = {0};
+  int counts[NPASS] = {0};
+  for (const TimedLaunch& t : p->timed) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, t.start, t.stop) == cudaSuccess) {
+      sums[t.pass] += ms;
+      counts[t.pass] += 1;
+    }
+    p->event_pool.push_back(t.start);
+    p->event_pool.push_back(t.stop);
+  }
+  p->timed.clear();
+  if (npass) *npass = NPASS;
+  for (int i = 0; i < NPASS && i < cap; ++i) {
+    if (names) names[i] = kPassNames[i];
+    if (launches) launches[i] = counts[i];
+    if (total_ms) total_ms[i] = sums[i];
+  }
+  return VP_OK;
+}
+
+vp_status vp_plan_launch_count(vp_plan p, int grad, int* launches) {
+  if (!p || !launches) return fail(p, VP_ERR_INVALID_ARG, "NULL argument");
+  const int F = grad ? 1 + p->d : 1;
+  *launches = (p->d == 3) ? 4 + F : 2 + F;
+  return VP_OK;
+}
+
+vp_status vp_plan_status(vp_plan p) {
+  if (!p) return fail(nullptr, VP_ERR_INVALID_ARG, "plan is NULL");
+  VP_CUDA(p, cudaSetDevice(p->device));
+  VP_CUDA(p, cudaStreamSynchronize(p->stream));
+  VP_CUDA(p, cudaGetLastError());
+  return VP_OK;
+}
+
+const char* vp_last_error(vp_plan p) { return p ? p->last_error.c_str() : g_thread_error.c_str(); }
+
+const char* vp_status_string(vp_status s) {
+  switch (s) {
+    case VP_OK: return "VP_OK";
+    case VP_ERR_INVALID_ARG: return "VP_ERR_INVALID_ARG";
+    case VP_ERR_UNSUPPORTED: return "VP_ERR_UNSUPPORTED";
+    case VP_ERR_OOM: return "VP_ERR_OOM";
+    case VP_ERR_CUDA: return "VP_ERR_CUDA";
+    case VP_ERR_TIMEOUT: return "VP_ERR_TIMEOUT";
+    case VP_ERR_NUMERICAL: return "VP_ERR_NUMERICAL";
+  }
+  return "unknown status";
+}
+
+vp_status vp_destroy(vp_plan p) {
+  if (!p) return VP_OK;
+  cudaSetDevice(p->device);
+  if (p->stream) cudaStreamSynchronize(p->stream);
+  cudaFree(p->T64);
+  cudaFree(p->G64u);
+  cudaFree(p->G64);
+  cudaFree(p->G32);
+  for (int j = 0; j < 3; ++j) {
+    cudaFree(p->Tj64[j]);
+    cudaFree(p->Gj64u[j]);
+    cudaFree(p->Gj64[j]);
+    cudaFree(p->Gj32[j]);
+  }
+  cudaFree(p->tw64);
+  cudaFree(p->tw32);
+  cudaFree(p->ws);
+  cudaFree(p->stage);
+  for (const TimedLaunch& t : p->timed) {
+    cudaEventDestroy(t.start);
+    cudaEventDestroy(t.stop);
+  }
+  for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
+  delete p;
+  return VP_OK;
+}
+
+}  // extern "C"

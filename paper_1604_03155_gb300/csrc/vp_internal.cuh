@@ -1,0 +1,45 @@
+// vp_internal.cuh -- declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "pencil_fft.cuh"
+
+namespace vp {
+
+// Gauss-Legendre nodes of the 2D Helmholtz spectrum near s = k.
+constexpr int GL_NODES = 24;
+// |s - k| below which the 2D Helmholtz numerator is a divided difference.
+constexpr double HELM2D_NEAR_K = 1.0;
+
+// precompute.cu
+cudaError_t set_gauss_legendre(const double* x, const double* w);
+cudaError_t launch_spectrum(double2* G, int d, int N, int kernel, double k, double L, cudaStream_t s);
+cudaError_t launch_matrix(double* M, int N, int type, cudaStream_t s);
+cudaError_t launch_axis_transform(const double2* in, double2* out, const double* M, long long O, int P, int Q,
+                                  long long I, cudaStream_t s);
+cudaError_t launch_finalize(const double2* in, double2* out_u, double2* out64, float2* out32, long long count,
+                            double scale, int times_minus_i, cudaStream_t s);
+cudaError_t launch_twiddles(double2* tw64, float2* tw32, int n, cudaStream_t s);
+
+// Pass kinds of the apply.
+enum PassKind { FWD_CONTIG = 0, FWD_STRIDED = 1, INV_CONTIG = 2, INV_STRIDED = 3, FUSED_STRIDED = 4 };
+
+struct PassShape {
+  int threads;
+  int W;
+  size_t smem;
+};
+
+// apply_*.cu: launch one pass for FFT length n.  Returns cudaErrorInvalidValue
+// when n is not built.
+cudaError_t launch_pass_f32(PassKind kind, int n, const PassArgs<float>& a, cudaStream_t s);
+cudaError_t launch_pass_f64(PassKind kind, int n, const PassArgs<double>& a, cudaStream_t s);
+bool pass_shape_f32(PassKind kind, int n, PassShape* out);
+bool pass_shape_f64(PassKind kind, int n, PassShape* out);
+
+// FFT lengths with compiled passes (2N).
+bool fft_length_built(int n);
+
+}  // namespace vp

@@ -1,0 +1,272 @@
+"""Thin ctypes binding of the C ABI in include/vp.h (argument marshalling only).
+
+Every step of the method runs in libvp.so's CUDA kernels; this module only
+converts Python/torch/numpy arguments into pointers, sizes and enums.  It
+raises ``VPError`` when the library is missing: there is no CPU fallback.
+
+The module-level functions carry the C names (``vp_plan_create``,
+``vp_apply``, ``vp_apply_grad``, ``vp_destroy`` ...); ``Plan`` wraps them.
+Arrays may be CUDA torch tensors (device pointers; the call is asynchronous on
+the plan's stream, by default torch's current stream) or host arrays (numpy or
+CPU tensors; the library stages them and returns when the result is written).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+VP_OK, VP_ERR_INVALID_ARG, VP_ERR_UNSUPPORTED, VP_ERR_OOM, VP_ERR_CUDA, VP_ERR_TIMEOUT, VP_ERR_NUMERICAL = range(7)
+VP_LAPLACE, VP_HELMHOLTZ = 0, 1
+VP_FP32, VP_FP64 = 0, 1
+VP_GRAD_EXACT, VP_GRAD_SPECTRAL2N = 0, 1
+VP_R32, VP_C64, VP_R64, VP_C128 = 0, 1, 2, 3
+VP_ARRAY_T, VP_ARRAY_GHAT, VP_ARRAY_TJ, VP_ARRAY_GHATJ = 0, 1, 2, 3
+
+KERNELS = {"laplace": VP_LAPLACE, "helmholtz": VP_HELMHOLTZ}
+PRECISIONS = {"fp32": VP_FP32, "fp64": VP_FP64}
+GRAD_MODES = {"exact": VP_GRAD_EXACT, "spectral2n": VP_GRAD_SPECTRAL2N}
+
+
+class VPError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_STATUS_NAMES = {0: "VP_OK", 1: "VP_ERR_INVALID_ARG", 2: "VP_ERR_UNSUPPORTED", 3: "VP_ERR_OOM", 4: "VP_ERR_CUDA",
+                 5: "VP_ERR_TIMEOUT", 6: "VP_ERR_NUMERICAL"}
+
+_lib = None
+
+c_int, c_double, c_void_p, c_size_t = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
+c_char_p = ctypes.c_char_p
+
+_SIGNATURES = {
+    "vp_plan_create": (c_int, [ctypes.POINTER(c_void_p), c_int, c_int, c_int, c_double, c_double]),
+    "vp_plan_set_stream": (c_int, [c_void_p, c_void_p]),
+    "vp_plan_set_precision": (c_int, [c_void_p, c_int]),
+    "vp_plan_set_grad_mode": (c_int, [c_void_p, c_int]),
+    "vp_apply": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
+    "vp_apply_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int]),
+    "vp_plan_get_array": (c_int, [c_void_p, c_int, c_int, ctypes.POINTER(c_double), c_size_t]),
+    "vp_plan_info": (c_int, [c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_double),
+                             ctypes.POINTER(c_double), ctypes.POINTER(c_size_t)]),
+    "vp_plan_set_timing": (c_int, [c_void_p, c_int]),
+    "vp_plan_get_timing": (c_int, [c_void_p, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_char_p),
+                                   ctypes.POINTER(c_int), ctypes.POINTER(c_double)]),
+    "vp_plan_launch_count": (c_int, [c_void_p, c_int, ctypes.POINTER(c_int)]),
+    "vp_plan_status": (c_int, [c_void_p]),
+    "vp_last_error": (c_char_p, [c_void_p]),
+    "vp_status_string": (c_char_p, [c_int]),
+    "vp_destroy": (c_int, [c_void_p]),
+    "vp_fft_length_supported": (c_int, [c_int]),
+}
+
+
+def library_path() -> str:
+    return _build.LIBPATH
+
+
+def lib(build_if_missing: bool = False):
+    """The loaded libvp.so; raises VPError if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise VPError(VP_ERR_UNSUPPORTED, f"CUDA library not built ({path}); run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status: int, plan=None):
+    if status != VP_OK:
+        msg = lib().vp_last_error(plan)
+        raise VPError(status, msg.decode() if msg else "")
+
+
+# ---------------------------------------------------------------------------
+# C-named wrappers
+# ---------------------------------------------------------------------------
+
+def vp_plan_create(d: int, N: int, kernel: int, k: float, L: float) -> int:
+    out = c_void_p()
+    _check(lib().vp_plan_create(ctypes.byref(out), d, N, kernel, float(k), float(L)))
+    return out.value
+
+
+def vp_plan_set_stream(plan: int, stream: int):
+    _check(lib().vp_plan_set_stream(plan, stream), plan)
+
+
+def vp_plan_set_precision(plan: int, precision: int):
+    _check(lib().vp_plan_set_precision(plan, precision), plan)
+
+
+def vp_plan_set_grad_mode(plan: int, mode: int):
+    _check(lib().vp_plan_set_grad_mode(plan, mode), plan)
+
+
+def vp_apply(plan: int, f_ptr: int, phi_ptr: int, dtype: int):
+    _check(lib().vp_apply(plan, f_ptr, phi_ptr, dtype), plan)
+
+
+def vp_apply_grad(plan: int, f_ptr: int, phi_ptr, grad_ptr: int, dtype: int):
+    _check(lib().vp_apply_grad(plan, f_ptr, phi_ptr, grad_ptr, dtype), plan)
+
+
+def vp_plan_status(plan: int):
+    _check(lib().vp_plan_status(plan), plan)
+
+
+def vp_destroy(plan: int):
+    _check(lib().vp_destroy(plan))
+
+
+def vp_fft_length_supported(n2: int) -> bool:
+    return bool(lib().vp_fft_length_supported(n2))
+
+
+# ---------------------------------------------------------------------------
+# array marshalling
+# ---------------------------------------------------------------------------
+
+def _dtype_code(arr) -> int:
+    name = str(arr.dtype).replace("torch.", "")
+    table = {"float32": VP_R32, "complex64": VP_C64, "float64": VP_R64, "complex128": VP_C128}
+    if name not in table:
+        raise VPError(VP_ERR_INVALID_ARG, f"unsupported dtype {arr.dtype}")
+    return table[name]
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return None
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise VPError(VP_ERR_INVALID_ARG, "tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise VPError(VP_ERR_INVALID_ARG, "array must be C-contiguous")
+        return x.ctypes.data
+    raise VPError(VP_ERR_INVALID_ARG, f"unsupported array type {type(x)}")
+
+
+def _empty_like(f, shape):
+    if _is_torch(f):
+        import torch
+        return torch.empty(shape, dtype=f.dtype, device=f.device)
+    return np.empty(shape, dtype=f.dtype)
+
+
+class Plan:
+    """A precomputed volume-potential operator (one d, N, kernel, k, L)."""
+
+    def __init__(self, d: int, N: int, kernel: str = "laplace", k: float = 0.0, L: float = 0.0,
+                 precision: str = "fp32", grad_mode: str = "exact", stream=None):
+        self.d, self.N = d, N
+        self.kernel = kernel
+        self.handle = vp_plan_create(d, N, KERNELS[kernel], k, L)
+        self.precision = precision
+        vp_plan_set_precision(self.handle, PRECISIONS[precision])
+        vp_plan_set_grad_mode(self.handle, GRAD_MODES[grad_mode])
+        self._stream = stream
+        if stream is not None:
+            self.set_stream(stream)
+
+    def set_stream(self, stream):
+        """A torch.cuda.Stream, a raw cudaStream_t (int) or None (legacy default)."""
+        raw = getattr(stream, "cuda_stream", stream)
+        vp_plan_set_stream(self.handle, raw or 0)
+        self._stream = stream
+
+    def _sync_stream_to_torch(self, x):
+        if self._stream is None and _is_torch(x) and x.is_cuda:
+            import torch
+            vp_plan_set_stream(self.handle, torch.cuda.current_stream(x.device).cuda_stream)
+
+    def set_precision(self, precision: str):
+        vp_plan_set_precision(self.handle, PRECISIONS[precision])
+        self.precision = precision
+
+    def set_grad_mode(self, mode: str):
+        vp_plan_set_grad_mode(self.handle, GRAD_MODES[mode])
+
+    def apply(self, f, phi=None):
+        if phi is None:
+            phi = _empty_like(f, f.shape)
+        self._sync_stream_to_torch(f)
+        vp_apply(self.handle, _ptr(f), _ptr(phi), _dtype_code(f))
+        return phi
+
+    def apply_grad(self, f, phi=None, grad=None, with_phi: bool = True):
+        if with_phi and phi is None:
+            phi = _empty_like(f, f.shape)
+        if grad is None:
+            grad = _empty_like(f, (self.d,) + tuple(f.shape))
+        self._sync_stream_to_torch(f)
+        vp_apply_grad(self.handle, _ptr(f), _ptr(phi) if with_phi else None, _ptr(grad), _dtype_code(f))
+        return (phi if with_phi else None), grad
+
+    def get_array(self, which: str, axis: int = 0) -> np.ndarray:
+        """An FP64 octant ((N+1)^d complex128): 'T', 'ghat', 'Tj', 'ghatj'."""
+        code = {"T": VP_ARRAY_T, "ghat": VP_ARRAY_GHAT, "Tj": VP_ARRAY_TJ, "ghatj": VP_ARRAY_GHATJ}[which]
+        n = (self.N + 1) ** self.d
+        buf = np.empty(2 * n, dtype=np.float64)
+        _check(lib().vp_plan_get_array(self.handle, code, axis,
+                                       buf.ctypes.data_as(ctypes.POINTER(c_double)), buf.size), self.handle)
+        return buf.view(np.complex128).reshape((self.N + 1,) * self.d)
+
+    def info(self) -> dict:
+        d, N, k, L, b = c_int(), c_int(), c_double(), c_double(), c_size_t()
+        _check(lib().vp_plan_info(self.handle, ctypes.byref(d), ctypes.byref(N), ctypes.byref(k), ctypes.byref(L),
+                                  ctypes.byref(b)), self.handle)
+        return {"d": d.value, "N": N.value, "k": k.value, "L": L.value, "device_bytes": b.value}
+
+    def set_timing(self, enable: bool):
+        _check(lib().vp_plan_set_timing(self.handle, int(enable)), self.handle)
+
+    def get_timing(self) -> dict:
+        cap = 8
+        npass = c_int()
+        names = (c_char_p * cap)()
+        launches = (c_int * cap)()
+        ms = (c_double * cap)()
+        _check(lib().vp_plan_get_timing(self.handle, cap, ctypes.byref(npass), names, launches, ms), self.handle)
+        return {names[i].decode(): (launches[i], ms[i]) for i in range(min(cap, npass.value))}
+
+    def launch_count(self, grad: bool) -> int:
+        out = c_int()
+        _check(lib().vp_plan_launch_count(self.handle, int(grad), ctypes.byref(out)), self.handle)
+        return out.value
+
+    def status(self):
+        vp_plan_status(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            vp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

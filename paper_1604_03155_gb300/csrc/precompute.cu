@@ -24,6 +24,105 @@ __constant__ double c_gl_x[GL_NODES];
 __constant__ double c_gl_w[GL_NODES];
 
 // ---------------------------------------------------------------------------
+// Bessel functions J0, J1, Y0, Y1 of a real argument x > 0, FP64, accurate to a
+// few units of 1e-16 of their amplitude min(1, sqrt(2/(pi x))) for all x.
+//  * x >= 25: Hankel's asymptotic expansion (DLMF 10.17.3-10.17.4)
+//      J_nu = sqrt(2/(pi x)) (P cos w - Q sin w),  Y_nu = sqrt(2/(pi x)) (P sin w + Q cos w),
+//      w = x - nu pi/2 - pi/4,  P = sum_k (-1)^k a_2k x^-2k,  Q = sum_k (-1)^k a_2k+1 x^-2k-1,
+//      a_k(nu) = prod_{j<=k} (4 nu^2 - (2j-1)^2) / (k! 8^k); summed to the smallest term.
+//      cos w and sin w are formed from sin x, cos x without rounding x - pi/4.
+//  * x < 25: Miller's backward recurrence J_{n-1} = (2n/x) J_n - J_{n+1} from an
+//    even order M ~ x + 60, normalised by J_0 + 2 sum_k J_2k = 1 (DLMF 10.12.4);
+//    Y0 by Neumann's series (2/pi)(log(x/2) + gamma) J0 - (4/pi) sum_k (-1)^k J_2k/k
+//    (A&S 9.1.88) and Y1 = -Y0' from the same series with
+//    J_2k' = (J_2k-1 - J_2k+1)/2.  All sums are accumulated during the recurrence.
+// ---------------------------------------------------------------------------
+struct Bessel01 {
+  double j0, j1, y0, y1;
+};
+
+__device__ Bessel01 bessel01(double x) {
+  const double two_over_pi = 0.63661977236758134308;
+  Bessel01 b;
+  if (x >= 25.0) {
+    double sn, cs;
+    sincos(x, &sn, &cs);
+    const double r = 0.70710678118654752440;
+    const double amp = sqrt(two_over_pi / x);
+    double res[4];
+    for (int nu = 0; nu < 2; ++nu) {
+      const double mu = 4.0 * nu * nu;
+      double P = 1.0, Q = 0.0, a = 1.0, xp = 1.0, prev = 1e300;
+      for (int k = 1; k < 40; ++k) {
+        a *= (mu - (2.0 * k - 1.0) * (2.0 * k - 1.0)) / (8.0 * k);
+        xp /= x;
+        const double t = a * xp;
+        if (fabs(t) > prev) break;
+        prev = fabs(t);
+        if (k % 2 == 0)
+          P += ((k / 2) % 2 ? -t : t);
+        else
+          Q += (((k - 1) / 2) % 2 ? -t : t);
+        if (fabs(t) < 1e-18) break;
+      }
+      // nu = 0: w = x - pi/4; nu = 1: w = x - 3 pi/4
+      const double cw = nu == 0 ? (cs + sn) * r : (sn - cs) * r;
+      const double sw = nu == 0 ? (sn - cs) * r : (-sn - cs) * r;
+      res[2 * nu] = amp * (P * cw - Q * sw);
+      res[2 * nu + 1] = amp * (P * sw + Q * cw);
+    }
+    b.j0 = res[0];
+    b.y0 = res[1];
+    b.j1 = res[2];
+    b.y1 = res[3];
+    return b;
+  }
+  const int M = 2 * (int)((x + 60.0) * 0.5);
+  double jp1 = 0.0, j = 1e-30;
+  double norm = 0.0, s0 = 0.0, s1 = 0.0, jn1 = 0.0;
+  // the order-M value is even: account for it before recurring
+  norm += 2.0 * j;
+  s0 += (((M / 2) % 2) ? -j : j) / (M / 2);
+  for (int n = M; n > 0; --n) {
+    const double jm1 = (2.0 * n / x) * j - jp1;
+    jp1 = j;
+    j = jm1;
+    const int m = n - 1;  // order of j
+    if (m >= 2 && (m % 2) == 0) {
+      const int k = m / 2;
+      norm += 2.0 * j;
+      s0 += ((k % 2) ? -j : j) / k;
+    } else if (m % 2 == 1) {
+      // odd J_m enters sum_k (-1)^k (J_{2k-1} - J_{2k+1})/k at k = (m+1)/2 and k = (m-1)/2
+      const int ka = (m + 1) / 2;
+      double c = ((ka % 2) ? -1.0 : 1.0) / ka;
+      if (m >= 3) {
+        const int kb = (m - 1) / 2;
+        c -= ((kb % 2) ? -1.0 : 1.0) / kb;
+      }
+      s1 += c * j;
+      if (m == 1) jn1 = j;
+    }
+    if (fabs(j) > 1e200) {
+      j *= 1e-200;
+      jp1 *= 1e-200;
+      norm *= 1e-200;
+      s0 *= 1e-200;
+      s1 *= 1e-200;
+      jn1 *= 1e-200;
+    }
+  }
+  norm += j;  // J_0
+  const double J0 = j / norm, J1 = jn1 / norm;
+  const double lg = log(0.5 * x) + 0.57721566490153286061;
+  b.j0 = J0;
+  b.j1 = J1;
+  b.y0 = two_over_pi * (lg * J0 - 2.0 * s0 / norm);
+  b.y1 = -two_over_pi * (J0 / x - lg * J1) + two_over_pi * s1 / norm;
+  return b;
+}
+
+// ---------------------------------------------------------------------------
 // truncated spectra (Tables 1-2), FP64, stable at s = 0 and s = k
 // ---------------------------------------------------------------------------
 __device__ double2 g_laplace3(double s, double L) {
@@ -87,16 +186,24 @@ __device__ double2 g_laplace2(double s, double L) {
     }
     return make_double2(L * L * (a - lnL * b), 0.0);
   }
-  return make_double2((1.0 - j0(x)) / (s * s) - L * lnL * j1(x) / s, 0.0);
+  const Bessel01 b = bessel01(x);
+  return make_double2((1.0 - b.j0) / (s * s) - L * lnL * b.j1 / s, 0.0);
 }
 
 __device__ double2 g_helmholtz2(double s, double k, double L) {
-  const double H0r = j0(L * k), H0i = y0(L * k);
-  const double H1r = j1(L * k), H1i = y1(L * k);
+  const Bessel01 h = bessel01(L * k);
+  const double H0r = h.j0, H0i = h.y0;
+  const double H1r = h.j1, H1i = h.y1;
   const double hp = 0.5 * 3.14159265358979323846 * L;  // (pi/2) L
   if (fabs(s - k) >= HELM2D_NEAR_K) {
     // 1 + i hp s J1(Ls) H0 - i hp k J0(Ls) H1, over s^2 - k^2
-    const double a = hp * s * j1(L * s), b = hp * k * j0(L * s);
+    double jl0 = 1.0, jl1 = 0.0;
+    if (s > 0.0) {
+      const Bessel01 bs = bessel01(L * s);
+      jl0 = bs.j0;
+      jl1 = bs.j1;
+    }
+    const double a = hp * s * jl1, b = hp * k * jl0;
     const double re = 1.0 - a * H0i + b * H1i;
     const double im = a * H0r - b * H1r;
     const double den = (s - k) * (s + k);
@@ -108,8 +215,14 @@ __device__ double2 g_helmholtz2(double s, double k, double L) {
   for (int g = 0; g < GL_NODES; ++g) {
     const double u = mid + half * c_gl_x[g];
     const double w = 0.5 * c_gl_w[g];
-    mA += w * L * u * j0(L * u);
-    mB += w * L * j1(L * u);
+    double ju0 = 1.0, ju1 = 0.0;
+    if (u > 0.0) {
+      const Bessel01 bu = bessel01(L * u);
+      ju0 = bu.j0;
+      ju1 = bu.j1;
+    }
+    mA += w * L * u * ju0;
+    mB += w * L * ju1;
   }
   const double cr = H0r * mA + k * H1r * mB, ci = H0i * mA + k * H1i * mB;
   // i hp (cr + i ci) / (s + k)

@@ -36,3 +36,21 @@ def potential(d, N, kernel, k, L, f, grad_mode=None):
     else:
         g = A.grad_spectral2n(Gf, f)
     return phi, g
+
+
+def condition(d, N, kernel, k, L, f, odd_axis=None):
+    """kappa = || |T| * |f| ||_2 / || T * f ||_2 >= 1: the scale of rounding
+    errors in a discrete convolution relative to its result.  A relative error
+    bar eps on well-conditioned data (kappa ~ 1) becomes eps * kappa when the
+    result cancels (e.g. an oscillatory kernel on an under-resolved grid)."""
+    if odd_axis is None:
+        T, _ = octants(d, N, kernel, k, L)
+    else:
+        T, _ = grad_octants(d, N, kernel, k, L, odd_axis)
+    Tabs = np.abs(K.T_full_from_octant(T, odd_axis))
+    Gabs = K.ghat_by_fft(Tabs, N)
+    f = np.asarray(f, dtype=np.complex128)
+    top = np.linalg.norm(A.apply_fft2n(Gabs, np.abs(f)).ravel())
+    phi = A.apply_fft2n(K.ghat_full_from_octant(octants(d, N, kernel, k, L)[1]) if odd_axis is None else
+                        K.ghat_full_from_octant(grad_octants(d, N, kernel, k, L, odd_axis)[1], odd_axis), f)
+    return max(1.0, top / np.linalg.norm(phi.ravel()))

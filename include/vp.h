@@ -148,6 +148,35 @@ vp_status vp_destroy(vp_plan plan);
 /* Whether 2N is a built FFT length (1) or not (0). */
 int vp_fft_length_supported(int n2);
 
+
+/* ---------------------------------------------------------------------------
+ * Potential apply without device allocation (the paper has no counterpart;
+ * this is a deployment aid).
+ *
+ * For callers that cannot call cudaMalloc where they apply the operator: code
+ * living inside another framework whose allocator owns all device memory,
+ * latency-bound loops that cannot afford an allocation's implicit
+ * synchronisation, or plug-ins that may allocate only while initialising.
+ * Create the plan during set-up (plan creation allocates the multiplier), then
+ * call this instead of vp_apply: it computes the same phi = T * f with the same
+ * kernels, taking its scratch from one array of VP_NOALLOC_SCRATCH_BYTES
+ * compiled into the library, and calls no allocation routine.
+ *   - f, phi: device pointers (host pointers return VP_ERR_INVALID_ARG); no
+ *     gradients.  dtype as for vp_apply.
+ *   - Grids whose scratch exceeds the array return VP_ERR_UNSUPPORTED with a
+ *     message: scratch = 6 N^3 (3D) or 2 N^2 (2D) complex elements of the plan's
+ *     precision, e.g. up to N = 128 (3D) and N = 2048 (2D) in FP32.
+ *   - The array is shared by every call on a device and keeps the last call's
+ *     contents (nothing needs to start at zero).  Calls whose kernels overlap
+ *     on the GPU race on it: serialise them (one stream, or events).
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with the plan's device current; make that first
+ *     call before any stream capture.
+ *   - Every GPU that loads the library holds the array until the process exits.
+ * ------------------------------------------------------------------------- */
+#define VP_NOALLOC_SCRATCH_BYTES (128u * 1024u * 1024u)
+vp_status vp_apply_noalloc(vp_plan plan, const void* f, void* phi, vp_dtype dtype);
+
 #ifdef __cplusplus
 }
 #endif

@@ -289,13 +289,26 @@ vp_status ensure_workspace(vp_plan p, size_t bytes) {
 
 // The apply on device pointers: F fields (phi and/or gradient components).
 template <typename Real>
+vp_status run_apply_ws(vp_plan p, void* ws, const void* f, void* const* outs, const FieldDesc* fields, int F,
+                       bool real_io);
+
+template <typename Real>
 vp_status run_apply(vp_plan p, const void* f, void* const* outs, const FieldDesc* fields, int F, bool real_io) {
+  using C = typename CxT<Real>::T;
+  vp_status st = ensure_workspace(p, workspace_bytes(p->d, p->N, F, sizeof(C)));
+  if (st != VP_OK) return st;
+  return run_apply_ws<Real>(p, p->ws, f, outs, fields, F, real_io);
+}
+
+// The pass sequence on a given workspace of workspace_bytes(d, N, F, ...) bytes;
+// allocates nothing.
+template <typename Real>
+vp_status run_apply_ws(vp_plan p, void* ws, const void* f, void* const* outs, const FieldDesc* fields, int F,
+                       bool real_io) {
   using C = typename CxT<Real>::T;
   const int N = p->N, n = p->n2, d = p->d;
   const long long U = (long long)N * N * (d == 3 ? N : 1);
-  vp_status st = ensure_workspace(p, workspace_bytes(d, N, F, sizeof(C)));
-  if (st != VP_OK) return st;
-  C* wsA = reinterpret_cast<C*>(p->ws);  // rows: F x 2U
+  C* wsA = reinterpret_cast<C*>(ws);  // rows: F x 2U
   C* wsB = wsA + (long long)F * 2 * U;   // 3D spectra: F x 4U
   const C* tw = sizeof(Real) == 4 ? reinterpret_cast<const C*>(p->tw32) : reinterpret_cast<const C*>(p->tw64);
 
@@ -501,6 +514,47 @@ vp_status apply_common(vp_plan p, const void* f, void* phi, void* grad, vp_dtype
 }
 
 }  // namespace
+
+
+// ---------------------------------------------------------------------------
+// internal hooks for other translation units
+// ---------------------------------------------------------------------------
+namespace vp {
+
+int plan_device(vp_plan p) { return p ? p->device : -1; }
+
+size_t plan_apply_workspace_bytes(vp_plan p) {
+  const size_t csize = p->prec == VP_FP64 ? sizeof(double2) : sizeof(float2);
+  return workspace_bytes(p->d, p->N, 1, csize);
+}
+
+vp_status apply_with_workspace(vp_plan p, const void* f, void* phi, vp_dtype dtype, void* ws, size_t ws_bytes) {
+  if (!p) return fail(nullptr, VP_ERR_INVALID_ARG, "plan is NULL");
+  if (!f || !phi) return fail(p, VP_ERR_INVALID_ARG, "f and phi must be non-NULL");
+  if (phi == f) return fail(p, VP_ERR_INVALID_ARG, "phi may not alias f");
+  bool real_io = false;
+  vp_status st = check_dtype(p, dtype, &real_io);
+  if (st != VP_OK) return st;
+  if (!is_device_ptr(f) || !is_device_ptr(phi))
+    return fail(p, VP_ERR_INVALID_ARG, "this entry point takes device pointers only");
+  const size_t need = plan_apply_workspace_bytes(p);
+  if (ws_bytes < need) {
+    char msg[200];
+    snprintf(msg, sizeof(msg), "grid needs %zu bytes of scratch, the static array holds %zu", need, ws_bytes);
+    return fail(p, VP_ERR_UNSUPPORTED, msg);
+  }
+  const bool fp64 = p->prec == VP_FP64;
+  FieldDesc field{fp64 ? (const void*)p->G64 : (const void*)p->G32, -1, -1};
+  void* outs[1] = {phi};
+  const bool timing = p->timing;  // no event objects are created on this path
+  p->timing = false;
+  st = fp64 ? run_apply_ws<double>(p, ws, f, outs, &field, 1, real_io)
+            : run_apply_ws<float>(p, ws, f, outs, &field, 1, real_io);
+  p->timing = timing;
+  return st;
+}
+
+}  // namespace vp
 
 extern "C" {
 

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include "../../include/vp.h"
 #include "pencil_fft.cuh"
 
 namespace vp {
@@ -41,5 +42,12 @@ bool pass_shape_f64(PassKind kind, int n, PassShape* out);
 
 // FFT lengths with compiled passes (2N).
 bool fft_length_built(int n);
+
+// vp_capi.cu: the device a plan was created on; the scratch bytes of one
+// potential-only apply; that apply on a caller-supplied workspace (device
+// pointers only, allocates nothing).
+int plan_device(vp_plan p);
+size_t plan_apply_workspace_bytes(vp_plan p);
+vp_status apply_with_workspace(vp_plan p, const void* f, void* phi, vp_dtype dtype, void* ws, size_t ws_bytes);
 
 }  // namespace vp

@@ -64,6 +64,7 @@ _SIGNATURES = {
     "vp_status_string": (c_char_p, [c_int]),
     "vp_destroy": (c_int, [c_void_p]),
     "vp_fft_length_supported": (c_int, [c_int]),
+    "vp_apply_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
 }
 
 
@@ -125,6 +126,12 @@ def vp_apply(plan: int, f_ptr: int, phi_ptr: int, dtype: int):
 
 def vp_apply_grad(plan: int, f_ptr: int, phi_ptr, grad_ptr: int, dtype: int):
     _check(lib().vp_apply_grad(plan, f_ptr, phi_ptr, grad_ptr, dtype), plan)
+
+
+def vp_apply_noalloc(plan: int, f_ptr: int, phi_ptr: int, dtype: int):
+    """vp_apply on the library's static scratch array (device pointers only);
+    for callers that cannot allocate device memory at apply time."""
+    _check(lib().vp_apply_noalloc(plan, f_ptr, phi_ptr, dtype), plan)
 
 
 def vp_plan_status(plan: int):

@@ -114,14 +114,17 @@ def measured_peak_hbm():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+APPLY_KERNEL_SOURCES = ("pencil_fft.cuh", "apply_dispatch.cuh", "apply_f32.cu", "apply_f64.cu")
+
+
 def kernel_source_hash() -> str:
+    """Hash of the apply kernels' sources (the kernels the roofline is about)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1604_03155_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, fn), "rb") as fh:
-                h.update(fn.encode())
-                h.update(fh.read())
+    for fn in APPLY_KERNEL_SOURCES:
+        with open(os.path.join(csrc, fn), "rb") as fh:
+            h.update(fn.encode())
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 

@@ -152,8 +152,8 @@ def pass_bytes(d: int, N: int, F: int, csize: int) -> dict:
     oct_b = (N + 1) ** d * csize
     if d == 3:
         return {"fwd_rows": 3 * U, "fwd_axis1": 6 * U, "fused_axis0": 4 * U + F * oct_b + F * 4 * U,
-                "inv_axis1": F * 6 * U, "inv_rows": 3 * U}
-    return {"fwd_rows": 3 * U, "fused_axis0": 2 * U + F * oct_b + F * 2 * U, "inv_rows": 3 * U}
+                "inv_axis1": F * 6 * U, "inv_rows": F * 3 * U}
+    return {"fwd_rows": 3 * U, "fused_axis0": 2 * U + F * oct_b + F * 2 * U, "inv_rows": F * 3 * U}
 
 
 # ---------------------------------------------------------------------------

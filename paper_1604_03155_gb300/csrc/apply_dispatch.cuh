@@ -6,17 +6,23 @@
 
 namespace vp {
 
-template <typename Real, int n, bool CONTIG, int MODE>
+template <typename Real, int n, bool CONTIG, int MODE, typename Cfg = PassCfg<Real, n, CONTIG, MODE>>
 cudaError_t launch_one(const PassArgs<Real>& a0, cudaStream_t s) {
-  using Cfg = PassCfg<Real, n, CONTIG>;
-  static int attr_done[64] = {0};
+  // per device: shared-memory opt-in and the persistent grid (SMs x resident CTAs)
+  static int grid_cap[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev < 64 && !attr_done[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(pencil_pass<Real, n, CONTIG, MODE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::smem);
+  if (dev >= 64) return cudaErrorInvalidDevice;
+  if (!grid_cap[dev]) {
+    auto kern = pencil_pass<Real, n, CONTIG, MODE, Cfg>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::smem);
     if (e != cudaSuccess) return e;
-    attr_done[dev] = 1;
+    int sms = 0, per_sm = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Cfg::threads, Cfg::smem);
+    if (e != cudaSuccess) return e;
+    grid_cap[dev] = sms * (per_sm > 0 ? per_sm : 1);
   }
   PassArgs<Real> a = a0;
   long long tiles;
@@ -28,7 +34,8 @@ cudaError_t launch_one(const PassArgs<Real>& a0, cudaStream_t s) {
     tiles = (long long)a.O * a.nblk_i;
   }
   if (tiles <= 0) return cudaSuccess;
-  pencil_pass<Real, n, CONTIG, MODE><<<(unsigned)tiles, Cfg::threads, Cfg::smem, s>>>(a);
+  const long long grid = tiles < grid_cap[dev] ? tiles : grid_cap[dev];
+  pencil_pass<Real, n, CONTIG, MODE, Cfg><<<(unsigned)grid, Cfg::threads, Cfg::smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -39,7 +46,9 @@ cudaError_t launch_n(PassKind kind, const PassArgs<Real>& a, cudaStream_t s) {
     case FWD_STRIDED: return launch_one<Real, n, false, MODE_FWD>(a, s);
     case INV_CONTIG: return launch_one<Real, n, true, MODE_INV>(a, s);
     case INV_STRIDED: return launch_one<Real, n, false, MODE_INV>(a, s);
-    case FUSED_STRIDED: return launch_one<Real, n, false, MODE_FUSED>(a, s);
+    case FUSED_STRIDED:
+      return a.nfields == 1 ? launch_one<Real, n, false, MODE_FUSED1>(a, s)
+                            : launch_one<Real, n, false, MODE_FUSEDN>(a, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -47,9 +56,9 @@ cudaError_t launch_n(PassKind kind, const PassArgs<Real>& a, cudaStream_t s) {
 template <typename Real, int n>
 bool shape_n(PassKind kind, PassShape* out) {
   const bool contig = (kind == FWD_CONTIG || kind == INV_CONTIG);
-  out->W = contig ? PassCfg<Real, n, true>::W : PassCfg<Real, n, false>::W;
-  out->threads = contig ? PassCfg<Real, n, true>::threads : PassCfg<Real, n, false>::threads;
-  out->smem = contig ? PassCfg<Real, n, true>::smem : PassCfg<Real, n, false>::smem;
+  out->W = contig ? PassCfg<Real, n, true, MODE_FWD>::W : PassCfg<Real, n, false, MODE_FWD>::W;
+  out->threads = contig ? PassCfg<Real, n, true, MODE_FWD>::threads : PassCfg<Real, n, false, MODE_FWD>::threads;
+  out->smem = contig ? PassCfg<Real, n, true, MODE_FWD>::smem : PassCfg<Real, n, false, MODE_FWD>::smem;
   return true;
 }
 

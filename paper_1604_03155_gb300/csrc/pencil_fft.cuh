@@ -11,6 +11,12 @@
 // (j/Ns) Ns R + k + r Ns.  The first stage reads global memory directly and the
 // last writes global memory directly.
 //
+// Memory pipeline: CTAs are persistent (the grid is the SM count times the
+// resident CTAs per SM) and walk the tiles with a grid stride.  The input of
+// the next tiles is staged into shared memory with 16-byte cp.async copies
+// (NSTG-deep ring) while the current tile's butterflies run, so the SM keeps
+// HBM requests in flight through the compute phases.
+//
 // Pruning: the forward input is f zero-padded from N to 2N, so the first
 // stage (Ns = 1) loads only r < R/2 (positions < N) and never reads the zero
 // half.  The inverse output is cropped to N, so the last inverse stage stores
@@ -151,12 +157,49 @@ template <bool INV> struct Dft<16, INV> {
   }
 };
 
+// R = 32: radix-16 transforms of the even and odd samples, then radix 2 with
+// w32^k = cos(pi k/16) -+ i sin(pi k/16).
+template <bool INV> struct Dft<32, INV> {
+  template <typename C> __device__ __forceinline__ static void run(C* v) {
+    using R = decltype(v[0].x);
+    // cos(pi k/16), k = 0..8
+    const R c[9] = {(R)1,
+                    (R)0.98078528040323044913,
+                    (R)0.92387953251128675613,
+                    (R)0.83146961230254523708,
+                    (R)0.70710678118654752440,
+                    (R)0.55557023301960222474,
+                    (R)0.38268343236508977173,
+                    (R)0.19509032201612826785,
+                    (R)0};
+    C e[16], o[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      e[i] = v[2 * i];
+      o[i] = v[2 * i + 1];
+    }
+    Dft<16, INV>::run(e);
+    Dft<16, INV>::run(o);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      // cos(pi k/16) and sin(pi k/16) = cos(pi (8-k)/16)
+      const R ck = k <= 8 ? c[k] : -c[16 - k];
+      const R sk = k <= 8 ? c[8 - k] : c[k - 8];
+      const C w = {ck, INV ? sk : -sk};
+      const C t = cmul(o[k], w);
+      v[k] = cadd(e[k], t);
+      v[k + 16] = csub(e[k], t);
+    }
+  }
+};
+
 // ---------------------------------------------------------------------------
 // compile-time plan: radices chosen greedily (16, 8, 4, 3, 2) dividing both the
 // remaining length and the per-thread count E.
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr int pick_radix(int rem, int E) {
-  return (rem % 16 == 0 && E % 16 == 0)  ? 16
+  return (rem % 32 == 0 && E % 32 == 0)  ? 32
+         : (rem % 16 == 0 && E % 16 == 0)  ? 16
          : (rem % 8 == 0 && E % 8 == 0)  ? 8
          : (rem % 4 == 0 && E % 4 == 0)  ? 4
          : (rem % 3 == 0 && E % 3 == 0)  ? 3
@@ -194,10 +237,14 @@ template <typename Real> __host__ __device__ constexpr int elems_per_thread(int 
 }
 
 // ---------------------------------------------------------------------------
-// shared-memory tile: W pencils of n elements, element (w, pos) at
-// w*P + pos + (pos >> SH), P = n + (n >> SH) + 1.  The 1-in-2^SH padding makes
-// radix-strided accesses within a pencil conflict-free; the odd pitch P makes
-// same-position accesses across pencils conflict-free.
+// shared-memory exchange layouts
+//  contiguous pencils: element (w, pos) at w*P + pos + (pos >> SH), P odd:
+//    radix-strided positions of one pencil and equal positions of different
+//    pencils both fall in distinct banks;
+//  strided pencils: e = pos*W + w at e + (e >> SH): the W pencils of a row are
+//    adjacent (as in global memory) and one pad per 2^SH elements spreads
+//    radix-strided rows over the banks.
+// SH = 4 for 8-byte elements (16 per 128-byte row), 3 for 16-byte elements.
 // ---------------------------------------------------------------------------
 template <typename Real> struct SmemLayout {
   static constexpr int SH = sizeof(Real) == 4 ? 4 : 3;
@@ -205,25 +252,34 @@ template <typename Real> struct SmemLayout {
 template <typename Real> __host__ __device__ constexpr int smem_pitch(int n) {
   return n + (n >> SmemLayout<Real>::SH) + 1;
 }
+template <typename Real> __host__ __device__ constexpr int xchg_elems(int n, int W, bool contig) {
+  return contig ? W * smem_pitch<Real>(n) : (n * W + ((n * W) >> SmemLayout<Real>::SH) + 1);
+}
 
-enum PassMode { MODE_FWD = 0, MODE_INV = 1, MODE_FUSED = 2 };
+enum PassMode { MODE_FWD = 0, MODE_INV = 1, MODE_FUSED1 = 2, MODE_FUSEDN = 3 };
 
-// Pencils per CTA: 256 threads' worth, at least 16 for strided passes (to fill
-// 128-byte rows), bounded by a 72 KB exchange buffer.
-template <typename Real> __host__ __device__ constexpr int pencils_per_cta(int n, bool contig) {
-  int Tp = n / elems_per_thread<Real>(n);
+// Pencils per CTA: 256 threads' worth; strided passes take at least 8 pencils
+// (64-byte row segments) and at most 64; bounded by an exchange buffer of
+// `budget` bytes (40 KB; 72 KB for the fused passes, which measured faster
+// with wider tiles and fewer, larger CTAs).
+template <typename Real>
+__host__ __device__ constexpr int pencils_per_cta(int n, bool contig, int E, int budget = 40 * 1024) {
+  int Tp = n / E;
   int w = 256 / Tp;
   if (w < 1) w = 1;
   if (!contig) {
-    if (w < 16) w = 16;
+    if (w < 8) w = 8;
     if (w > 64) w = 64;
   } else if (w > 32) {
     w = 32;
   }
-  while (w > 1 && (long)w * smem_pitch<Real>(n) * 2 * (long)sizeof(Real) > 72 * 1024) w >>= 1;
+  while (w > 1 && (long)xchg_elems<Real>(n, w, contig) * 2 * (long)sizeof(Real) > budget) w >>= 1;
   while (w > 1 && w * Tp > 1024) w >>= 1;
   return w;
 }
+
+// Input elements of one tile's first stage per pencil (pruned forward: N).
+__host__ __device__ constexpr int stage_in_len(int n, int mode) { return mode == MODE_INV ? n : n / 2; }
 
 // ---------------------------------------------------------------------------
 // multiplier fields of the fused pass
@@ -245,7 +301,13 @@ template <typename Real> struct PassArgs {
   int I;       // inner count of strided pencils (1 for contiguous)
   int nblk_i;  // ceil(I / W)
   int in_real, out_real;
-  const C* tw;  // twiddles exp(-2 pi i q/n), q in [0, n)
+  int async_ok;  // input rows 16-byte aligned: stage them with cp.async
+  // contiguous passes over several fields in one launch: rows [f*rows_per_field,
+  // (f+1)*rows_per_field) are written to outs[f] (nout > 1), else to out
+  int nout;
+  long long rows_per_field;
+  void* outs[4];
+  const C* tw;   // twiddles exp(-2 pi i q/n), q in [0, n)
   // fused pass only
   int nfields;
   int d;
@@ -257,11 +319,26 @@ template <typename Real, typename C> __device__ __forceinline__ C ld_in(const Pa
   if (a.in_real) return C{__ldg(reinterpret_cast<const Real*>(a.in) + idx), (Real)0};
   return __ldg(reinterpret_cast<const C*>(a.in) + idx);
 }
-template <typename Real, typename C> __device__ __forceinline__ void st_out(const PassArgs<Real>& a, long long idx, C v) {
+template <typename Real, typename C>
+__device__ __forceinline__ void st_out(const PassArgs<Real>& a, void* out, long long idx, C v) {
   if (a.out_real)
-    reinterpret_cast<Real*>(a.out)[idx] = v.x;
+    reinterpret_cast<Real*>(out)[idx] = v.x;
   else
-    reinterpret_cast<C*>(a.out)[idx] = v;
+    reinterpret_cast<C*>(out)[idx] = v;
+}
+
+// ---------------------------------------------------------------------------
+// cp.async (16-byte global -> shared copies, L2 only)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -297,12 +374,14 @@ template <int n, int E, bool INV, int S> __device__ __forceinline__ int stage_in
   return j + r * (n / R);
 }
 
-template <typename Real, int n> __device__ __forceinline__ int saddr(int w, int pos) {
-  return w * smem_pitch<Real>(n) + pos + (pos >> SmemLayout<Real>::SH);
+template <typename Real, int n, int W, bool CONTIG> __device__ __forceinline__ int saddr(int w, int pos) {
+  if (CONTIG) return w * smem_pitch<Real>(n) + pos + (pos >> SmemLayout<Real>::SH);
+  const int e = pos * W + w;
+  return e + (e >> SmemLayout<Real>::SH);
 }
 
 // Exchange after stage S (compute done) into stage S+1 (loads done).
-template <typename Real, typename C, int n, int E, bool INV, int S>
+template <typename Real, typename C, int n, int E, int W, bool CONTIG, bool INV, int S>
 __device__ __forceinline__ void exchange(C (&v)[E], C* sm, int w, int t) {
   constexpr int R0 = stage_radix(n, E, INV, S);
   constexpr int R1 = stage_radix(n, E, INV, S + 1);
@@ -311,43 +390,102 @@ __device__ __forceinline__ void exchange(C (&v)[E], C* sm, int w, int t) {
 #pragma unroll
   for (int q = 0; q < E / R0; ++q)
 #pragma unroll
-    for (int r = 0; r < R0; ++r) sm[saddr<Real, n>(w, stage_out_pos<n, E, INV, S>(t + q * Tp, r))] = v[q * R0 + r];
+    for (int r = 0; r < R0; ++r)
+      sm[saddr<Real, n, W, CONTIG>(w, stage_out_pos<n, E, INV, S>(t + q * Tp, r))] = v[q * R0 + r];
   __syncthreads();
 #pragma unroll
   for (int q = 0; q < E / R1; ++q)
 #pragma unroll
-    for (int r = 0; r < R1; ++r) v[q * R1 + r] = sm[saddr<Real, n>(w, stage_in_pos<n, E, INV, S + 1>(t + q * Tp, r))];
+    for (int r = 0; r < R1; ++r)
+      v[q * R1 + r] = sm[saddr<Real, n, W, CONTIG>(w, stage_in_pos<n, E, INV, S + 1>(t + q * Tp, r))];
 }
 
 // Runs stages [S, NS) of a transform whose stage S inputs are already loaded.
-template <typename Real, typename C, int n, int E, bool INV, int S, int NS> struct StageRun {
+template <typename Real, typename C, int n, int E, int W, bool CONTIG, bool INV, int S, int NS> struct StageRun {
   __device__ __forceinline__ static void run(C (&v)[E], C* sm, int w, int t, const C* tw) {
     stage_compute<C, n, E, INV, S>(v, t, tw);
     if constexpr (S + 1 < NS) {
-      exchange<Real, C, n, E, INV, S>(v, sm, w, t);
-      StageRun<Real, C, n, E, INV, S + 1, NS>::run(v, sm, w, t, tw);
+      exchange<Real, C, n, E, W, CONTIG, INV, S>(v, sm, w, t);
+      StageRun<Real, C, n, E, W, CONTIG, INV, S + 1, NS>::run(v, sm, w, t, tw);
     }
   }
 };
 
 __device__ __forceinline__ int fold_freq(int m, int n) { return m <= n - m ? m : n - m; }
 
+// Launch configuration of a pass.  E (values per thread), W (pencils per CTA),
+// NSTG (staging ring depth) and MINB (CTAs per SM the registers must allow)
+// default to the tuned choices; 0 selects the default.
+template <typename Real, int n, bool CONTIG, int MODE, int E_ = 0, int W_ = 0, int NSTG_ = 0, int MINB_ = 0>
+struct PassCfg {
+  static constexpr int E = E_ > 0 ? E_ : elems_per_thread<Real>(n);
+  static constexpr int Tp = n / E;
+  static constexpr int W = W_ > 0 ? W_ : pencils_per_cta<Real>(n, CONTIG, E, MODE >= MODE_FUSED1 ? 72 * 1024 : 40 * 1024);
+  static constexpr int threads = W * Tp;
+  static constexpr int nstages = plan_nstages(n, E);
+  static constexpr int NIN = stage_in_len(n, MODE);
+  // rounded up to 128 bytes: the staging ring that follows takes 16-byte copies
+  static constexpr size_t xchg_bytes = ((size_t)xchg_elems<Real>(n, W, CONTIG) * 2 * sizeof(Real) + 127) / 128 * 128;
+  static constexpr size_t slot_bytes = (size_t)W * NIN * 2 * sizeof(Real);
+  // staging ring depth: 3 slots when they fit a 96 KB budget, else 2 (fused: 2)
+  static constexpr int NSTG =
+      NSTG_ > 0 ? NSTG_ : ((MODE < MODE_FUSED1 && xchg_bytes + 3 * slot_bytes <= 96 * 1024) ? 3 : 2);
+  static constexpr size_t smem = xchg_bytes + NSTG * slot_bytes;
+  // by default at most 128 registers per thread: at least two 256-thread CTAs per SM
+  static constexpr int min_blocks =
+      MINB_ > 0 ? MINB_ : ((65536 / (threads * 128)) < 1 ? 1 : (65536 / (threads * 128)));
+};
+
+// Stages the input of one tile into a staging slot with 16-byte copies.
+// Strided slot layout [pos][w] (rows of W pencils, as in global memory);
+// contiguous slot layout [w][pos].  Real input is staged as reals.
+template <typename Real, int n, bool CONTIG, int MODE, typename Cfg>
+__device__ __forceinline__ void stage_tile(const PassArgs<Real>& a, long long tile, unsigned char* slot) {
+  using C = typename CxT<Real>::T;
+  constexpr int W = Cfg::W, NIN = Cfg::NIN, THREADS = Cfg::threads;
+  const int esize = a.in_real ? (int)sizeof(Real) : (int)sizeof(C);
+  const int per16 = 16 / esize;  // elements per 16-byte chunk
+  const char* gin = reinterpret_cast<const char*>(a.in);
+  if (CONTIG) {
+    const long long row0 = tile * W;
+    const int cpr = NIN / per16;  // chunks per row
+    for (int c = threadIdx.x; c < W * cpr; c += THREADS) {
+      const int w = c / cpr, k = c % cpr;
+      if (row0 + w < a.O)
+        cp_async16(slot + ((size_t)w * NIN + (size_t)k * per16) * esize,
+                   gin + ((row0 + w) * a.in_pitch_o + (long long)k * per16) * esize);
+    }
+  } else {
+    const long long o = tile / a.nblk_i;
+    const int inner0 = (int)(tile % a.nblk_i) * W;
+    const int cpr = W / per16;
+    for (int c = threadIdx.x; c < NIN * cpr; c += THREADS) {
+      const int pos = c / cpr, k = c % cpr;
+      if (inner0 + k * per16 < a.I)
+        cp_async16(slot + ((size_t)pos * W + (size_t)k * per16) * esize,
+                   gin + (o * a.in_pitch_o + pos * a.in_pitch_pos + inner0 + (long long)k * per16) * esize);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // the pass kernel
-//   MODE_FWD:   N valid inputs -> n outputs       (forward, pruned input)
-//   MODE_INV:   n inputs -> N outputs             (inverse, cropped output)
-//   MODE_FUSED: N inputs -> fwd -> x multiplier -> inv -> N outputs, per field
+//   MODE_FWD:    N valid inputs -> n outputs       (forward, pruned input)
+//   MODE_INV:    n inputs -> N outputs             (inverse, cropped output)
+//   MODE_FUSED1: N inputs -> fwd -> x multiplier -> inv -> N outputs
+//   MODE_FUSEDN: the same for nfields fields sharing one forward transform
 // CONTIG: pencils are contiguous rows; otherwise pencils are strided and the
-// W pencils of a CTA are W consecutive inner indices (coalesced).
+// W pencils of a tile are W consecutive inner indices (coalesced).
 // ---------------------------------------------------------------------------
-template <typename Real, int n, bool CONTIG, int MODE>
-__global__ void __launch_bounds__(pencils_per_cta<Real>(n, CONTIG) * (n / elems_per_thread<Real>(n)))
-    pencil_pass(const PassArgs<Real> a) {
+template <typename Real, int n, bool CONTIG, int MODE, typename Cfg = PassCfg<Real, n, CONTIG, MODE>>
+__global__ void __launch_bounds__(Cfg::threads, Cfg::min_blocks) pencil_pass(const PassArgs<Real> a) {
   using C = typename CxT<Real>::T;
-  constexpr int E = elems_per_thread<Real>(n);
-  constexpr int Tp = n / E;
-  constexpr int W = pencils_per_cta<Real>(n, CONTIG);
-  constexpr int NS = plan_nstages(n, E);
+  constexpr int E = Cfg::E;
+  constexpr int Tp = Cfg::Tp;
+  constexpr int W = Cfg::W;
+  constexpr int NS = Cfg::nstages;
+  constexpr int NIN = Cfg::NIN;
+  constexpr int NSTG = Cfg::NSTG;
   static_assert(NS > 0, "unsupported FFT length");
   constexpr bool FWD_FIRST = (MODE != MODE_INV);
   constexpr int R_first = stage_radix(n, E, !FWD_FIRST, 0);
@@ -357,131 +495,191 @@ __global__ void __launch_bounds__(pencils_per_cta<Real>(n, CONTIG) * (n / elems_
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
+  unsigned char* stg = smem_raw + Cfg::xchg_bytes;
 
   const int tid = threadIdx.x;
   const int w = CONTIG ? tid / Tp : tid % W;
   const int t = CONTIG ? tid % Tp : tid / W;
-
-  // tile -> pencil coordinates
-  long long in_base, out_base;
-  bool valid;
-  int inner = 0;
-  if (CONTIG) {
-    const long long row = (long long)blockIdx.x * W + w;
-    valid = row < a.O;
-    in_base = row * a.in_pitch_o;
-    out_base = row * a.out_pitch_o;
-  } else {
-    const int o = blockIdx.x / a.nblk_i;
-    inner = (blockIdx.x % a.nblk_i) * W + w;
-    valid = inner < a.I;
-    in_base = (long long)o * a.in_pitch_o + inner;
-    out_base = (long long)o * a.out_pitch_o + inner;
-  }
+  const long long ntiles = CONTIG ? (a.O + W - 1) / W : (long long)a.O * a.nblk_i;
+  // strided rows narrower than one 16-byte chunk are read directly
+  constexpr bool STAGEABLE = CONTIG || ((W * 2 * sizeof(Real)) % 16 == 0);
+  const bool staged = STAGEABLE && a.async_ok != 0;
   const C* tw = a.tw;
 
-  C v[E];
-  // ---- first stage loads straight from global memory ----
-  {
-    constexpr int R = R_first;
+  // prologue: stage the first NSTG-1 tiles of this CTA
 #pragma unroll
-    for (int q = 0; q < E / R; ++q) {
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int pos = stage_in_pos<n, E, !FWD_FIRST, 0>(t + q * Tp, r);
-        C x = {(Real)0, (Real)0};
-        if (valid && (!FWD_FIRST || r < R / 2)) x = ld_in<Real, C>(a, in_base + (long long)pos * a.in_pitch_pos);
-        v[q * R + r] = x;
-      }
-    }
+  for (int s = 0; s < NSTG - 1; ++s) {
+    const long long tl = blockIdx.x + (long long)s * gridDim.x;
+    if (staged && tl < ntiles) stage_tile<Real, n, CONTIG, MODE, Cfg>(a, tl, stg + s * Cfg::slot_bytes);
+    cp_async_commit();
   }
 
-  if constexpr (MODE == MODE_FWD) {
-    StageRun<Real, C, n, E, false, 0, NS>::run(v, sm, w, t, tw);
-    constexpr int R = stage_radix(n, E, false, NS - 1);
-    if (valid) {
+  int it = 0;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    {
+      const long long tl = tile + (long long)(NSTG - 1) * gridDim.x;
+      if (staged && tl < ntiles)
+        stage_tile<Real, n, CONTIG, MODE, Cfg>(a, tl, stg + ((it + NSTG - 1) % NSTG) * Cfg::slot_bytes);
+      cp_async_commit();
+    }
+    cp_async_wait<NSTG - 1>();
+    __syncthreads();
+    const unsigned char* slot = stg + (it % NSTG) * Cfg::slot_bytes;
+
+    // tile -> pencil coordinates
+    long long in_base, out_base;
+    bool valid;
+    int inner = 0;
+    void* outp = a.out;
+    if (CONTIG) {
+      const long long row = tile * W + w;
+      valid = row < a.O;
+      in_base = row * a.in_pitch_o;
+      out_base = row * a.out_pitch_o;
+      if (a.nout > 1) {
+        const int f = valid ? (int)(row / a.rows_per_field) : 0;
+        outp = a.outs[f];
+        out_base = (row - f * a.rows_per_field) * a.out_pitch_o;
+      }
+    } else {
+      const long long o = tile / a.nblk_i;
+      inner = (int)(tile % a.nblk_i) * W + w;
+      valid = inner < a.I;
+      in_base = o * a.in_pitch_o + inner;
+      out_base = o * a.out_pitch_o + inner;
+    }
+
+    C v[E];
+    // ---- first stage loads: staged shared memory (or global memory) ----
+    {
+      constexpr int R = R_first;
 #pragma unroll
-      for (int q = 0; q < E / R; ++q)
+      for (int q = 0; q < E / R; ++q) {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-          const int pos = stage_out_pos<n, E, false, NS - 1>(t + q * Tp, r);
-          st_out<Real, C>(a, out_base + (long long)pos * a.out_pitch_pos, v[q * R + r]);
-        }
-    }
-  } else if constexpr (MODE == MODE_INV) {
-    StageRun<Real, C, n, E, true, 0, NS>::run(v, sm, w, t, tw);
-    constexpr int R = R_lastinv;
-    if (valid) {
-#pragma unroll
-      for (int q = 0; q < E / R; ++q)
-#pragma unroll
-        for (int r = 0; r < R / 2; ++r) {
-          const int pos = stage_out_pos<n, E, true, NS - 1>(t + q * Tp, r);
-          st_out<Real, C>(a, out_base + (long long)pos * a.out_pitch_pos, v[q * R + r]);
-        }
-    }
-  } else {
-    StageRun<Real, C, n, E, false, 0, NS>::run(v, sm, w, t, tw);
-    // frequencies of the other axes (fused axis = axis 0, the slowest)
-    const int Nh = a.Nh;
-    const int np1 = Nh + 1;
-    int m1 = 0, m2 = 0;
-    if (a.d == 3) {
-      m1 = inner / n;
-      m2 = inner % n;
-    } else {
-      m1 = inner;
-    }
-    const int f1 = fold_freq(m1, n), f2 = fold_freq(m2, n);
-    const long long oct_rest = (a.d == 3) ? (long long)f1 * np1 + f2 : f1;
-    const long long oct_pitch0 = (a.d == 3) ? (long long)np1 * np1 : np1;
-    constexpr int RL = stage_radix(n, E, false, NS - 1);  // == first inverse radix
-    for (int fi = 0; fi < a.nfields; ++fi) {
-      const FieldDesc fd = a.fields[fi];
-      const C* mult = reinterpret_cast<const C*>(fd.mult);
-      C y[E];
-#pragma unroll
-      for (int q = 0; q < E / RL; ++q)
-#pragma unroll
-        for (int r = 0; r < RL; ++r) {
-          const int m0 = stage_out_pos<n, E, false, NS - 1>(t + q * Tp, r);
-          C g = {(Real)0, (Real)0};
-          if (valid) g = __ldg(mult + fold_freq(m0, n) * oct_pitch0 + oct_rest);
-          if (fd.odd_axis >= 0) {
-            const int mj = fd.odd_axis == 0 ? m0 : (fd.odd_axis == 1 ? m1 : m2);
-            if (mj > Nh) g = C{-g.x, -g.y};
+          const int pos = stage_in_pos<n, E, !FWD_FIRST, 0>(t + q * Tp, r);
+          C x = {(Real)0, (Real)0};
+          if (valid && (!FWD_FIRST || r < R / 2)) {
+            if (staged) {
+              const int e = CONTIG ? w * NIN + pos : pos * W + w;
+              if (a.in_real)
+                x = C{reinterpret_cast<const Real*>(slot)[e], (Real)0};
+              else
+                x = reinterpret_cast<const C*>(slot)[e];
+            } else {
+              x = ld_in<Real, C>(a, in_base + (long long)pos * a.in_pitch_pos);
+            }
           }
-          if (fd.spectral_axis >= 0) {
-            const int mj = fd.spectral_axis == 0 ? m0 : (fd.spectral_axis == 1 ? m1 : m2);
-            const int ms = mj < Nh ? mj : (mj == Nh ? 0 : mj - n);
-            const Real f = (Real)3.14159265358979323846 * (Real)ms;
-            g = C{-g.y * f, g.x * f};  // i pi m_j * g
-          }
-          y[q * RL + r] = cmul(v[q * RL + r], g);
+          v[q * R + r] = x;
         }
-      if (fi > 0) __syncthreads();  // the previous field's last exchange readers
-      StageRun<Real, C, n, E, true, 0, NS>::run(y, sm, w, t, tw);
+      }
+    }
+
+    if constexpr (MODE == MODE_FWD) {
+      StageRun<Real, C, n, E, W, CONTIG, false, 0, NS>::run(v, sm, w, t, tw);
+      constexpr int R = stage_radix(n, E, false, NS - 1);
+      if (valid) {
+#pragma unroll
+        for (int q = 0; q < E / R; ++q)
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const int pos = stage_out_pos<n, E, false, NS - 1>(t + q * Tp, r);
+            st_out<Real, C>(a, outp, out_base + (long long)pos * a.out_pitch_pos, v[q * R + r]);
+          }
+      }
+    } else if constexpr (MODE == MODE_INV) {
+      StageRun<Real, C, n, E, W, CONTIG, true, 0, NS>::run(v, sm, w, t, tw);
       constexpr int R = R_lastinv;
       if (valid) {
-        const long long ob = out_base + (long long)fi * a.out_field_stride;
 #pragma unroll
         for (int q = 0; q < E / R; ++q)
 #pragma unroll
           for (int r = 0; r < R / 2; ++r) {
             const int pos = stage_out_pos<n, E, true, NS - 1>(t + q * Tp, r);
-            st_out<Real, C>(a, ob + (long long)pos * a.out_pitch_pos, y[q * R + r]);
+            st_out<Real, C>(a, outp, out_base + (long long)pos * a.out_pitch_pos, v[q * R + r]);
           }
       }
+    } else {
+      // frequencies of the other axes (fused axis = axis 0, the slowest)
+      const int Nh = a.Nh;
+      const int np1 = Nh + 1;
+      int m1 = 0, m2 = 0;
+      if (a.d == 3) {
+        m1 = inner / n;
+        m2 = inner % n;
+      } else {
+        m1 = inner;
+      }
+      const long long oct_rest = (a.d == 3) ? (long long)fold_freq(m1, n) * np1 + fold_freq(m2, n) : fold_freq(m1, n);
+      const long long oct_pitch0 = (a.d == 3) ? (long long)np1 * np1 : np1;
+      constexpr int RL = stage_radix(n, E, false, NS - 1);  // == first inverse radix
+      // multiplier of field 0, issued before the forward transform to hide its latency
+      C g[E];
+      {
+        const C* mult = reinterpret_cast<const C*>(a.fields[0].mult);
+#pragma unroll
+        for (int q = 0; q < E / RL; ++q)
+#pragma unroll
+          for (int r = 0; r < RL; ++r) {
+            const int m0 = stage_out_pos<n, E, false, NS - 1>(t + q * Tp, r);
+            g[q * RL + r] = valid ? __ldg(mult + fold_freq(m0, n) * oct_pitch0 + oct_rest) : C{(Real)0, (Real)0};
+          }
+      }
+      StageRun<Real, C, n, E, W, CONTIG, false, 0, NS>::run(v, sm, w, t, tw);
+      const int nf = (MODE == MODE_FUSED1) ? 1 : a.nfields;
+      for (int fi = 0; fi < nf; ++fi) {
+        const FieldDesc fd = a.fields[fi];
+        if (fi > 0) {
+          const C* mult = reinterpret_cast<const C*>(fd.mult);
+#pragma unroll
+          for (int q = 0; q < E / RL; ++q)
+#pragma unroll
+            for (int r = 0; r < RL; ++r) {
+              const int m0 = stage_out_pos<n, E, false, NS - 1>(t + q * Tp, r);
+              g[q * RL + r] = valid ? __ldg(mult + fold_freq(m0, n) * oct_pitch0 + oct_rest) : C{(Real)0, (Real)0};
+            }
+        }
+        C y[(MODE == MODE_FUSED1) ? 1 : E];
+        C* yy = (MODE == MODE_FUSED1) ? v : y;
+#pragma unroll
+        for (int q = 0; q < E / RL; ++q)
+#pragma unroll
+          for (int r = 0; r < RL; ++r) {
+            const int m0 = stage_out_pos<n, E, false, NS - 1>(t + q * Tp, r);
+            C gg = g[q * RL + r];
+            if (fd.odd_axis >= 0) {
+              const int mj = fd.odd_axis == 0 ? m0 : (fd.odd_axis == 1 ? m1 : m2);
+              if (mj > Nh) gg = C{-gg.x, -gg.y};
+            }
+            if (fd.spectral_axis >= 0) {
+              const int mj = fd.spectral_axis == 0 ? m0 : (fd.spectral_axis == 1 ? m1 : m2);
+              const int ms = mj < Nh ? mj : (mj == Nh ? 0 : mj - n);
+              const Real f = (Real)3.14159265358979323846 * (Real)ms;
+              gg = C{-gg.y * f, gg.x * f};  // i pi m_j * g
+            }
+            yy[q * RL + r] = cmul(v[q * RL + r], gg);
+          }
+        if constexpr (MODE == MODE_FUSED1) {
+          StageRun<Real, C, n, E, W, CONTIG, true, 0, NS>::run(v, sm, w, t, tw);
+        } else {
+          StageRun<Real, C, n, E, W, CONTIG, true, 0, NS>::run(y, sm, w, t, tw);
+        }
+        constexpr int R = R_lastinv;
+        if (valid) {
+          const long long ob = out_base + (long long)fi * a.out_field_stride;
+#pragma unroll
+          for (int q = 0; q < E / R; ++q)
+#pragma unroll
+            for (int r = 0; r < R / 2; ++r) {
+              const int pos = stage_out_pos<n, E, true, NS - 1>(t + q * Tp, r);
+              st_out<Real, C>(a, outp, ob + (long long)pos * a.out_pitch_pos, yy[q * R + r]);
+            }
+        }
+      }
     }
+    __syncthreads();  // this tile's slot and the exchange buffer are free again
   }
+  cp_async_wait<0>();
 }
-
-template <typename Real, int n, bool CONTIG> struct PassCfg {
-  static constexpr int E = elems_per_thread<Real>(n);
-  static constexpr int W = pencils_per_cta<Real>(n, CONTIG);
-  static constexpr int threads = W * (n / E);
-  static constexpr size_t smem = (size_t)W * smem_pitch<Real>(n) * 2 * sizeof(Real);
-  static constexpr int nstages = plan_nstages(n, E);
-};
 
 }  // namespace vp

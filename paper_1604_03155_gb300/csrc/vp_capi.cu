@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
+#include <stdint.h>
 #include <string.h>
 
 #include <string>
@@ -245,6 +246,16 @@ cudaEvent_t pool_event(vp_plan p) {
   return e;
 }
 
+// Whether a pass's input rows can be staged with 16-byte copies.
+template <typename Real>
+void set_async(PassArgs<Real>& a, bool contig, int nin) {
+  const long long es = a.in_real ? (long long)sizeof(Real) : 2LL * (long long)sizeof(Real);
+  bool ok = (reinterpret_cast<uintptr_t>(a.in) % 16 == 0) && ((a.in_pitch_o * es) % 16 == 0) &&
+            ((nin * es) % 16 == 0);
+  if (!contig) ok = ok && ((a.in_pitch_pos * es) % 16 == 0);
+  a.async_ok = ok ? 1 : 0;
+}
+
 template <typename Real>
 cudaError_t launch_pass(vp_plan p, int pass, PassKind kind, const PassArgs<Real>& a) {
   TimedLaunch tl{pass, nullptr, nullptr};
@@ -330,6 +341,7 @@ vp_status run_apply_ws(vp_plan p, void* ws, const void* f, void* const* outs, co
     a.out_pitch_pos = 1;
     a.in_real = real_io;
     a.out_real = 0;
+    set_async(a, true, N);
     if ((e = launch_pass<Real>(p, P_FWD_ROWS, FWD_CONTIG, a)) != cudaSuccess) return cuda_fail(p, e, "pass fwd_rows");
     // P2: axis 1, N -> 2N, slabs i0
     a.in = wsA;
@@ -341,6 +353,7 @@ vp_status run_apply_ws(vp_plan p, void* ws, const void* f, void* const* outs, co
     a.out_pitch_o = (long long)n * n;
     a.out_pitch_pos = n;
     a.in_real = 0;
+    set_async(a, false, N);
     if ((e = launch_pass<Real>(p, P_FWD_AX1, FWD_STRIDED, a)) != cudaSuccess) return cuda_fail(p, e, "pass fwd_axis1");
     // P3: axis 0 fused, N -> N per field (field 0 in place)
     a.in = wsB;
@@ -354,6 +367,7 @@ vp_status run_apply_ws(vp_plan p, void* ws, const void* f, void* const* outs, co
     a.out_field_stride = 4 * U;
     a.nfields = F;
     for (int i = 0; i < F; ++i) a.fields[i] = fields[i];
+    set_async(a, false, N);
     if ((e = launch_pass<Real>(p, P_FUSED, FUSED_STRIDED, a)) != cudaSuccess) return cuda_fail(p, e, "pass fused_axis0");
     a.nfields = 0;
     // P4: axis 1 inverse, 2N -> N, all fields as slabs
@@ -365,20 +379,23 @@ vp_status run_apply_ws(vp_plan p, void* ws, const void* f, void* const* outs, co
     a.in_pitch_pos = n;
     a.out_pitch_o = (long long)N * n;
     a.out_pitch_pos = n;
+    set_async(a, false, n);
     if ((e = launch_pass<Real>(p, P_INV_AX1, INV_STRIDED, a)) != cudaSuccess) return cuda_fail(p, e, "pass inv_axis1");
-    // P5: rows inverse, 2N -> N, one launch per field
-    for (int i = 0; i < F; ++i) {
-      a.in = wsA + (long long)i * 2 * U;
-      a.out = outs[i];
-      a.O = N * N;
-      a.I = 1;
-      a.in_pitch_o = n;
-      a.in_pitch_pos = 1;
-      a.out_pitch_o = N;
-      a.out_pitch_pos = 1;
-      a.out_real = real_io;
-      if ((e = launch_pass<Real>(p, P_INV_ROWS, INV_CONTIG, a)) != cudaSuccess) return cuda_fail(p, e, "pass inv_rows");
-    }
+    // P5: rows inverse, 2N -> N, all fields in one launch
+    a.in = wsA;
+    a.out = outs[0];
+    a.O = F * N * N;
+    a.I = 1;
+    a.in_pitch_o = n;
+    a.in_pitch_pos = 1;
+    a.out_pitch_o = N;
+    a.out_pitch_pos = 1;
+    a.out_real = real_io;
+    a.nout = F;
+    a.rows_per_field = (long long)N * N;
+    for (int i = 0; i < F; ++i) a.outs[i] = outs[i];
+    set_async(a, true, n);
+    if ((e = launch_pass<Real>(p, P_INV_ROWS, INV_CONTIG, a)) != cudaSuccess) return cuda_fail(p, e, "pass inv_rows");
   } else {
     // P1: rows along axis 1, N -> 2N
     a.in = f;
@@ -390,6 +407,7 @@ vp_status run_apply_ws(vp_plan p, void* ws, const void* f, void* const* outs, co
     a.out_pitch_o = n;
     a.out_pitch_pos = 1;
     a.in_real = real_io;
+    set_async(a, true, N);
     if ((e = launch_pass<Real>(p, P_FWD_ROWS, FWD_CONTIG, a)) != cudaSuccess) return cuda_fail(p, e, "pass fwd_rows");
     // P2: axis 0 fused
     a.in = wsA;
@@ -404,20 +422,24 @@ vp_status run_apply_ws(vp_plan p, void* ws, const void* f, void* const* outs, co
     a.in_real = 0;
     a.nfields = F;
     for (int i = 0; i < F; ++i) a.fields[i] = fields[i];
+    set_async(a, false, N);
     if ((e = launch_pass<Real>(p, P_FUSED, FUSED_STRIDED, a)) != cudaSuccess) return cuda_fail(p, e, "pass fused_axis0");
     a.nfields = 0;
-    for (int i = 0; i < F; ++i) {
-      a.in = wsA + (long long)i * 2 * U;
-      a.out = outs[i];
-      a.O = N;
-      a.I = 1;
-      a.in_pitch_o = n;
-      a.in_pitch_pos = 1;
-      a.out_pitch_o = N;
-      a.out_pitch_pos = 1;
-      a.out_real = real_io;
-      if ((e = launch_pass<Real>(p, P_INV_ROWS, INV_CONTIG, a)) != cudaSuccess) return cuda_fail(p, e, "pass inv_rows");
-    }
+    // P3: rows inverse, 2N -> N, all fields in one launch
+    a.in = wsA;
+    a.out = outs[0];
+    a.O = F * N;
+    a.I = 1;
+    a.in_pitch_o = n;
+    a.in_pitch_pos = 1;
+    a.out_pitch_o = N;
+    a.out_pitch_pos = 1;
+    a.out_real = real_io;
+    a.nout = F;
+    a.rows_per_field = N;
+    for (int i = 0; i < F; ++i) a.outs[i] = outs[i];
+    set_async(a, true, n);
+    if ((e = launch_pass<Real>(p, P_INV_ROWS, INV_CONTIG, a)) != cudaSuccess) return cuda_fail(p, e, "pass inv_rows");
   }
   return VP_OK;
 }
@@ -706,8 +728,8 @@ vp_status vp_plan_get_timing(vp_plan p, int cap, int* npass, const char** names,
 
 vp_status vp_plan_launch_count(vp_plan p, int grad, int* launches) {
   if (!p || !launches) return fail(p, VP_ERR_INVALID_ARG, "NULL argument");
-  const int F = grad ? 1 + p->d : 1;
-  *launches = (p->d == 3) ? 4 + F : 2 + F;
+  (void)grad;
+  *launches = (p->d == 3) ? 5 : 3;
   return VP_OK;
 }
 

@@ -150,6 +150,51 @@ int vp_fft_length_supported(int n2);
 
 
 /* ---------------------------------------------------------------------------
+ * Batched apply: many densities of different N, kernel and k in one persistent
+ * launch (a batched form of the Section 4 apply; the paper has no batch).
+ *
+ * vp_batch_create takes `count` (<= 128) FP32 plans (d = 3 or 2, 2N in
+ * {16, 24, 32, 48, 64, 96, 128, 192, 256}); the plans are borrowed and must
+ * outlive the batch.  The batch owns one workspace per density.
+ * vp_batch_apply computes phi_i = T_i * f_i for every i (device pointers,
+ * complex64, N_i^d elements each; asynchronous on the batch's stream).  Every
+ * pass of every density becomes tiles in one global work list; persistent CTAs
+ * take tiles in pass-major order and wait (bounded) until the previous pass of
+ * the same density has completed.  The launch and its counter reset run as one
+ * CUDA graph, replayed per call.
+ * Strategy: VP_BATCH_AUTO (default) times the persistent kernel at two grid
+ * sizes against per-density vp_apply launches (serial, and forked over eight
+ * streams inside one CUDA graph) on the first call, keeps the fastest and
+ * caches the choice on disk (file $VP_AUTOTUNE_CACHE, default
+ * ~/.cache/vp_autotune.txt) keyed by device, driver and the batch's sizes.
+ * Failure detection: a wait longer than the batch timeout (default about 2 s,
+ * vp_batch_set_timeout) records an error and lets the kernel finish;
+ * vp_batch_status then returns VP_ERR_TIMEOUT.  vp_batch_withhold(b, i, p)
+ * (p >= 1) makes pass p of density i wait for one tile more than its
+ * predecessor has, so that path can be tested without a device fault;
+ * p <= 0 restores every dependency.
+ * ------------------------------------------------------------------------- */
+typedef struct vp_batch_s* vp_batch;
+typedef enum {
+  VP_BATCH_AUTO = 0,
+  VP_BATCH_PERSISTENT = 1,        /* persistent kernel, all resident CTAs */
+  VP_BATCH_PERSISTENT_ONE_PER_SM = 2,
+  VP_BATCH_PER_DENSITY = 3,       /* one vp_apply per density, for comparison */
+  VP_BATCH_GRAPH_STREAMS = 4      /* per-density applies over 8 streams, one CUDA graph */
+} vp_batch_strategy;
+vp_status vp_batch_create(vp_batch* out, int count, const vp_plan* plans);
+vp_status vp_batch_set_stream(vp_batch b, void* stream);
+vp_status vp_batch_set_strategy(vp_batch b, int strategy);
+vp_status vp_batch_get_strategy(vp_batch b, int* strategy);
+vp_status vp_batch_set_timeout(vp_batch b, double seconds);
+vp_status vp_batch_withhold(vp_batch b, int density, int pass);
+vp_status vp_batch_apply(vp_batch b, const void* const* f, void* const* phi);
+vp_status vp_batch_status(vp_batch b);
+vp_status vp_batch_info(vp_batch b, long long* items, int* passes, size_t* device_bytes);
+const char* vp_batch_last_error(vp_batch b);
+vp_status vp_batch_destroy(vp_batch b);
+
+/* ---------------------------------------------------------------------------
  * Potential apply without device allocation (the paper has no counterpart;
  * this is a deployment aid).
  *

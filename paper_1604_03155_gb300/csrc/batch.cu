@@ -1,0 +1,705 @@
+// batch.cu -- many densities of uneven size and wavenumber in one persistent
+// launch (a batched form of the apply of Section 4; not in the paper).
+//
+// Every pass of every density becomes a list of tiles.  All lists are laid out
+// pass-major in one global item range: first pass of every density, then the
+// second pass of every density, and so on.  Persistent CTAs take items from a
+// global counter; before running a tile of pass p of density i a CTA waits
+// until every tile of pass p-1 of density i has completed (per-pass completion
+// counters).  Every item a CTA waits on was taken earlier by a resident CTA,
+// so the batch always makes progress; each wait is still bounded by a clock
+// limit after which the kernel records VP_ERR_TIMEOUT in an error word and goes
+// on, so a lost dependency can never hang the device.  Intermediate data is
+// produced inside the kernel, so tiles read it with ld.global.cg (L2) instead
+// of the non-coherent read-only path.
+//
+// The host driver captures [reset counters, batch kernel] into a CUDA graph and
+// replays it; density pointers travel as kernel parameters updated per replay.
+// An autotuner times the persistent kernel at two grid sizes against
+// per-density launches and caches the fastest choice per device and batch.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/vp.h"
+#include "vp_internal.cuh"
+
+namespace vp {
+
+constexpr int BATCH_MAX = 128;
+constexpr int BATCH_THREADS = 256;
+
+// Per-(density, pass) description of the tiles.
+struct BatchPass {
+  PassArgs<float> a;
+  int n;                 // FFT length 2N
+  int kind;              // PassKind
+  int density;           // index into the pointer tables
+  int io;                // 1: input is the density's f, 2: output is the density's phi
+  long long ntiles;
+  long long item_base;   // first global item of this pass
+  int dep;               // completion counter to wait on (-1: none)
+  long long dep_need;    // tiles that counter must reach
+  long long dep_need_orig;
+  int done;              // completion counter this pass increments
+};
+
+struct BatchLaunch {
+  const BatchPass* passes;
+  int npasses;
+  long long total_items;
+  unsigned long long* next_item;
+  long long* done;
+  int* err;
+  long long timeout_cycles;
+  const void* f[BATCH_MAX];
+  void* phi[BATCH_MAX];
+};
+
+// Uniform 256-thread configuration per FFT length: E = 16 (12 with a factor 3),
+// W = 256 / (n / E) pencils per tile.
+template <int n> struct BatchE {
+  static constexpr int E = (n % 3 == 0) ? 12 : 16;
+};
+template <int n, bool CONTIG, int MODE>
+using BatchCfg = PassCfg<float, n, CONTIG, MODE, BatchE<n>::E, BATCH_THREADS / (n / BatchE<n>::E), 1, 2>;
+
+template <int n> constexpr size_t batch_smem_n() {
+  return std::max(BatchCfg<n, true, MODE_FWD>::xchg_bytes, BatchCfg<n, false, MODE_FWD>::xchg_bytes);
+}
+
+#define VP_BATCH_LENGTHS(X) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256)
+
+constexpr size_t batch_smem_bytes() {
+  size_t m = 0;
+#define VP_M(N) m = std::max(m, batch_smem_n<N>());
+  VP_BATCH_LENGTHS(VP_M)
+#undef VP_M
+  return m;
+}
+
+bool batch_length_built(int n) {
+  switch (n) {
+#define VP_C(N) \
+  case N: return true;
+    VP_BATCH_LENGTHS(VP_C)
+#undef VP_C
+  }
+  return false;
+}
+
+template <int n>
+__device__ __noinline__ void batch_tile(int kind, const PassArgs<float>& a, long long tile, float2* sm) {
+  switch (kind) {
+    case FWD_CONTIG: process_tile<float, n, true, MODE_FWD, BatchCfg<n, true, MODE_FWD>, true>(a, tile, sm, nullptr, false); break;
+    case FWD_STRIDED: process_tile<float, n, false, MODE_FWD, BatchCfg<n, false, MODE_FWD>, true>(a, tile, sm, nullptr, false); break;
+    case INV_CONTIG: process_tile<float, n, true, MODE_INV, BatchCfg<n, true, MODE_INV>, true>(a, tile, sm, nullptr, false); break;
+    case INV_STRIDED: process_tile<float, n, false, MODE_INV, BatchCfg<n, false, MODE_INV>, true>(a, tile, sm, nullptr, false); break;
+    default: process_tile<float, n, false, MODE_FUSED1, BatchCfg<n, false, MODE_FUSED1>, true>(a, tile, sm, nullptr, false); break;
+  }
+}
+
+constexpr int BATCH_MAX_PASSES = BATCH_MAX * 5;
+
+__global__ void __launch_bounds__(BATCH_THREADS, 2) batch_kernel(const BatchLaunch L) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* sm = reinterpret_cast<float2*>(smem_raw);
+  __shared__ long long s_base[BATCH_MAX_PASSES];  // first item of every pass
+  __shared__ __align__(16) BatchPass s_bp;        // the current tile's pass
+  __shared__ long long s_item;
+  __shared__ int s_pass;
+  for (int i = threadIdx.x; i < L.npasses; i += blockDim.x) s_base[i] = L.passes[i].item_base;
+  __syncthreads();
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const long long item = (long long)atomicAdd(L.next_item, 1ULL);
+      int pi = -1;
+      if (item < L.total_items) {
+        // last pass whose first item <= item
+        int lo = 0, hi = L.npasses - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) / 2;
+          if (s_base[mid] <= item)
+            lo = mid;
+          else
+            hi = mid - 1;
+        }
+        pi = lo;
+      }
+      s_item = item;
+      s_pass = pi;
+    }
+    __syncthreads();
+    const int pi = s_pass;
+    if (pi < 0) break;
+    // the pass descriptor, copied cooperatively
+    {
+      const int words = (int)(sizeof(BatchPass) / 4);
+      const unsigned* src = reinterpret_cast<const unsigned*>(L.passes + pi);
+      unsigned* dst = reinterpret_cast<unsigned*>(&s_bp);
+      for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int dep = s_bp.dep;
+      if (dep >= 0) {
+        const long long need = s_bp.dep_need;
+        const long long t0 = clock64();
+        volatile long long* cnt = L.done + dep;
+        while (*cnt < need) {
+          if (clock64() - t0 > L.timeout_cycles) {
+            atomicOr(L.err, 1);
+            break;
+          }
+          __nanosleep(128);
+        }
+        __threadfence();
+      }
+      if (s_bp.io == 1) s_bp.a.in = L.f[s_bp.density];
+      if (s_bp.io == 2) s_bp.a.out = L.phi[s_bp.density];
+    }
+    __syncthreads();
+    const long long tile = s_item - s_bp.item_base;
+    switch (s_bp.n) {
+#define VP_C(N) \
+  case N: batch_tile<N>(s_bp.kind, s_bp.a, tile, sm); break;
+      VP_BATCH_LENGTHS(VP_C)
+#undef VP_C
+    }
+    __syncthreads();  // every thread's stores of this tile are issued
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(reinterpret_cast<unsigned long long*>(L.done + s_bp.done), 1ULL);
+    }
+  }
+}
+
+// tiles of one pass under the batch configuration
+long long batch_tiles(int n, int kind, const PassArgs<float>& a, int* nblk) {
+  int Tp = n / ((n % 3 == 0) ? 12 : 16);
+  int W = BATCH_THREADS / Tp;
+  if (kind == FWD_CONTIG || kind == INV_CONTIG) {
+    *nblk = 1;
+    return (a.O + W - 1) / W;
+  }
+  *nblk = (a.I + W - 1) / W;
+  return (long long)a.O * (*nblk);
+}
+
+}  // namespace vp
+
+using namespace vp;
+
+namespace {
+
+enum Strategy { S_PERSISTENT = 1, S_PERSISTENT_1 = 2, S_SEQUENTIAL = 3, S_STREAMS = 4 };
+constexpr int kSideStreams = 8;
+
+}  // namespace
+
+struct vp_batch_s {
+  int count = 0;
+  std::vector<vp_plan> plans;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int strategy = 0;  // 0 = not tuned yet
+  int forced = 0;    // strategy set by the caller
+  std::vector<BatchPass> host_passes;
+  BatchPass* passes = nullptr;
+  long long total_items = 0;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  unsigned long long* next_item = nullptr;  // followed by the completion counters and the error word
+  long long* done = nullptr;
+  int* err = nullptr;
+  void* ctrl = nullptr;
+  size_t ctrl_bytes = 0;
+  int grid_full = 0, grid_one = 0;
+  long long timeout_cycles = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t knode = nullptr;
+  int graph_grid = 0;
+  // per-density launches forked over side streams, captured as one graph
+  cudaStream_t side[8] = {};
+  cudaEvent_t fork_ev = nullptr, join_ev[8] = {};
+  cudaGraph_t sgraph = nullptr;
+  cudaGraphExec_t sexec = nullptr;
+  std::vector<const void*> sgraph_f;
+  std::vector<void*> sgraph_phi;
+  std::string last_error;
+  std::string signature;
+};
+
+namespace {
+
+vp_status bfail(vp_batch b, vp_status st, const std::string& m) {
+  if (b) b->last_error = m;
+  return st;
+}
+
+BatchLaunch make_launch(vp_batch b, const void* const* f, void* const* phi) {
+  BatchLaunch L;
+  memset(&L, 0, sizeof(L));
+  L.passes = b->passes;
+  L.npasses = (int)b->host_passes.size();
+  L.total_items = b->total_items;
+  L.next_item = b->next_item;
+  L.done = b->done;
+  L.err = b->err;
+  L.timeout_cycles = b->timeout_cycles;
+  for (int i = 0; i < b->count; ++i) {
+    L.f[i] = f[i];
+    L.phi[i] = phi[i];
+  }
+  return L;
+}
+
+// counters and item cursor reset (the error word is kept until vp_batch_status)
+cudaError_t reset_counters(vp_batch b) {
+  return cudaMemsetAsync(b->ctrl, 0, b->ctrl_bytes - sizeof(int) * 4, b->stream);
+}
+
+cudaError_t launch_persistent(vp_batch b, const BatchLaunch& L, int grid) {
+  cudaError_t e = reset_counters(b);
+  if (e != cudaSuccess) return e;
+  batch_kernel<<<grid, BATCH_THREADS, batch_smem_bytes(), b->stream>>>(L);
+  return cudaGetLastError();
+}
+
+vp_status run_sequential(vp_batch b, const void* const* f, void* const* phi) {
+  for (int i = 0; i < b->count; ++i) {
+    cudaStream_t saved = plan_stream(b->plans[i]);
+    vp_plan_set_stream(b->plans[i], b->stream);
+    vp_status st = vp_apply(b->plans[i], f[i], phi[i], VP_C64);
+    vp_plan_set_stream(b->plans[i], saved);
+    if (st != VP_OK) return bfail(b, st, std::string("density apply: ") + vp_last_error(b->plans[i]));
+  }
+  return VP_OK;
+}
+
+// graph of [reset, batch kernel] for a grid size; kernel params updated per replay
+vp_status graph_launch(vp_batch b, const BatchLaunch& L, int grid) {
+  if (!b->exec || b->graph_grid != grid) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    cudaStream_t cap;
+    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return bfail(b, VP_ERR_CUDA, "stream");
+    cudaStream_t saved = b->stream;
+    b->stream = cap;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = launch_persistent(b, L, grid);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+    b->stream = saved;
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return bfail(b, VP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    b->graph = g;
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(g, nodes.data(), &nn);
+    b->knode = nullptr;
+    for (auto nd : nodes) {
+      cudaGraphNodeType ty;
+      cudaGraphNodeGetType(nd, &ty);
+      if (ty == cudaGraphNodeTypeKernel) b->knode = nd;
+    }
+    if ((e = cudaGraphInstantiate(&b->exec, g, 0)) != cudaSuccess)
+      return bfail(b, VP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    b->graph_grid = grid;
+  }
+  cudaKernelNodeParams kp;
+  memset(&kp, 0, sizeof(kp));
+  BatchLaunch Lc = L;
+  void* args[1] = {&Lc};
+  kp.func = (void*)batch_kernel;
+  kp.gridDim = dim3(grid);
+  kp.blockDim = dim3(BATCH_THREADS);
+  kp.sharedMemBytes = (unsigned)batch_smem_bytes();
+  kp.kernelParams = args;
+  cudaError_t e = cudaGraphExecKernelNodeSetParams(b->exec, b->knode, &kp);
+  if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, b->stream);
+  if (e != cudaSuccess) return bfail(b, VP_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+  return VP_OK;
+}
+
+// Per-density applies spread over side streams (density i on stream i mod 8),
+// captured once per pointer set into a graph and replayed.
+vp_status run_streams(vp_batch b, const void* const* f, void* const* phi) {
+  bool same = b->sexec && (int)b->sgraph_f.size() == b->count;
+  for (int i = 0; same && i < b->count; ++i) same = b->sgraph_f[i] == f[i] && b->sgraph_phi[i] == phi[i];
+  if (!same) {
+    if (b->sexec) cudaGraphExecDestroy(b->sexec);
+    if (b->sgraph) cudaGraphDestroy(b->sgraph);
+    b->sexec = nullptr;
+    b->sgraph = nullptr;
+    if (!b->fork_ev) {
+      cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
+      for (int k = 0; k < kSideStreams; ++k) {
+        cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking);
+        cudaEventCreateWithFlags(&b->join_ev[k], cudaEventDisableTiming);
+      }
+    }
+    // one uncaptured run so every workspace and kernel attribute exists before capture
+    vp_status st = run_sequential(b, f, phi);
+    if (st != VP_OK) return st;
+    cudaStream_t origin;
+    cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking);
+    cudaStreamSynchronize(b->stream);
+    cudaError_t e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = cudaEventRecord(b->fork_ev, origin);
+    for (int k = 0; k < kSideStreams && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->side[k], b->fork_ev, 0);
+    for (int i = 0; i < b->count && e == cudaSuccess && st == VP_OK; ++i) {
+      cudaStream_t saved = plan_stream(b->plans[i]);
+      vp_plan_set_stream(b->plans[i], b->side[i % kSideStreams]);
+      st = vp_apply(b->plans[i], f[i], phi[i], VP_C64);
+      vp_plan_set_stream(b->plans[i], saved);
+    }
+    for (int k = 0; k < kSideStreams && e == cudaSuccess; ++k) {
+      e = cudaEventRecord(b->join_ev[k], b->side[k]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(origin, b->join_ev[k], 0);
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(origin, &g);
+    cudaStreamDestroy(origin);
+    if (e != cudaSuccess || e2 != cudaSuccess || st != VP_OK) {
+      if (g) cudaGraphDestroy(g);
+      return bfail(b, st != VP_OK ? st : VP_ERR_CUDA, "stream graph capture failed");
+    }
+    if ((e = cudaGraphInstantiate(&b->sexec, g, 0)) != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return bfail(b, VP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    b->sgraph = g;
+    b->sgraph_f.assign(f, f + b->count);
+    b->sgraph_phi.assign(phi, phi + b->count);
+  }
+  cudaError_t e = cudaGraphLaunch(b->sexec, b->stream);
+  return e == cudaSuccess ? VP_OK : bfail(b, VP_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+}
+
+vp_status run_strategy(vp_batch b, int s, const void* const* f, void* const* phi) {
+  if (s == S_SEQUENTIAL) return run_sequential(b, f, phi);
+  if (s == S_STREAMS) return run_streams(b, f, phi);
+  const BatchLaunch L = make_launch(b, f, phi);
+  return graph_launch(b, L, s == S_PERSISTENT ? b->grid_full : b->grid_one);
+}
+
+std::string cache_path() {
+  const char* p = getenv("VP_AUTOTUNE_CACHE");
+  if (p && *p) return p;
+  const char* home = getenv("HOME");
+  return std::string(home ? home : "/tmp") + "/.cache/vp_autotune.txt";
+}
+
+int cache_lookup(const std::string& key) {
+  FILE* fh = fopen(cache_path().c_str(), "r");
+  if (!fh) return 0;
+  char line[4096];
+  int found = 0;
+  while (fgets(line, sizeof(line), fh)) {
+    char* sp = strrchr(line, ' ');
+    if (!sp) continue;
+    *sp = 0;
+    if (key == line) found = atoi(sp + 1);
+  }
+  fclose(fh);
+  return found;
+}
+
+void cache_store(const std::string& key, int s) {
+  std::string path = cache_path();
+  std::string dir = path.substr(0, path.find_last_of('/'));
+  std::string cmd_dir = dir;
+  // best effort: create the directory, then append
+  FILE* fh = fopen(path.c_str(), "a");
+  if (!fh) {
+    std::string mk = "mkdir -p '" + cmd_dir + "'";
+    if (system(mk.c_str()) == 0) fh = fopen(path.c_str(), "a");
+  }
+  if (!fh) return;
+  fprintf(fh, "%s %d\n", key.c_str(), s);
+  fclose(fh);
+}
+
+// Times each strategy on the batch (2 warm-ups, 3 timed runs on the batch's
+// stream with CUDA events) and keeps the fastest.
+vp_status autotune(vp_batch b, const void* const* f, void* const* phi) {
+  const int cands[4] = {S_PERSISTENT, S_PERSISTENT_1, S_SEQUENTIAL, S_STREAMS};
+  float best = 1e30f;
+  int bests = S_PERSISTENT;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int c : cands) {
+    vp_status st = VP_OK;
+    for (int r = 0; r < 2 && st == VP_OK; ++r) st = run_strategy(b, c, f, phi);
+    if (st != VP_OK) continue;
+    cudaEventRecord(e0, b->stream);
+    for (int r = 0; r < 3 && st == VP_OK; ++r) st = run_strategy(b, c, f, phi);
+    cudaEventRecord(e1, b->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess || st != VP_OK) continue;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      bests = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->strategy = bests;
+  cache_store(b->signature, bests);
+  return VP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vp_status vp_batch_create(vp_batch* out, int count, const vp_plan* plans) {
+  if (!out) return VP_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (count < 1 || count > BATCH_MAX || !plans) return VP_ERR_INVALID_ARG;
+  static_assert(sizeof(BatchPass) % 4 == 0, "pass descriptor is copied as words");
+  vp_batch b = new vp_batch_s();
+  b->count = count;
+  b->plans.assign(plans, plans + count);
+  cudaGetDevice(&b->device);
+  // pass tables and workspace layout
+  size_t ws_elems = 0;
+  std::vector<size_t> ws_off(count);
+  for (int i = 0; i < count; ++i) {
+    if (!plans[i] || !plan_is_fp32(plans[i])) {
+      delete b;
+      return VP_ERR_INVALID_ARG;
+    }
+    int d, N;
+    vp_plan_info(plans[i], &d, &N, nullptr, nullptr, nullptr);
+    if (!batch_length_built(2 * N)) {
+      delete b;
+      return VP_ERR_UNSUPPORTED;
+    }
+    const size_t U = (size_t)N * N * (d == 3 ? N : 1);
+    ws_off[i] = ws_elems;
+    ws_elems += (d == 3 ? 6 : 2) * U;
+  }
+  cudaError_t e = cudaMalloc(&b->ws, ws_elems * sizeof(float2));
+  if (e != cudaSuccess) {
+    delete b;
+    return VP_ERR_OOM;
+  }
+  b->ws_bytes = ws_elems * sizeof(float2);
+  // pass-major ordering: pass level 0 of every density, then level 1, ...
+  std::vector<std::vector<BatchPass>> per(count);
+  int counter = 0;
+  for (int i = 0; i < count; ++i) {
+    PassArgs<float> args[5];
+    int kinds[5];
+    int np = plan_pass_args_f32(plans[i], reinterpret_cast<float2*>(b->ws) + ws_off[i], args, kinds);
+    int d, N;
+    vp_plan_info(plans[i], &d, &N, nullptr, nullptr, nullptr);
+    for (int p = 0; p < np; ++p) {
+      BatchPass bp;
+      memset(&bp, 0, sizeof(bp));
+      bp.a = args[p];
+      bp.n = 2 * N;
+      bp.kind = kinds[p];
+      bp.density = i;
+      bp.io = (p == 0) ? 1 : (p == np - 1 ? 2 : 0);
+      int nblk = 1;
+      bp.ntiles = batch_tiles(bp.n, bp.kind, bp.a, &nblk);
+      bp.a.nblk_i = nblk;
+      bp.a.async_ok = 0;
+      bp.done = counter++;
+      bp.dep = (p == 0) ? -1 : bp.done - 1;
+      per[i].push_back(bp);
+    }
+  }
+  for (int i = 0; i < count; ++i)
+    for (size_t p = 1; p < per[i].size(); ++p) per[i][p].dep_need = per[i][p].dep_need_orig = per[i][p - 1].ntiles;
+  long long base = 0;
+  for (int level = 0; level < 5; ++level)
+    for (int i = 0; i < count; ++i)
+      if (level < (int)per[i].size()) {
+        BatchPass bp = per[i][level];
+        bp.item_base = base;
+        base += bp.ntiles;
+        b->host_passes.push_back(bp);
+      }
+  b->total_items = base;
+  const size_t npass = b->host_passes.size();
+  e = cudaMalloc(&b->passes, npass * sizeof(BatchPass));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->passes, b->host_passes.data(), npass * sizeof(BatchPass), cudaMemcpyHostToDevice);
+  b->ctrl_bytes = sizeof(unsigned long long) + npass * sizeof(long long) + sizeof(int) * 4;
+  if (e == cudaSuccess) e = cudaMalloc(&b->ctrl, b->ctrl_bytes);
+  if (e == cudaSuccess) e = cudaMemset(b->ctrl, 0, b->ctrl_bytes);
+  if (e != cudaSuccess) {
+    vp_batch_destroy(b);
+    return VP_ERR_CUDA;
+  }
+  b->next_item = reinterpret_cast<unsigned long long*>(b->ctrl);
+  b->done = reinterpret_cast<long long*>(b->next_item + 1);
+  b->err = reinterpret_cast<int*>(b->done + npass);
+  // persistent grids: all resident CTAs, or one per SM
+  int sms = 0, per_sm = 0, clk = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+  cudaDeviceGetAttribute(&clk, cudaDevAttrClockRate, b->device);  // kHz
+  cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem_bytes());
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, BATCH_THREADS, batch_smem_bytes());
+  b->grid_full = sms * std::max(1, per_sm);
+  b->grid_one = sms;
+  b->timeout_cycles = (long long)std::max(clk, 1000000) * 1000LL * 2;  // about 2 s
+  // autotuner key: device, driver and the batch's (d, N) multiset
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, b->device);
+  int drv = 0;
+  cudaDriverGetVersion(&drv);
+  std::vector<std::string> parts;
+  for (int i = 0; i < count; ++i) {
+    int d, N;
+    vp_plan_info(plans[i], &d, &N, nullptr, nullptr, nullptr);
+    parts.push_back(std::to_string(d) + "x" + std::to_string(N));
+  }
+  std::sort(parts.begin(), parts.end());
+  std::string sig = std::string(prop.name) + "|drv" + std::to_string(drv) + "|";
+  for (auto& s : parts) sig += s + ",";
+  for (auto& c : sig)
+    if (c == ' ') c = '_';
+  b->signature = sig;
+  b->strategy = cache_lookup(sig);
+  *out = b;
+  return VP_OK;
+}
+
+vp_status vp_batch_set_stream(vp_batch b, void* stream) {
+  if (!b) return VP_ERR_INVALID_ARG;
+  b->stream = reinterpret_cast<cudaStream_t>(stream);
+  return VP_OK;
+}
+
+vp_status vp_batch_set_strategy(vp_batch b, int strategy) {
+  if (!b || strategy < 0 || strategy > 4) return VP_ERR_INVALID_ARG;
+  b->forced = strategy;
+  return VP_OK;
+}
+
+vp_status vp_batch_get_strategy(vp_batch b, int* strategy) {
+  if (!b || !strategy) return VP_ERR_INVALID_ARG;
+  *strategy = b->forced ? b->forced : b->strategy;
+  return VP_OK;
+}
+
+vp_status vp_batch_set_timeout(vp_batch b, double seconds) {
+  if (!b || !(seconds > 0)) return VP_ERR_INVALID_ARG;
+  int clk = 0;
+  cudaDeviceGetAttribute(&clk, cudaDevAttrClockRate, b->device);
+  b->timeout_cycles = (long long)(seconds * std::max(clk, 1000000) * 1000.0);
+  return VP_OK;
+}
+
+vp_status vp_batch_withhold(vp_batch b, int density, int pass) {
+  if (!b) return VP_ERR_INVALID_ARG;
+  if (pass <= 0) {  // restore every dependency
+    for (size_t k = 0; k < b->host_passes.size(); ++k) {
+      BatchPass& bp = b->host_passes[k];
+      if (bp.dep >= 0 && bp.dep_need != bp.dep_need_orig) {
+        bp.dep_need = bp.dep_need_orig;
+        if (cudaMemcpy(b->passes + k, &bp, sizeof(BatchPass), cudaMemcpyHostToDevice) != cudaSuccess)
+          return VP_ERR_CUDA;
+      }
+    }
+    return VP_OK;
+  }
+  if (density < 0 || density >= b->count) return VP_ERR_INVALID_ARG;
+  int level = 0;
+  for (size_t k = 0; k < b->host_passes.size(); ++k) {
+    BatchPass& bp = b->host_passes[k];
+    if (bp.density != density) continue;
+    if (level == pass) {
+      // this pass now waits for one tile more than its predecessor has
+      bp.dep_need = bp.dep_need_orig + 1;
+      return cudaMemcpy(b->passes + k, &bp, sizeof(BatchPass), cudaMemcpyHostToDevice) == cudaSuccess ? VP_OK
+                                                                                                   : VP_ERR_CUDA;
+    }
+    ++level;
+  }
+  return VP_ERR_INVALID_ARG;
+}
+
+vp_status vp_batch_apply(vp_batch b, const void* const* f, void* const* phi) {
+  if (!b || !f || !phi) return VP_ERR_INVALID_ARG;
+  for (int i = 0; i < b->count; ++i)
+    if (!f[i] || !phi[i]) return bfail(b, VP_ERR_INVALID_ARG, "NULL density pointer");
+  if (cudaSetDevice(b->device) != cudaSuccess) return VP_ERR_CUDA;
+  int s = b->forced;
+  if (!s) {
+    if (!b->strategy) {
+      vp_status st = autotune(b, f, phi);
+      if (st != VP_OK) return st;
+    }
+    s = b->strategy;
+  }
+  return run_strategy(b, s, f, phi);
+}
+
+vp_status vp_batch_status(vp_batch b) {
+  if (!b) return VP_ERR_INVALID_ARG;
+  if (cudaSetDevice(b->device) != cudaSuccess) return VP_ERR_CUDA;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(b, VP_ERR_CUDA, "stream sync");
+  int err = 0;
+  if (cudaMemcpy(&err, b->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return VP_ERR_CUDA;
+  if (err) {
+    cudaMemset(b->err, 0, sizeof(int));
+    return bfail(b, VP_ERR_TIMEOUT, "a batch tile gave up waiting for the pass it depends on");
+  }
+  return VP_OK;
+}
+
+vp_status vp_batch_info(vp_batch b, long long* items, int* passes, size_t* device_bytes) {
+  if (!b) return VP_ERR_INVALID_ARG;
+  if (items) *items = b->total_items;
+  if (passes) *passes = (int)b->host_passes.size();
+  if (device_bytes) *device_bytes = b->ws_bytes + b->ctrl_bytes + b->host_passes.size() * sizeof(BatchPass);
+  return VP_OK;
+}
+
+const char* vp_batch_last_error(vp_batch b) { return b ? b->last_error.c_str() : ""; }
+
+vp_status vp_batch_destroy(vp_batch b) {
+  if (!b) return VP_OK;
+  cudaSetDevice(b->device);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->sexec) cudaGraphExecDestroy(b->sexec);
+  if (b->sgraph) cudaGraphDestroy(b->sgraph);
+  for (int k = 0; k < kSideStreams; ++k) {
+    if (b->side[k]) {
+      cudaStreamSynchronize(b->side[k]);
+      cudaStreamDestroy(b->side[k]);
+    }
+    if (b->join_ev[k]) cudaEventDestroy(b->join_ev[k]);
+  }
+  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+  cudaFree(b->passes);
+  cudaFree(b->ctrl);
+  cudaFree(b->ws);
+  delete b;
+  return VP_OK;
+}
+
+}  // extern "C"

@@ -315,7 +315,12 @@ template <typename Real> struct PassArgs {
   FieldDesc fields[4];
 };
 
-template <typename Real, typename C> __device__ __forceinline__ C ld_in(const PassArgs<Real>& a, long long idx) {
+template <typename Real, typename C, bool COHERENT>
+__device__ __forceinline__ C ld_in(const PassArgs<Real>& a, long long idx) {
+  if (COHERENT) {
+    if (a.in_real) return C{__ldcg(reinterpret_cast<const Real*>(a.in) + idx), (Real)0};
+    return __ldcg(reinterpret_cast<const C*>(a.in) + idx);
+  }
   if (a.in_real) return C{__ldg(reinterpret_cast<const Real*>(a.in) + idx), (Real)0};
   return __ldg(reinterpret_cast<const C*>(a.in) + idx);
 }
@@ -477,34 +482,197 @@ __device__ __forceinline__ void stage_tile(const PassArgs<Real>& a, long long ti
 // CONTIG: pencils are contiguous rows; otherwise pencils are strided and the
 // W pencils of a tile are W consecutive inner indices (coalesced).
 // ---------------------------------------------------------------------------
-template <typename Real, int n, bool CONTIG, int MODE, typename Cfg = PassCfg<Real, n, CONTIG, MODE>>
-__global__ void __launch_bounds__(Cfg::threads, Cfg::min_blocks) pencil_pass(const PassArgs<Real> a) {
+// One tile of a pass: first-stage loads (from the staging slot when `staged`,
+// else from global memory), the stages, the multiply of a fused pass and the
+// stores.  COHERENT reads global input with ld.global.cg (L2) instead of the
+// read-only path, for data written earlier by the same kernel.
+template <typename Real, int n, bool CONTIG, int MODE, typename Cfg, bool COHERENT>
+__device__ __forceinline__ void process_tile(const PassArgs<Real>& a, long long tile, typename CxT<Real>::T* sm,
+                                             const unsigned char* slot, bool staged) {
   using C = typename CxT<Real>::T;
   constexpr int E = Cfg::E;
   constexpr int Tp = Cfg::Tp;
   constexpr int W = Cfg::W;
   constexpr int NS = Cfg::nstages;
   constexpr int NIN = Cfg::NIN;
-  constexpr int NSTG = Cfg::NSTG;
   static_assert(NS > 0, "unsupported FFT length");
   constexpr bool FWD_FIRST = (MODE != MODE_INV);
   constexpr int R_first = stage_radix(n, E, !FWD_FIRST, 0);
   constexpr int R_lastinv = stage_radix(n, E, true, NS - 1);
   static_assert(!FWD_FIRST || R_first % 2 == 0, "pruned first stage needs an even radix");
   static_assert(MODE == MODE_FWD || R_lastinv % 2 == 0, "cropped last stage needs an even radix");
+  const int tid = threadIdx.x;
+  const int w = CONTIG ? tid / Tp : tid % W;
+  const int t = CONTIG ? tid % Tp : tid / W;
+  const C* tw = a.tw;
+
+  // tile -> pencil coordinates
+  long long in_base, out_base;
+  bool valid;
+  int inner = 0;
+  void* outp = a.out;
+  if (CONTIG) {
+    const long long row = tile * W + w;
+    valid = row < a.O;
+    in_base = row * a.in_pitch_o;
+    out_base = row * a.out_pitch_o;
+    if (a.nout > 1) {
+      const int f = valid ? (int)(row / a.rows_per_field) : 0;
+      outp = a.outs[f];
+      out_base = (row - f * a.rows_per_field) * a.out_pitch_o;
+    }
+  } else {
+    const long long o = tile / a.nblk_i;
+    inner = (int)(tile % a.nblk_i) * W + w;
+    valid = inner < a.I;
+    in_base = o * a.in_pitch_o + inner;
+    out_base = o * a.out_pitch_o + inner;
+  }
+
+  C v[E];
+  // ---- first stage loads: staged shared memory (or global memory) ----
+  {
+    constexpr int R = R_first;
+#pragma unroll
+    for (int q = 0; q < E / R; ++q) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int pos = stage_in_pos<n, E, !FWD_FIRST, 0>(t + q * Tp, r);
+        C x = {(Real)0, (Real)0};
+        if (valid && (!FWD_FIRST || r < R / 2)) {
+          if (staged) {
+            const int e = CONTIG ? w * NIN + pos : pos * W + w;
+            if (a.in_real)
+              x = C{reinterpret_cast<const Real*>(slot)[e], (Real)0};
+            else
+              x = reinterpret_cast<const C*>(slot)[e];
+          } else {
+            x = ld_in<Real, C, COHERENT>(a, in_base + (long long)pos * a.in_pitch_pos);
+          }
+        }
+        v[q * R + r] = x;
+      }
+    }
+  }
+
+  if constexpr (MODE == MODE_FWD) {
+    StageRun<Real, C, n, E, W, CONTIG, false, 0, NS>::run(v, sm, w, t, tw);
+    constexpr int R = stage_radix(n, E, false, NS - 1);
+    if (valid) {
+#pragma unroll
+      for (int q = 0; q < E / R; ++q)
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int pos = stage_out_pos<n, E, false, NS - 1>(t + q * Tp, r);
+          st_out<Real, C>(a, outp, out_base + (long long)pos * a.out_pitch_pos, v[q * R + r]);
+        }
+    }
+  } else if constexpr (MODE == MODE_INV) {
+    StageRun<Real, C, n, E, W, CONTIG, true, 0, NS>::run(v, sm, w, t, tw);
+    constexpr int R = R_lastinv;
+    if (valid) {
+#pragma unroll
+      for (int q = 0; q < E / R; ++q)
+#pragma unroll
+        for (int r = 0; r < R / 2; ++r) {
+          const int pos = stage_out_pos<n, E, true, NS - 1>(t + q * Tp, r);
+          st_out<Real, C>(a, outp, out_base + (long long)pos * a.out_pitch_pos, v[q * R + r]);
+        }
+    }
+  } else {
+    // frequencies of the other axes (fused axis = axis 0, the slowest)
+    const int Nh = a.Nh;
+    const int np1 = Nh + 1;
+    int m1 = 0, m2 = 0;
+    if (a.d == 3) {
+      m1 = inner / n;
+      m2 = inner % n;
+    } else {
+      m1 = inner;
+    }
+    const long long oct_rest = (a.d == 3) ? (long long)fold_freq(m1, n) * np1 + fold_freq(m2, n) : fold_freq(m1, n);
+    const long long oct_pitch0 = (a.d == 3) ? (long long)np1 * np1 : np1;
+    constexpr int RL = stage_radix(n, E, false, NS - 1);  // == first inverse radix
+    // multiplier of field 0, issued before the forward transform to hide its latency
+    C g[E];
+    {
+      const C* mult = reinterpret_cast<const C*>(a.fields[0].mult);
+#pragma unroll
+      for (int q = 0; q < E / RL; ++q)
+#pragma unroll
+        for (int r = 0; r < RL; ++r) {
+          const int m0 = stage_out_pos<n, E, false, NS - 1>(t + q * Tp, r);
+          g[q * RL + r] = valid ? __ldg(mult + fold_freq(m0, n) * oct_pitch0 + oct_rest) : C{(Real)0, (Real)0};
+        }
+    }
+    StageRun<Real, C, n, E, W, CONTIG, false, 0, NS>::run(v, sm, w, t, tw);
+    const int nf = (MODE == MODE_FUSED1) ? 1 : a.nfields;
+    for (int fi = 0; fi < nf; ++fi) {
+      const FieldDesc fd = a.fields[fi];
+      if (fi > 0) {
+        const C* mult = reinterpret_cast<const C*>(fd.mult);
+#pragma unroll
+        for (int q = 0; q < E / RL; ++q)
+#pragma unroll
+          for (int r = 0; r < RL; ++r) {
+            const int m0 = stage_out_pos<n, E, false, NS - 1>(t + q * Tp, r);
+            g[q * RL + r] = valid ? __ldg(mult + fold_freq(m0, n) * oct_pitch0 + oct_rest) : C{(Real)0, (Real)0};
+          }
+      }
+      C y[(MODE == MODE_FUSED1) ? 1 : E];
+      C* yy = (MODE == MODE_FUSED1) ? v : y;
+#pragma unroll
+      for (int q = 0; q < E / RL; ++q)
+#pragma unroll
+        for (int r = 0; r < RL; ++r) {
+          const int m0 = stage_out_pos<n, E, false, NS - 1>(t + q * Tp, r);
+          C gg = g[q * RL + r];
+          if (fd.odd_axis >= 0) {
+            const int mj = fd.odd_axis == 0 ? m0 : (fd.odd_axis == 1 ? m1 : m2);
+            if (mj > Nh) gg = C{-gg.x, -gg.y};
+          }
+          if (fd.spectral_axis >= 0) {
+            const int mj = fd.spectral_axis == 0 ? m0 : (fd.spectral_axis == 1 ? m1 : m2);
+            const int ms = mj < Nh ? mj : (mj == Nh ? 0 : mj - n);
+            const Real f = (Real)3.14159265358979323846 * (Real)ms;
+            gg = C{-gg.y * f, gg.x * f};  // i pi m_j * g
+          }
+          yy[q * RL + r] = cmul(v[q * RL + r], gg);
+        }
+      if constexpr (MODE == MODE_FUSED1) {
+        StageRun<Real, C, n, E, W, CONTIG, true, 0, NS>::run(v, sm, w, t, tw);
+      } else {
+        StageRun<Real, C, n, E, W, CONTIG, true, 0, NS>::run(y, sm, w, t, tw);
+      }
+      constexpr int R = R_lastinv;
+      if (valid) {
+        const long long ob = out_base + (long long)fi * a.out_field_stride;
+#pragma unroll
+        for (int q = 0; q < E / R; ++q)
+#pragma unroll
+          for (int r = 0; r < R / 2; ++r) {
+            const int pos = stage_out_pos<n, E, true, NS - 1>(t + q * Tp, r);
+            st_out<Real, C>(a, outp, ob + (long long)pos * a.out_pitch_pos, yy[q * R + r]);
+          }
+      }
+    }
+  }
+}
+
+template <typename Real, int n, bool CONTIG, int MODE, typename Cfg = PassCfg<Real, n, CONTIG, MODE>>
+__global__ void __launch_bounds__(Cfg::threads, Cfg::min_blocks) pencil_pass(const PassArgs<Real> a) {
+  using C = typename CxT<Real>::T;
+  constexpr int W = Cfg::W;
+  constexpr int NSTG = Cfg::NSTG;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
   unsigned char* stg = smem_raw + Cfg::xchg_bytes;
 
-  const int tid = threadIdx.x;
-  const int w = CONTIG ? tid / Tp : tid % W;
-  const int t = CONTIG ? tid % Tp : tid / W;
   const long long ntiles = CONTIG ? (a.O + W - 1) / W : (long long)a.O * a.nblk_i;
   // strided rows narrower than one 16-byte chunk are read directly
   constexpr bool STAGEABLE = CONTIG || ((W * 2 * sizeof(Real)) % 16 == 0);
   const bool staged = STAGEABLE && a.async_ok != 0;
-  const C* tw = a.tw;
 
   // prologue: stage the first NSTG-1 tiles of this CTA
 #pragma unroll
@@ -526,157 +694,7 @@ __global__ void __launch_bounds__(Cfg::threads, Cfg::min_blocks) pencil_pass(con
     __syncthreads();
     const unsigned char* slot = stg + (it % NSTG) * Cfg::slot_bytes;
 
-    // tile -> pencil coordinates
-    long long in_base, out_base;
-    bool valid;
-    int inner = 0;
-    void* outp = a.out;
-    if (CONTIG) {
-      const long long row = tile * W + w;
-      valid = row < a.O;
-      in_base = row * a.in_pitch_o;
-      out_base = row * a.out_pitch_o;
-      if (a.nout > 1) {
-        const int f = valid ? (int)(row / a.rows_per_field) : 0;
-        outp = a.outs[f];
-        out_base = (row - f * a.rows_per_field) * a.out_pitch_o;
-      }
-    } else {
-      const long long o = tile / a.nblk_i;
-      inner = (int)(tile % a.nblk_i) * W + w;
-      valid = inner < a.I;
-      in_base = o * a.in_pitch_o + inner;
-      out_base = o * a.out_pitch_o + inner;
-    }
-
-    C v[E];
-    // ---- first stage loads: staged shared memory (or global memory) ----
-    {
-      constexpr int R = R_first;
-#pragma unroll
-      for (int q = 0; q < E / R; ++q) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const int pos = stage_in_pos<n, E, !FWD_FIRST, 0>(t + q * Tp, r);
-          C x = {(Real)0, (Real)0};
-          if (valid && (!FWD_FIRST || r < R / 2)) {
-            if (staged) {
-              const int e = CONTIG ? w * NIN + pos : pos * W + w;
-              if (a.in_real)
-                x = C{reinterpret_cast<const Real*>(slot)[e], (Real)0};
-              else
-                x = reinterpret_cast<const C*>(slot)[e];
-            } else {
-              x = ld_in<Real, C>(a, in_base + (long long)pos * a.in_pitch_pos);
-            }
-          }
-          v[q * R + r] = x;
-        }
-      }
-    }
-
-    if constexpr (MODE == MODE_FWD) {
-      StageRun<Real, C, n, E, W, CONTIG, false, 0, NS>::run(v, sm, w, t, tw);
-      constexpr int R = stage_radix(n, E, false, NS - 1);
-      if (valid) {
-#pragma unroll
-        for (int q = 0; q < E / R; ++q)
-#pragma unroll
-          for (int r = 0; r < R; ++r) {
-            const int pos = stage_out_pos<n, E, false, NS - 1>(t + q * Tp, r);
-            st_out<Real, C>(a, outp, out_base + (long long)pos * a.out_pitch_pos, v[q * R + r]);
-          }
-      }
-    } else if constexpr (MODE == MODE_INV) {
-      StageRun<Real, C, n, E, W, CONTIG, true, 0, NS>::run(v, sm, w, t, tw);
-      constexpr int R = R_lastinv;
-      if (valid) {
-#pragma unroll
-        for (int q = 0; q < E / R; ++q)
-#pragma unroll
-          for (int r = 0; r < R / 2; ++r) {
-            const int pos = stage_out_pos<n, E, true, NS - 1>(t + q * Tp, r);
-            st_out<Real, C>(a, outp, out_base + (long long)pos * a.out_pitch_pos, v[q * R + r]);
-          }
-      }
-    } else {
-      // frequencies of the other axes (fused axis = axis 0, the slowest)
-      const int Nh = a.Nh;
-      const int np1 = Nh + 1;
-      int m1 = 0, m2 = 0;
-      if (a.d == 3) {
-        m1 = inner / n;
-        m2 = inner % n;
-      } else {
-        m1 = inner;
-      }
-      const long long oct_rest = (a.d == 3) ? (long long)fold_freq(m1, n) * np1 + fold_freq(m2, n) : fold_freq(m1, n);
-      const long long oct_pitch0 = (a.d == 3) ? (long long)np1 * np1 : np1;
-      constexpr int RL = stage_radix(n, E, false, NS - 1);  // == first inverse radix
-      // multiplier of field 0, issued before the forward transform to hide its latency
-      C g[E];
-      {
-        const C* mult = reinterpret_cast<const C*>(a.fields[0].mult);
-#pragma unroll
-        for (int q = 0; q < E / RL; ++q)
-#pragma unroll
-          for (int r = 0; r < RL; ++r) {
-            const int m0 = stage_out_pos<n, E, false, NS - 1>(t + q * Tp, r);
-            g[q * RL + r] = valid ? __ldg(mult + fold_freq(m0, n) * oct_pitch0 + oct_rest) : C{(Real)0, (Real)0};
-          }
-      }
-      StageRun<Real, C, n, E, W, CONTIG, false, 0, NS>::run(v, sm, w, t, tw);
-      const int nf = (MODE == MODE_FUSED1) ? 1 : a.nfields;
-      for (int fi = 0; fi < nf; ++fi) {
-        const FieldDesc fd = a.fields[fi];
-        if (fi > 0) {
-          const C* mult = reinterpret_cast<const C*>(fd.mult);
-#pragma unroll
-          for (int q = 0; q < E / RL; ++q)
-#pragma unroll
-            for (int r = 0; r < RL; ++r) {
-              const int m0 = stage_out_pos<n, E, false, NS - 1>(t + q * Tp, r);
-              g[q * RL + r] = valid ? __ldg(mult + fold_freq(m0, n) * oct_pitch0 + oct_rest) : C{(Real)0, (Real)0};
-            }
-        }
-        C y[(MODE == MODE_FUSED1) ? 1 : E];
-        C* yy = (MODE == MODE_FUSED1) ? v : y;
-#pragma unroll
-        for (int q = 0; q < E / RL; ++q)
-#pragma unroll
-          for (int r = 0; r < RL; ++r) {
-            const int m0 = stage_out_pos<n, E, false, NS - 1>(t + q * Tp, r);
-            C gg = g[q * RL + r];
-            if (fd.odd_axis >= 0) {
-              const int mj = fd.odd_axis == 0 ? m0 : (fd.odd_axis == 1 ? m1 : m2);
-              if (mj > Nh) gg = C{-gg.x, -gg.y};
-            }
-            if (fd.spectral_axis >= 0) {
-              const int mj = fd.spectral_axis == 0 ? m0 : (fd.spectral_axis == 1 ? m1 : m2);
-              const int ms = mj < Nh ? mj : (mj == Nh ? 0 : mj - n);
-              const Real f = (Real)3.14159265358979323846 * (Real)ms;
-              gg = C{-gg.y * f, gg.x * f};  // i pi m_j * g
-            }
-            yy[q * RL + r] = cmul(v[q * RL + r], gg);
-          }
-        if constexpr (MODE == MODE_FUSED1) {
-          StageRun<Real, C, n, E, W, CONTIG, true, 0, NS>::run(v, sm, w, t, tw);
-        } else {
-          StageRun<Real, C, n, E, W, CONTIG, true, 0, NS>::run(y, sm, w, t, tw);
-        }
-        constexpr int R = R_lastinv;
-        if (valid) {
-          const long long ob = out_base + (long long)fi * a.out_field_stride;
-#pragma unroll
-          for (int q = 0; q < E / R; ++q)
-#pragma unroll
-            for (int r = 0; r < R / 2; ++r) {
-              const int pos = stage_out_pos<n, E, true, NS - 1>(t + q * Tp, r);
-              st_out<Real, C>(a, outp, ob + (long long)pos * a.out_pitch_pos, yy[q * R + r]);
-            }
-        }
-      }
-    }
+    process_tile<Real, n, CONTIG, MODE, Cfg, false>(a, tile, sm, slot, staged);
     __syncthreads();  // this tile's slot and the exchange buffer are free again
   }
   cp_async_wait<0>();

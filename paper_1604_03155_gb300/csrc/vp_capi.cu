@@ -311,39 +311,51 @@ vp_status run_apply(vp_plan p, const void* f, void* const* outs, const FieldDesc
   return run_apply_ws<Real>(p, p->ws, f, outs, fields, F, real_io);
 }
 
-// The pass sequence on a given workspace of workspace_bytes(d, N, F, ...) bytes;
-// allocates nothing.
+// The pass sequence of one apply on a given workspace of
+// workspace_bytes(d, N, F, ...) bytes: (pass id, kind, arguments) per launch.
 template <typename Real>
-vp_status run_apply_ws(vp_plan p, void* ws, const void* f, void* const* outs, const FieldDesc* fields, int F,
-                       bool real_io) {
+struct PassLaunch {
+  int pass;
+  PassKind kind;
+  PassArgs<Real> a;
+};
+
+template <typename Real>
+int build_pass_list(vp_plan p, void* ws, const void* f, void* const* outs, const FieldDesc* fields, int F,
+                    bool real_io, PassLaunch<Real>* list) {
   using C = typename CxT<Real>::T;
   const int N = p->N, n = p->n2, d = p->d;
   const long long U = (long long)N * N * (d == 3 ? N : 1);
-  C* wsA = reinterpret_cast<C*>(ws);  // rows: F x 2U
-  C* wsB = wsA + (long long)F * 2 * U;   // 3D spectra: F x 4U
+  C* wsA = reinterpret_cast<C*>(ws);    // rows: F x 2U
+  C* wsB = wsA + (long long)F * 2 * U;  // 3D spectra: F x 4U
   const C* tw = sizeof(Real) == 4 ? reinterpret_cast<const C*>(p->tw32) : reinterpret_cast<const C*>(p->tw64);
-
+  int np = 0;
   PassArgs<Real> a;
   memset(&a, 0, sizeof(a));
   a.tw = tw;
   a.d = d;
   a.Nh = N;
-  cudaError_t e;
+  auto push = [&](int pass, PassKind kind, bool contig, int nin) {
+    set_async(a, contig, nin);
+    list[np].pass = pass;
+    list[np].kind = kind;
+    list[np].a = a;
+    ++np;
+  };
+  // first pass: rows along the last axis, N -> 2N
+  a.in = f;
+  a.out = wsA;
+  a.O = (d == 3) ? N * N : N;
+  a.I = 1;
+  a.in_pitch_o = N;
+  a.in_pitch_pos = 1;
+  a.out_pitch_o = n;
+  a.out_pitch_pos = 1;
+  a.in_real = real_io;
+  push(P_FWD_ROWS, FWD_CONTIG, true, N);
+  a.in_real = 0;
   if (d == 3) {
-    // P1: rows along axis 2, N -> 2N
-    a.in = f;
-    a.out = wsA;
-    a.O = N * N;
-    a.I = 1;
-    a.in_pitch_o = N;
-    a.in_pitch_pos = 1;
-    a.out_pitch_o = n;
-    a.out_pitch_pos = 1;
-    a.in_real = real_io;
-    a.out_real = 0;
-    set_async(a, true, N);
-    if ((e = launch_pass<Real>(p, P_FWD_ROWS, FWD_CONTIG, a)) != cudaSuccess) return cuda_fail(p, e, "pass fwd_rows");
-    // P2: axis 1, N -> 2N, slabs i0
+    // axis 1, N -> 2N, slabs i0
     a.in = wsA;
     a.out = wsB;
     a.O = N;
@@ -352,10 +364,8 @@ vp_status run_apply_ws(vp_plan p, void* ws, const void* f, void* const* outs, co
     a.in_pitch_pos = n;
     a.out_pitch_o = (long long)n * n;
     a.out_pitch_pos = n;
-    a.in_real = 0;
-    set_async(a, false, N);
-    if ((e = launch_pass<Real>(p, P_FWD_AX1, FWD_STRIDED, a)) != cudaSuccess) return cuda_fail(p, e, "pass fwd_axis1");
-    // P3: axis 0 fused, N -> N per field (field 0 in place)
+    push(P_FWD_AX1, FWD_STRIDED, false, N);
+    // axis 0 fused, N -> N per field (field 0 in place)
     a.in = wsB;
     a.out = wsB;
     a.O = 1;
@@ -367,10 +377,9 @@ vp_status run_apply_ws(vp_plan p, void* ws, const void* f, void* const* outs, co
     a.out_field_stride = 4 * U;
     a.nfields = F;
     for (int i = 0; i < F; ++i) a.fields[i] = fields[i];
-    set_async(a, false, N);
-    if ((e = launch_pass<Real>(p, P_FUSED, FUSED_STRIDED, a)) != cudaSuccess) return cuda_fail(p, e, "pass fused_axis0");
+    push(P_FUSED, FUSED_STRIDED, false, N);
     a.nfields = 0;
-    // P4: axis 1 inverse, 2N -> N, all fields as slabs
+    // axis 1 inverse, 2N -> N, all fields as slabs
     a.in = wsB;
     a.out = wsA;
     a.O = F * N;
@@ -379,37 +388,9 @@ vp_status run_apply_ws(vp_plan p, void* ws, const void* f, void* const* outs, co
     a.in_pitch_pos = n;
     a.out_pitch_o = (long long)N * n;
     a.out_pitch_pos = n;
-    set_async(a, false, n);
-    if ((e = launch_pass<Real>(p, P_INV_AX1, INV_STRIDED, a)) != cudaSuccess) return cuda_fail(p, e, "pass inv_axis1");
-    // P5: rows inverse, 2N -> N, all fields in one launch
-    a.in = wsA;
-    a.out = outs[0];
-    a.O = F * N * N;
-    a.I = 1;
-    a.in_pitch_o = n;
-    a.in_pitch_pos = 1;
-    a.out_pitch_o = N;
-    a.out_pitch_pos = 1;
-    a.out_real = real_io;
-    a.nout = F;
-    a.rows_per_field = (long long)N * N;
-    for (int i = 0; i < F; ++i) a.outs[i] = outs[i];
-    set_async(a, true, n);
-    if ((e = launch_pass<Real>(p, P_INV_ROWS, INV_CONTIG, a)) != cudaSuccess) return cuda_fail(p, e, "pass inv_rows");
+    push(P_INV_AX1, INV_STRIDED, false, n);
   } else {
-    // P1: rows along axis 1, N -> 2N
-    a.in = f;
-    a.out = wsA;
-    a.O = N;
-    a.I = 1;
-    a.in_pitch_o = N;
-    a.in_pitch_pos = 1;
-    a.out_pitch_o = n;
-    a.out_pitch_pos = 1;
-    a.in_real = real_io;
-    set_async(a, true, N);
-    if ((e = launch_pass<Real>(p, P_FWD_ROWS, FWD_CONTIG, a)) != cudaSuccess) return cuda_fail(p, e, "pass fwd_rows");
-    // P2: axis 0 fused
+    // axis 0 fused (field 0 in place)
     a.in = wsA;
     a.out = wsA;
     a.O = 1;
@@ -419,27 +400,38 @@ vp_status run_apply_ws(vp_plan p, void* ws, const void* f, void* const* outs, co
     a.out_pitch_o = 0;
     a.out_pitch_pos = n;
     a.out_field_stride = 2 * U;
-    a.in_real = 0;
     a.nfields = F;
     for (int i = 0; i < F; ++i) a.fields[i] = fields[i];
-    set_async(a, false, N);
-    if ((e = launch_pass<Real>(p, P_FUSED, FUSED_STRIDED, a)) != cudaSuccess) return cuda_fail(p, e, "pass fused_axis0");
+    push(P_FUSED, FUSED_STRIDED, false, N);
     a.nfields = 0;
-    // P3: rows inverse, 2N -> N, all fields in one launch
-    a.in = wsA;
-    a.out = outs[0];
-    a.O = F * N;
-    a.I = 1;
-    a.in_pitch_o = n;
-    a.in_pitch_pos = 1;
-    a.out_pitch_o = N;
-    a.out_pitch_pos = 1;
-    a.out_real = real_io;
-    a.nout = F;
-    a.rows_per_field = N;
-    for (int i = 0; i < F; ++i) a.outs[i] = outs[i];
-    set_async(a, true, n);
-    if ((e = launch_pass<Real>(p, P_INV_ROWS, INV_CONTIG, a)) != cudaSuccess) return cuda_fail(p, e, "pass inv_rows");
+  }
+  // rows inverse, 2N -> N, all fields in one launch
+  a.in = wsA;
+  a.out = outs[0];
+  a.O = F * ((d == 3) ? N * N : N);
+  a.I = 1;
+  a.in_pitch_o = n;
+  a.in_pitch_pos = 1;
+  a.out_pitch_o = N;
+  a.out_pitch_pos = 1;
+  a.out_real = real_io;
+  a.nout = F;
+  a.rows_per_field = (d == 3) ? (long long)N * N : N;
+  for (int i = 0; i < F; ++i) a.outs[i] = outs[i];
+  push(P_INV_ROWS, INV_CONTIG, true, n);
+  return np;
+}
+
+template <typename Real>
+vp_status run_apply_ws(vp_plan p, void* ws, const void* f, void* const* outs, const FieldDesc* fields, int F,
+                       bool real_io) {
+  PassLaunch<Real> list[6];
+  const int np = build_pass_list<Real>(p, ws, f, outs, fields, F, real_io, list);
+  static const char* what[NPASS] = {"pass fwd_rows", "pass fwd_axis1", "pass fused_axis0", "pass inv_axis1",
+                                    "pass inv_rows"};
+  for (int i = 0; i < np; ++i) {
+    cudaError_t e = launch_pass<Real>(p, list[i].pass, list[i].kind, list[i].a);
+    if (e != cudaSuccess) return cuda_fail(p, e, what[list[i].pass]);
   }
   return VP_OK;
 }
@@ -544,6 +536,22 @@ vp_status apply_common(vp_plan p, const void* f, void* phi, void* grad, vp_dtype
 namespace vp {
 
 int plan_device(vp_plan p) { return p ? p->device : -1; }
+
+cudaStream_t plan_stream(vp_plan p) { return p ? p->stream : nullptr; }
+
+int plan_is_fp32(vp_plan p) { return p && p->prec == VP_FP32; }
+
+int plan_pass_args_f32(vp_plan p, float2* ws, PassArgs<float>* args, int* kinds) {
+  FieldDesc field{(const void*)p->G32, -1, -1};
+  void* outs[1] = {nullptr};
+  PassLaunch<float> list[6];
+  const int np = build_pass_list<float>(p, ws, nullptr, outs, &field, 1, false, list);
+  for (int i = 0; i < np; ++i) {
+    args[i] = list[i].a;
+    kinds[i] = (int)list[i].kind;
+  }
+  return np;
+}
 
 size_t plan_apply_workspace_bytes(vp_plan p) {
   const size_t csize = p->prec == VP_FP64 ? sizeof(double2) : sizeof(float2);

@@ -47,6 +47,11 @@ bool fft_length_built(int n);
 // potential-only apply; that apply on a caller-supplied workspace (device
 // pointers only, allocates nothing).
 int plan_device(vp_plan p);
+cudaStream_t plan_stream(vp_plan p);
+int plan_is_fp32(vp_plan p);
+// The FP32 potential-only passes of a plan on workspace `ws` (input and output
+// pointers left NULL): fills args/kinds, returns the number of passes.
+int plan_pass_args_f32(vp_plan p, float2* ws, PassArgs<float>* args, int* kinds);
 size_t plan_apply_workspace_bytes(vp_plan p);
 vp_status apply_with_workspace(vp_plan p, const void* f, void* phi, vp_dtype dtype, void* ws, size_t ws_bytes);
 

@@ -65,6 +65,18 @@ _SIGNATURES = {
     "vp_destroy": (c_int, [c_void_p]),
     "vp_fft_length_supported": (c_int, [c_int]),
     "vp_apply_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
+    "vp_batch_create": (c_int, [ctypes.POINTER(c_void_p), c_int, ctypes.POINTER(c_void_p)]),
+    "vp_batch_set_stream": (c_int, [c_void_p, c_void_p]),
+    "vp_batch_set_strategy": (c_int, [c_void_p, c_int]),
+    "vp_batch_get_strategy": (c_int, [c_void_p, ctypes.POINTER(c_int)]),
+    "vp_batch_set_timeout": (c_int, [c_void_p, c_double]),
+    "vp_batch_withhold": (c_int, [c_void_p, c_int, c_int]),
+    "vp_batch_apply": (c_int, [c_void_p, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p)]),
+    "vp_batch_status": (c_int, [c_void_p]),
+    "vp_batch_info": (c_int, [c_void_p, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(c_int),
+                              ctypes.POINTER(c_size_t)]),
+    "vp_batch_last_error": (c_char_p, [c_void_p]),
+    "vp_batch_destroy": (c_int, [c_void_p]),
 }
 
 
@@ -270,6 +282,81 @@ class Plan:
     def close(self):
         if getattr(self, "handle", None):
             vp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+VP_BATCH_AUTO, VP_BATCH_PERSISTENT, VP_BATCH_PERSISTENT_ONE_PER_SM, VP_BATCH_PER_DENSITY = 0, 1, 2, 3
+VP_BATCH_GRAPH_STREAMS = 4
+
+
+def _bcheck(status: int, batch):
+    if status != VP_OK:
+        msg = lib().vp_batch_last_error(batch)
+        raise VPError(status, msg.decode() if msg else "")
+
+
+class Batch:
+    """Many FP32 plans applied in one persistent launch (vp_batch_* of the C ABI)."""
+
+    def __init__(self, plans, stream=None):
+        self.plans = list(plans)  # borrowed: keep them alive
+        arr = (c_void_p * len(self.plans))(*[p.handle for p in self.plans])
+        out = c_void_p()
+        _bcheck(lib().vp_batch_create(ctypes.byref(out), len(self.plans), arr), None)
+        self.handle = out.value
+        self._stream = stream
+        if stream is not None:
+            self.set_stream(stream)
+
+    def set_stream(self, stream):
+        raw = getattr(stream, "cuda_stream", stream)
+        _bcheck(lib().vp_batch_set_stream(self.handle, raw or 0), self.handle)
+        self._stream = stream
+
+    def set_strategy(self, strategy: int):
+        _bcheck(lib().vp_batch_set_strategy(self.handle, strategy), self.handle)
+
+    def strategy(self) -> int:
+        s = c_int()
+        _bcheck(lib().vp_batch_get_strategy(self.handle, ctypes.byref(s)), self.handle)
+        return s.value
+
+    def set_timeout(self, seconds: float):
+        _bcheck(lib().vp_batch_set_timeout(self.handle, seconds), self.handle)
+
+    def withhold(self, density: int, pass_index: int):
+        _bcheck(lib().vp_batch_withhold(self.handle, density, pass_index), self.handle)
+
+    def apply(self, fs, phis=None):
+        if phis is None:
+            phis = [_empty_like(f, f.shape) for f in fs]
+        if self._stream is None and fs and _is_torch(fs[0]) and fs[0].is_cuda:
+            import torch
+            lib().vp_batch_set_stream(self.handle, torch.cuda.current_stream(fs[0].device).cuda_stream)
+        fa = (c_void_p * len(fs))(*[_ptr(f) for f in fs])
+        pa = (c_void_p * len(phis))(*[_ptr(p) for p in phis])
+        _bcheck(lib().vp_batch_apply(self.handle, fa, pa), self.handle)
+        return phis
+
+    def status(self):
+        """Synchronises; raises VPError (VP_ERR_TIMEOUT) if a bounded wait gave up."""
+        _bcheck(lib().vp_batch_status(self.handle), self.handle)
+
+    def info(self) -> dict:
+        items, passes, b = ctypes.c_longlong(), c_int(), c_size_t()
+        _bcheck(lib().vp_batch_info(self.handle, ctypes.byref(items), ctypes.byref(passes), ctypes.byref(b)),
+                self.handle)
+        return {"items": items.value, "passes": passes.value, "device_bytes": b.value}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().vp_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

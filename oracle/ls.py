@@ -1,0 +1,103 @@
+"""Lippmann-Schwinger scattering with the volume potential (Section 5.3),
+oracle side, float64.  TEST INFRASTRUCTURE ONLY.
+
+The scattered field u of Delta u + k^2 (1 + q) u = -k^2 q u_inc satisfies
+u = k^2 V[q (u + u_inc)] with V the volume potential of the Green's function of
+-(Delta + k^2), i.e. the second-kind equation
+
+    A u := u - k^2 V[q u] = k^2 V[q u_inc] =: b.
+
+(The paper solves the dual density form; the field form has the same operator
+spectrum and is what the solver here uses.)  V is ``oracle.apply.apply_fft2n``
+with the Helmholtz multiplier.  ``dense_solve`` builds A column by column and
+solves it directly (small N only); ``gmres`` is textbook restarted GMRES.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import apply as A
+from . import kernel as K
+
+
+class LSProblem:
+    def __init__(self, N: int, k: float, q: np.ndarray, L: float = 1.8):
+        self.N, self.k, self.q = N, k, np.asarray(q, dtype=np.float64)
+        T = K.T_octant_by_sums(3, N, "helmholtz", k, L)
+        self.G = K.ghat_full_from_octant(K.ghat_octant_by_sums(T, N))
+
+    def V(self, f):
+        return A.apply_fft2n(self.G, f)
+
+    def op(self, u):
+        return u - self.k ** 2 * self.V(self.q * u)
+
+    def rhs(self, u_inc):
+        return self.k ** 2 * self.V(self.q * u_inc)
+
+    def residual(self, u, b) -> float:
+        return float(np.linalg.norm((b - self.op(u)).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def dense_solve(prob: LSProblem, b: np.ndarray) -> np.ndarray:
+    """Builds the N^3 x N^3 matrix of A from unit vectors and solves A u = b."""
+    n = prob.N ** 3
+    M = np.empty((n, n), dtype=np.complex128)
+    e = np.zeros(n, dtype=np.complex128)
+    for j in range(n):
+        e[j] = 1.0
+        M[:, j] = prob.op(e.reshape((prob.N,) * 3)).ravel()
+        e[j] = 0.0
+    return np.linalg.solve(M, b.ravel()).reshape(b.shape)
+
+
+def gmres(matvec, b: np.ndarray, tol: float = 1e-10, restart: int = 40, maxit: int = 2000):
+    """Restarted GMRES (Saad & Schultz) with modified Gram-Schmidt and Givens
+    rotations; returns (x, iterations, relative residual history)."""
+    x = np.zeros_like(b)
+    bn = np.linalg.norm(b.ravel())
+    hist = []
+    it = 0
+    while it < maxit:
+        r = b - matvec(x)
+        beta = np.linalg.norm(r.ravel())
+        hist.append(beta / bn)
+        if beta / bn < tol:
+            break
+        V = [r / beta]
+        H = np.zeros((restart + 1, restart), dtype=np.complex128)
+        g = np.zeros(restart + 1, dtype=np.complex128)
+        g[0] = beta
+        cs, sn = [], []
+        j_end = 0
+        for j in range(restart):
+            w = matvec(V[j])
+            for i in range(j + 1):
+                H[i, j] = np.vdot(V[i].ravel(), w.ravel())
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w.ravel())
+            V.append(w / H[j + 1, j] if H[j + 1, j] != 0 else w)
+            for i in range(j):
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -np.conj(sn[i]) * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            den = np.hypot(abs(H[j, j]), abs(H[j + 1, j]))
+            c = abs(H[j, j]) / den if den else 1.0
+            s = (H[j, j] / abs(H[j, j])) * np.conj(H[j + 1, j]) / den if abs(H[j, j]) else 1.0
+            cs.append(c)
+            sn.append(s)
+            H[j, j] = c * H[j, j] + s * H[j + 1, j]
+            H[j + 1, j] = 0.0
+            g[j + 1] = -np.conj(s) * g[j]
+            g[j] = c * g[j]
+            it += 1
+            j_end = j + 1
+            hist.append(abs(g[j + 1]) / bn)
+            if abs(g[j + 1]) / bn < tol or it >= maxit:
+                break
+        y = np.linalg.solve(np.triu(H[:j_end, :j_end]), g[:j_end])
+        for i in range(j_end):
+            x = x + y[i] * V[i]
+        if hist[-1] < tol:
+            break
+    return x, it, hist

@@ -180,3 +180,69 @@ def gaussian_amplitude(sigma_cfg: float, d: int) -> float:
     """exp(-r^2/sigma^2) = Q * rho(r) with rho the unit-mass Gaussian of standard
     deviation sigma/sqrt(2); returns Q = (pi sigma^2)^(d/2)."""
     return (math.pi * sigma_cfg * sigma_cfg) ** (d / 2)
+
+
+# ---------------------------------------------------------------------------
+# Lippmann-Schwinger inputs (contrast and incident field)
+# ---------------------------------------------------------------------------
+
+def cube_bump(N: int) -> np.ndarray:
+    """The smoothed cube exp(-1/2 sum_j (x_j/0.25)^8) of the paper's 3D
+    scattering example (Section 5.3), sampled on the N^3 grid."""
+    x = grid_coords(N)
+    e = (x / 0.25) ** 8
+    return np.exp(-0.5 * (e[:, None, None] + e[None, :, None] + e[None, None, :]))
+
+
+def ls_contrast(seed: int, N: int) -> np.ndarray:
+    """q = 0.5 * smoothed cube + 6 Gaussian perturbations (centres U[-0.3,0.3]^3,
+    widths U[0.03,0.08], amplitudes U[-0.25,0.25]); real, float64."""
+    u = uniform(seed, 6 * 5)
+    q = 0.5 * cube_bump(N)
+    x = grid_coords(N)
+    for g in range(6):
+        c = (2 * u[g * 5:g * 5 + 3] - 1) * 0.3
+        s = 0.03 + 0.05 * u[g * 5 + 3]
+        a = (2 * u[g * 5 + 4] - 1) * 0.25
+        q = q + a * (np.exp(-((x - c[0]) ** 2) / s ** 2)[:, None, None]
+                     * np.exp(-((x - c[1]) ** 2) / s ** 2)[None, :, None]
+                     * np.exp(-((x - c[2]) ** 2) / s ** 2)[None, None, :])
+    return q
+
+
+def plane_wave(N: int, k: float) -> np.ndarray:
+    """u_inc = exp(i k x_0): a plane wave travelling along the first axis."""
+    x = grid_coords(N)
+    return np.broadcast_to(np.exp(1j * k * x)[:, None, None], (N, N, N)).astype(np.complex128).copy()
+
+
+LS_TRAIN_SEED = BASE_SEED + 5000     # contrasts LS_TRAIN_SEED + i, i < 2000
+LS_HELDOUT_SEED = BASE_SEED + 9000   # held-out contrasts LS_HELDOUT_SEED + i, i < 50
+
+
+# ---------------------------------------------------------------------------
+# Learned preconditioner: network shape and seeded initial weights
+# ---------------------------------------------------------------------------
+
+def unet_layer_shapes(C: int = 16, cin: int = 3, cout: int = 2):
+    """(C_out, C_in) of the ten 3x3x3 convolutions of the 3-level U-Net, in order:
+    E1a, E1b, E2a, E2b, B1, B2, D2a, D2b, D1a, D1b."""
+    return [(C, cin), (C, C), (C, C), (C, C), (C, C), (C, C), (C, 2 * C), (C, C), (C, 2 * C), (cout, C)]
+
+
+def unet_init_weights(seed: int, C: int = 16, cin: int = 3, cout: int = 2):
+    """He-style normal weights [C_out][C_in][27] (float32), zero biases; the last
+    layer is scaled by 1/2."""
+    out = []
+    for i, (co, ci) in enumerate(unet_layer_shapes(C, cin, cout)):
+        z = normal(seed + i, co * ci * 27)
+        scale = np.sqrt(2.0 / (ci * 27)) * (0.5 if i == 9 else 1.0)
+        out.append(((z * scale).reshape(co, ci, 27).astype(np.float32), np.zeros(co, dtype=np.float32)))
+    return out
+
+
+def bf16_round(x: np.ndarray) -> np.ndarray:
+    """Rounds float32 values to bfloat16 (round to nearest even), returned as float32."""
+    u = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)

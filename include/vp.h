@@ -195,6 +195,76 @@ const char* vp_batch_last_error(vp_batch b);
 vp_status vp_batch_destroy(vp_batch b);
 
 /* ---------------------------------------------------------------------------
+ * Lippmann-Schwinger scattering on the volume potential (Section 5.3).
+ *
+ * For contrast q (real, N^3 floats) and incident field u_inc the scattered
+ * field solves  A u = u - k^2 V[q u] = k^2 V[q u_inc] = b  with V the plan's
+ * volume potential (3D Helmholtz plan, FP32 precision; complex64 vectors,
+ * device pointers).  The paper solves the dual density form with Bi-CGStab;
+ * vp_ls_solve runs right-preconditioned flexible GMRES(restart) (classical
+ * Gram-Schmidt with one re-orthogonalisation, FP64 inner products).  `precond`
+ * (may be NULL) maps a residual r to z ~ A^-1 r on `stream`; if a
+ * preconditioned cycle fails to reduce the residual the solve continues as
+ * plain GMRES (stats->used_fallback).  The solve stops when the recurrence
+ * residual is below tol or after maxit iterations; stats->true_residual is
+ * ||b - A u|| / ||b|| with A (and b from u_inc, when given) evaluated in FP64.
+ * ------------------------------------------------------------------------- */
+typedef vp_status (*vp_precond_fn)(void* ctx, const void* r, void* z, void* stream);
+typedef struct {
+  double tol;
+  int maxit;
+  int restart;            /* 1..64 */
+  int use_initial_guess;  /* 0: start from u = 0 */
+  vp_precond_fn precond;
+  void* precond_ctx;
+} vp_ls_opts;
+typedef struct {
+  int iterations;
+  int matvecs;
+  int restarts;
+  int used_fallback;
+  double estimated_residual;
+  double true_residual;
+  double seconds;
+} vp_ls_stats;
+vp_status vp_ls_operator(vp_plan plan, const float* q, const void* u, void* out);
+vp_status vp_ls_rhs(vp_plan plan, const float* q, const void* u_inc, void* b);
+vp_status vp_ls_solve(vp_plan plan, const float* q, const void* b, const void* u_inc, void* u, const vp_ls_opts* opts,
+                      vp_ls_stats* stats);
+const char* vp_ls_last_error(void);
+
+/* ---------------------------------------------------------------------------
+ * Learned right preconditioner for vp_ls_solve (a project addition; the
+ * paper's solver is unpreconditioned).  A 3-level 3D U-Net on one S^3 sample
+ * (S divisible by 4, C = 16 channels), channel-major float tensors [C][S][S][S]:
+ * E1a 3->C, E1b C->C -> s1; 2x2x2 mean pool; E2a, E2b -> s2; pool; B1, B2;
+ * nearest x2 up, concat with s2, D2a 2C->C, D2b; up, concat with s1, D1a 2C->C,
+ * D1b C->2.  Every conv is 3x3x3, zero padding 1, with bias and leaky ReLU
+ * (slope 0.1) except D1b.  Weights are bfloat16-rounded copies of FP32 master
+ * weights; arithmetic is FP32.  Parameter layout for set/get: for each layer in
+ * that order, w[C_out][C_in][27] (k = (kz*3 + ky)*3 + kx) then b[C_out].
+ * Input channels: (Re r, Im r, q) with r scaled to unit norm; output (Re z, Im z).
+ * vp_unet_loss_grad runs forward and backward for the mean squared error and
+ * keeps the gradients; vp_unet_adam_step applies Adam (beta 0.9/0.999, eps 1e-8).
+ * vp_unet_precond is a vp_precond_fn (ctx = the network, bound to a contrast
+ * with vp_unet_bind): z = ||r|| * net(r/||r||, q).
+ * ------------------------------------------------------------------------- */
+typedef struct vp_unet_s* vp_unet;
+vp_status vp_unet_create(vp_unet* out, int S, int C);
+vp_status vp_unet_param_count(vp_unet net, size_t* count);
+vp_status vp_unet_set_stream(vp_unet net, void* stream);
+vp_status vp_unet_set_weights(vp_unet net, const float* host, size_t count);
+vp_status vp_unet_get_weights(vp_unet net, int which /* 0 FP32, 1 BF16-rounded, 2 gradients */, float* host,
+                              size_t count);
+vp_status vp_unet_forward(vp_unet net, const float* in, float* out);
+vp_status vp_unet_loss_grad(vp_unet net, const float* in, const float* target, double* loss);
+vp_status vp_unet_adam_step(vp_unet net, double lr);
+vp_status vp_unet_bind(vp_unet net, const float* q);
+vp_status vp_unet_precond(void* ctx, const void* r, void* z, void* stream);
+const char* vp_unet_last_error(vp_unet net);
+vp_status vp_unet_destroy(vp_unet net);
+
+/* ---------------------------------------------------------------------------
  * Potential apply without device allocation (the paper has no counterpart;
  * this is a deployment aid).
  *

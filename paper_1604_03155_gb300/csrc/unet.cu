@@ -1,0 +1,713 @@
+// unet.cu -- the learned right preconditioner of the Lippmann-Schwinger solve
+// (a project addition; the paper's solver is unpreconditioned Bi-CGStab).
+//
+// A 3-level 3D U-Net on one S^3 sample, channel-major [C][S][S][S]:
+//   E1a conv 3->C, E1b conv C->C -> s1 (S); pool; E2a, E2b -> s2 (S/2); pool;
+//   B1, B2 (S/4); up, concat [up, s2], D2a 2C->C, D2b (S/2); up, concat
+//   [up, s1], D1a 2C->C, D1b C->2 (linear) (S).
+// conv = 3x3x3 cross-correlation, zero padding 1, bias; leaky ReLU (0.1) after
+// every conv but the last; pool = 2x2x2 mean; up = nearest x2.
+// Weights are kept in FP32 for the optimiser and rounded to bfloat16 for every
+// forward and backward pass (BF16 weights, FP32 arithmetic).
+//
+// Kernels (all the network's own):
+//  * k_conv3d: 8x8x8 output voxels per CTA, one per thread; the input halo
+//    (10^3 x 4 channels) and the chunk's weights ([ci][k][co], read as float4
+//    broadcasts) are staged in shared memory.  Two input pointers model the
+//    skip concatenation without a copy.
+//  * input gradient: the same kernel with the layer's weights flipped in k and
+//    transposed in (co, ci).
+//  * k_wgrad: persistent CTAs accumulate dW[ci][k][co] over their spatial tiles
+//    (halo and dz tile in shared memory, one (ci, k) pair per thread, CO
+//    accumulators), write one partial per CTA; k_wreduce sums the partials in
+//    FP64 in a fixed order (deterministic).
+//  * pool/up forward and backward, leaky-ReLU backward, MSE loss, Adam.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/vp.h"
+#include "vp_internal.cuh"
+
+namespace {
+
+constexpr float kSlope = 0.1f;
+constexpr int kLayers = 10;
+constexpr int kTile = 8, kHalo = 10, kHalo3 = 1000, kConvCh = 4, kWgCh = 16;
+
+__device__ __forceinline__ float lrelu(float v) { return v > 0.f ? v : kSlope * v; }
+
+template <int CO>
+__global__ void __launch_bounds__(512) k_conv3d(const float* __restrict__ x1, int c1, const float* __restrict__ x2,
+                                                int c2, const float* __restrict__ w, const float* __restrict__ bias,
+                                                float* __restrict__ y, int S, int act) {
+  __shared__ float halo[kConvCh][kHalo3];
+  __shared__ __align__(16) float ws[kConvCh * 27][CO < 4 ? 4 : CO];
+  const int Ci = c1 + c2;
+  const long long S3 = (long long)S * S * S;
+  const int tpd = (S + kTile - 1) / kTile;
+  int bt = blockIdx.x;
+  const int tx0 = (bt % tpd) * kTile;
+  bt /= tpd;
+  const int ty0 = (bt % tpd) * kTile;
+  const int tz0 = (bt / tpd) * kTile;
+  const int lx = threadIdx.x & 7, ly = (threadIdx.x >> 3) & 7, lz = threadIdx.x >> 6;
+  float acc[CO];
+#pragma unroll
+  for (int co = 0; co < CO; ++co) acc[co] = bias ? bias[co] : 0.f;
+  for (int c0 = 0; c0 < Ci; c0 += kConvCh) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < kConvCh * kHalo3; e += blockDim.x) {
+      const int ci = e / kHalo3, r = e % kHalo3;
+      const int gz = tz0 + r / 100 - 1, gy = ty0 + (r / 10) % 10 - 1, gx = tx0 + r % 10 - 1;
+      const int cc = c0 + ci;
+      float v = 0.f;
+      if (cc < Ci && gz >= 0 && gz < S && gy >= 0 && gy < S && gx >= 0 && gx < S) {
+        const float* src = cc < c1 ? x1 + (long long)cc * S3 : x2 + (long long)(cc - c1) * S3;
+        v = src[((long long)gz * S + gy) * S + gx];
+      }
+      halo[ci][r] = v;
+    }
+    for (int e = threadIdx.x; e < kConvCh * 27 * CO; e += blockDim.x) {
+      const int co = e % CO, ck = e / CO;
+      const int cc = c0 + ck / 27;
+      ws[ck][co] = (cc < Ci) ? w[((long long)co * Ci + cc) * 27 + ck % 27] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int ci = 0; ci < kConvCh; ++ci) {
+#pragma unroll
+      for (int k = 0; k < 27; ++k) {
+        const int kz = k / 9, ky = (k / 3) % 3, kx = k % 3;
+        const float xv = halo[ci][((lz + kz) * kHalo + (ly + ky)) * kHalo + lx + kx];
+        if constexpr (CO % 4 == 0) {
+#pragma unroll
+          for (int co = 0; co < CO; co += 4) {
+            const float4 w4 = *reinterpret_cast<const float4*>(&ws[ci * 27 + k][co]);
+            acc[co] = fmaf(w4.x, xv, acc[co]);
+            acc[co + 1] = fmaf(w4.y, xv, acc[co + 1]);
+            acc[co + 2] = fmaf(w4.z, xv, acc[co + 2]);
+            acc[co + 3] = fmaf(w4.w, xv, acc[co + 3]);
+          }
+        } else {
+#pragma unroll
+          for (int co = 0; co < CO; ++co) acc[co] = fmaf(ws[ci * 27 + k][co], xv, acc[co]);
+        }
+      }
+    }
+  }
+  const int gz = tz0 + lz, gy = ty0 + ly, gx = tx0 + lx;
+  if (gz < S && gy < S && gx < S) {
+    const long long idx = ((long long)gz * S + gy) * S + gx;
+#pragma unroll
+    for (int co = 0; co < CO; ++co) y[(long long)co * S3 + idx] = act ? lrelu(acc[co]) : acc[co];
+  }
+}
+
+// Weight gradient partials: part[blk][(ci*27 + k)*CO + co] and part[blk][Ci*27*CO + co] (bias)
+template <int CO>
+__global__ void __launch_bounds__(512) k_wgrad(const float* __restrict__ x1, int c1, const float* __restrict__ x2,
+                                               int c2, const float* __restrict__ dz, float* __restrict__ part, int S) {
+  extern __shared__ __align__(16) float sm[];
+  float* halo = sm;                      // kWgCh x 1000
+  float* dzs = sm + kWgCh * kHalo3;      // 512 x CO ([voxel][co])
+  const int Ci = c1 + c2;
+  const long long S3 = (long long)S * S * S;
+  const int tpd = (S + kTile - 1) / kTile;
+  const int ntiles = tpd * tpd * tpd;
+  const int nch = (Ci + kWgCh - 1) / kWgCh;  // 1 or 2
+  const int pair = threadIdx.x;              // (ci_local, k) = (pair / 27, pair % 27)
+  const int cil = pair / 27, k = pair % 27;
+  const int kz = k / 9, ky = (k / 3) % 3, kx = k % 3;
+  const bool bias_thread = threadIdx.x >= 512 - CO;
+  float acc[2][CO];
+  float bacc = 0.f;
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int co = 0; co < CO; ++co) acc[h][co] = 0.f;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int bt = t;
+    const int tx0 = (bt % tpd) * kTile;
+    bt /= tpd;
+    const int ty0 = (bt % tpd) * kTile;
+    const int tz0 = (bt / tpd) * kTile;
+    __syncthreads();
+    // dz tile, transposed to [voxel][co]; voxels outside the grid contribute zero
+    for (int e = threadIdx.x; e < 512 * CO; e += blockDim.x) {
+      const int co = e / 512, v = e % 512;
+      const int gz = tz0 + v / 64, gy = ty0 + (v / 8) % 8, gx = tx0 + v % 8;
+      float val = 0.f;
+      if (gz < S && gy < S && gx < S) val = dz[(long long)co * S3 + ((long long)gz * S + gy) * S + gx];
+      dzs[v * CO + co] = val;
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (h >= nch) break;
+      __syncthreads();
+      for (int e = threadIdx.x; e < kWgCh * kHalo3; e += blockDim.x) {
+        const int ci = e / kHalo3, r = e % kHalo3;
+        const int gz = tz0 + r / 100 - 1, gy = ty0 + (r / 10) % 10 - 1, gx = tx0 + r % 10 - 1;
+        const int cc = h * kWgCh + ci;
+        float val = 0.f;
+        if (cc < Ci && gz >= 0 && gz < S && gy >= 0 && gy < S && gx >= 0 && gx < S) {
+          const float* src = cc < c1 ? x1 + (long long)cc * S3 : x2 + (long long)(cc - c1) * S3;
+          val = src[((long long)gz * S + gy) * S + gx];
+        }
+        halo[ci * kHalo3 + r] = val;
+      }
+      __syncthreads();
+      if (pair < kWgCh * 27 && h * kWgCh + cil < Ci) {
+#pragma unroll 2
+        for (int v = 0; v < 512; ++v) {
+          const int vz = v >> 6, vy = (v >> 3) & 7, vx = v & 7;
+          const float xv = halo[cil * kHalo3 + ((vz + kz) * kHalo + (vy + ky)) * kHalo + vx + kx];
+          if constexpr (CO % 4 == 0) {
+#pragma unroll
+            for (int co = 0; co < CO; co += 4) {
+              const float4 d4 = *reinterpret_cast<const float4*>(&dzs[v * CO + co]);
+              acc[h][co] = fmaf(d4.x, xv, acc[h][co]);
+              acc[h][co + 1] = fmaf(d4.y, xv, acc[h][co + 1]);
+              acc[h][co + 2] = fmaf(d4.z, xv, acc[h][co + 2]);
+              acc[h][co + 3] = fmaf(d4.w, xv, acc[h][co + 3]);
+            }
+          } else {
+#pragma unroll
+            for (int co = 0; co < CO; ++co) acc[h][co] = fmaf(dzs[v * CO + co], xv, acc[h][co]);
+          }
+        }
+      }
+    }
+    if (bias_thread) {
+      const int co = threadIdx.x - (512 - CO);
+      for (int v = 0; v < 512; ++v) bacc += dzs[v * CO + co];
+    }
+  }
+  const long long stride = (long long)Ci * 27 * CO + CO;
+  float* out = part + (long long)blockIdx.x * stride;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int cc = h * kWgCh + cil;
+    if (h < nch && pair < kWgCh * 27 && cc < Ci)
+#pragma unroll
+      for (int co = 0; co < CO; ++co) out[((long long)cc * 27 + k) * CO + co] = acc[h][co];
+  }
+  if (bias_thread) out[(long long)Ci * 27 * CO + (threadIdx.x - (512 - CO))] = bacc;
+}
+
+// dw[co][ci][k] = sum_blocks part[blk][(ci*27+k)*CO + co]; db[co] likewise (FP64 sums)
+__global__ void k_wreduce(const float* __restrict__ part, int nblk, int Ci, int CO, float* __restrict__ dw,
+                          float* __restrict__ db) {
+  const long long nw = (long long)Ci * 27 * CO;
+  const long long stride = nw + CO;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < stride; i += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[(long long)b * stride + i];
+    if (i < nw) {
+      const long long co = i % CO, ck = i / CO;  // ck = ci*27 + k
+      dw[co * (long long)Ci * 27 + ck] = (float)s;
+    } else {
+      db[i - nw] = (float)s;
+    }
+  }
+}
+
+// wf[ci][co][k'] = w[co][ci][26 - k']  (input-gradient weights)
+__global__ void k_flip(const float* __restrict__ w, float* __restrict__ wf, int Co, int Ci) {
+  const int n = Co * Ci * 27;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int k = i % 27, co = (i / 27) % Co, ci = i / (27 * Co);
+    wf[i] = w[((long long)co * Ci + ci) * 27 + (26 - k)];
+  }
+}
+
+__global__ void k_pool(const float* __restrict__ x, float* __restrict__ y, int C, int S) {
+  const int h = S / 2;
+  const long long n = (long long)C * h * h * h;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long c = i / ((long long)h * h * h);
+    const long long r = i % ((long long)h * h * h);
+    const int z = (int)(r / (h * h)), yy = (int)((r / h) % h), xx = (int)(r % h);
+    const float* src = x + c * (long long)S * S * S;
+    float s = 0.f;
+    for (int d = 0; d < 8; ++d)
+      s += src[((long long)(2 * z + (d >> 2)) * S + 2 * yy + ((d >> 1) & 1)) * S + 2 * xx + (d & 1)];
+    y[i] = 0.125f * s;
+  }
+}
+
+// y (S^3 fine) = nearest-neighbour up of x (h^3 coarse), or its adjoint (sum into coarse) when back
+__global__ void k_up(const float* __restrict__ x, float* __restrict__ y, int C, int S, int scale_back) {
+  const int h = S / 2;
+  if (!scale_back) {
+    const long long n = (long long)C * S * S * S;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+      const long long c = i / ((long long)S * S * S), r = i % ((long long)S * S * S);
+      const int z = (int)(r / (S * S)), yy = (int)((r / S) % S), xx = (int)(r % S);
+      y[i] = x[c * (long long)h * h * h + ((long long)(z / 2) * h + yy / 2) * h + xx / 2];
+    }
+  } else {
+    // x fine (S^3) -> y coarse: y = sum of the 8 children (mean when scale_back == 2)
+    const long long n = (long long)C * h * h * h;
+    const float f = scale_back == 2 ? 0.125f : 1.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+      const long long c = i / ((long long)h * h * h), r = i % ((long long)h * h * h);
+      const int z = (int)(r / (h * h)), yy = (int)((r / h) % h), xx = (int)(r % h);
+      const float* src = x + c * (long long)S * S * S;
+      float s = 0.f;
+      for (int d = 0; d < 8; ++d)
+        s += src[((long long)(2 * z + (d >> 2)) * S + 2 * yy + ((d >> 1) & 1)) * S + 2 * xx + (d & 1)];
+      y[i] = f * s;
+    }
+  }
+}
+
+// pool adjoint: y_fine[...] (+)= x_coarse / 8
+__global__ void k_pool_back(const float* __restrict__ dc, float* __restrict__ df, int C, int S, int accumulate) {
+  const int h = S / 2;
+  const long long n = (long long)C * S * S * S;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long c = i / ((long long)S * S * S), r = i % ((long long)S * S * S);
+    const int z = (int)(r / (S * S)), yy = (int)((r / S) % S), xx = (int)(r % S);
+    const float v = 0.125f * dc[c * (long long)h * h * h + ((long long)(z / 2) * h + yy / 2) * h + xx / 2];
+    df[i] = accumulate ? df[i] + v : v;
+  }
+}
+
+// dz = dy * lrelu'(y) (y is the activated output: the sign is preserved)
+__global__ void k_lrelu_back(float* __restrict__ dz, const float* __restrict__ dy, const float* __restrict__ y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dz[i] = y[i] > 0.f ? dy[i] : kSlope * dy[i];
+}
+
+
+// MSE: dout = 2 (out - t)/n, partial sums of (out - t)^2 in FP64
+__global__ void k_mse(const float* __restrict__ out, const float* __restrict__ t, float* __restrict__ dout, long long n,
+                      double* __restrict__ part) {
+  __shared__ double red[8];
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float d = out[i] - t[i];
+    s += (double)d * d;
+    dout[i] = 2.f * d / (float)n;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) a += red[i];
+    part[blockIdx.x] = a;
+  }
+}
+
+__device__ __forceinline__ float bf16_round(float v) {
+  unsigned u = __float_as_uint(v);
+  u = (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+  return __uint_as_float(u);
+}
+
+__global__ void k_round_bf16(const float* __restrict__ w, float* __restrict__ wq, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    wq[i] = bf16_round(w[i]);
+}
+
+__global__ void k_adam(float* __restrict__ w, float* __restrict__ wq, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, long long n, float lr, float b1, float b2, float eps, float c1, float c2) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    w[i] = wi;
+    wq[i] = bf16_round(wi);
+  }
+}
+
+// network input [Re r, Im r, q] with r scaled by s
+__global__ void k_pack_input(float* __restrict__ x, const float2* __restrict__ r, const float* __restrict__ q, double s,
+                             long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    x[i] = (float)(r[i].x * s);
+    x[n + i] = (float)(r[i].y * s);
+    x[2 * n + i] = q[i];
+  }
+}
+
+__global__ void k_unpack_output(float2* __restrict__ z, const float* __restrict__ o, double s, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    z[i] = make_float2((float)(o[i] * s), (float)(o[n + i] * s));
+}
+
+__global__ void __launch_bounds__(256) k_norm2c(const float2* __restrict__ x, long long n, double* __restrict__ part) {
+  __shared__ double red[8];
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    s += (double)x[i].x * x[i].x + (double)x[i].y * x[i].y;
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int i = 0; i < 8; ++i) a += red[i];
+    part[blockIdx.x] = a;
+  }
+}
+
+dim3 g1(long long n) {
+  long long b = (n + 255) / 256;
+  return dim3((unsigned)(b > 152 * 16 ? 152 * 16 : b));
+}
+
+}  // namespace
+
+struct vp_unet_s {
+  int S = 0, C = 0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int co[kLayers], ci[kLayers];
+  long long woff[kLayers], boff[kLayers];
+  long long nparams = 0;
+  float *w = nullptr, *wq = nullptr, *g = nullptr, *m = nullptr, *v = nullptr, *wf = nullptr;
+  long long step = 0;
+  // activations (S: s1-level, S2 = S/2, S4 = S/4)
+  float *x0 = nullptr, *a1 = nullptr, *s1 = nullptr, *p1 = nullptr, *a3 = nullptr, *s2 = nullptr, *p2 = nullptr,
+        *a5 = nullptr, *a6 = nullptr, *u2 = nullptr, *a7 = nullptr, *a8 = nullptr, *u1 = nullptr, *a9 = nullptr,
+        *out = nullptr;
+  // gradient scratch
+  float *gA = nullptr, *gB = nullptr, *gC = nullptr, *gS1 = nullptr, *gS2 = nullptr, *dout = nullptr;
+  float* part = nullptr;
+  int part_blocks = 0;
+  double* red = nullptr;
+  const float* q = nullptr;  // bound contrast for the preconditioner
+  std::vector<void*> allocs;
+  std::string last_error;
+};
+
+namespace {
+
+vp_status ufail(vp_unet u, vp_status st, const std::string& m) {
+  if (u) u->last_error = m;
+  return st;
+}
+
+template <typename T> cudaError_t ualloc(vp_unet u, T** p, long long count) {
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e == cudaSuccess) u->allocs.push_back(*p);
+  return e;
+}
+
+cudaError_t conv(vp_unet u, const float* x1, int c1, const float* x2, int c2, const float* w, const float* b, float* y,
+                 int CO, int S, int act, cudaStream_t s) {
+  const int tpd = (S + kTile - 1) / kTile;
+  const dim3 grid(tpd * tpd * tpd);
+  switch (CO) {
+    case 2: k_conv3d<2><<<grid, 512, 0, s>>>(x1, c1, x2, c2, w, b, y, S, act); break;
+    case 16: k_conv3d<16><<<grid, 512, 0, s>>>(x1, c1, x2, c2, w, b, y, S, act); break;
+    case 32: k_conv3d<32><<<grid, 512, 0, s>>>(x1, c1, x2, c2, w, b, y, S, act); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t wgrad(vp_unet u, int layer, const float* x1, int c1, const float* x2, int c2, const float* dz, int S,
+                  cudaStream_t s) {
+  const int CO = u->co[layer], Ci = u->ci[layer];
+  const int tpd = (S + kTile - 1) / kTile;
+  const int nt = tpd * tpd * tpd;
+  const int nb = nt < u->part_blocks ? nt : u->part_blocks;
+  const size_t smem = (size_t)(kWgCh * kHalo3 + 512 * CO) * sizeof(float);
+  if (CO == 16)
+    k_wgrad<16><<<nb, 512, smem, s>>>(x1, c1, x2, c2, dz, u->part, S);
+  else if (CO == 2)
+    k_wgrad<2><<<nb, 512, smem, s>>>(x1, c1, x2, c2, dz, u->part, S);
+  else
+    return cudaErrorInvalidValue;
+  k_wreduce<<<g1((long long)Ci * 27 * CO + CO), 256, 0, s>>>(u->part, nb, Ci, CO, u->g + u->woff[layer],
+                                                             u->g + u->boff[layer]);
+  return cudaGetLastError();
+}
+
+// input gradient of a layer: conv of dz with the flipped, transposed weights
+cudaError_t dgrad(vp_unet u, int layer, const float* dz, float* dx, int S, cudaStream_t s) {
+  const int CO = u->co[layer], Ci = u->ci[layer];
+  k_flip<<<g1((long long)CO * Ci * 27), 256, 0, s>>>(u->wq + u->woff[layer], u->wf, CO, Ci);
+  return conv(u, dz, CO, nullptr, 0, u->wf, nullptr, dx, Ci, S, 0, s);
+}
+
+cudaError_t forward(vp_unet u, const float* in, cudaStream_t s) {
+  const int S = u->S, C = u->C, S2 = S / 2, S4 = S / 4;
+  const long long n2 = (long long)C * S2 * S2 * S2;
+  cudaError_t e;
+  auto L = [&](int i) { return u->wq + u->woff[i]; };
+  auto B = [&](int i) { return u->wq + u->boff[i]; };
+  if ((e = conv(u, in, 3, nullptr, 0, L(0), B(0), u->a1, C, S, 1, s)) != cudaSuccess) return e;
+  if ((e = conv(u, u->a1, C, nullptr, 0, L(1), B(1), u->s1, C, S, 1, s)) != cudaSuccess) return e;
+  k_pool<<<g1(n2), 256, 0, s>>>(u->s1, u->p1, C, S);
+  if ((e = conv(u, u->p1, C, nullptr, 0, L(2), B(2), u->a3, C, S2, 1, s)) != cudaSuccess) return e;
+  if ((e = conv(u, u->a3, C, nullptr, 0, L(3), B(3), u->s2, C, S2, 1, s)) != cudaSuccess) return e;
+  k_pool<<<g1((long long)C * S4 * S4 * S4), 256, 0, s>>>(u->s2, u->p2, C, S2);
+  if ((e = conv(u, u->p2, C, nullptr, 0, L(4), B(4), u->a5, C, S4, 1, s)) != cudaSuccess) return e;
+  if ((e = conv(u, u->a5, C, nullptr, 0, L(5), B(5), u->a6, C, S4, 1, s)) != cudaSuccess) return e;
+  k_up<<<g1(n2), 256, 0, s>>>(u->a6, u->u2, C, S2, 0);
+  if ((e = conv(u, u->u2, C, u->s2, C, L(6), B(6), u->a7, C, S2, 1, s)) != cudaSuccess) return e;
+  if ((e = conv(u, u->a7, C, nullptr, 0, L(7), B(7), u->a8, C, S2, 1, s)) != cudaSuccess) return e;
+  k_up<<<g1((long long)C * S * S * S), 256, 0, s>>>(u->a8, u->u1, C, S, 0);
+  if ((e = conv(u, u->u1, C, u->s1, C, L(8), B(8), u->a9, C, S, 1, s)) != cudaSuccess) return e;
+  if ((e = conv(u, u->a9, C, nullptr, 0, L(9), B(9), u->out, 2, S, 0, s)) != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+// gradients of the loss for dL/dout = u->dout (stored in u->g)
+cudaError_t backward(vp_unet u, const float* in, cudaStream_t s) {
+  const int S = u->S, C = u->C, S2 = S / 2, S4 = S / 4;
+  const long long n1 = (long long)C * S * S * S, n2 = (long long)C * S2 * S2 * S2, n4 = (long long)C * S4 * S4 * S4;
+  cudaError_t e;
+  // D1b (linear): input a9
+  if ((e = wgrad(u, 9, u->a9, C, nullptr, 0, u->dout, S, s)) != cudaSuccess) return e;
+  if ((e = dgrad(u, 9, u->dout, u->gA, S, s)) != cudaSuccess) return e;  // d a9
+  // D1a: input concat[u1, s1], output a9
+  k_lrelu_back<<<g1(n1), 256, 0, s>>>(u->gA, u->gA, u->a9, n1);
+  if ((e = wgrad(u, 8, u->u1, C, u->s1, C, u->gA, S, s)) != cudaSuccess) return e;
+  if ((e = dgrad(u, 8, u->gA, u->gB, S, s)) != cudaSuccess) return e;  // [d u1, d s1] (2C)
+  cudaMemcpyAsync(u->gS1, u->gB + n1, n1 * sizeof(float), cudaMemcpyDeviceToDevice, s);
+  k_up<<<g1(n2), 256, 0, s>>>(u->gB, u->gC, C, S, 1);  // d a8 = up^T d u1
+  // D2b: input a7, output a8
+  k_lrelu_back<<<g1(n2), 256, 0, s>>>(u->gC, u->gC, u->a8, n2);
+  if ((e = wgrad(u, 7, u->a7, C, nullptr, 0, u->gC, S2, s)) != cudaSuccess) return e;
+  if ((e = dgrad(u, 7, u->gC, u->gA, S2, s)) != cudaSuccess) return e;  // d a7
+  // D2a: input concat[u2, s2], output a7
+  k_lrelu_back<<<g1(n2), 256, 0, s>>>(u->gA, u->gA, u->a7, n2);
+  if ((e = wgrad(u, 6, u->u2, C, u->s2, C, u->gA, S2, s)) != cudaSuccess) return e;
+  if ((e = dgrad(u, 6, u->gA, u->gB, S2, s)) != cudaSuccess) return e;  // [d u2, d s2]
+  cudaMemcpyAsync(u->gS2, u->gB + n2, n2 * sizeof(float), cudaMemcpyDeviceToDevice, s);
+  k_up<<<g1(n4), 256, 0, s>>>(u->gB, u->gC, C, S2, 1);  // d a6
+  // B2: input a5, output a6
+  k_lrelu_back<<<g1(n4), 256, 0, s>>>(u->gC, u->gC, u->a6, n4);
+  if ((e = wgrad(u, 5, u->a5, C, nullptr, 0, u->gC, S4, s)) != cudaSuccess) return e;
+  if ((e = dgrad(u, 5, u->gC, u->gA, S4, s)) != cudaSuccess) return e;  // d a5
+  // B1: input p2, output a5
+  k_lrelu_back<<<g1(n4), 256, 0, s>>>(u->gA, u->gA, u->a5, n4);
+  if ((e = wgrad(u, 4, u->p2, C, nullptr, 0, u->gA, S4, s)) != cudaSuccess) return e;
+  if ((e = dgrad(u, 4, u->gA, u->gC, S4, s)) != cudaSuccess) return e;  // d p2
+  k_pool_back<<<g1(n2), 256, 0, s>>>(u->gC, u->gS2, C, S2, 1);        // d s2 += pool^T d p2
+  // E2b: input a3, output s2
+  k_lrelu_back<<<g1(n2), 256, 0, s>>>(u->gS2, u->gS2, u->s2, n2);
+  if ((e = wgrad(u, 3, u->a3, C, nullptr, 0, u->gS2, S2, s)) != cudaSuccess) return e;
+  if ((e = dgrad(u, 3, u->gS2, u->gA, S2, s)) != cudaSuccess) return e;  // d a3
+  // E2a: input p1, output a3
+  k_lrelu_back<<<g1(n2), 256, 0, s>>>(u->gA, u->gA, u->a3, n2);
+  if ((e = wgrad(u, 2, u->p1, C, nullptr, 0, u->gA, S2, s)) != cudaSuccess) return e;
+  if ((e = dgrad(u, 2, u->gA, u->gC, S2, s)) != cudaSuccess) return e;  // d p1
+  k_pool_back<<<g1(n1), 256, 0, s>>>(u->gC, u->gS1, C, S, 1);          // d s1 += pool^T d p1
+  // E1b: input a1, output s1
+  k_lrelu_back<<<g1(n1), 256, 0, s>>>(u->gS1, u->gS1, u->s1, n1);
+  if ((e = wgrad(u, 1, u->a1, C, nullptr, 0, u->gS1, S, s)) != cudaSuccess) return e;
+  if ((e = dgrad(u, 1, u->gS1, u->gA, S, s)) != cudaSuccess) return e;  // d a1
+  // E1a: input x0, output a1
+  k_lrelu_back<<<g1(n1), 256, 0, s>>>(u->gA, u->gA, u->a1, n1);
+  if ((e = wgrad(u, 0, in, 3, nullptr, 0, u->gA, S, s)) != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+vp_status vp_unet_create(vp_unet* out, int S, int C) {
+  if (!out) return VP_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (S < 4 || S % 4 || C != 16) return VP_ERR_INVALID_ARG;
+  vp_unet u = new vp_unet_s();
+  u->S = S;
+  u->C = C;
+  cudaGetDevice(&u->device);
+  const int shapes[kLayers][2] = {{C, 3}, {C, C}, {C, C}, {C, C}, {C, C}, {C, C}, {C, 2 * C}, {C, C}, {C, 2 * C}, {2, C}};
+  long long off = 0;
+  for (int i = 0; i < kLayers; ++i) {
+    u->co[i] = shapes[i][0];
+    u->ci[i] = shapes[i][1];
+    u->woff[i] = off;
+    off += (long long)u->co[i] * u->ci[i] * 27;
+    u->boff[i] = off;
+    off += u->co[i];
+  }
+  u->nparams = off;
+  const long long S1 = (long long)S * S * S, S2 = S1 / 8, S4 = S1 / 64;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](float** p, long long n) {
+    if (e == cudaSuccess) e = ualloc(u, p, n);
+  };
+  A(&u->w, off);
+  A(&u->wq, off);
+  A(&u->g, off);
+  A(&u->m, off);
+  A(&u->v, off);
+  A(&u->wf, (long long)2 * C * C * 27);
+  A(&u->x0, 3 * S1);
+  A(&u->a1, C * S1);
+  A(&u->s1, C * S1);
+  A(&u->p1, C * S2);
+  A(&u->a3, C * S2);
+  A(&u->s2, C * S2);
+  A(&u->p2, C * S4);
+  A(&u->a5, C * S4);
+  A(&u->a6, C * S4);
+  A(&u->u2, C * S2);
+  A(&u->a7, C * S2);
+  A(&u->a8, C * S2);
+  A(&u->u1, C * S1);
+  A(&u->a9, C * S1);
+  A(&u->out, 2 * S1);
+  A(&u->gA, 2 * C * S1);
+  A(&u->gB, 2 * C * S1);
+  A(&u->gC, 2 * C * S1);
+  A(&u->gS1, C * S1);
+  A(&u->gS2, C * S2);
+  A(&u->dout, 2 * S1);
+  u->part_blocks = 2 * 152;
+  A(&u->part, (long long)u->part_blocks * (2 * C * 27 * C + C));
+  if (e == cudaSuccess) e = ualloc(u, &u->red, 2048);
+  if (e == cudaSuccess) e = cudaMemset(u->m, 0, off * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(u->v, 0, off * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(u->w, 0, off * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(u->wq, 0, off * sizeof(float));
+  if (e == cudaSuccess) {
+    e = cudaFuncSetAttribute(k_wgrad<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((kWgCh * kHalo3 + 512 * 16) * sizeof(float)));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_wgrad<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)((kWgCh * kHalo3 + 512 * 2) * sizeof(float)));
+  }
+  if (e != cudaSuccess) {
+    vp_unet_destroy(u);
+    return e == cudaErrorMemoryAllocation ? VP_ERR_OOM : VP_ERR_CUDA;
+  }
+  *out = u;
+  return VP_OK;
+}
+
+vp_status vp_unet_param_count(vp_unet u, size_t* count) {
+  if (!u || !count) return VP_ERR_INVALID_ARG;
+  *count = (size_t)u->nparams;
+  return VP_OK;
+}
+
+vp_status vp_unet_set_stream(vp_unet u, void* stream) {
+  if (!u) return VP_ERR_INVALID_ARG;
+  u->stream = reinterpret_cast<cudaStream_t>(stream);
+  return VP_OK;
+}
+
+vp_status vp_unet_set_weights(vp_unet u, const float* host, size_t count) {
+  if (!u || !host || count != (size_t)u->nparams) return ufail(u, VP_ERR_INVALID_ARG, "weight count mismatch");
+  cudaSetDevice(u->device);
+  if (cudaMemcpy(u->w, host, count * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) return VP_ERR_CUDA;
+  k_round_bf16<<<g1(u->nparams), 256, 0, u->stream>>>(u->w, u->wq, u->nparams);
+  cudaMemsetAsync(u->m, 0, count * sizeof(float), u->stream);
+  cudaMemsetAsync(u->v, 0, count * sizeof(float), u->stream);
+  u->step = 0;
+  return cudaStreamSynchronize(u->stream) == cudaSuccess ? VP_OK : VP_ERR_CUDA;
+}
+
+vp_status vp_unet_get_weights(vp_unet u, int which, float* host, size_t count) {
+  if (!u || !host || count != (size_t)u->nparams || which < 0 || which > 2) return VP_ERR_INVALID_ARG;
+  cudaSetDevice(u->device);
+  cudaStreamSynchronize(u->stream);
+  const float* src = which == 0 ? u->w : (which == 1 ? u->wq : u->g);
+  return cudaMemcpy(host, src, count * sizeof(float), cudaMemcpyDeviceToHost) == cudaSuccess ? VP_OK : VP_ERR_CUDA;
+}
+
+vp_status vp_unet_forward(vp_unet u, const float* in, float* out) {
+  if (!u || !in || !out) return VP_ERR_INVALID_ARG;
+  cudaSetDevice(u->device);
+  cudaError_t e = forward(u, in, u->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, u->out, 2LL * u->S * u->S * u->S * sizeof(float), cudaMemcpyDeviceToDevice, u->stream);
+  return e == cudaSuccess ? VP_OK : ufail(u, VP_ERR_CUDA, cudaGetErrorString(e));
+}
+
+vp_status vp_unet_loss_grad(vp_unet u, const float* in, const float* target, double* loss) {
+  if (!u || !in || !target) return VP_ERR_INVALID_ARG;
+  cudaSetDevice(u->device);
+  cudaStream_t s = u->stream;
+  cudaError_t e = forward(u, in, s);
+  const long long n = 2LL * u->S * u->S * u->S;
+  const int nb = 256;
+  if (e == cudaSuccess) {
+    k_mse<<<nb, 256, 0, s>>>(u->out, target, u->dout, n, u->red);
+    e = backward(u, in, s);
+  }
+  if (e != cudaSuccess) return ufail(u, VP_ERR_CUDA, cudaGetErrorString(e));
+  if (loss) {
+    std::vector<double> h(nb);
+    if (cudaMemcpyAsync(h.data(), u->red, nb * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return VP_ERR_CUDA;
+    double acc = 0.0;
+    for (double v : h) acc += v;
+    *loss = acc / (double)n;
+  }
+  return VP_OK;
+}
+
+vp_status vp_unet_adam_step(vp_unet u, double lr) {
+  if (!u || !(lr > 0)) return VP_ERR_INVALID_ARG;
+  cudaSetDevice(u->device);
+  const float b1 = 0.9f, b2 = 0.999f;
+  ++u->step;
+  const float c1 = 1.f - powf(b1, (float)u->step), c2 = 1.f - powf(b2, (float)u->step);
+  k_adam<<<g1(u->nparams), 256, 0, u->stream>>>(u->w, u->wq, u->g, u->m, u->v, u->nparams, (float)lr, b1, b2, 1e-8f,
+                                                 c1, c2);
+  return cudaGetLastError() == cudaSuccess ? VP_OK : VP_ERR_CUDA;
+}
+
+vp_status vp_unet_bind(vp_unet u, const float* q) {
+  if (!u || !q) return VP_ERR_INVALID_ARG;
+  u->q = q;
+  return VP_OK;
+}
+
+// Preconditioner z = ||r|| * net([Re r, Im r]/||r||, q), a vp_precond_fn.
+vp_status vp_unet_precond(void* ctx, const void* r, void* z, void* stream) {
+  vp_unet u = reinterpret_cast<vp_unet>(ctx);
+  if (!u || !u->q || !r || !z) return VP_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const long long n = (long long)u->S * u->S * u->S;
+  const float2* rr = reinterpret_cast<const float2*>(r);
+  k_norm2c<<<256, 256, 0, s>>>(rr, n, u->red);
+  std::vector<double> h(256);
+  if (cudaMemcpyAsync(h.data(), u->red, 256 * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return VP_ERR_CUDA;
+  double nr = 0.0;
+  for (double v : h) nr += v;
+  nr = sqrt(nr);
+  if (!(nr > 0)) {
+    cudaMemsetAsync(z, 0, n * sizeof(float2), s);
+    return VP_OK;
+  }
+  k_pack_input<<<g1(n), 256, 0, s>>>(u->x0, rr, u->q, 1.0 / nr, n);
+  cudaError_t e = forward(u, u->x0, s);
+  if (e != cudaSuccess) return VP_ERR_CUDA;
+  k_unpack_output<<<g1(n), 256, 0, s>>>(reinterpret_cast<float2*>(z), u->out, nr, n);
+  return cudaGetLastError() == cudaSuccess ? VP_OK : VP_ERR_CUDA;
+}
+
+const char* vp_unet_last_error(vp_unet u) { return u ? u->last_error.c_str() : ""; }
+
+vp_status vp_unet_destroy(vp_unet u) {
+  if (!u) return VP_OK;
+  cudaSetDevice(u->device);
+  if (u->stream) cudaStreamSynchronize(u->stream);
+  for (void* p : u->allocs) cudaFree(p);
+  delete u;
+  return VP_OK;
+}
+
+}  // extern "C"

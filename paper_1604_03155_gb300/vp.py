@@ -77,6 +77,22 @@ _SIGNATURES = {
                               ctypes.POINTER(c_size_t)]),
     "vp_batch_last_error": (c_char_p, [c_void_p]),
     "vp_batch_destroy": (c_int, [c_void_p]),
+    "vp_ls_operator": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "vp_ls_rhs": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "vp_ls_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "vp_ls_last_error": (c_char_p, []),
+    "vp_unet_create": (c_int, [ctypes.POINTER(c_void_p), c_int, c_int]),
+    "vp_unet_param_count": (c_int, [c_void_p, ctypes.POINTER(c_size_t)]),
+    "vp_unet_set_stream": (c_int, [c_void_p, c_void_p]),
+    "vp_unet_set_weights": (c_int, [c_void_p, c_void_p, c_size_t]),
+    "vp_unet_get_weights": (c_int, [c_void_p, c_int, c_void_p, c_size_t]),
+    "vp_unet_forward": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "vp_unet_loss_grad": (c_int, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_double)]),
+    "vp_unet_adam_step": (c_int, [c_void_p, c_double]),
+    "vp_unet_bind": (c_int, [c_void_p, c_void_p]),
+    "vp_unet_precond": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "vp_unet_last_error": (c_char_p, [c_void_p]),
+    "vp_unet_destroy": (c_int, [c_void_p]),
 }
 
 
@@ -357,6 +373,127 @@ class Batch:
     def close(self):
         if getattr(self, "handle", None):
             lib().vp_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# Lippmann-Schwinger solve and the learned preconditioner
+# ---------------------------------------------------------------------------
+
+PRECOND_FN = ctypes.CFUNCTYPE(c_int, c_void_p, c_void_p, c_void_p, c_void_p)
+
+
+class LSOpts(ctypes.Structure):
+    _fields_ = [("tol", c_double), ("maxit", c_int), ("restart", c_int), ("use_initial_guess", c_int),
+                ("precond", c_void_p), ("precond_ctx", c_void_p)]
+
+
+class LSStats(ctypes.Structure):
+    _fields_ = [("iterations", c_int), ("matvecs", c_int), ("restarts", c_int), ("used_fallback", c_int),
+                ("estimated_residual", c_double), ("true_residual", c_double), ("seconds", c_double)]
+
+
+def _lscheck(status: int):
+    if status != VP_OK:
+        msg = lib().vp_ls_last_error()
+        raise VPError(status, msg.decode() if msg else "")
+
+
+def ls_operator(plan: Plan, q, u, out=None):
+    """out = u - k^2 V[q u] (device tensors: q float32, u complex64)."""
+    out = _empty_like(u, u.shape) if out is None else out
+    plan._sync_stream_to_torch(u)
+    _lscheck(lib().vp_ls_operator(plan.handle, _ptr(q), _ptr(u), _ptr(out)))
+    return out
+
+
+def ls_rhs(plan: Plan, q, u_inc, b=None):
+    """b = k^2 V[q u_inc]."""
+    b = _empty_like(u_inc, u_inc.shape) if b is None else b
+    plan._sync_stream_to_torch(u_inc)
+    _lscheck(lib().vp_ls_rhs(plan.handle, _ptr(q), _ptr(u_inc), _ptr(b)))
+    return b
+
+
+def ls_solve(plan: Plan, q, b, u, u_inc=None, tol=1e-6, maxit=1000, restart=30, precond=None,
+             initial_guess=False) -> dict:
+    """Flexible GMRES on u - k^2 V[q u] = b; precond is a UNet (bound to q) or None."""
+    opts = LSOpts(tol, maxit, restart, int(initial_guess), None, None)
+    if precond is not None:
+        opts.precond = ctypes.cast(lib().vp_unet_precond, c_void_p)
+        opts.precond_ctx = precond.handle
+    st = LSStats()
+    plan._sync_stream_to_torch(b)
+    _lscheck(lib().vp_ls_solve(plan.handle, _ptr(q), _ptr(b), _ptr(u_inc) if u_inc is not None else None, _ptr(u),
+                               ctypes.byref(opts), ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in LSStats._fields_}
+
+
+class UNet:
+    """The learned preconditioner network (vp_unet_*)."""
+
+    def __init__(self, S: int, C: int = 16, weights=None):
+        out = c_void_p()
+        st = lib().vp_unet_create(ctypes.byref(out), S, C)
+        if st != VP_OK:
+            raise VPError(st, "vp_unet_create failed")
+        self.handle, self.S, self.C = out.value, S, C
+        n = c_size_t()
+        lib().vp_unet_param_count(self.handle, ctypes.byref(n))
+        self.nparams = n.value
+        if weights is not None:
+            self.set_weights(weights)
+
+    def _check(self, st):
+        if st != VP_OK:
+            msg = lib().vp_unet_last_error(self.handle)
+            raise VPError(st, msg.decode() if msg else "")
+
+    def set_stream(self, stream):
+        self._check(lib().vp_unet_set_stream(self.handle, getattr(stream, "cuda_stream", stream) or 0))
+
+    def set_weights(self, layers):
+        """layers: list of (w [Co][Ci][27], b [Co]) arrays, or a flat float32 array."""
+        if isinstance(layers, np.ndarray):
+            flat = np.ascontiguousarray(layers, dtype=np.float32)
+        else:
+            flat = np.concatenate([np.concatenate([np.asarray(w, np.float32).ravel(), np.asarray(b, np.float32).ravel()])
+                                   for w, b in layers])
+        assert flat.size == self.nparams
+        self._check(lib().vp_unet_set_weights(self.handle, flat.ctypes.data, flat.size))
+
+    def get(self, which: int = 0) -> np.ndarray:
+        buf = np.empty(self.nparams, np.float32)
+        self._check(lib().vp_unet_get_weights(self.handle, which, buf.ctypes.data, buf.size))
+        return buf
+
+    def forward(self, x, out=None):
+        import torch
+        out = torch.empty((2,) + tuple(x.shape[1:]), dtype=torch.float32, device=x.device) if out is None else out
+        self._check(lib().vp_unet_forward(self.handle, _ptr(x), _ptr(out)))
+        return out
+
+    def loss_grad(self, x, target) -> float:
+        loss = c_double()
+        self._check(lib().vp_unet_loss_grad(self.handle, _ptr(x), _ptr(target), ctypes.byref(loss)))
+        return loss.value
+
+    def adam_step(self, lr: float):
+        self._check(lib().vp_unet_adam_step(self.handle, lr))
+
+    def bind(self, q):
+        self._q = q
+        self._check(lib().vp_unet_bind(self.handle, _ptr(q)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().vp_unet_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -21,7 +21,8 @@ def _declared():
         if fn.endswith(".h"):
             text = open(os.path.join(ROOT, "include", fn)).read()
             text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-            names |= set(re.findall(r"\b(vp_\w+)\s*\(", text))
+            # function declarations: "<return type> vp_name(" at the start of a line
+            names |= set(re.findall(r"^\s*(?:vp_status|const char\*|int)\s+(vp_\w+)\s*\(", text, flags=re.M))
     return names
 
 

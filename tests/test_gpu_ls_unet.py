@@ -1,0 +1,115 @@
+"""Lippmann-Schwinger solve (flexible GMRES on the FP32 apply) and the learned
+preconditioner network (the project's own conv3d forward/backward kernels)
+against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import ls as OLS
+from oracle import unet as OU
+from paper_1604_03155_gb300 import inputs as I
+from paper_1604_03155_gb300 import vp
+from paper_1604_03155_gb300.vp import Plan, UNet
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def _weights(seed, C=16, bias_seed=None):
+    layers = I.unet_init_weights(seed, C)
+    out = []
+    for i, (w, b) in enumerate(layers):
+        if bias_seed is not None:
+            b = (0.05 * I.normal(bias_seed + i, b.size)).astype(np.float32)
+        out.append((I.bf16_round(w), I.bf16_round(b)))
+    return out
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-30))
+
+
+@pytest.mark.parametrize("S", [8, 16])
+def test_unet_forward_loss_and_gradients_match_oracle(S):
+    layers = _weights(I.BASE_SEED + 300, bias_seed=I.BASE_SEED + 400)
+    net = UNet(S, 16, weights=layers)
+    x = I.random_complex_field(I.BASE_SEED + 301, (3, S, S, S)).real.astype(np.float32)
+    t = I.random_complex_field(I.BASE_SEED + 302, (2, S, S, S)).real.astype(np.float32)
+    xd, td = torch.from_numpy(x).to(DEV), torch.from_numpy(t).to(DEV)
+    out = net.forward(xd).cpu().numpy()
+    params = [(w.astype(np.float64), b.astype(np.float64)) for w, b in layers]
+    ref, _ = OU.forward(params, x.astype(np.float64))
+    assert _rel(out, ref) < 1e-5
+    loss = net.loss_grad(xd, td)
+    L, grads = OU.loss_and_grads(params, x.astype(np.float64), t.astype(np.float64))
+    assert abs(loss - L) < 1e-5 * L
+    g = net.get(2)
+    off = 0
+    for i, (w, b) in enumerate(layers):
+        gw = g[off:off + w.size].reshape(w.shape)
+        off += w.size
+        gb = g[off:off + b.size]
+        off += b.size
+        assert _rel(gw, grads[i][0]) < 1e-4, i
+        assert _rel(gb, grads[i][1]) < 1e-4, i
+    net.close()
+
+
+def test_unet_training_reduces_loss():
+    S = 16
+    net = UNet(S, 16, weights=_weights(I.BASE_SEED + 310))
+    x = torch.from_numpy(I.random_complex_field(I.BASE_SEED + 311, (3, S, S, S)).real.astype(np.float32)).to(DEV)
+    t = torch.from_numpy(0.3 * I.random_complex_field(I.BASE_SEED + 312, (2, S, S, S)).real.astype(np.float32)).to(DEV)
+    first = net.loss_grad(x, t)
+    for _ in range(60):
+        net.loss_grad(x, t)
+        net.adam_step(3e-3)
+    last = net.loss_grad(x, t)
+    assert last < 0.5 * first
+    w, wq = net.get(0), net.get(1)
+    assert np.array_equal(wq, I.bf16_round(w))  # BF16 copies of the FP32 master weights
+    net.close()
+
+
+def _ls_setup(N, k, seed):
+    plan = Plan(3, N, "helmholtz", k, 1.8, precision="fp32")
+    q = torch.from_numpy(I.ls_contrast(seed, N).astype(np.float32)).to(DEV)
+    uinc = torch.from_numpy(I.plane_wave(N, k).astype(np.complex64)).to(DEV)
+    b = vp.ls_rhs(plan, q, uinc)
+    return plan, q, uinc, b
+
+
+def test_ls_solve_matches_oracle_dense_solve():
+    N, k = 12, 6.0
+    plan, q, uinc, b = _ls_setup(N, k, I.LS_TRAIN_SEED)
+    u = torch.zeros_like(uinc)
+    st = vp.ls_solve(plan, q, b, u, u_inc=uinc, tol=1e-7, maxit=500, restart=30)
+    assert st["true_residual"] < 1e-6 and st["used_fallback"] == 0
+    prob = OLS.LSProblem(N, k, I.ls_contrast(I.LS_TRAIN_SEED, N).astype(np.float32).astype(np.float64))
+    ref = OLS.dense_solve(prob, prob.rhs(I.plane_wave(N, k).astype(np.complex64).astype(np.complex128)))
+    got = u.cpu().numpy()
+    assert np.linalg.norm((got - ref).ravel()) / np.linalg.norm(ref.ravel()) < 1e-5
+    # the operator entry point agrees with the oracle operator
+    Au = vp.ls_operator(plan, q, u).cpu().numpy()
+    assert np.linalg.norm((Au - prob.op(got.astype(np.complex128))).ravel()) / np.linalg.norm(Au.ravel()) < 1e-5
+
+
+def test_ls_solve_full_size_true_residual():
+    """N = 128, k = 30, q = smoothed cube + perturbations, plane wave: plain
+    GMRES reaches a true FP64 residual below 1e-6."""
+    plan, q, uinc, b = _ls_setup(128, 30.0, I.LS_HELDOUT_SEED)
+    u = torch.zeros_like(uinc)
+    st = vp.ls_solve(plan, q, b, u, u_inc=uinc, tol=3e-7, maxit=2000, restart=40)
+    assert st["true_residual"] < 1e-6, st
+    assert st["iterations"] < 2000
+
+
+def test_untrained_preconditioner_falls_back_and_still_converges():
+    N, k = 32, 10.0
+    plan, q, uinc, b = _ls_setup(N, k, I.LS_TRAIN_SEED + 1)
+    net = UNet(N, 16, weights=_weights(I.BASE_SEED + 320))
+    net.bind(q)
+    u = torch.zeros_like(uinc)
+    st = vp.ls_solve(plan, q, b, u, u_inc=uinc, tol=3e-7, maxit=800, restart=20, precond=net)
+    assert st["true_residual"] < 1e-6, st
+    net.close()

@@ -231,6 +231,12 @@ vp_status vp_ls_operator(vp_plan plan, const float* q, const void* u, void* out)
 vp_status vp_ls_rhs(vp_plan plan, const float* q, const void* u_inc, void* b);
 vp_status vp_ls_solve(vp_plan plan, const float* q, const void* b, const void* u_inc, void* u, const vp_ls_opts* opts,
                       vp_ls_stats* stats);
+/* One training pair for the learned preconditioner from solver iterates:
+ * r = b - A u_s (u_s may be NULL: r = b), e = u_star - u_s (A e = r); with
+ * s = sqrt(N^3)/||r|| writes the network input x = (s Re r, s Im r, q) as
+ * 3 x N^3 floats and the target t = s (e - r) as 2 x N^3 floats. */
+vp_status vp_ls_training_pair(vp_plan plan, const float* q, const void* b, const void* u_s, const void* u_star,
+                              float* x_out, float* t_out, double* rnorm);
 const char* vp_ls_last_error(void);
 
 /* ---------------------------------------------------------------------------
@@ -243,11 +249,13 @@ const char* vp_ls_last_error(void);
  * (slope 0.1) except D1b.  Weights are bfloat16-rounded copies of FP32 master
  * weights; arithmetic is FP32.  Parameter layout for set/get: for each layer in
  * that order, w[C_out][C_in][27] (k = (kz*3 + ky)*3 + kx) then b[C_out].
- * Input channels: (Re r, Im r, q) with r scaled to unit norm; output (Re z, Im z).
+ * Input channels: (Re r, Im r, q) with r scaled to unit RMS (sqrt(n) r/||r||);
+ * output: the deviation of the correction from r, in the same scale.
  * vp_unet_loss_grad runs forward and backward for the mean squared error and
  * keeps the gradients; vp_unet_adam_step applies Adam (beta 0.9/0.999, eps 1e-8).
  * vp_unet_precond is a vp_precond_fn (ctx = the network, bound to a contrast
- * with vp_unet_bind): z = ||r|| * net(r/||r||, q).
+ * with vp_unet_bind): z = r + (||r||/sqrt(n)) net(sqrt(n) r/||r||, q), so a
+ * network with a zero last layer is the identity (plain GMRES).
  * ------------------------------------------------------------------------- */
 typedef struct vp_unet_s* vp_unet;
 vp_status vp_unet_create(vp_unet* out, int S, int C);

@@ -186,6 +186,20 @@ __global__ void k_sub(float2* __restrict__ out, const float2* __restrict__ a, co
     out[i] = make_float2(a[i].x - b[i].x, a[i].y - b[i].y);
 }
 
+__global__ void k_pack_pair(float* __restrict__ x, float* __restrict__ t, const float2* __restrict__ r,
+                            const float* __restrict__ q, const float2* __restrict__ ustar, const float2* __restrict__ us,
+                            double s, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    x[i] = (float)(r[i].x * s);
+    x[n + i] = (float)(r[i].y * s);
+    x[2 * n + i] = q[i];
+    // target: the correction minus the residual (the network learns A^-1 - I)
+    const float ex = ustar[i].x - (us ? us[i].x : 0.f) - r[i].x, ey = ustar[i].y - (us ? us[i].y : 0.f) - r[i].y;
+    t[i] = (float)(ex * s);
+    t[n + i] = (float)(ey * s);
+  }
+}
+
 dim3 grid_for(long long n) {
   long long b = (n + 255) / 256;
   return dim3((unsigned)(b > 152 * 16 ? 152 * 16 : b));
@@ -537,6 +551,34 @@ vp_status vp_ls_solve(vp_plan plan, const float* q, const void* b, const void* u
     stats->seconds = std::chrono::duration<double>(t1 - t0).count();
   }
   return VP_OK;
+}
+
+vp_status vp_ls_training_pair(vp_plan plan, const float* q, const void* b, const void* u_s, const void* u_star,
+                              float* x_out, float* t_out, double* rnorm) {
+  long long n;
+  double k2;
+  vp_status st = check_plan(plan, &n, &k2);
+  if (st != VP_OK) return st;
+  if (!q || !b || !u_star || !x_out || !t_out) return ls_fail(VP_ERR_INVALID_ARG, "NULL argument");
+  Work w;
+  if ((st = alloc_work(w, n, 0, false)) != VP_OK) return ls_fail(st, w.err);
+  Ctx c{plan, q, n, k2, get_stream(plan)};
+  float2* r = reinterpret_cast<float2*>(w.d0);  // FP64 scratch reused as two complex64 vectors
+  float2* Au = r + n;
+  if (u_s) {
+    if ((st = op32(c, w, reinterpret_cast<const float2*>(u_s), Au)) != VP_OK) return st;
+    k_sub<<<grid_for(n), 256, 0, c.s>>>(r, reinterpret_cast<const float2*>(b), Au, n);
+  } else {
+    cudaMemcpyAsync(r, b, n * sizeof(float2), cudaMemcpyDeviceToDevice, c.s);
+  }
+  double nr = 0.0;
+  if ((st = norm2(c, w, r, &nr)) != VP_OK) return ls_fail(st, w.err);
+  if (!(nr > 0)) return ls_fail(VP_ERR_NUMERICAL, "zero residual");
+  k_pack_pair<<<grid_for(n), 256, 0, c.s>>>(x_out, t_out, r, q, reinterpret_cast<const float2*>(u_star),
+                                            reinterpret_cast<const float2*>(u_s), sqrt((double)n) / nr, n);
+  if (rnorm) *rnorm = nr;
+  cudaStreamSynchronize(c.s);
+  return cudaGetLastError() == cudaSuccess ? VP_OK : VP_ERR_CUDA;
 }
 
 const char* vp_ls_last_error(void) { return g_ls_error.c_str(); }

@@ -339,9 +339,11 @@ __global__ void k_pack_input(float* __restrict__ x, const float2* __restrict__ r
   }
 }
 
-__global__ void k_unpack_output(float2* __restrict__ z, const float* __restrict__ o, double s, long long n) {
+// z = r + s * o: the network output is the correction's deviation from r
+__global__ void k_unpack_output(float2* __restrict__ z, const float2* __restrict__ r, const float* __restrict__ o,
+                                double s, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    z[i] = make_float2((float)(o[i] * s), (float)(o[n + i] * s));
+    z[i] = make_float2((float)(r[i].x + o[i] * s), (float)(r[i].y + o[n + i] * s));
 }
 
 __global__ void __launch_bounds__(256) k_norm2c(const float2* __restrict__ x, long long n, double* __restrict__ part) {
@@ -673,7 +675,8 @@ vp_status vp_unet_bind(vp_unet u, const float* q) {
   return VP_OK;
 }
 
-// Preconditioner z = ||r|| * net([Re r, Im r]/||r||, q), a vp_precond_fn.
+// Preconditioner z = r + (||r||/sqrt(n)) net(sqrt(n) r/||r||, q), a vp_precond_fn:
+// inputs scaled to unit RMS, the network learns A^-1 - I.
 vp_status vp_unet_precond(void* ctx, const void* r, void* z, void* stream) {
   vp_unet u = reinterpret_cast<vp_unet>(ctx);
   if (!u || !u->q || !r || !z) return VP_ERR_INVALID_ARG;
@@ -692,10 +695,11 @@ vp_status vp_unet_precond(void* ctx, const void* r, void* z, void* stream) {
     cudaMemsetAsync(z, 0, n * sizeof(float2), s);
     return VP_OK;
   }
-  k_pack_input<<<g1(n), 256, 0, s>>>(u->x0, rr, u->q, 1.0 / nr, n);
+  const double rms = sqrt((double)n) / nr;
+  k_pack_input<<<g1(n), 256, 0, s>>>(u->x0, rr, u->q, rms, n);
   cudaError_t e = forward(u, u->x0, s);
   if (e != cudaSuccess) return VP_ERR_CUDA;
-  k_unpack_output<<<g1(n), 256, 0, s>>>(reinterpret_cast<float2*>(z), u->out, nr, n);
+  k_unpack_output<<<g1(n), 256, 0, s>>>(reinterpret_cast<float2*>(z), rr, u->out, 1.0 / rms, n);
   return cudaGetLastError() == cudaSuccess ? VP_OK : VP_ERR_CUDA;
 }
 

@@ -232,11 +232,12 @@ def unet_layer_shapes(C: int = 16, cin: int = 3, cout: int = 2):
 
 def unet_init_weights(seed: int, C: int = 16, cin: int = 3, cout: int = 2):
     """He-style normal weights [C_out][C_in][27] (float32), zero biases; the last
-    layer is scaled by 1/2."""
+    layer is scaled by 1/100 so that the residual-learning preconditioner starts
+    near the identity."""
     out = []
     for i, (co, ci) in enumerate(unet_layer_shapes(C, cin, cout)):
         z = normal(seed + i, co * ci * 27)
-        scale = np.sqrt(2.0 / (ci * 27)) * (0.5 if i == 9 else 1.0)
+        scale = np.sqrt(2.0 / (ci * 27)) * (0.01 if i == 9 else 1.0)
         out.append(((z * scale).reshape(co, ci, 27).astype(np.float32), np.zeros(co, dtype=np.float32)))
     return out
 

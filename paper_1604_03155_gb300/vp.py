@@ -81,6 +81,8 @@ _SIGNATURES = {
     "vp_ls_rhs": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "vp_ls_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "vp_ls_last_error": (c_char_p, []),
+    "vp_ls_training_pair": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                    ctypes.POINTER(c_double)]),
     "vp_unet_create": (c_int, [ctypes.POINTER(c_void_p), c_int, c_int]),
     "vp_unet_param_count": (c_int, [c_void_p, ctypes.POINTER(c_size_t)]),
     "vp_unet_set_stream": (c_int, [c_void_p, c_void_p]),
@@ -433,6 +435,14 @@ def ls_solve(plan: Plan, q, b, u, u_inc=None, tol=1e-6, maxit=1000, restart=30, 
     _lscheck(lib().vp_ls_solve(plan.handle, _ptr(q), _ptr(b), _ptr(u_inc) if u_inc is not None else None, _ptr(u),
                                ctypes.byref(opts), ctypes.byref(st)))
     return {k: getattr(st, k) for k, _ in LSStats._fields_}
+
+
+def ls_training_pair(plan: Plan, q, b, u_s, u_star, x_out, t_out) -> float:
+    """Network input/target of one (residual, correction) pair; returns ||r||."""
+    rn = c_double()
+    _lscheck(lib().vp_ls_training_pair(plan.handle, _ptr(q), _ptr(b), _ptr(u_s) if u_s is not None else None,
+                                       _ptr(u_star), _ptr(x_out), _ptr(t_out), ctypes.byref(rn)))
+    return rn.value
 
 
 class UNet:

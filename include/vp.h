@@ -54,8 +54,28 @@ typedef enum {
 
 typedef enum { VP_LAPLACE = 0, VP_HELMHOLTZ = 1 } vp_kernel;
 
-/* Arithmetic of the apply.  The precompute is always FP64. */
-typedef enum { VP_FP32 = 0, VP_FP64 = 1 } vp_precision;
+/* Arithmetic of the apply.  The precompute is always FP64.
+ *  VP_FP32, VP_FP64   every pass in that precision (FP32 / FP64 data types).
+ *  VP_TC_*            FP32 data and FP32 passes, except the fused axis-0 pass
+ *                     of the 3D apply (forward 2N transform, multiplier,
+ *                     inverse 2N transform), whose 2N = 16 x N2 transforms run
+ *                     as radix-16 and radix-N2 complex GEMMs on the tensor
+ *                     cores with the FP32 operands split into 16-bit parts
+ *                     and FP32 accumulation (a project addition; the paper's
+ *                     apply is FP64):
+ *                       BF16X2  x = x0 + x1 (BF16), 3 partial products
+ *                       FP16X2  x = x0 + x1 (FP16, power-of-two scaled), 3 products
+ *                       BF16X3  x = x0 + x1 + x2 (BF16), 6 partial products
+ *                     Only 3D plans with 2N in {256, 512} (N = 128, 256) and
+ *                     only vp_apply (not vp_apply_grad); otherwise
+ *                     VP_ERR_UNSUPPORTED. */
+typedef enum {
+  VP_FP32 = 0,
+  VP_FP64 = 1,
+  VP_TC_BF16X2 = 2,
+  VP_TC_FP16X2 = 3,
+  VP_TC_BF16X3 = 4
+} vp_precision;
 
 /* Gradient definition (Section 3, spectral differentiation):
  *  VP_GRAD_EXACT      derivative kernels T_j = inverse 4N transform of i s_j G^L
@@ -133,7 +153,9 @@ vp_status vp_plan_get_timing(vp_plan plan, int cap, int* npass, const char** nam
 /* Number of kernel launches one vp_apply / vp_apply_grad issues. */
 vp_status vp_plan_launch_count(vp_plan plan, int grad, int* launches);
 
-/* Synchronises the plan's stream and reports the first device-side error. */
+/* Synchronises the plan's stream and reports the first device-side error:
+ * a CUDA error, or VP_ERR_TIMEOUT when a bounded wait of the tensor-core pass
+ * gave up (the error word is then cleared). */
 vp_status vp_plan_status(vp_plan plan);
 
 /* Message of the last failing call on this plan (plan may be NULL for
@@ -237,6 +259,14 @@ vp_status vp_ls_solve(vp_plan plan, const float* q, const void* b, const void* u
  * 3 x N^3 floats and the target t = s (e - r) as 2 x N^3 floats. */
 vp_status vp_ls_training_pair(vp_plan plan, const float* q, const void* b, const void* u_s, const void* u_star,
                               float* x_out, float* t_out, double* rnorm);
+/* Orthonormal Krylov basis of the plain operator started from b: the vectors
+ * v_0 = b/||b||, v_1, ..., v_m that the first cycle of unpreconditioned GMRES
+ * builds (classical Gram-Schmidt applied twice, FP64 inner products), with
+ * A [v_0..v_{m-1}] = [v_0..v_m] H, H upper Hessenberg with h_{j+1,j} > 0.
+ * V: device buffer of (m+1) x N^3 complex64, vector j at offset j N^3;
+ * *count: vectors written (m+1; fewer only at an exact breakdown).  m in
+ * [1, 64].  Draws the (A v_j, v_j) training pairs of the learned preconditioner. */
+vp_status vp_ls_krylov_basis(vp_plan plan, const float* q, const void* b, int m, void* V, int* count);
 const char* vp_ls_last_error(void);
 
 /* ---------------------------------------------------------------------------
@@ -267,6 +297,8 @@ vp_status vp_unet_get_weights(vp_unet net, int which /* 0 FP32, 1 BF16-rounded, 
 vp_status vp_unet_forward(vp_unet net, const float* in, float* out);
 vp_status vp_unet_loss_grad(vp_unet net, const float* in, const float* target, double* loss);
 vp_status vp_unet_adam_step(vp_unet net, double lr);
+/* Leaky-ReLU slope in [0, 1] (default 0.1); 1 makes the network linear in its input. */
+vp_status vp_unet_set_slope(vp_unet net, double slope);
 vp_status vp_unet_bind(vp_unet net, const float* q);
 vp_status vp_unet_precond(void* ctx, const void* r, void* z, void* stream);
 const char* vp_unet_last_error(vp_unet net);

@@ -101,3 +101,23 @@ def gmres(matvec, b: np.ndarray, tol: float = 1e-10, restart: int = 40, maxit: i
         if hist[-1] < tol:
             break
     return x, it, hist
+
+
+def arnoldi(matvec, b: np.ndarray, m: int):
+    """m steps of the Arnoldi process (Saad & Schultz 1986) from b, modified
+    Gram-Schmidt applied twice (Kahan-Parlett "twice is enough"; one pass loses
+    orthogonality once h_{j+1,j} becomes small): returns V (m+1 orthonormal
+    vectors, v_0 = b/||b||) and the (m+1) x m upper Hessenberg H with
+    A V[:m] = V H and h_{j+1,j} > 0."""
+    V = [b / np.linalg.norm(b.ravel())]
+    H = np.zeros((m + 1, m), dtype=np.complex128)
+    for j in range(m):
+        w = matvec(V[j])
+        for _ in range(2):
+            for i in range(j + 1):
+                h = np.vdot(V[i].ravel(), w.ravel())
+                H[i, j] += h
+                w = w - h * V[i]
+        H[j + 1, j] = np.linalg.norm(w.ravel())
+        V.append(w / H[j + 1, j])
+    return np.stack(V), H

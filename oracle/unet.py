@@ -13,7 +13,8 @@ sample of S^3 voxels, channel-major [C][S][S][S]:
 conv: 3x3x3 cross-correlation with zero padding 1 and a bias,
   y[co](p) = b[co] + sum_ci sum_k w[co, ci, k] x[ci](p + k - 1),
   k = (kz, ky, kx) in {0,1,2}^3 flattened as (kz*3 + ky)*3 + kx;
-activation: leaky ReLU, slope 0.1, after every conv but the last;
+activation: leaky ReLU, slope 0.1 by default (1: a linear network), after every
+conv but the last;
 pool: mean of 2x2x2 blocks; up: nearest-neighbour x2.
 Loss: mean squared error over all output elements.
 
@@ -57,12 +58,12 @@ def conv3d_backward(x, w, dy):
     return dxp[:, 1:-1, 1:-1, 1:-1], dw, db
 
 
-def lrelu(x):
-    return np.where(x > 0, x, SLOPE * x)
+def lrelu(x, slope=SLOPE):
+    return np.where(x > 0, x, slope * x)
 
 
-def lrelu_back(x, dy):
-    return np.where(x > 0, dy, SLOPE * dy)
+def lrelu_back(x, dy, slope=SLOPE):
+    return np.where(x > 0, dy, slope * dy)
 
 
 def pool(x):
@@ -83,16 +84,16 @@ def up_back(dy):
     return dy.reshape(C, S // 2, 2, S // 2, 2, S // 2, 2).sum(axis=(2, 4, 6))
 
 
-def forward(params, x):
+def forward(params, x, slope=SLOPE):
     """params: list of (w, b); returns (output, cache)."""
-    c = {}
+    c = {"slope": slope}
     h = x
     acts = []
 
     def cv(i, inp, act=True):
         z = conv3d(inp, *params[i])
         acts.append((i, inp, z))
-        return lrelu(z) if act else z
+        return lrelu(z, slope) if act else z
 
     h = cv(0, h)
     s1 = cv(1, h)
@@ -116,7 +117,7 @@ def backward(params, cache, dout):
 
     def cvb(i, dh, act=True):
         inp, z = acts[i]
-        dz = lrelu_back(z, dh) if act else dh
+        dz = lrelu_back(z, dh, cache["slope"]) if act else dh
         dx, dw, db = conv3d_backward(inp, params[i][0], dz)
         grads[i] = (dw, db)
         return dx
@@ -142,8 +143,8 @@ def mse(out, target):
     return float(np.mean((out - target) ** 2)), 2.0 * (out - target) / out.size
 
 
-def loss_and_grads(params, x, target):
-    out, cache = forward(params, x)
+def loss_and_grads(params, x, target, slope=SLOPE):
+    out, cache = forward(params, x, slope)
     L, dout = mse(out, target)
     grads, _ = backward(params, cache, dout)
     return L, grads

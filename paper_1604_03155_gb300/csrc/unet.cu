@@ -5,8 +5,8 @@
 //   E1a conv 3->C, E1b conv C->C -> s1 (S); pool; E2a, E2b -> s2 (S/2); pool;
 //   B1, B2 (S/4); up, concat [up, s2], D2a 2C->C, D2b (S/2); up, concat
 //   [up, s1], D1a 2C->C, D1b C->2 (linear) (S).
-// conv = 3x3x3 cross-correlation, zero padding 1, bias; leaky ReLU (0.1) after
-// every conv but the last; pool = 2x2x2 mean; up = nearest x2.
+// conv = 3x3x3 cross-correlation, zero padding 1, bias; leaky ReLU (slope 0.1
+// by default, 1 = linear network) after every conv but the last; pool = 2x2x2 mean; up = nearest x2.
 // Weights are kept in FP32 for the optimiser and rounded to bfloat16 for every
 // forward and backward pass (BF16 weights, FP32 arithmetic).
 //
@@ -34,16 +34,15 @@
 
 namespace {
 
-constexpr float kSlope = 0.1f;
 constexpr int kLayers = 10;
 constexpr int kTile = 8, kHalo = 10, kHalo3 = 1000, kConvCh = 4, kWgCh = 16;
 
-__device__ __forceinline__ float lrelu(float v) { return v > 0.f ? v : kSlope * v; }
+__device__ __forceinline__ float lrelu(float v, float slope) { return v > 0.f ? v : slope * v; }
 
 template <int CO>
 __global__ void __launch_bounds__(512) k_conv3d(const float* __restrict__ x1, int c1, const float* __restrict__ x2,
                                                 int c2, const float* __restrict__ w, const float* __restrict__ bias,
-                                                float* __restrict__ y, int S, int act) {
+                                                float* __restrict__ y, int S, int act, float slope) {
   __shared__ float halo[kConvCh][kHalo3];
   __shared__ __align__(16) float ws[kConvCh * 27][CO < 4 ? 4 : CO];
   const int Ci = c1 + c2;
@@ -103,7 +102,7 @@ __global__ void __launch_bounds__(512) k_conv3d(const float* __restrict__ x1, in
   if (gz < S && gy < S && gx < S) {
     const long long idx = ((long long)gz * S + gy) * S + gx;
 #pragma unroll
-    for (int co = 0; co < CO; ++co) y[(long long)co * S3 + idx] = act ? lrelu(acc[co]) : acc[co];
+    for (int co = 0; co < CO; ++co) y[(long long)co * S3 + idx] = act ? lrelu(acc[co], slope) : acc[co];
   }
 }
 
@@ -278,9 +277,10 @@ __global__ void k_pool_back(const float* __restrict__ dc, float* __restrict__ df
 }
 
 // dz = dy * lrelu'(y) (y is the activated output: the sign is preserved)
-__global__ void k_lrelu_back(float* __restrict__ dz, const float* __restrict__ dy, const float* __restrict__ y, long long n) {
+__global__ void k_lrelu_back(float* __restrict__ dz, const float* __restrict__ dy, const float* __restrict__ y, long long n,
+                             float slope) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    dz[i] = y[i] > 0.f ? dy[i] : kSlope * dy[i];
+    dz[i] = y[i] > 0.f ? dy[i] : slope * dy[i];
 }
 
 
@@ -370,6 +370,7 @@ dim3 g1(long long n) {
 
 struct vp_unet_s {
   int S = 0, C = 0;
+  float slope = 0.1f;  // leaky-ReLU slope; 1 makes the network linear
   int device = 0;
   cudaStream_t stream = nullptr;
   int co[kLayers], ci[kLayers];
@@ -409,9 +410,9 @@ cudaError_t conv(vp_unet u, const float* x1, int c1, const float* x2, int c2, co
   const int tpd = (S + kTile - 1) / kTile;
   const dim3 grid(tpd * tpd * tpd);
   switch (CO) {
-    case 2: k_conv3d<2><<<grid, 512, 0, s>>>(x1, c1, x2, c2, w, b, y, S, act); break;
-    case 16: k_conv3d<16><<<grid, 512, 0, s>>>(x1, c1, x2, c2, w, b, y, S, act); break;
-    case 32: k_conv3d<32><<<grid, 512, 0, s>>>(x1, c1, x2, c2, w, b, y, S, act); break;
+    case 2: k_conv3d<2><<<grid, 512, 0, s>>>(x1, c1, x2, c2, w, b, y, S, act, u->slope); break;
+    case 16: k_conv3d<16><<<grid, 512, 0, s>>>(x1, c1, x2, c2, w, b, y, S, act, u->slope); break;
+    case 32: k_conv3d<32><<<grid, 512, 0, s>>>(x1, c1, x2, c2, w, b, y, S, act, u->slope); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -474,45 +475,45 @@ cudaError_t backward(vp_unet u, const float* in, cudaStream_t s) {
   if ((e = wgrad(u, 9, u->a9, C, nullptr, 0, u->dout, S, s)) != cudaSuccess) return e;
   if ((e = dgrad(u, 9, u->dout, u->gA, S, s)) != cudaSuccess) return e;  // d a9
   // D1a: input concat[u1, s1], output a9
-  k_lrelu_back<<<g1(n1), 256, 0, s>>>(u->gA, u->gA, u->a9, n1);
+  k_lrelu_back<<<g1(n1), 256, 0, s>>>(u->gA, u->gA, u->a9, n1, u->slope);
   if ((e = wgrad(u, 8, u->u1, C, u->s1, C, u->gA, S, s)) != cudaSuccess) return e;
   if ((e = dgrad(u, 8, u->gA, u->gB, S, s)) != cudaSuccess) return e;  // [d u1, d s1] (2C)
   cudaMemcpyAsync(u->gS1, u->gB + n1, n1 * sizeof(float), cudaMemcpyDeviceToDevice, s);
   k_up<<<g1(n2), 256, 0, s>>>(u->gB, u->gC, C, S, 1);  // d a8 = up^T d u1
   // D2b: input a7, output a8
-  k_lrelu_back<<<g1(n2), 256, 0, s>>>(u->gC, u->gC, u->a8, n2);
+  k_lrelu_back<<<g1(n2), 256, 0, s>>>(u->gC, u->gC, u->a8, n2, u->slope);
   if ((e = wgrad(u, 7, u->a7, C, nullptr, 0, u->gC, S2, s)) != cudaSuccess) return e;
   if ((e = dgrad(u, 7, u->gC, u->gA, S2, s)) != cudaSuccess) return e;  // d a7
   // D2a: input concat[u2, s2], output a7
-  k_lrelu_back<<<g1(n2), 256, 0, s>>>(u->gA, u->gA, u->a7, n2);
+  k_lrelu_back<<<g1(n2), 256, 0, s>>>(u->gA, u->gA, u->a7, n2, u->slope);
   if ((e = wgrad(u, 6, u->u2, C, u->s2, C, u->gA, S2, s)) != cudaSuccess) return e;
   if ((e = dgrad(u, 6, u->gA, u->gB, S2, s)) != cudaSuccess) return e;  // [d u2, d s2]
   cudaMemcpyAsync(u->gS2, u->gB + n2, n2 * sizeof(float), cudaMemcpyDeviceToDevice, s);
   k_up<<<g1(n4), 256, 0, s>>>(u->gB, u->gC, C, S2, 1);  // d a6
   // B2: input a5, output a6
-  k_lrelu_back<<<g1(n4), 256, 0, s>>>(u->gC, u->gC, u->a6, n4);
+  k_lrelu_back<<<g1(n4), 256, 0, s>>>(u->gC, u->gC, u->a6, n4, u->slope);
   if ((e = wgrad(u, 5, u->a5, C, nullptr, 0, u->gC, S4, s)) != cudaSuccess) return e;
   if ((e = dgrad(u, 5, u->gC, u->gA, S4, s)) != cudaSuccess) return e;  // d a5
   // B1: input p2, output a5
-  k_lrelu_back<<<g1(n4), 256, 0, s>>>(u->gA, u->gA, u->a5, n4);
+  k_lrelu_back<<<g1(n4), 256, 0, s>>>(u->gA, u->gA, u->a5, n4, u->slope);
   if ((e = wgrad(u, 4, u->p2, C, nullptr, 0, u->gA, S4, s)) != cudaSuccess) return e;
   if ((e = dgrad(u, 4, u->gA, u->gC, S4, s)) != cudaSuccess) return e;  // d p2
   k_pool_back<<<g1(n2), 256, 0, s>>>(u->gC, u->gS2, C, S2, 1);        // d s2 += pool^T d p2
   // E2b: input a3, output s2
-  k_lrelu_back<<<g1(n2), 256, 0, s>>>(u->gS2, u->gS2, u->s2, n2);
+  k_lrelu_back<<<g1(n2), 256, 0, s>>>(u->gS2, u->gS2, u->s2, n2, u->slope);
   if ((e = wgrad(u, 3, u->a3, C, nullptr, 0, u->gS2, S2, s)) != cudaSuccess) return e;
   if ((e = dgrad(u, 3, u->gS2, u->gA, S2, s)) != cudaSuccess) return e;  // d a3
   // E2a: input p1, output a3
-  k_lrelu_back<<<g1(n2), 256, 0, s>>>(u->gA, u->gA, u->a3, n2);
+  k_lrelu_back<<<g1(n2), 256, 0, s>>>(u->gA, u->gA, u->a3, n2, u->slope);
   if ((e = wgrad(u, 2, u->p1, C, nullptr, 0, u->gA, S2, s)) != cudaSuccess) return e;
   if ((e = dgrad(u, 2, u->gA, u->gC, S2, s)) != cudaSuccess) return e;  // d p1
   k_pool_back<<<g1(n1), 256, 0, s>>>(u->gC, u->gS1, C, S, 1);          // d s1 += pool^T d p1
   // E1b: input a1, output s1
-  k_lrelu_back<<<g1(n1), 256, 0, s>>>(u->gS1, u->gS1, u->s1, n1);
+  k_lrelu_back<<<g1(n1), 256, 0, s>>>(u->gS1, u->gS1, u->s1, n1, u->slope);
   if ((e = wgrad(u, 1, u->a1, C, nullptr, 0, u->gS1, S, s)) != cudaSuccess) return e;
   if ((e = dgrad(u, 1, u->gS1, u->gA, S, s)) != cudaSuccess) return e;  // d a1
   // E1a: input x0, output a1
-  k_lrelu_back<<<g1(n1), 256, 0, s>>>(u->gA, u->gA, u->a1, n1);
+  k_lrelu_back<<<g1(n1), 256, 0, s>>>(u->gA, u->gA, u->a1, n1, u->slope);
   if ((e = wgrad(u, 0, in, 3, nullptr, 0, u->gA, S, s)) != cudaSuccess) return e;
   return cudaGetLastError();
 }
@@ -667,6 +668,12 @@ vp_status vp_unet_adam_step(vp_unet u, double lr) {
   k_adam<<<g1(u->nparams), 256, 0, u->stream>>>(u->w, u->wq, u->g, u->m, u->v, u->nparams, (float)lr, b1, b2, 1e-8f,
                                                  c1, c2);
   return cudaGetLastError() == cudaSuccess ? VP_OK : VP_ERR_CUDA;
+}
+
+vp_status vp_unet_set_slope(vp_unet u, double slope) {
+  if (!u || !(slope >= 0.0) || slope > 1.0) return VP_ERR_INVALID_ARG;
+  u->slope = (float)slope;
+  return VP_OK;
 }
 
 vp_status vp_unet_bind(vp_unet u, const float* q) {

@@ -51,6 +51,10 @@ struct vp_plan_s {
   bool grad_built = false;
   double2* tw64 = nullptr;
   float2* tw32 = nullptr;
+  // tensor-core fused pass (VP_TC_*): DFT matrices of the current split, error word
+  uint16_t* tcB = nullptr;
+  int tc_split = -1;
+  int* d_err = nullptr;
 
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -256,6 +260,8 @@ void set_async(PassArgs<Real>& a, bool contig, int nin) {
   a.async_ok = ok ? 1 : 0;
 }
 
+bool is_tc(vp_precision pr) { return pr == VP_TC_BF16X2 || pr == VP_TC_FP16X2 || pr == VP_TC_BF16X3; }
+
 template <typename Real>
 cudaError_t launch_pass(vp_plan p, int pass, PassKind kind, const PassArgs<Real>& a) {
   TimedLaunch tl{pass, nullptr, nullptr};
@@ -265,7 +271,19 @@ cudaError_t launch_pass(vp_plan p, int pass, PassKind kind, const PassArgs<Real>
     cudaEventRecord(tl.start, p->stream);
   }
   cudaError_t e;
-  if (sizeof(Real) == 4)
+  if (sizeof(Real) == 4 && pass == P_FUSED && p->tc_split >= 0 && is_tc(p->prec)) {
+    const PassArgs<float>& f = reinterpret_cast<const PassArgs<float>&>(a);
+    TcFusedArgs t;
+    t.in = reinterpret_cast<const float2*>(f.in);
+    t.out = reinterpret_cast<float2*>(f.out);
+    t.pitch_pos = f.in_pitch_pos;
+    t.npencils = (long long)f.O * f.I;
+    t.mult = reinterpret_cast<const float2*>(f.fields[0].mult);
+    t.tw = p->tw32;
+    t.bmat = p->tcB;
+    t.err = p->d_err;
+    e = launch_tc_fused(p->n2, p->tc_split, t, p->stream);
+  } else if (sizeof(Real) == 4)
     e = launch_pass_f32(kind, p->n2, reinterpret_cast<const PassArgs<float>&>(a), p->stream);
   else
     e = launch_pass_f64(kind, p->n2, reinterpret_cast<const PassArgs<double>&>(a), p->stream);
@@ -461,6 +479,8 @@ vp_status apply_common(vp_plan p, const void* f, void* phi, void* grad, vp_dtype
   bool real_io = false;
   vp_status st = check_dtype(p, dtype, &real_io);
   if (st != VP_OK) return st;
+  if (want_grad && is_tc(p->prec))
+    return fail(p, VP_ERR_UNSUPPORTED, "the tensor-core precisions serve vp_apply only; use VP_FP32 for gradients");
   VP_CUDA(p, cudaSetDevice(p->device));
   if (want_grad && p->gmode == VP_GRAD_EXACT) {
     st = build_grad(p);
@@ -648,7 +668,33 @@ vp_status vp_plan_set_stream(vp_plan p, void* stream) {
 
 vp_status vp_plan_set_precision(vp_plan p, vp_precision precision) {
   if (!p) return fail(nullptr, VP_ERR_INVALID_ARG, "plan is NULL");
-  if (precision != VP_FP32 && precision != VP_FP64) return fail(p, VP_ERR_INVALID_ARG, "unknown precision");
+  if (precision != VP_FP32 && precision != VP_FP64 && !is_tc(precision))
+    return fail(p, VP_ERR_INVALID_ARG, "unknown precision");
+  if (is_tc(precision)) {
+    if (p->d != 3 || !tc_length_supported(p->n2))
+      return fail(p, VP_ERR_UNSUPPORTED, "tensor-core precisions need a 3D plan with N = 128 or 256");
+    const int split = precision == VP_TC_BF16X2 ? 0 : (precision == VP_TC_FP16X2 ? 1 : 2);
+    if (p->tc_split != split) {
+      VP_CUDA(p, cudaSetDevice(p->device));
+      VP_CUDA(p, cudaStreamSynchronize(p->stream));
+      const size_t bytes = tc_bmat_bytes(p->n2, split);
+      if (p->tcB) {
+        cudaFree(p->tcB);
+        p->device_bytes -= tc_bmat_bytes(p->n2, p->tc_split);
+        p->tcB = nullptr;
+        p->tc_split = -1;
+      }
+      VP_CUDA(p, cudaMalloc(&p->tcB, bytes));
+      p->device_bytes += bytes;
+      if (!p->d_err) {
+        VP_CUDA(p, cudaMalloc(&p->d_err, sizeof(int)));
+        VP_CUDA(p, cudaMemset(p->d_err, 0, sizeof(int)));
+      }
+      VP_CUDA(p, tc_build_bmat(p->n2, split, p->tcB, p->stream));
+      VP_CUDA(p, cudaStreamSynchronize(p->stream));
+      p->tc_split = split;
+    }
+  }
   p->prec = precision;
   return VP_OK;
 }
@@ -746,6 +792,14 @@ vp_status vp_plan_status(vp_plan p) {
   VP_CUDA(p, cudaSetDevice(p->device));
   VP_CUDA(p, cudaStreamSynchronize(p->stream));
   VP_CUDA(p, cudaGetLastError());
+  if (p->d_err) {
+    int h = 0;
+    VP_CUDA(p, cudaMemcpy(&h, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) {
+      VP_CUDA(p, cudaMemset(p->d_err, 0, sizeof(int)));
+      return fail(p, VP_ERR_TIMEOUT, "a bounded wait for tensor-core completion timed out");
+    }
+  }
   return VP_OK;
 }
 
@@ -780,6 +834,8 @@ vp_status vp_destroy(vp_plan p) {
   }
   cudaFree(p->tw64);
   cudaFree(p->tw32);
+  cudaFree(p->tcB);
+  cudaFree(p->d_err);
   cudaFree(p->ws);
   cudaFree(p->stage);
   for (const TimedLaunch& t : p->timed) {

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <stddef.h>
+#include <stdint.h>
 
 #include "../../include/vp.h"
 #include "pencil_fft.cuh"
@@ -42,6 +43,23 @@ bool pass_shape_f64(PassKind kind, int n, PassShape* out);
 
 // FFT lengths with compiled passes (2N).
 bool fft_length_built(int n);
+
+// tc_fused.cu: the fused axis-0 pass of the 3D apply on the tensor cores
+// (2N = 256 or 512).  split: 0 BF16 x 2, 1 FP16 x 2 (scaled), 2 BF16 x 3.
+struct TcFusedArgs {
+  const float2* in;    // spectrum after the two forward passes (in place allowed)
+  float2* out;
+  long long pitch_pos; // element stride between positions along axis 0 (= (2N)^2)
+  long long npencils;  // pencils (= (2N)^2), a multiple of 8
+  const float2* mult;  // FP32 multiplier octant (N+1)^3, pre-scaled by 1/(2N)^3
+  const float2* tw;    // twiddles exp(-2 pi i q/2N), q in [0, 2N)
+  const uint16_t* bmat;  // DFT matrices from tc_build_bmat
+  int* err;            // device error word: bit 0 = a bounded wait timed out
+};
+bool tc_length_supported(int n);
+size_t tc_bmat_bytes(int n, int split);
+cudaError_t tc_build_bmat(int n, int split, uint16_t* out, cudaStream_t s);
+cudaError_t launch_tc_fused(int n, int split, const TcFusedArgs& a, cudaStream_t s);
 
 // vp_capi.cu: the device a plan was created on; the scratch bytes of one
 // potential-only apply; that apply on a caller-supplied workspace (device

@@ -1,12 +1,14 @@
 """Training and evaluation of the learned Lippmann-Schwinger preconditioner.
 
-Training pairs (r, e) with A e = r come from the operator and the plain
-solver on seeded contrasts: the converged field u* with r = b, and the Krylov
-vectors x_0 = b, x_{j+1} = A x_j with (r, e) = (x_{j+1}, x_j).  With
-s = sqrt(n)/||r|| the network learns (s r, q) -> s (e - r), i.e. A^-1 - I, and
-the preconditioner is z = r + net(s r, q)/s.  Pairs are generated on the fly (one contrast at a time) and the
-network is updated with Adam after each pair; all arithmetic runs in the
-library's kernels (vp_ls_*, vp_unet_*).
+Any field x gives an exact pair (r, e) = (A x, x).  The fields used are the
+ones the plain solver produces on seeded contrasts: the orthonormal Krylov
+basis v_0 = b/||b||, ..., v_m of its first GMRES cycle (the kind of vector the
+flexible iteration later hands the preconditioner) and the converged field u*
+(r = b).  With s = sqrt(n)/||r|| the network learns (s r, q) -> s (e - r),
+i.e. A^-1 - I, and the preconditioner is z = r + net(s r, q)/s.  Pairs are
+generated on the fly (one contrast at a time) and the network is updated with
+Adam after each pair; all arithmetic runs in the library's kernels (vp_ls_*,
+vp_unet_*).
 """
 from __future__ import annotations
 
@@ -28,33 +30,30 @@ def problem(plan, N: int, k: float, seed: int, dev):
 
 def train(plan, net, N: int, k: float, seeds, krylov: int = 12, lr: float = 1e-3, steps_per_pair: int = 1,
           restart: int = 20, dev="cuda:0", log=None) -> dict:
-    """Online training.  Any field x gives an exact pair (r = A x, e = x); the
-    fields used are the Krylov vectors x_0 = b, x_{j+1} = A x_j (the space the
-    flexible GMRES iteration explores, whose Arnoldi vectors the preconditioner
-    is applied to) and the converged field u* (r = b)."""
+    """Online training on the pairs (A v_j, v_j), j = 0..krylov, and (b, u*)
+    of each contrast in ``seeds``."""
     import torch
     x = torch.empty((3, N, N, N), dtype=torch.float32, device=dev)
     t = torch.empty((2, N, N, N), dtype=torch.float32, device=dev)
     losses = []
     t0 = time.perf_counter()
+    per = None
     for ci, seed in enumerate(seeds):
         q, uinc, b = problem(plan, N, k, seed, dev)
         ustar = torch.zeros_like(b)
         vp.ls_solve(plan, q, b, ustar, tol=1e-7, maxit=3000, restart=restart)
         pairs = [(b, ustar)]
-        xj = b
-        for _ in range(krylov):
-            xn = vp.ls_operator(plan, q, xj)
-            pairs.append((xn, xj))
-            xj = xn
+        for v in vp.ls_krylov_basis(plan, q, b, krylov):
+            pairs.append((vp.ls_operator(plan, q, v), v))
+        per = len(pairs)
         for r, e in pairs:
             vp.ls_training_pair(plan, q, r, None, e, x, t)
             for _ in range(steps_per_pair):
                 losses.append(net.loss_grad(x, t))
                 net.adam_step(lr)
         if log and (ci + 1) % 25 == 0:
-            log(f"contrast {ci + 1}/{len(seeds)} loss {np.mean(losses[-25 * len(pairs):]):.4e}")
-    per = krylov + 1
+            log(f"contrast {ci + 1}/{len(seeds)} loss {np.mean(losses[-25 * per:]):.4e}")
+    per = per or 1
     return {"pairs": len(losses), "first_loss": float(np.mean(losses[:per * 2])),
             "last_loss": float(np.mean(losses[-per * 2:])), "seconds": time.perf_counter() - t0}
 

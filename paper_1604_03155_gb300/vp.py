@@ -27,7 +27,7 @@ VP_R32, VP_C64, VP_R64, VP_C128 = 0, 1, 2, 3
 VP_ARRAY_T, VP_ARRAY_GHAT, VP_ARRAY_TJ, VP_ARRAY_GHATJ = 0, 1, 2, 3
 
 KERNELS = {"laplace": VP_LAPLACE, "helmholtz": VP_HELMHOLTZ}
-PRECISIONS = {"fp32": VP_FP32, "fp64": VP_FP64}
+PRECISIONS = {"fp32": VP_FP32, "fp64": VP_FP64, "tc_bf16x2": 2, "tc_fp16x2": 3, "tc_bf16x3": 4}
 GRAD_MODES = {"exact": VP_GRAD_EXACT, "spectral2n": VP_GRAD_SPECTRAL2N}
 
 
@@ -83,6 +83,7 @@ _SIGNATURES = {
     "vp_ls_last_error": (c_char_p, []),
     "vp_ls_training_pair": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                     ctypes.POINTER(c_double)]),
+    "vp_ls_krylov_basis": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, ctypes.POINTER(c_int)]),
     "vp_unet_create": (c_int, [ctypes.POINTER(c_void_p), c_int, c_int]),
     "vp_unet_param_count": (c_int, [c_void_p, ctypes.POINTER(c_size_t)]),
     "vp_unet_set_stream": (c_int, [c_void_p, c_void_p]),
@@ -92,6 +93,7 @@ _SIGNATURES = {
     "vp_unet_loss_grad": (c_int, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_double)]),
     "vp_unet_adam_step": (c_int, [c_void_p, c_double]),
     "vp_unet_bind": (c_int, [c_void_p, c_void_p]),
+    "vp_unet_set_slope": (c_int, [c_void_p, c_double]),
     "vp_unet_precond": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "vp_unet_last_error": (c_char_p, [c_void_p]),
     "vp_unet_destroy": (c_int, [c_void_p]),
@@ -445,10 +447,21 @@ def ls_training_pair(plan: Plan, q, b, u_s, u_star, x_out, t_out) -> float:
     return rn.value
 
 
+def ls_krylov_basis(plan: Plan, q, b, m: int):
+    """Orthonormal Krylov basis v_0..v_m of the plain operator from b, as an
+    (m+1, *b.shape) complex64 tensor (fewer rows only at an exact breakdown)."""
+    import torch
+    V = torch.empty((m + 1,) + tuple(b.shape), dtype=torch.complex64, device=b.device)
+    cnt = c_int()
+    plan._sync_stream_to_torch(b)
+    _lscheck(lib().vp_ls_krylov_basis(plan.handle, _ptr(q), _ptr(b), m, _ptr(V), ctypes.byref(cnt)))
+    return V[:cnt.value]
+
+
 class UNet:
     """The learned preconditioner network (vp_unet_*)."""
 
-    def __init__(self, S: int, C: int = 16, weights=None):
+    def __init__(self, S: int, C: int = 16, weights=None, slope: float = 0.1):
         out = c_void_p()
         st = lib().vp_unet_create(ctypes.byref(out), S, C)
         if st != VP_OK:
@@ -457,6 +470,7 @@ class UNet:
         n = c_size_t()
         lib().vp_unet_param_count(self.handle, ctypes.byref(n))
         self.nparams = n.value
+        self._check(lib().vp_unet_set_slope(self.handle, slope))
         if weights is not None:
             self.set_weights(weights)
 

@@ -29,19 +29,19 @@ def _rel(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-30))
 
 
-@pytest.mark.parametrize("S", [8, 16])
-def test_unet_forward_loss_and_gradients_match_oracle(S):
+@pytest.mark.parametrize("S,slope", [(8, 0.1), (16, 0.1), (8, 1.0)])
+def test_unet_forward_loss_and_gradients_match_oracle(S, slope):
     layers = _weights(I.BASE_SEED + 300, bias_seed=I.BASE_SEED + 400)
-    net = UNet(S, 16, weights=layers)
+    net = UNet(S, 16, weights=layers, slope=slope)
     x = I.random_complex_field(I.BASE_SEED + 301, (3, S, S, S)).real.astype(np.float32)
     t = I.random_complex_field(I.BASE_SEED + 302, (2, S, S, S)).real.astype(np.float32)
     xd, td = torch.from_numpy(x).to(DEV), torch.from_numpy(t).to(DEV)
     out = net.forward(xd).cpu().numpy()
     params = [(w.astype(np.float64), b.astype(np.float64)) for w, b in layers]
-    ref, _ = OU.forward(params, x.astype(np.float64))
+    ref, _ = OU.forward(params, x.astype(np.float64), slope)
     assert _rel(out, ref) < 1e-5
     loss = net.loss_grad(xd, td)
-    L, grads = OU.loss_and_grads(params, x.astype(np.float64), t.astype(np.float64))
+    L, grads = OU.loss_and_grads(params, x.astype(np.float64), t.astype(np.float64), slope)
     assert abs(loss - L) < 1e-5 * L
     g = net.get(2)
     off = 0
@@ -58,14 +58,17 @@ def test_unet_forward_loss_and_gradients_match_oracle(S):
 def test_unet_training_reduces_loss():
     S = 16
     net = UNet(S, 16, weights=_weights(I.BASE_SEED + 310))
-    x = torch.from_numpy(I.random_complex_field(I.BASE_SEED + 311, (3, S, S, S)).real.astype(np.float32)).to(DEV)
-    t = torch.from_numpy(0.3 * I.random_complex_field(I.BASE_SEED + 312, (2, S, S, S)).real.astype(np.float32)).to(DEV)
+    xh = I.random_complex_field(I.BASE_SEED + 311, (3, S, S, S)).real.astype(np.float32)
+    x = torch.from_numpy(xh).to(DEV)
+    # a target the network can represent (half of the first two input channels);
+    # the FP64 oracle with the same Adam steps ends near 0.12 x the first loss
+    t = torch.from_numpy(0.5 * xh[:2]).to(DEV)
     first = net.loss_grad(x, t)
     for _ in range(60):
         net.loss_grad(x, t)
         net.adam_step(3e-3)
     last = net.loss_grad(x, t)
-    assert last < 0.5 * first
+    assert last < 0.3 * first
     w, wq = net.get(0), net.get(1)
     assert np.array_equal(wq, I.bf16_round(w))  # BF16 copies of the FP32 master weights
     net.close()
@@ -92,6 +95,19 @@ def test_ls_solve_matches_oracle_dense_solve():
     # the operator entry point agrees with the oracle operator
     Au = vp.ls_operator(plan, q, u).cpu().numpy()
     assert np.linalg.norm((Au - prob.op(got.astype(np.complex128))).ravel()) / np.linalg.norm(Au.ravel()) < 1e-5
+
+
+def test_krylov_basis_matches_oracle_arnoldi():
+    N, k, m = 12, 6.0, 8
+    plan, q, uinc, b = _ls_setup(N, k, I.LS_TRAIN_SEED)
+    V = vp.ls_krylov_basis(plan, q, b, m).cpu().numpy().astype(np.complex128)
+    assert V.shape == (m + 1, N, N, N)
+    prob = OLS.LSProblem(N, k, I.ls_contrast(I.LS_TRAIN_SEED, N).astype(np.float32).astype(np.float64))
+    Vr, _ = OLS.arnoldi(prob.op, b.cpu().numpy().astype(np.complex128), m)
+    G = V.reshape(m + 1, -1).conj() @ V.reshape(m + 1, -1).T
+    assert np.abs(G - np.eye(m + 1)).max() < 1e-5
+    for j in range(m + 1):
+        assert np.linalg.norm((V[j] - Vr[j]).ravel()) < 1e-4, j
 
 
 def test_ls_solve_full_size_true_residual():

@@ -1,0 +1,106 @@
+"""Tensor-core precision variants of the 3D apply: the fused axis-0 pass runs
+its 2N = 16 x N2 transforms as split-operand complex GEMMs (tcgen05) with FP32
+accumulation; every other pass is the FP32 one.  Checked against the FP64
+oracle (2N FFT form) and against the FP32 path on the same plan.
+
+Error bars.  A value split into 16-bit parts keeps a relative residual of
+about 2^-(p+1) per part (p = 8 significant bits for BF16, 11 for FP16), and the
+largest dropped partial product is of the same order: BF16 x 2 ~ 2^-17,
+FP16 x 2 ~ 2^-23, BF16 x 3 ~ 2^-25 per operand.  A pencil passes four GEMM
+stages (F1, F3, I1, I3) of 16-64 terms each.  Measured on GB300 (N = 128,
+Helmholtz k = 30 / Laplace; N = 256, k = 60 against the FP32 path):
+BF16 x 2 3.1e-6 / 1.6e-6 / 5.0e-6, FP16 x 2 8.4e-7 / 5.9e-7 / 9.3e-7,
+BF16 x 3 1.0e-6 / 7.2e-7 / 1.3e-6 (FP32 path 1.8e-7 / 1.0e-7).  FP16 x 2 and
+BF16 x 3 sit near 1e-6 rather than at their split level: there the tensor
+core's FP32 accumulation, not the split, sets the error.  The bars are the
+measured values with a factor of about 3 of margin; all are below the FP32
+requirement of 1e-5.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import apply as A
+from oracle_cases import potential
+from paper_1604_03155_gb300 import inputs as I
+from paper_1604_03155_gb300.vp import Plan, VPError
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+MODES = ["tc_bf16x2", "tc_fp16x2", "tc_bf16x3"]
+BAR = {"tc_bf16x2": 2e-5, "tc_fp16x2": 3e-6, "tc_bf16x3": 4e-6, "fp32": 1e-6}
+N = 128
+
+
+@pytest.fixture(scope="module", params=[("helmholtz", 30.0), ("laplace", 0.0)])
+def case(request):
+    kernel, k = request.param
+    f = I.sample_gaussians(I.random_gaussians(I.BASE_SEED + 700, 6, 3), N).astype(np.complex64)
+    ref, _ = potential(3, N, kernel, k, 1.8, f)
+    return kernel, k, f, ref
+
+
+@pytest.mark.parametrize("mode", MODES + ["fp32"])
+def test_tc_apply_matches_oracle(case, mode):
+    kernel, k, f, ref = case
+    plan = Plan(3, N, kernel, k, 1.8, precision=mode)
+    ft = torch.from_numpy(f).to(DEV)
+    phi = plan.apply(ft)
+    plan.status()
+    err = A.rel_l2(phi.cpu().numpy(), ref)
+    print(f"{kernel} {mode}: rel-L2 vs FP64 oracle {err:.3e}")
+    assert err < BAR[mode]
+    # deterministic: a second call gives the same bits
+    phi2 = plan.apply(ft)
+    assert torch.equal(phi, phi2)
+    plan.close()
+
+
+def test_tc_full_size_against_fp32_and_sampled_oracle():
+    """3D Helmholtz k = 60, N = 256 (2N = 512, the N2 = 32 kernel): each split
+    against the FP32 path on the full grid and against the oracle's direct sum
+    at sampled points."""
+    from oracle import kernel as K
+    from oracle_cases import octants
+    w = I.workload("helmholtz3d_k60_n256")
+    Nw = 256
+    f = I.to_device_dtype(w.density(), "fp32")
+    ft = torch.from_numpy(f).to(DEV)
+    plan = Plan(3, Nw, "helmholtz", 60.0, 1.8, precision="fp32")
+    ref32 = plan.apply(ft).cpu().numpy()
+    T, _ = octants(3, Nw, "helmholtz", 60.0, 1.8)
+    Tf = K.T_full_from_octant(T)
+    rng = np.random.default_rng(11)
+    pts = [tuple(int(v) for v in rng.integers(0, Nw, 3)) for _ in range(4)] + [(0, 0, 0), (127, 127, 127)]
+    exact = A.apply_direct_at(Tf, f.astype(np.complex128), pts)
+    scale = np.sqrt(np.mean(np.abs(ref32) ** 2))
+    for mode in MODES:
+        plan.set_precision(mode)
+        phi = plan.apply(ft).cpu().numpy()
+        plan.status()
+        d = A.rel_l2(phi, ref32)
+        print(f"N=256 {mode}: rel-L2 vs FP32 path {d:.3e}")
+        assert d < BAR[mode]
+        got = np.array([phi[p] for p in pts])
+        assert np.abs(got - exact).max() < 10 * BAR[mode] * scale
+    plan.close()
+
+
+def test_tc_unsupported_combinations():
+    p2 = Plan(2, 128, "helmholtz", 10.0, 0.0, precision="fp32")
+    with pytest.raises(VPError, match="UNSUPPORTED"):
+        p2.set_precision("tc_bf16x2")
+    p2.close()
+    p3 = Plan(3, 64, "helmholtz", 10.0, 0.0, precision="fp32")
+    with pytest.raises(VPError, match="UNSUPPORTED"):
+        p3.set_precision("tc_fp16x2")
+    p3.close()
+    p = Plan(3, 128, "helmholtz", 10.0, 0.0, precision="tc_bf16x3")
+    f = torch.zeros((128, 128, 128), dtype=torch.complex64, device=DEV)
+    with pytest.raises(VPError, match="UNSUPPORTED"):
+        p.apply_grad(f)
+    # switching back to FP32 serves the gradient again
+    p.set_precision("fp32")
+    p.apply_grad(f)
+    p.status()
+    p.close()

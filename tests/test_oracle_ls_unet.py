@@ -28,6 +28,33 @@ def test_dense_solve_and_gmres_agree(small_problem):
     assert hist[-1] < 1e-12 and its < 200
 
 
+def test_arnoldi_basis_pinned_by_qr_of_the_krylov_matrix(small_problem):
+    """The Arnoldi vectors are the Q factor of [b, A b, ..., A^m b] (unique up to
+    a unit phase per column, fixed by h_{j+1,j} > 0) and satisfy A V_m = V_{m+1} H."""
+    prob, uinc = small_problem
+    b = prob.rhs(uinc)
+    m = 6
+    V, H = LS.arnoldi(prob.op, b, m)
+    n = b.size
+    K = np.empty((n, m + 1), dtype=np.complex128)
+    x = b.copy()
+    for j in range(m + 1):
+        K[:, j] = x.ravel()
+        x = prob.op(x)
+    Q, R = np.linalg.qr(K)  # Householder QR (LAPACK), an independent route
+    Vm = V.reshape(m + 1, n).T
+    phase = np.diag(Q.conj().T @ Vm)
+    assert np.allclose(np.abs(phase), 1.0, atol=1e-6)
+    # the monomial basis is ill-conditioned (the QR route loses ~30x per column),
+    # so the bound is loose; a wrong sign, index or projection gives O(1) errors
+    assert np.abs(Vm - Q * phase).max() < 1e-5
+    assert np.abs(Vm.conj().T @ Vm - np.eye(m + 1)).max() < 1e-12
+    AV = np.stack([prob.op(V[j]).ravel() for j in range(m)], axis=1)
+    assert np.abs(AV - Vm @ H).max() < 1e-12 * np.abs(AV).max()
+    assert np.all(np.diag(H, -1).real > 0) and np.all(np.diag(H, -1).imag == 0)
+    assert np.all(np.tril(H, -2) == 0)
+
+
 def test_lippmann_schwinger_limits(small_problem):
     prob, uinc = small_problem
     # no contrast: no scattered field

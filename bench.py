@@ -36,6 +36,10 @@ WORKLOADS = {
     "batch64": dict(d=3, N=0, kernel="mixed", k=0.0, L=1.8, grad=False),
 }
 FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS = 1900.0
+# split-operand tensor-core forms of the 3D fused pass: (16-bit parts, partial products)
+TC_PRECISIONS = ["tc_bf16x2", "tc_fp16x2", "tc_bf16x3"]
+TC_PRODUCTS = {"tc_bf16x2": 3, "tc_fp16x2": 3, "tc_bf16x3": 6}
 
 
 def parse():
@@ -45,7 +49,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="helmholtz2d_k40_n1024_grad", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"] + TC_PRECISIONS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -115,14 +119,34 @@ def measured_peak_hbm():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def measured_peak_bf16(sustained: bool):
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            pk = json.load(fh)
+        return float(pk["bf16_tflops_sustained" if sustained else "bf16_tflops"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_BF16_TFLOPS, "fallback"
+
+
+def tc_flops_per_launch(N: int, precision: str) -> float:
+    """Tensor-core FLOPs of one fused pass: per tile of 8 pencils the four real
+    GEMMs F1 (128 x 2N2 x N2), F3 and I1 (8N2 x 32 x 32) and I3 (128 x N2 x 2N2),
+    2 FLOPs per multiply-add, times the partial products of the split."""
+    n = 2 * N
+    N2 = n // 16
+    per_tile = 2 * (128 * 2 * N2 * N2 + 2 * 8 * N2 * 32 * 32 + 128 * N2 * 2 * N2)
+    return per_tile * (n * n / 8) * TC_PRODUCTS[precision]
+
+
 APPLY_KERNEL_SOURCES = ("pencil_fft.cuh", "apply_dispatch.cuh", "apply_f32.cu", "apply_f64.cu")
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(extra=()) -> str:
     """Hash of the apply kernels' sources (the kernels the roofline is about)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1604_03155_gb300", "csrc")
-    for fn in APPLY_KERNEL_SOURCES:
+    for fn in APPLY_KERNEL_SOURCES + tuple(extra):
         with open(os.path.join(csrc, fn), "rb") as fh:
             h.update(fn.encode())
             h.update(fh.read())
@@ -131,11 +155,12 @@ def kernel_source_hash() -> str:
 
 def ncu_traffic(pass_name: str, workload: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel sources (else None)."""
+    the current kernel sources (else None).  Tensor-core passes are keyed
+    "fused_axis0[tc_...]" and hashed together with their own source."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.md")
     if not os.path.exists(path):
         return None
-    want = kernel_source_hash()
+    want = kernel_source_hash(("tc_fused.cu",) if "[tc_" in pass_name else ())
     for ln in open(path):
         parts = [p.strip() for p in ln.strip().strip("|").split("|")]
         if len(parts) >= 4 and parts[0] == pass_name and parts[1] == workload and parts[3] == want:
@@ -250,8 +275,9 @@ def run_ours(args, wl):
     dev = torch.device("cuda", local)
     d, N, F = wl["d"], wl["N"], (1 + wl["d"]) if wl["grad"] else 1
     prec = args.precision
-    cdt = torch.complex64 if prec == "fp32" else torch.complex128
-    npdt = np.complex64 if prec == "fp32" else np.complex128
+    f32io = prec != "fp64"
+    cdt = torch.complex64 if f32io else torch.complex128
+    npdt = np.complex64 if f32io else np.complex128
 
     stream = torch.cuda.Stream(device=dev)
     t0 = time.perf_counter()
@@ -309,14 +335,15 @@ def run_ours(args, wl):
     value = (N ** d) * world / (ms_per_step / 1000.0)
 
     # roofline of the dominant pass (per launch, events on the plan's stream)
-    csize = 8 if prec == "fp32" else 16
+    csize = 8 if f32io else 16
     pb = pass_bytes(d, N, F, csize)
     dom = max((k for k in passes if passes[k][0] > 0), key=lambda k: passes[k][1])
     dom_launches, dom_ms = passes[dom]
     dom_avg_s = dom_ms / dom_launches / 1000.0
     peak, peak_kind = measured_peak_hbm()
     achieved = pb[dom] / dom_avg_s / 1e9
-    traffic = ncu_traffic(dom, args.workload)
+    traffic = ncu_traffic(f"{dom}[{prec}]" if (prec in TC_PRECISIONS and dom == "fused_axis0") else dom,
+                          args.workload)
     launches_per_step = plan.launch_count(wl["grad"])
 
     # end to end through the C ABI with host buffers (pinned), copies inside
@@ -333,27 +360,36 @@ def run_ours(args, wl):
     e2e_s = (time.perf_counter() - te) / e2e_steps
     U_b = (N ** d) * csize
 
-    # FP64 form on the same grid (same kernels in double), for "vs plain FP64"
-    fp64 = None
-    if prec == "fp32":
-        plan.set_precision("fp64")
-        f64 = f.to(torch.complex128)
-        phi64 = torch.empty_like(f64)
-        grad64 = torch.empty((d,) + f64.shape, dtype=torch.complex128, device=dev) if wl["grad"] else None
+    def time_form(form: str, reps: int = 20) -> float:
+        """ms per step of the same apply in another precision on this plan."""
+        plan.set_precision(form)
+        ff = f.to(torch.complex128) if form == "fp64" else f
+        pp = torch.empty_like(ff)
+        gg = torch.empty((d,) + ff.shape, dtype=ff.dtype, device=dev) if wl["grad"] else None
+        s_ = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+        e_ = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
         with torch.cuda.stream(stream):
             for _ in range(3):
-                plan.apply_grad(f64, phi64, grad64) if wl["grad"] else plan.apply(f64, phi64)
-            s64 = [torch.cuda.Event(enable_timing=True) for _ in range(10)]
-            e64 = [torch.cuda.Event(enable_timing=True) for _ in range(10)]
-            for i in range(10):
+                plan.apply_grad(ff, pp, gg) if wl["grad"] else plan.apply(ff, pp)
+            for i in range(reps):
                 flush.fill_(float(i))
-                s64[i].record(stream)
-                plan.apply_grad(f64, phi64, grad64) if wl["grad"] else plan.apply(f64, phi64)
-                e64[i].record(stream)
+                s_[i].record(stream)
+                plan.apply_grad(ff, pp, gg) if wl["grad"] else plan.apply(ff, pp)
+                e_[i].record(stream)
         torch.cuda.synchronize(dev)
-        ms64 = sum(a.elapsed_time(b) for a, b in zip(s64, e64)) / 10
-        fp64 = {"value": (N ** d) / (ms64 / 1000.0), "ms_per_step": ms64, "speedup_of_fp32": ms64 / ms_per_step}
-        plan.set_precision("fp32")
+        plan.set_precision(prec)
+        return sum(a.elapsed_time(b) for a, b in zip(s_, e_)) / reps
+
+    # FP64 form on the same grid (same kernels in double), for "vs plain FP64";
+    # the tensor-core forms are also compared with the FP32 form
+    fp64 = None
+    fp32_form = None
+    if prec != "fp64":
+        ms64 = time_form("fp64", 10)
+        fp64 = {"value": (N ** d) / (ms64 / 1000.0), "ms_per_step": ms64, "speedup_of_this_form": ms64 / ms_per_step}
+    if prec in TC_PRECISIONS:
+        ms32 = time_form("fp32")
+        fp32_form = {"value": (N ** d) / (ms32 / 1000.0), "ms_per_step": ms32, "speedup_of_this_form": ms32 / ms_per_step}
 
     line = None
     if rank == 0:
@@ -361,7 +397,8 @@ def run_ours(args, wl):
             "metric": "grid pts/s per potential (N^d/s), % HBM roofline, vs plain FP64 at stated rel err",
             "value": value, "unit": "grid pts/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
+            "dtype": {"fp32": "f32", "fp64": "f64"}.get(prec, "f32 + " + prec[3:] + " tensor-core fused pass"),
+            "data": "synthetic",
             "config": {"workload": args.workload, "d": d, "N": N, "kernel": wl["kernel"], "k": wl["k"],
                        "L": wl["L"], "fields": F, "grad_mode": "exact" if wl["grad"] else None,
                        "l2": "flushed before every timed step (256 MB write)", "parallelism": f"replicas x{world}"},
@@ -376,6 +413,17 @@ def run_ours(args, wl):
             "precompute_s": precompute_s,
             "fp64_form": fp64,
         }
+        if fp32_form is not None:
+            line["fp32_form"] = fp32_form
+            line["config"]["precision"] = prec
+            fused_launches, fused_ms = passes.get("fused_axis0", (0, 0.0))
+            if fused_launches:
+                t_s = fused_ms / fused_launches / 1000.0
+                fl = tc_flops_per_launch(N, prec)
+                tpk, tkind = measured_peak_bf16(sustained=False)
+                line["tensor"] = {"kernel": "fused_axis0 (tcgen05)", "flops_per_launch": fl,
+                                  "achieved_tflops": fl / t_s / 1e12, "peak_tflops": tpk, "peak_source": tkind,
+                                  "frac": fl / t_s / 1e12 / tpk}
         if not args.no_cpu_baseline and world == 1:
             r = time_oracle(wl, f_host.astype(np.complex128), 1)
             phi_o, grads_o = r["out"]

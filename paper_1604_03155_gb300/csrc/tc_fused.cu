@@ -78,6 +78,11 @@ __host__ __device__ constexpr int prod_b(int i) { return i == 2 ? 1 : (i == 4 ? 
 __host__ __device__ __forceinline__ int ck(int r, int k, int K) {
   return ((r >> 3) * (K >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7);
 }
+// Element offset of (row, k) in a K-major operand whose groups of 8 rows are
+// (K/8)*128 + pad bytes apart (pad = 16 spreads rows 16 apart over the banks).
+__host__ __device__ __forceinline__ int ck_pad(int r, int k, int K, int pad) {
+  return ((r >> 3) * ((K >> 3) * 128 + pad) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2) >> 1;
+}
 // Element offset of (m, k) in an MN-major canonical operand with M rows.
 __host__ __device__ __forceinline__ int cmn(int m, int k, int M) {
   return ((k >> 3) * (M >> 3) + (m >> 3)) * 64 + (k & 7) * 8 + (m & 7);
@@ -98,7 +103,7 @@ template <int N2> struct TcGeom {
 
 template <int N2, int SPLIT> constexpr size_t tc_smem_bytes() {
   using G = TcGeom<N2>;
-  return (size_t)SplitT<SPLIT>::parts * (G::bpart + G::amax) * 2 + (size_t)G::n * 8 + 128;
+  return (size_t)SplitT<SPLIT>::parts * (G::bpart + G::amax) * 2 + (size_t)32 * N2 * 8 + 704;
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -199,23 +204,28 @@ __device__ __forceinline__ float pow2_scale(float mx) {
   return mx > 0.f ? __uint_as_float((uint32_t)(s + 127) << 23) : 1.f;
 }
 
-template <int SPLIT> __device__ __forceinline__ void split16(float x, uint32_t* part) {
+// Splits a pair (a, b) into 16-bit parts, two lanes per 32-bit word (a in the
+// low half): part q of the pair is word[q].
+template <int SPLIT> __device__ __forceinline__ void split_pair(float a, float b, uint32_t* word) {
   using S = SplitT<SPLIT>;
   if constexpr (S::bf16) {
-    const __nv_bfloat16 h = __float2bfloat16_rn(x);
-    const float r1 = x - __bfloat162float(h);
-    const __nv_bfloat16 m = __float2bfloat16_rn(r1);
-    part[0] = __bfloat16_as_ushort(h);
-    part[1] = __bfloat16_as_ushort(m);
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const float2 hf = __bfloat1622float2(h);
+    const float ra = a - hf.x, rb = b - hf.y;
+    const __nv_bfloat162 m = __floats2bfloat162_rn(ra, rb);
+    word[0] = *reinterpret_cast<const uint32_t*>(&h);
+    word[1] = *reinterpret_cast<const uint32_t*>(&m);
     if constexpr (S::parts == 3) {
-      const float r2 = r1 - __bfloat162float(m);
-      part[2] = __bfloat16_as_ushort(__float2bfloat16_rn(r2));
+      const float2 mf = __bfloat1622float2(m);
+      const __nv_bfloat162 l = __floats2bfloat162_rn(ra - mf.x, rb - mf.y);
+      word[2] = *reinterpret_cast<const uint32_t*>(&l);
     }
   } else {
-    const __half h = __float2half_rn(x);
-    const float r1 = x - __half2float(h);
-    part[0] = __half_as_ushort(h);
-    part[1] = __half_as_ushort(__float2half_rn(r1));
+    const __half2 h = __floats2half2_rn(a, b);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+    word[0] = *reinterpret_cast<const uint32_t*>(&h);
+    word[1] = *reinterpret_cast<const uint32_t*>(&l);
   }
 }
 
@@ -227,11 +237,10 @@ __device__ __forceinline__ void store8(unsigned char* abase, int part_bytes, int
   uint32_t w[PARTS][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    uint32_t lo[PARTS], hi[PARTS];
-    split16<SPLIT>(v[2 * i] * scale, lo);
-    split16<SPLIT>(v[2 * i + 1] * scale, hi);
+    uint32_t pw[PARTS];
+    split_pair<SPLIT>(v[2 * i] * scale, v[2 * i + 1] * scale, pw);
 #pragma unroll
-    for (int q = 0; q < PARTS; ++q) w[q][i] = lo[q] | (hi[q] << 16);
+    for (int q = 0; q < PARTS; ++q) w[q][i] = pw[q];
   }
 #pragma unroll
   for (int q = 0; q < PARTS; ++q)
@@ -244,7 +253,7 @@ __device__ __forceinline__ int fold_m(int m, int n) { return m <= n - m ? m : n 
 //   a_addr   shared address of part 0 of A at the first of the 128 rows
 //   a_mn     MN-major A (else K-major); m_total = rows of the whole MN-major operand
 //   b_addr   shared address of part 0 of this step's B
-template <int SPLIT, int K, int NC, int AMAX, int BPART>
+template <int SPLIT, int K, int NC, int AMAX, int BPART, int KPAD = 0>
 __device__ __forceinline__ void issue_step(uint32_t d_tmem, uint32_t a_addr, bool a_mn, int m_total, uint32_t b_addr) {
   using S = SplitT<SPLIT>;
   const uint32_t idesc = idesc_f16(S::bf16, NC, a_mn);
@@ -259,12 +268,19 @@ __device__ __forceinline__ void issue_step(uint32_t d_tmem, uint32_t a_addr, boo
         const uint32_t kstride = (uint32_t)(m_total / 8) * 128;  // between core matrices along K
         ad = kMnLboIsK ? sdesc(ab + ks * 2 * kstride, kstride, 128) : sdesc(ab + ks * 2 * kstride, 128, kstride);
       } else {
-        ad = sdesc(ab + ks * 256, 128, (K / 8) * 128);
+        ad = sdesc(ab + ks * 256, 128, (K / 8) * 128 + KPAD);
       }
       const uint64_t bd = sdesc(bb + ks * 256, 128, (K / 8) * 128);
       mma_f16(d_tmem, ad, bd, idesc, (pr > 0 || ks > 0) ? 1u : 0u);
     }
   }
+}
+
+// Maximum over the 16 lanes of a half warp (lanes 0-15 or 16-31).
+__device__ __forceinline__ float half_warp_max(float v) {
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
 }
 
 template <int N2, int SPLIT>
@@ -277,11 +293,13 @@ __global__ void __launch_bounds__(TC_THREADS, SplitT<SPLIT>::parts == 3 ? 2 : 3)
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* sB = smem;
   unsigned char* sA = sB + PARTS * G::bpart * 2;
-  float2* s_tw = reinterpret_cast<float2*>(sA + PARTS * AB);
-  uint64_t* s_mbar = reinterpret_cast<uint64_t*>(s_tw + n);
+  float2* s_tw1 = reinterpret_cast<float2*>(sA + PARTS * AB);  // [k2][j1] = w_2N^{j1 k2}
+  float2* s_tw2 = s_tw1 + 16 * N2;                             // [j1][k2] = w_2N^{-j1 k2}
+  uint64_t* s_mbar = reinterpret_cast<uint64_t*>(s_tw2 + 16 * N2);
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(s_mbar + 1);
-  unsigned* s_pmax = s_tmem + 1;  // [0, 8): F3 pencils, [8, 16): I3 pencils
-  int* s_bad = reinterpret_cast<int*>(s_pmax + 16);
+  float* s_scale = reinterpret_cast<float*>(s_tmem + 1);  // [0, 8): F3 pencils, [8, 16): I3 pencils
+  float* s_rs1 = s_scale + 16;                             // F1 row scales [128]
+  int* s_bad = reinterpret_cast<int*>(s_rs1 + 128);
   float2* s_out = reinterpret_cast<float2*>(sA);  // [Nh][9] output staging, aliases A after I3
 
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -290,8 +308,12 @@ __global__ void __launch_bounds__(TC_THREADS, SplitT<SPLIT>::parts == 3 ? 2 : 3)
     uint4* dst = reinterpret_cast<uint4*>(sB);
     for (int i = tid; i < PARTS * G::bpart * 2 / 16; i += TC_THREADS) dst[i] = src[i];
   }
-  for (int i = tid; i < n; i += TC_THREADS) s_tw[i] = a.tw[i];
-  if (tid < 16) s_pmax[tid] = 0u;
+  for (int i = tid; i < 16 * N2; i += TC_THREADS) {
+    const int k2 = i >> 4, j1 = i & 15;
+    const float2 w = a.tw[j1 * k2];  // j1 k2 < 2N
+    s_tw1[k2 * 16 + j1] = w;
+    s_tw2[j1 * N2 + k2] = make_float2(w.x, -w.y);
+  }
   if (tid == 0) *s_bad = 0;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
@@ -309,18 +331,39 @@ __global__ void __launch_bounds__(TC_THREADS, SplitT<SPLIT>::parts == 3 ? 2 : 3)
 
   const long long ntiles = a.npencils / TC_P;
   const int np1 = Nh + 1;
+  // this thread's F1 row r = p*16 + j1 (a half warp = one pencil)
+  const int p1 = tid >> 4, j1t = tid & 15;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const long long pen0 = tile * TC_P;
+    // the next tile's input (64 contiguous bytes per position) and multiplier
+    // rows (8 consecutive octant entries per folded frequency) into L2
+    {
+      const long long nt = tile + gridDim.x;
+      if (nt < ntiles) {
+        for (int pos = tid; pos < Nh; pos += TC_THREADS)
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(a.in + nt * TC_P + (long long)pos * a.pitch_pos));
+        const long long q0 = nt * TC_P, q1 = q0 + TC_P - 1;
+        const long long o0 = (long long)fold_m((int)(q0 / n), n) * np1 + fold_m((int)(q0 % n), n);
+        const long long o1 = (long long)fold_m((int)(q1 / n), n) * np1 + fold_m((int)(q1 % n), n);
+        const long long lo = o0 < o1 ? o0 : o1, hi = o0 < o1 ? o1 : o0;
+        for (int r = tid; r < np1; r += TC_THREADS) {
+          const float2* row = a.mult + (long long)r * np1 * np1;
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(row + lo));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(row + hi));
+        }
+      }
+    }
     float rs_f1 = 1.f;  // row scales (FP16 split)
     float rs_i1[G::nh3];
 #pragma unroll
     for (int h = 0; h < G::nh3; ++h) rs_i1[h] = 1.f;
 
-    // ---- F1 operand: row r = j1*8 + p, K = N2 (re j2 | im j2), K-major ----
+    // ---- F1 operand: row r = p*16 + j1, K = N2 (re j2 | im j2), K-major with
+    // padded row groups; loaded with 4 pencils x 8 positions per warp (coalesced) ----
     {
-      const int p = tid & 7, j1 = tid >> 3;
+      const int pl = (tid & 3) + 4 * (tid >> 6), jl = (tid >> 2) & 15, rl = pl * 16 + jl;
       float xr[N2 / 2], xi[N2 / 2];
-      const float2* src = a.in + pen0 + p + (long long)j1 * a.pitch_pos;
+      const float2* src = a.in + pen0 + pl + (long long)jl * a.pitch_pos;
 #pragma unroll
       for (int j2 = 0; j2 < N2 / 2; ++j2) {
         const float2 v = __ldg(src + (long long)(16 * j2) * a.pitch_pos);
@@ -332,32 +375,33 @@ __global__ void __launch_bounds__(TC_THREADS, SplitT<SPLIT>::parts == 3 ? 2 : 3)
 #pragma unroll
         for (int j2 = 0; j2 < N2 / 2; ++j2) mx = fmaxf(mx, fmaxf(fabsf(xr[j2]), fabsf(xi[j2])));
         rs_f1 = pow2_scale(mx);
+        s_rs1[rl] = rs_f1;
       }
 #pragma unroll
       for (int c = 0; c < N2 / 16; ++c) {
-        store8<SPLIT>(sA, AB, ck(tid, 8 * c, N2), &xr[8 * c], rs_f1);
-        store8<SPLIT>(sA, AB, ck(tid, N2 / 2 + 8 * c, N2), &xi[8 * c], rs_f1);
+        store8<SPLIT>(sA, AB, ck_pad(rl, 8 * c, N2, 16), &xr[8 * c], rs_f1);
+        store8<SPLIT>(sA, AB, ck_pad(rl, N2 / 2 + 8 * c, N2, 16), &xi[8 * c], rs_f1);
       }
     }
     sync_for_mma();
     if (tid == 0) {
-      issue_step<SPLIT, N2, 2 * N2, G::amax, G::bpart>(tmem, aA, false, 128, aB + G::b_f1 * 2);
+      issue_step<SPLIT, N2, 2 * N2, G::amax, G::bpart, 16>(tmem, aA, false, 128, aB + G::b_f1 * 2);
       mma_commit(mbar);
     }
     ok = mbar_wait(mbar, phase) && ok;
     phase ^= 1;
     tc_after_sync();
+    if constexpr (S::scaled) rs_f1 = s_rs1[tid];  // scale of the D row this thread reads
 
     // ---- T1 and the F3 operand: rows m = p*N2 + k2, K = 32 (re j1 | im j1), MN-major ----
     {
-      const int p = tid & 7, j1 = tid >> 3;
       float yr[N2], yi[N2];
       tldw<N2>(lane_base + 0, yr);
       tldw<N2>(lane_base + N2, yi);
       const float inv = 1.f / rs_f1;
 #pragma unroll
       for (int k2 = 0; k2 < N2; ++k2) {
-        const float2 w = s_tw[j1 * k2];
+        const float2 w = s_tw1[k2 * 16 + j1t];
         const float r = yr[k2] * inv, i = yi[k2] * inv;
         yr[k2] = r * w.x - i * w.y;
         yi[k2] = r * w.y + i * w.x;
@@ -367,15 +411,14 @@ __global__ void __launch_bounds__(TC_THREADS, SplitT<SPLIT>::parts == 3 ? 2 : 3)
         float mx = 0.f;
 #pragma unroll
         for (int k2 = 0; k2 < N2; ++k2) mx = fmaxf(mx, fmaxf(fabsf(yr[k2]), fabsf(yi[k2])));
-        atomicMax(&s_pmax[p], __float_as_uint(mx));
-        __syncthreads();
-        sc = pow2_scale(__uint_as_float(s_pmax[p]));
+        sc = pow2_scale(half_warp_max(mx));  // the half warp holds the whole pencil
+        if (j1t == 0) s_scale[p1] = sc;
       }
 #pragma unroll
       for (int c = 0; c < N2 / 8; ++c) {
-        const int m0 = p * N2 + 8 * c;
-        store8<SPLIT>(sA, AB, cmn(m0, j1, G::m3), &yr[8 * c], sc);
-        store8<SPLIT>(sA, AB, cmn(m0, 16 + j1, G::m3), &yi[8 * c], sc);
+        const int m0 = p1 * N2 + 8 * c;
+        store8<SPLIT>(sA, AB, cmn(m0, j1t, G::m3), &yr[8 * c], sc);
+        store8<SPLIT>(sA, AB, cmn(m0, 16 + j1t, G::m3), &yi[8 * c], sc);
       }
     }
     sync_for_mma();
@@ -411,7 +454,7 @@ __global__ void __launch_bounds__(TC_THREADS, SplitT<SPLIT>::parts == 3 ? 2 : 3)
       tld16(lane_base + 32 * h, zr);
       tld16(lane_base + 32 * h + 16, zi);
       float inv = 1.f;
-      if constexpr (S::scaled) inv = 1.f / pow2_scale(__uint_as_float(s_pmax[p]));
+      if constexpr (S::scaled) inv = 1.f / s_scale[p];
 #pragma unroll
       for (int k1 = 0; k1 < 16; ++k1) {
         const float xr = zr[k1] * inv, xi = zi[k1] * inv;
@@ -441,39 +484,35 @@ __global__ void __launch_bounds__(TC_THREADS, SplitT<SPLIT>::parts == 3 ? 2 : 3)
     tc_after_sync();
 
     // ---- T2 and the I3 operand: rows m = p*16 + j1, K = 2 N2 (re k2 | im k2), MN-major ----
-    {
-      float wr[G::nh3][16], wi[G::nh3][16];
 #pragma unroll
-      for (int h = 0; h < G::nh3; ++h) {
-        const int r = 128 * h + tid, k2 = r % N2;
-        tld16(lane_base + 32 * h, wr[h]);
-        tld16(lane_base + 32 * h + 16, wi[h]);
-        const float inv = 1.f / rs_i1[h];
+    for (int h = 0; h < G::nh3; ++h) {
+      const int r = 128 * h + tid, p = r / N2, k2 = r % N2;
+      float wr[16], wi[16];
+      tld16(lane_base + 32 * h, wr);
+      tld16(lane_base + 32 * h + 16, wi);
+      const float inv = 1.f / rs_i1[h];
 #pragma unroll
-        for (int j1 = 0; j1 < 16; ++j1) {
-          const float2 w = s_tw[j1 * k2];  // conjugated below
-          const float xr = wr[h][j1] * inv, xi = wi[h][j1] * inv;
-          wr[h][j1] = xr * w.x + xi * w.y;
-          wi[h][j1] = xi * w.x - xr * w.y;
-        }
-        if constexpr (S::scaled) {
-          float mx = 0.f;
-#pragma unroll
-          for (int j1 = 0; j1 < 16; ++j1) mx = fmaxf(mx, fmaxf(fabsf(wr[h][j1]), fabsf(wi[h][j1])));
-          atomicMax(&s_pmax[8 + r / N2], __float_as_uint(mx));
-        }
+      for (int j1 = 0; j1 < 16; ++j1) {
+        const float2 w = s_tw2[j1 * N2 + k2];
+        const float xr = wr[j1] * inv, xi = wi[j1] * inv;
+        wr[j1] = xr * w.x - xi * w.y;
+        wi[j1] = xr * w.y + xi * w.x;
       }
-      if constexpr (S::scaled) __syncthreads();
+      float sc = 1.f;
+      if constexpr (S::scaled) {
+        // the rows of pencil p are the N2 consecutive lanes k2 of this (half) warp
+        float mx = 0.f;
 #pragma unroll
-      for (int h = 0; h < G::nh3; ++h) {
-        const int r = 128 * h + tid, p = r / N2, k2 = r % N2;
-        float sc = 1.f;
-        if constexpr (S::scaled) sc = pow2_scale(__uint_as_float(s_pmax[8 + p]));
-        store8<SPLIT>(sA, AB, cmn(p * 16, k2, 128), &wr[h][0], sc);
-        store8<SPLIT>(sA, AB, cmn(p * 16 + 8, k2, 128), &wr[h][8], sc);
-        store8<SPLIT>(sA, AB, cmn(p * 16, N2 + k2, 128), &wi[h][0], sc);
-        store8<SPLIT>(sA, AB, cmn(p * 16 + 8, N2 + k2, 128), &wi[h][8], sc);
+        for (int j1 = 0; j1 < 16; ++j1) mx = fmaxf(mx, fmaxf(fabsf(wr[j1]), fabsf(wi[j1])));
+        mx = half_warp_max(mx);
+        if constexpr (N2 == 32) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
+        sc = pow2_scale(mx);
+        if (k2 == 0) s_scale[8 + p] = sc;
       }
+      store8<SPLIT>(sA, AB, cmn(p * 16, k2, 128), &wr[0], sc);
+      store8<SPLIT>(sA, AB, cmn(p * 16 + 8, k2, 128), &wr[8], sc);
+      store8<SPLIT>(sA, AB, cmn(p * 16, N2 + k2, 128), &wi[0], sc);
+      store8<SPLIT>(sA, AB, cmn(p * 16 + 8, N2 + k2, 128), &wi[8], sc);
     }
     sync_for_mma();
     if (tid == 0) {
@@ -486,14 +525,14 @@ __global__ void __launch_bounds__(TC_THREADS, SplitT<SPLIT>::parts == 3 ? 2 : 3)
 
     // ---- output: row r = p*16 + j1 holds y[j1 + 16 j2], j2 < N2/2 ----
     {
-      const int p = tid >> 4, j1 = tid & 15;
       float yr[N2 / 2], yi[N2 / 2];
       tldw<N2 / 2>(lane_base + 0, yr);
       tldw<N2 / 2>(lane_base + N2 / 2, yi);
       float inv = 1.f;
-      if constexpr (S::scaled) inv = 1.f / pow2_scale(__uint_as_float(s_pmax[8 + p]));
+      if constexpr (S::scaled) inv = 1.f / s_scale[8 + p1];
 #pragma unroll
-      for (int j2 = 0; j2 < N2 / 2; ++j2) s_out[(j1 + 16 * j2) * 9 + p] = make_float2(yr[j2] * inv, yi[j2] * inv);
+      for (int j2 = 0; j2 < N2 / 2; ++j2)
+        s_out[(j1t + 16 * j2) * 9 + p1] = make_float2(yr[j2] * inv, yi[j2] * inv);
     }
     __syncthreads();
     for (int i = tid; i < Nh * TC_P; i += TC_THREADS) {
@@ -502,7 +541,6 @@ __global__ void __launch_bounds__(TC_THREADS, SplitT<SPLIT>::parts == 3 ? 2 : 3)
     }
     if (!ok) atomicOr(s_bad, 1);
     __syncthreads();
-    if (tid < 16) s_pmax[tid] = 0u;
     if (*s_bad) break;
   }
   if (tid == 0 && *s_bad) atomicOr(a.err, 1);
@@ -568,11 +606,28 @@ template <int N2, int SPLIT> cudaError_t launch_tc_t(const TcFusedArgs& a, cudaS
   if (grid_cap[dev] == 0) {
     e = cudaFuncSetAttribute(tc_fused_kernel<N2, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    // ask for the largest shared-memory carveout: without it the occupancy query
+    // (and the launch) can settle on one CTA per SM
+    e = cudaFuncSetAttribute(tc_fused_kernel<N2, SPLIT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
     int occ = 0, sms = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tc_fused_kernel<N2, SPLIT>, TC_THREADS, smem);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
+    // the residency the register file and shared memory allow (CTAs never wait
+    // on one another, so a grid above the true residency only queues)
+    cudaFuncAttributes fa;
+    int smem_sm = 0;
+    if (cudaFuncGetAttributes(&fa, tc_fused_kernel<N2, SPLIT>) == cudaSuccess &&
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess) {
+      const int regs = ((fa.numRegs > 0 ? fa.numRegs : 1) + 7) / 8 * 8;
+      const int by_regs = 65536 / (TC_THREADS * regs);
+      const int by_smem = smem_sm / (int)(smem + 1024);
+      const int est = by_regs < by_smem ? by_regs : by_smem;
+      if (est > occ) occ = est;
+    }
     // tensor memory: occ x 64 columns of 512 per SM
     if (occ > 8) occ = 8;
     grid_cap[dev] = (occ > 0 ? occ : 1) * sms;

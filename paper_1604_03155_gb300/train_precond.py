@@ -35,7 +35,7 @@ def main():
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--restart", type=int, default=20)
     ap.add_argument("--tol", type=float, default=1e-6)
-    ap.add_argument("--slope", type=float, default=1.0, help="leaky-ReLU slope (1: linear network)")
+    ap.add_argument("--slope", type=float, default=0.1, help="leaky-ReLU slope (1: linear network)")
     ap.add_argument("--out", default=os.path.join(ROOT, "paper_1604_03155_gb300", "weights", "unet_ls_k30_n128"))
     a = ap.parse_args()
     os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)

@@ -129,3 +129,31 @@ def test_untrained_preconditioner_falls_back_and_still_converges():
     st = vp.ls_solve(plan, q, b, u, u_inc=uinc, tol=3e-7, maxit=800, restart=20, precond=net)
     assert st["true_residual"] < 1e-6, st
     net.close()
+
+
+@pytest.mark.parametrize("tag", ["c300", "c2000"])
+def test_trained_preconditioner_against_plain_gmres(tag):
+    """Held-out contrasts (N = 128, k = 30, plane wave): plain flexible GMRES
+    against the trained network as right preconditioner, same restart length,
+    both judged by the true FP64 residual.  The committed reports
+    (weights/unet_ls_k30_n128_<tag>.json, 50 held-out contrasts) measured 20.2
+    plain iterations against 30.6 (trained on 300 contrasts, no fallback) and
+    66.4 (2000 contrasts, every solve fell back): on this well-conditioned
+    problem the network does not reduce the iteration count.  The test pins
+    what holds: the preconditioned solve reaches the same true residual and
+    stays within 4x the plain iterations."""
+    import os
+
+    from paper_1604_03155_gb300 import precond as P
+    wdir = os.path.join(os.path.dirname(vp.__file__), "weights")
+    N, k = 128, 30.0
+    plan = Plan(3, N, "helmholtz", k, 1.8, precision="fp32")
+    net = UNet(N, 16, slope=0.1)
+    P.load_weights(net, os.path.join(wdir, f"unet_ls_k30_n128_{tag}.npy"))
+    ev = P.evaluate(plan, net, N, k, [I.LS_HELDOUT_SEED + i for i in range(3)], tol=1e-6, restart=20)
+    s = ev["summary"]
+    print(tag, s)
+    assert s["plain_true_residual_max"] < 1e-6 and s["precond_true_residual_max"] < 1e-6
+    assert s["precond_iterations"] <= 4 * s["plain_iterations"]
+    net.close()
+    plan.close()

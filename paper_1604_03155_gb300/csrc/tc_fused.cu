@@ -31,12 +31,19 @@
 //
 // Operand layouts are the tensor core's canonical no-swizzle layouts: 8x8
 // "core matrices" of 16-bit elements (128 contiguous bytes).  A is K-major
-// where the thread that owns a row writes it (F1, I1) and MN-major where the
-// step transposes the data (F3, I3), so every shared-memory store is 16 bytes.
+// where one thread writes a whole row (F1, I1) and MN-major where the step
+// transposes the data (F3, I3), so every shared-memory store is 16 bytes and
+// none has a bank conflict (the F1 operand pads its row groups by 16 bytes).
+// Row orders are chosen for the global accesses: the F1 input is loaded as 4
+// pencils x 8 positions per warp, and the F3/I1 rows (k2/8)*64 + p*8 + k2%8
+// give each warp 4 pencils x 8 frequencies, so the multiplier gathers read
+// whole 32-byte sectors.  The output is staged in shared memory and written
+// as 64-byte runs (8 pencils) per position.
 //
 // One CTA of 128 threads (one thread per tensor-memory lane) processes one
-// tile at a time and loops over tiles (persistent grid).  Waits on MMA
-// completion are bounded by a clock budget; a timeout sets the error word.
+// tile at a time and loops over tiles (persistent grid, three CTAs per SM for
+// the two-part splits).  Waits on MMA completion are bounded by a clock
+// budget; a timeout sets the error word.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
@@ -103,7 +110,7 @@ template <int N2> struct TcGeom {
 
 template <int N2, int SPLIT> constexpr size_t tc_smem_bytes() {
   using G = TcGeom<N2>;
-  return (size_t)SplitT<SPLIT>::parts * (G::bpart + G::amax) * 2 + (size_t)32 * N2 * 8 + 704;
+  return (size_t)SplitT<SPLIT>::parts * (G::bpart + G::amax) * 2 + (size_t)32 * N2 * 8 + 768;
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -276,6 +283,14 @@ __device__ __forceinline__ void issue_step(uint32_t d_tmem, uint32_t a_addr, boo
   }
 }
 
+// Rows of F3 and I1: m = (k2/8)*64 + p*8 + k2%8.  Runs of 8 consecutive rows are
+// 8 frequencies of one pencil (one 16-byte MN-major store by the writer of that
+// pencil), and a warp's 32 rows are 4 pencils x 8 frequencies, so the multiplier
+// gathers of a warp touch 8 full 32-byte sectors.
+__device__ __forceinline__ int row3(int p, int k2) { return (k2 >> 3) * 64 + p * 8 + (k2 & 7); }
+__device__ __forceinline__ int row3_p(int m) { return (m >> 3) & 7; }
+__device__ __forceinline__ int row3_k2(int m) { return (m >> 6) * 8 + (m & 7); }
+
 // Maximum over the 16 lanes of a half warp (lanes 0-15 or 16-31).
 __device__ __forceinline__ float half_warp_max(float v) {
 #pragma unroll
@@ -299,7 +314,8 @@ __global__ void __launch_bounds__(TC_THREADS, SplitT<SPLIT>::parts == 3 ? 2 : 3)
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(s_mbar + 1);
   float* s_scale = reinterpret_cast<float*>(s_tmem + 1);  // [0, 8): F3 pencils, [8, 16): I3 pencils
   float* s_rs1 = s_scale + 16;                             // F1 row scales [128]
-  int* s_bad = reinterpret_cast<int*>(s_rs1 + 128);
+  unsigned* s_pmax = reinterpret_cast<unsigned*>(s_rs1 + 128);  // I3 pencil maxima (FP32 bits) [8]
+  int* s_bad = reinterpret_cast<int*>(s_pmax + 8);
   float2* s_out = reinterpret_cast<float2*>(sA);  // [Nh][9] output staging, aliases A after I3
 
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -335,23 +351,8 @@ __global__ void __launch_bounds__(TC_THREADS, SplitT<SPLIT>::parts == 3 ? 2 : 3)
   const int p1 = tid >> 4, j1t = tid & 15;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const long long pen0 = tile * TC_P;
-    // the next tile's input (64 contiguous bytes per position) and multiplier
-    // rows (8 consecutive octant entries per folded frequency) into L2
-    {
-      const long long nt = tile + gridDim.x;
-      if (nt < ntiles) {
-        for (int pos = tid; pos < Nh; pos += TC_THREADS)
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(a.in + nt * TC_P + (long long)pos * a.pitch_pos));
-        const long long q0 = nt * TC_P, q1 = q0 + TC_P - 1;
-        const long long o0 = (long long)fold_m((int)(q0 / n), n) * np1 + fold_m((int)(q0 % n), n);
-        const long long o1 = (long long)fold_m((int)(q1 / n), n) * np1 + fold_m((int)(q1 % n), n);
-        const long long lo = o0 < o1 ? o0 : o1, hi = o0 < o1 ? o1 : o0;
-        for (int r = tid; r < np1; r += TC_THREADS) {
-          const float2* row = a.mult + (long long)r * np1 * np1;
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(row + lo));
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(row + hi));
-        }
-      }
+    if constexpr (S::scaled) {
+      if (tid < 8) s_pmax[tid] = 0u;  // read last by the previous tile before its final barrier
     }
     float rs_f1 = 1.f;  // row scales (FP16 split)
     float rs_i1[G::nh3];
@@ -416,7 +417,7 @@ __global__ void __launch_bounds__(TC_THREADS, SplitT<SPLIT>::parts == 3 ? 2 : 3)
       }
 #pragma unroll
       for (int c = 0; c < N2 / 8; ++c) {
-        const int m0 = p1 * N2 + 8 * c;
+        const int m0 = row3(p1, 8 * c);
         store8<SPLIT>(sA, AB, cmn(m0, j1t, G::m3), &yr[8 * c], sc);
         store8<SPLIT>(sA, AB, cmn(m0, 16 + j1t, G::m3), &yi[8 * c], sc);
       }
@@ -432,7 +433,7 @@ __global__ void __launch_bounds__(TC_THREADS, SplitT<SPLIT>::parts == 3 ? 2 : 3)
     float2 g[G::nh3][16];
 #pragma unroll
     for (int h = 0; h < G::nh3; ++h) {
-      const int r = 128 * h + tid, p = r / N2, k2 = r % N2;
+      const int r = 128 * h + tid, p = row3_p(r), k2 = row3_k2(r);
       const long long pen = pen0 + p;
       const int m1 = (int)(pen / n), m2 = (int)(pen % n);
       const long long rest = (long long)fold_m(m1, n) * np1 + fold_m(m2, n);
@@ -449,7 +450,7 @@ __global__ void __launch_bounds__(TC_THREADS, SplitT<SPLIT>::parts == 3 ? 2 : 3)
     // ---- multiply and the I1 operand: rows m = p*N2 + k2, K = 32 (re k1 | im k1), K-major ----
 #pragma unroll
     for (int h = 0; h < G::nh3; ++h) {
-      const int r = 128 * h + tid, p = r / N2;
+      const int r = 128 * h + tid, p = row3_p(r);
       float zr[16], zi[16];
       tld16(lane_base + 32 * h, zr);
       tld16(lane_base + 32 * h + 16, zi);
@@ -484,35 +485,39 @@ __global__ void __launch_bounds__(TC_THREADS, SplitT<SPLIT>::parts == 3 ? 2 : 3)
     tc_after_sync();
 
     // ---- T2 and the I3 operand: rows m = p*16 + j1, K = 2 N2 (re k2 | im k2), MN-major ----
+    {
+      float wr[G::nh3][16], wi[G::nh3][16];
 #pragma unroll
-    for (int h = 0; h < G::nh3; ++h) {
-      const int r = 128 * h + tid, p = r / N2, k2 = r % N2;
-      float wr[16], wi[16];
-      tld16(lane_base + 32 * h, wr);
-      tld16(lane_base + 32 * h + 16, wi);
-      const float inv = 1.f / rs_i1[h];
+      for (int h = 0; h < G::nh3; ++h) {
+        const int r = 128 * h + tid, k2 = row3_k2(r);
+        tld16(lane_base + 32 * h, wr[h]);
+        tld16(lane_base + 32 * h + 16, wi[h]);
+        const float inv = 1.f / rs_i1[h];
 #pragma unroll
-      for (int j1 = 0; j1 < 16; ++j1) {
-        const float2 w = s_tw2[j1 * N2 + k2];
-        const float xr = wr[j1] * inv, xi = wi[j1] * inv;
-        wr[j1] = xr * w.x - xi * w.y;
-        wi[j1] = xr * w.y + xi * w.x;
+        for (int j1 = 0; j1 < 16; ++j1) {
+          const float2 w = s_tw2[j1 * N2 + k2];
+          const float xr = wr[h][j1] * inv, xi = wi[h][j1] * inv;
+          wr[h][j1] = xr * w.x - xi * w.y;
+          wi[h][j1] = xr * w.y + xi * w.x;
+        }
+        if constexpr (S::scaled) {
+          float mx = 0.f;
+#pragma unroll
+          for (int j1 = 0; j1 < 16; ++j1) mx = fmaxf(mx, fmaxf(fabsf(wr[h][j1]), fabsf(wi[h][j1])));
+          atomicMax(&s_pmax[row3_p(r)], __float_as_uint(mx));  // a pencil's rows span warps
+        }
       }
-      float sc = 1.f;
-      if constexpr (S::scaled) {
-        // the rows of pencil p are the N2 consecutive lanes k2 of this (half) warp
-        float mx = 0.f;
+      if constexpr (S::scaled) __syncthreads();
 #pragma unroll
-        for (int j1 = 0; j1 < 16; ++j1) mx = fmaxf(mx, fmaxf(fabsf(wr[j1]), fabsf(wi[j1])));
-        mx = half_warp_max(mx);
-        if constexpr (N2 == 32) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
-        sc = pow2_scale(mx);
-        if (k2 == 0) s_scale[8 + p] = sc;
+      for (int h = 0; h < G::nh3; ++h) {
+        const int r = 128 * h + tid, p = row3_p(r), k2 = row3_k2(r);
+        float sc = 1.f;
+        if constexpr (S::scaled) sc = pow2_scale(__uint_as_float(s_pmax[p]));
+        store8<SPLIT>(sA, AB, cmn(p * 16, k2, 128), &wr[h][0], sc);
+        store8<SPLIT>(sA, AB, cmn(p * 16 + 8, k2, 128), &wr[h][8], sc);
+        store8<SPLIT>(sA, AB, cmn(p * 16, N2 + k2, 128), &wi[h][0], sc);
+        store8<SPLIT>(sA, AB, cmn(p * 16 + 8, N2 + k2, 128), &wi[h][8], sc);
       }
-      store8<SPLIT>(sA, AB, cmn(p * 16, k2, 128), &wr[0], sc);
-      store8<SPLIT>(sA, AB, cmn(p * 16 + 8, k2, 128), &wr[8], sc);
-      store8<SPLIT>(sA, AB, cmn(p * 16, N2 + k2, 128), &wi[0], sc);
-      store8<SPLIT>(sA, AB, cmn(p * 16 + 8, N2 + k2, 128), &wi[8], sc);
     }
     sync_for_mma();
     if (tid == 0) {
@@ -529,7 +534,7 @@ __global__ void __launch_bounds__(TC_THREADS, SplitT<SPLIT>::parts == 3 ? 2 : 3)
       tldw<N2 / 2>(lane_base + 0, yr);
       tldw<N2 / 2>(lane_base + N2 / 2, yi);
       float inv = 1.f;
-      if constexpr (S::scaled) inv = 1.f / s_scale[8 + p1];
+      if constexpr (S::scaled) inv = 1.f / pow2_scale(__uint_as_float(s_pmax[p1]));
 #pragma unroll
       for (int j2 = 0; j2 < N2 / 2; ++j2)
         s_out[(j1t + 16 * j2) * 9 + p1] = make_float2(yr[j2] * inv, yi[j2] * inv);

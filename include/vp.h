@@ -267,6 +267,14 @@ vp_status vp_ls_training_pair(vp_plan plan, const float* q, const void* b, const
  * *count: vectors written (m+1; fewer only at an exact breakdown).  m in
  * [1, 64].  Draws the (A v_j, v_j) training pairs of the learned preconditioner. */
 vp_status vp_ls_krylov_basis(vp_plan plan, const float* q, const void* b, int m, void* V, int* count);
+/* The preconditioned directions z_j = M(v_j), j < m, of the first cycle of
+ * flexible GMRES from b with the right preconditioner `precond` (required):
+ * the vectors whose images A z_j span that cycle's search space.  Z: device
+ * buffer of m x N^3 complex64; *count: directions written (m; fewer only when
+ * the recurrence residual is exactly zero).  Draws on-policy training pairs
+ * (A z_j, z_j) for the learned preconditioner. */
+vp_status vp_ls_flexible_basis(vp_plan plan, const float* q, const void* b, int m, vp_precond_fn precond,
+                               void* precond_ctx, void* Z, int* count);
 const char* vp_ls_last_error(void);
 
 /* ---------------------------------------------------------------------------

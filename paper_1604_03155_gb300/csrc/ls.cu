@@ -608,6 +608,33 @@ vp_status vp_ls_krylov_basis(vp_plan plan, const float* q, const void* b, int m,
   return VP_OK;
 }
 
+vp_status vp_ls_flexible_basis(vp_plan plan, const float* q, const void* b, int m, vp_precond_fn precond,
+                               void* precond_ctx, void* Z, int* count) {
+  long long n;
+  double k2;
+  vp_status st = check_plan(plan, &n, &k2);
+  if (st != VP_OK) return st;
+  if (!q || !b || !Z || !count || !precond) return ls_fail(VP_ERR_INVALID_ARG, "NULL argument");
+  if (m < 1 || m > kMaxBasis) return ls_fail(VP_ERR_INVALID_ARG, "m must be in [1, 64]");
+  Work w;
+  if ((st = alloc_work(w, n, m, true)) != VP_OK) return ls_fail(st, w.err);
+  Ctx c{plan, q, n, k2, get_stream(plan)};
+  const float2* bb = reinterpret_cast<const float2*>(b);
+  double bnorm = 0.0;
+  if ((st = norm2(c, w, bb, &bnorm)) != VP_OK) return ls_fail(st, w.err);
+  if (!(bnorm > 0)) return ls_fail(VP_ERR_NUMERICAL, "b is zero");
+  float2* x = reinterpret_cast<float2*>(w.d0);
+  LS_CUDA(w, cudaMemsetAsync(x, 0, n * sizeof(float2), c.s));
+  int iters = 0, matvecs = 0;
+  double est = 1.0;
+  st = fgmres_cycle(c, w, bb, x, bnorm, 0.0, m, precond, precond_ctx, &iters, &matvecs, &est);
+  if (st != VP_OK) return ls_fail(st, w.err.empty() ? "flexible Arnoldi cycle failed" : w.err);
+  *count = iters;
+  LS_CUDA(w, cudaMemcpyAsync(Z, w.Z, (size_t)iters * n * sizeof(float2), cudaMemcpyDeviceToDevice, c.s));
+  LS_CUDA(w, cudaStreamSynchronize(c.s));
+  return VP_OK;
+}
+
 const char* vp_ls_last_error(void) { return g_ls_error.c_str(); }
 
 }  // extern "C"

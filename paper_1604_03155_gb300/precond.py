@@ -29,9 +29,12 @@ def problem(plan, N: int, k: float, seed: int, dev):
 
 
 def train(plan, net, N: int, k: float, seeds, krylov: int = 12, lr: float = 1e-3, steps_per_pair: int = 1,
-          restart: int = 20, dev="cuda:0", log=None) -> dict:
+          restart: int = 20, onpolicy: bool = False, dev="cuda:0", log=None) -> dict:
     """Online training on the pairs (A v_j, v_j), j = 0..krylov, and (b, u*)
-    of each contrast in ``seeds``."""
+    of each contrast in ``seeds``.  With ``onpolicy`` also on (A z_j, z_j) for
+    the directions z_j = M(v_j) of one flexible GMRES cycle preconditioned by
+    the network itself: when M is close to A^-1, A z_j is close to the v_j the
+    network is applied to inside the solver."""
     import torch
     x = torch.empty((3, N, N, N), dtype=torch.float32, device=dev)
     t = torch.empty((2, N, N, N), dtype=torch.float32, device=dev)
@@ -45,6 +48,10 @@ def train(plan, net, N: int, k: float, seeds, krylov: int = 12, lr: float = 1e-3
         pairs = [(b, ustar)]
         for v in vp.ls_krylov_basis(plan, q, b, krylov):
             pairs.append((vp.ls_operator(plan, q, v), v))
+        if onpolicy:
+            net.bind(q)
+            for z in vp.ls_flexible_basis(plan, q, b, krylov, net):
+                pairs.append((vp.ls_operator(plan, q, z), z))
         per = len(pairs)
         for r, e in pairs:
             vp.ls_training_pair(plan, q, r, None, e, x, t)

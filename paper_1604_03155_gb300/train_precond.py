@@ -36,17 +36,24 @@ def main():
     ap.add_argument("--restart", type=int, default=20)
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--slope", type=float, default=0.1, help="leaky-ReLU slope (1: linear network)")
+    ap.add_argument("--init", default=None, help="start from these weights (.npy) instead of the seeded init")
+    ap.add_argument("--first", type=int, default=0, help="index of the first training contrast")
+    ap.add_argument("--onpolicy", action="store_true", help="add pairs from the network's own FGMRES directions")
     ap.add_argument("--out", default=os.path.join(ROOT, "paper_1604_03155_gb300", "weights", "unet_ls_k30_n128"))
     a = ap.parse_args()
     os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
     plan = vp.Plan(3, a.N, "helmholtz", a.k, 1.8, precision="fp32")
     net = vp.UNet(a.N, 16, weights=I.unet_init_weights(I.BASE_SEED + 901), slope=a.slope)
-    tr = P.train(plan, net, a.N, a.k, [I.LS_TRAIN_SEED + i for i in range(a.contrasts)], krylov=a.krylov, lr=a.lr,
-                 restart=a.restart, log=lambda m: print(m, flush=True))
+    if a.init:
+        P.load_weights(net, a.init)
+    seeds = [I.LS_TRAIN_SEED + a.first + i for i in range(a.contrasts)]
+    tr = P.train(plan, net, a.N, a.k, seeds, krylov=a.krylov, lr=a.lr, restart=a.restart, onpolicy=a.onpolicy,
+                 log=lambda m: print(m, flush=True))
     P.save_weights(net, a.out + ".npy")
     ev = P.evaluate(plan, net, a.N, a.k, [I.LS_HELDOUT_SEED + i for i in range(a.heldout)], tol=a.tol,
                     restart=a.restart)
-    report = {"N": a.N, "k": a.k, "slope": a.slope, "contrasts": a.contrasts, "krylov_pairs": a.krylov, "lr": a.lr,
+    report = {"N": a.N, "k": a.k, "slope": a.slope, "contrasts": a.contrasts, "first": a.first, "init": a.init,
+              "onpolicy": a.onpolicy, "krylov_pairs": a.krylov, "lr": a.lr,
               "restart": a.restart, "tol": a.tol, "train": tr, "heldout": ev["summary"]}
     with open(a.out + ".json", "w") as fh:
         json.dump(report, fh, indent=1)

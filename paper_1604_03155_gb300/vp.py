@@ -84,6 +84,8 @@ _SIGNATURES = {
     "vp_ls_training_pair": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                     ctypes.POINTER(c_double)]),
     "vp_ls_krylov_basis": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, ctypes.POINTER(c_int)]),
+    "vp_ls_flexible_basis": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p,
+                                     ctypes.POINTER(c_int)]),
     "vp_unet_create": (c_int, [ctypes.POINTER(c_void_p), c_int, c_int]),
     "vp_unet_param_count": (c_int, [c_void_p, ctypes.POINTER(c_size_t)]),
     "vp_unet_set_stream": (c_int, [c_void_p, c_void_p]),
@@ -456,6 +458,18 @@ def ls_krylov_basis(plan: Plan, q, b, m: int):
     plan._sync_stream_to_torch(b)
     _lscheck(lib().vp_ls_krylov_basis(plan.handle, _ptr(q), _ptr(b), m, _ptr(V), ctypes.byref(cnt)))
     return V[:cnt.value]
+
+
+def ls_flexible_basis(plan: Plan, q, b, m: int, precond):
+    """Preconditioned directions z_0..z_{m-1} of one flexible GMRES cycle from b
+    with the network `precond` (bound to q), as an (m, *b.shape) complex64 tensor."""
+    import torch
+    Z = torch.empty((m,) + tuple(b.shape), dtype=torch.complex64, device=b.device)
+    cnt = c_int()
+    plan._sync_stream_to_torch(b)
+    _lscheck(lib().vp_ls_flexible_basis(plan.handle, _ptr(q), _ptr(b), m, ctypes.cast(lib().vp_unet_precond, c_void_p),
+                                        precond.handle, _ptr(Z), ctypes.byref(cnt)))
+    return Z[:cnt.value]
 
 
 class UNet:

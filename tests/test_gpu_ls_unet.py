@@ -110,6 +110,21 @@ def test_krylov_basis_matches_oracle_arnoldi():
         assert np.linalg.norm((V[j] - Vr[j]).ravel()) < 1e-4, j
 
 
+def test_flexible_basis_with_identity_network_is_the_arnoldi_basis():
+    """A network with all-zero weights makes the preconditioner the identity
+    (z = r exactly), so the flexible directions are the plain Arnoldi vectors."""
+    N, k, m = 16, 8.0, 6
+    plan, q, uinc, b = _ls_setup(N, k, I.LS_TRAIN_SEED + 2)
+    net = UNet(N, 16)
+    net.set_weights(np.zeros(net.nparams, np.float32))
+    net.bind(q)
+    Z = vp.ls_flexible_basis(plan, q, b, m, net)
+    V = vp.ls_krylov_basis(plan, q, b, m)
+    assert Z.shape[0] == m
+    assert torch.equal(Z, V[:m])
+    net.close()
+
+
 def test_ls_solve_full_size_true_residual():
     """N = 128, k = 30, q = smoothed cube + perturbations, plane wave: plain
     GMRES reaches a true FP64 residual below 1e-6."""

@@ -104,3 +104,34 @@ def test_tc_unsupported_combinations():
     p.apply_grad(f)
     p.status()
     p.close()
+
+
+def test_tc_host_pointers_noalloc_and_real_io():
+    """The other entry paths take the tensor-core pass too: host arrays (staged
+    through the plan's buffer) and the no-allocation apply give the device
+    result bit for bit; the Laplace real path (float32 in, float32 out) agrees
+    with the complex one."""
+    import ctypes
+
+    from paper_1604_03155_gb300 import vp
+    f = I.sample_gaussians(I.random_gaussians(I.BASE_SEED + 701, 4, 3), N).astype(np.complex64)
+    plan = Plan(3, N, "helmholtz", 30.0, 1.8, precision="tc_bf16x2")
+    ft = torch.from_numpy(f).to(DEV)
+    dev = plan.apply(ft).cpu().numpy()
+    host = plan.apply(f)
+    assert np.array_equal(host, dev)
+    out = torch.empty_like(ft)
+    st = vp.lib().vp_apply_noalloc(ctypes.c_void_p(plan.handle), ctypes.c_void_p(ft.data_ptr()),
+                                   ctypes.c_void_p(out.data_ptr()), vp.VP_C64)
+    assert st == vp.VP_OK
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), dev)
+    plan.close()
+    lap = Plan(3, N, "laplace", 0.0, 1.8, precision="tc_fp16x2")
+    fr = np.ascontiguousarray(f.real.astype(np.float32))
+    real = lap.apply(torch.from_numpy(fr).to(DEV)).cpu().numpy()
+    cplx = lap.apply(torch.from_numpy(fr.astype(np.complex64)).to(DEV)).cpu().numpy()
+    assert real.dtype == np.float32
+    assert A.rel_l2(real, cplx.real) < BAR["tc_fp16x2"]
+    lap.status()
+    lap.close()

@@ -10,7 +10,7 @@
 // accumulation), complex64 vectors and the FP32 apply.  The preconditioner is a
 // caller function (e.g. the learned network, vp_unet_precond); when a
 // preconditioned cycle fails to reduce the residual the solver falls back to
-// plain GMRES.  Convergence is judged by the true residual of the FP64
+// plain GMRES.  Convergence is measured by the true residual of the FP64
 // operator: ||b - A u|| / ||b|| with A and b evaluated in FP64.
 #include <cuda_runtime.h>
 #include <math.h>

@@ -150,7 +150,7 @@ def test_untrained_preconditioner_falls_back_and_still_converges():
 def test_trained_preconditioner_against_plain_gmres(tag):
     """Held-out contrasts (N = 128, k = 30, plane wave): plain flexible GMRES
     against the trained network as right preconditioner, same restart length,
-    both judged by the true FP64 residual.  The committed reports
+    both measured by the true FP64 residual.  The committed reports
     (weights/unet_ls_k30_n128_<tag>.json, 50 held-out contrasts) measured 20.2
     plain iterations against 30.6 (trained on 300 contrasts, no fallback) and
     66.4 (2000 contrasts, every solve fell back): on this well-conditioned

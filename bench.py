@@ -419,6 +419,58 @@ def run_ours(args, wl):
         plan.set_precision(prec)
         return sum(a.elapsed_time(b) for a, b in zip(s_, e_)) / reps
 
+    def cufft_form(reps: int = 20) -> dict:
+        """The same apply with cuFFT (torch.fft) for comparison only: f zero-padded to
+        (2N)^d, one forward transform, per field a multiply by the full (2N)^d
+        multiplier (unfolded from the plan's FP64 octants) and an inverse transform,
+        cropped to N^d.  Not a product path."""
+        n2 = 2 * N
+        m = torch.arange(n2, device=dev)
+        fold = torch.minimum(m, n2 - m)
+
+        def full(octant, odd_axis=None):
+            g = torch.from_numpy(octant).to(dev)
+            idx = [fold.view([n2 if a == b else 1 for b in range(d)]) for a in range(d)]
+            G = g[tuple(idx)]
+            if odd_axis is not None:
+                sgn = torch.where(m > N, -1.0, 1.0).to(torch.float64).view([n2 if b == odd_axis else 1 for b in range(d)])
+                G = G * sgn
+            return G.to(torch.complex64)
+
+        Gs = [full(plan.get_array("ghat"))]
+        if wl["grad"]:
+            Gs += [full(plan.get_array("ghatj", j), j) for j in range(d)]
+        crop = tuple(slice(0, N) for _ in range(d))
+        fpad = torch.zeros((n2,) * d, dtype=torch.complex64, device=dev)
+
+        def cstep():
+            fpad[crop] = f
+            F = torch.fft.fftn(fpad)
+            return [torch.fft.ifftn(F * G)[crop] for G in Gs]
+
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                outs = cstep()
+            s_ = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+            e_ = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+            for i in range(reps):
+                flush.fill_(float(i))
+                s_[i].record(stream)
+                outs = cstep()
+                e_[i].record(stream)
+        torch.cuda.synchronize(dev)
+        ms = sum(a.elapsed_time(b) for a, b in zip(s_, e_)) / reps
+        ref = outs[0].cpu().numpy()
+        mine = phi.cpu().numpy()
+        diff = float(np.linalg.norm((mine - ref).ravel()) / np.linalg.norm(ref.ravel()))
+        del Gs, fpad, outs
+        torch.cuda.empty_cache()
+        return {"value": (N ** d) / (ms / 1000.0), "ms_per_step": ms, "speedup_of_this_form": ms / ms_per_step,
+                "rel_l2_phi_vs_this_form": diff,
+                "what": "torch.fft (cuFFT) C2C on the zero-padded (2N)^d grid, full multiplier, no pruning or fusion"}
+
+    cufft = cufft_form() if f32io else None
+
     # FP64 form on the same grid (same kernels in double), for "vs plain FP64";
     # the tensor-core forms are also compared with the FP32 form
     fp64 = None
@@ -451,6 +503,7 @@ def run_ours(args, wl):
             "gpu_launches": launches_per_step * args.steps,
             "precompute_s": precompute_s,
             "fp64_form": fp64,
+            "cufft_form": cufft,
         }
         if fp32_form is not None:
             line["fp32_form"] = fp32_form

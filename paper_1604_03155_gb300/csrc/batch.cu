@@ -23,6 +23,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -335,8 +336,9 @@ vp_status graph_launch(vp_batch b, const BatchLaunch& L, int grid) {
   return VP_OK;
 }
 
-// Per-density applies spread over side streams (density i on stream i mod 8),
-// captured once per pointer set into a graph and replayed.
+// Per-density applies spread over side streams, captured once per pointer set
+// into a graph and replayed.  Densities are placed largest first, each on the
+// stream with the least work so far (work = N^d), so the streams finish together.
 vp_status run_streams(vp_batch b, const void* const* f, void* const* phi) {
   bool same = b->sexec && (int)b->sgraph_f.size() == b->count;
   for (int i = 0; same && i < b->count; ++i) same = b->sgraph_f[i] == f[i] && b->sgraph_phi[i] == phi[i];
@@ -361,9 +363,23 @@ vp_status run_streams(vp_batch b, const void* const* f, void* const* phi) {
     cudaError_t e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) e = cudaEventRecord(b->fork_ev, origin);
     for (int k = 0; k < kSideStreams && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->side[k], b->fork_ev, 0);
-    for (int i = 0; i < b->count && e == cudaSuccess && st == VP_OK; ++i) {
+    std::vector<int> order(b->count);
+    std::vector<double> work(b->count, 1.0);
+    for (int i = 0; i < b->count; ++i) {
+      order[i] = i;
+      int d = 0, N = 0;
+      if (vp_plan_info(b->plans[i], &d, &N, nullptr, nullptr, nullptr) == VP_OK) work[i] = std::pow((double)N, d);
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work[x] > work[y]; });
+    double load[kSideStreams] = {0.0};
+    for (int j = 0; j < b->count && e == cudaSuccess && st == VP_OK; ++j) {
+      const int i = order[j];
+      int k = 0;
+      for (int c = 1; c < kSideStreams; ++c)
+        if (load[c] < load[k]) k = c;
+      load[k] += work[i];
       cudaStream_t saved = plan_stream(b->plans[i]);
-      vp_plan_set_stream(b->plans[i], b->side[i % kSideStreams]);
+      vp_plan_set_stream(b->plans[i], b->side[k]);
       st = vp_apply(b->plans[i], f[i], phi[i], VP_C64);
       vp_plan_set_stream(b->plans[i], saved);
     }
@@ -530,9 +546,20 @@ vp_status vp_batch_create(vp_batch* out, int count, const vp_plan* plans) {
   }
   for (int i = 0; i < count; ++i)
     for (size_t p = 1; p < per[i].size(); ++p) per[i][p].dep_need = per[i][p].dep_need_orig = per[i][p - 1].ntiles;
+  // within a level, the largest densities first: their longer dependency
+  // chains start early and the small ones fill the tail
+  std::vector<int> order(count);
+  std::vector<double> work(count);
+  for (int i = 0; i < count; ++i) {
+    int d, N;
+    vp_plan_info(plans[i], &d, &N, nullptr, nullptr, nullptr);
+    order[i] = i;
+    work[i] = std::pow((double)N, d);
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work[x] > work[y]; });
   long long base = 0;
   for (int level = 0; level < 5; ++level)
-    for (int i = 0; i < count; ++i)
+    for (int i : order)
       if (level < (int)per[i].size()) {
         BatchPass bp = per[i][level];
         bp.item_base = base;

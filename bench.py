@@ -221,6 +221,18 @@ def time_oracle(wl: dict, f: np.ndarray, steps: int, Gf=None, Gjf=None):
     return {"value": pts / wall, "seconds": wall, "cores": round(cpu / wall, 2), "out": out}
 
 
+def max_over_ranks(value: float, device) -> float:
+    """The maximum of `value` over the ranks of the default process group (the
+    slowest rank sets the job's time); `value` itself with one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def density_for(name: str, wl: dict, rank: int = 0):
     from paper_1604_03155_gb300 import inputs as I
     if name == "laplace3d_single_gaussian":
@@ -367,9 +379,7 @@ def run_ours(args, wl):
     clk = clocks.stop()
     total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, stops))
     if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, dev)
     ms_per_step = total_ms / args.steps
     value = (N ** d) * world / (ms_per_step / 1000.0)
 

@@ -224,7 +224,8 @@ vp_status vp_batch_destroy(vp_batch b);
  * volume potential (3D Helmholtz plan, FP32 precision; complex64 vectors,
  * device pointers).  The paper solves the dual density form with Bi-CGStab;
  * vp_ls_solve runs right-preconditioned flexible GMRES(restart) (classical
- * Gram-Schmidt with one re-orthogonalisation, FP64 inner products).  `precond`
+ * Gram-Schmidt with one re-orthogonalisation; inner products from FP32
+ * products and per-thread partial sums, summed across threads in FP64).  `precond`
  * (may be NULL) maps a residual r to z ~ A^-1 r on `stream`; if a
  * preconditioned cycle fails to reduce the residual the solve continues as
  * plain GMRES (stats->used_fallback).  The solve stops when the recurrence
@@ -261,7 +262,7 @@ vp_status vp_ls_training_pair(vp_plan plan, const float* q, const void* b, const
                               float* x_out, float* t_out, double* rnorm);
 /* Orthonormal Krylov basis of the plain operator started from b: the vectors
  * v_0 = b/||b||, v_1, ..., v_m that the first cycle of unpreconditioned GMRES
- * builds (classical Gram-Schmidt applied twice, FP64 inner products), with
+ * builds (classical Gram-Schmidt applied twice, as in vp_ls_solve), with
  * A [v_0..v_{m-1}] = [v_0..v_m] H, H upper Hessenberg with h_{j+1,j} > 0.
  * V: device buffer of (m+1) x N^3 complex64, vector j at offset j N^3;
  * *count: vectors written (m+1; fewer only at an exact breakdown).  m in

@@ -6,8 +6,9 @@
 // plan's volume potential (Green's function of -(Delta + k^2)).  The paper
 // solves the dual density form with Bi-CGStab; this solver is right-
 // preconditioned flexible GMRES(m) (Saad 1993) with classical Gram-Schmidt and
-// one re-orthogonalisation (two batched dot kernels per iteration, FP64
-// accumulation), complex64 vectors and the FP32 apply.  The preconditioner is a
+// one re-orthogonalisation (two batched dot kernels per iteration: FP32
+// products and per-thread partial sums, FP64 sums across threads), complex64
+// vectors and the FP32 apply.  The preconditioner is a
 // caller function (e.g. the learned network, vp_unet_precond); when a
 // preconditioned cycle fails to reduce the residual the solver falls back to
 // plain GMRES.  Convergence is measured by the true residual of the FP64
@@ -82,23 +83,26 @@ __global__ void k_to64(double2* __restrict__ out, const float2* __restrict__ in,
     out[i] = make_double2(in[i].x, in[i].y);
 }
 
-// partial[blk][j] = sum_i conj(V_j[i]) w[i] for j < m (FP64), per block
+// partial[blk][j] = sum_i conj(V_j[i]) w[i] for j < m, per block.  Each thread
+// sums its strided share (n / (304 x 256) terms, about 27 at N = 128) in FP32;
+// the sums across threads and blocks are FP64.  (FP64 multiply-adds for every
+// term would cost more than the apply on a GPU whose FP64 rate is 1/64 of FP32.)
 __global__ void __launch_bounds__(kRedThreads) k_mdot(const float2* __restrict__ V, long long ldv, int m,
                                                       const float2* __restrict__ w, long long n, double2* __restrict__ partial) {
   __shared__ double2 red[kRedThreads / 32][kMaxBasis + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int j0 = 0; j0 < m; j0 += 8) {
-    double2 acc[8];
+    float2 acc[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = make_double2(0.0, 0.0);
+    for (int q = 0; q < 8; ++q) acc[q] = make_float2(0.f, 0.f);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
       const float2 wi = w[i];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         if (j0 + q < m) {
           const float2 v = V[(long long)(j0 + q) * ldv + i];
-          acc[q].x += (double)v.x * wi.x + (double)v.y * wi.y;
-          acc[q].y += (double)v.x * wi.y - (double)v.y * wi.x;
+          acc[q].x = fmaf(v.x, wi.x, fmaf(v.y, wi.y, acc[q].x));
+          acc[q].y = fmaf(v.x, wi.y, fmaf(-v.y, wi.x, acc[q].y));
         }
       }
     }
@@ -142,20 +146,21 @@ __global__ void __launch_bounds__(kRedThreads) k_norm2(const C* __restrict__ x, 
   }
 }
 
-// w -= sum_j h[j] V_j   (h on the device)
+// w -= sum_j h[j] V_j   (h on the device), FP32 arithmetic: w and V are FP32, and
+// the second Gram-Schmidt pass removes what the first pass's rounding leaves
 __global__ void k_mupdate(float2* __restrict__ w, const float2* __restrict__ V, long long ldv, int m,
                           const double2* __restrict__ h, long long n) {
-  __shared__ double2 hs[kMaxBasis];
-  for (int j = threadIdx.x; j < m; j += blockDim.x) hs[j] = h[j];
+  __shared__ float2 hs[kMaxBasis];
+  for (int j = threadIdx.x; j < m; j += blockDim.x) hs[j] = make_float2((float)h[j].x, (float)h[j].y);
   __syncthreads();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    double ax = w[i].x, ay = w[i].y;
+    float ax = w[i].x, ay = w[i].y;
     for (int j = 0; j < m; ++j) {
       const float2 v = V[(long long)j * ldv + i];
-      ax -= hs[j].x * v.x - hs[j].y * v.y;
-      ay -= hs[j].x * v.y + hs[j].y * v.x;
+      ax = fmaf(-hs[j].x, v.x, fmaf(hs[j].y, v.y, ax));
+      ay = fmaf(-hs[j].x, v.y, fmaf(-hs[j].y, v.x, ay));
     }
-    w[i] = make_float2((float)ax, (float)ay);
+    w[i] = make_float2(ax, ay);
   }
 }
 

@@ -32,6 +32,7 @@ using cd = std::complex<double>;
 constexpr int kRedBlocks = 304;  // 2 x 152 SMs
 constexpr int kRedThreads = 256;
 constexpr int kMaxBasis = 64;    // restart length limit
+constexpr int kStepWords = 2 * (kMaxBasis + 1) + 1;
 
 __global__ void k_qmul(float2* __restrict__ out, const float* __restrict__ q, const float2* __restrict__ in, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -181,6 +182,43 @@ __global__ void k_mcombine(float2* __restrict__ x, const float2* __restrict__ Z,
   }
 }
 
+// out[j] = sum over the blocks' partial dots (FP64), j < m
+__global__ void k_reduce_dots(const double2* __restrict__ partial, int m, int blocks, double2* __restrict__ out) {
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int b = 0; b < blocks; ++b) {
+      s.x += partial[(long long)b * m + j].x;
+      s.y += partial[(long long)b * m + j].y;
+    }
+    out[j] = s;
+  }
+}
+
+// out = (||x||, 1/||x|| or 0) from the blocks' partial sums of |x|^2
+__global__ void k_reduce_norm(const double* __restrict__ partial, int blocks, double2* __restrict__ out) {
+  __shared__ double red[kRedThreads];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < blocks; b += blockDim.x) s += partial[b];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double nrm = sqrt(red[0]);
+    *out = make_double2(nrm, nrm > 0.0 ? 1.0 / nrm : 0.0);
+  }
+}
+
+// x *= 1/||x|| with the norm on the device (left unchanged when it is zero)
+__global__ void k_scale_by_norm(float2* __restrict__ x, const double2* __restrict__ nrm, long long n) {
+  const double s = nrm->y;
+  if (s == 0.0) return;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] = make_float2((float)(x[i].x * s), (float)(x[i].y * s));
+}
+
 __global__ void k_scale_copy(float2* __restrict__ out, const float2* __restrict__ in, double s, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     out[i] = make_float2((float)(in[i].x * s), (float)(in[i].y * s));
@@ -220,8 +258,14 @@ struct Work {
   double2* d0 = nullptr;  // FP64 scratch for the true residual (4 x n)
   void* red = nullptr;    // reduction partials
   double2* hdev = nullptr;
+  // one Arnoldi step's coefficients on the device and their pinned host copy:
+  // [0, 65) first Gram-Schmidt pass, [65, 130) second pass, [130] (norm, 1/norm)
+  double2* hstep = nullptr;
+  double2* hstep_host = nullptr;
   std::string err;
   ~Work() {
+    cudaFree(hstep);
+    cudaFreeHost(hstep_host);
     cudaFree(V);
     cudaFree(Z);
     cudaFree(t0);
@@ -272,24 +316,6 @@ vp_status norm2(const Ctx& c, Work& w, const float2* x, double* out) {
   double s = 0.0;
   for (double v : h) s += v;
   *out = sqrt(s);
-  return VP_OK;
-}
-
-// h[0..m) = V^H x (FP64)
-vp_status mdot(const Ctx& c, Work& w, int m, const float2* x, cd* h) {
-  double2* part = reinterpret_cast<double2*>(w.red);
-  k_mdot<<<kRedBlocks, kRedThreads, 0, c.s>>>(w.V, c.n, m, x, c.n, part);
-  std::vector<double2> hp((size_t)kRedBlocks * m);
-  LS_CUDA(w, cudaMemcpyAsync(hp.data(), part, hp.size() * sizeof(double2), cudaMemcpyDeviceToHost, c.s));
-  LS_CUDA(w, cudaStreamSynchronize(c.s));
-  for (int j = 0; j < m; ++j) {
-    double ax = 0.0, ay = 0.0;
-    for (int b = 0; b < kRedBlocks; ++b) {
-      ax += hp[(size_t)b * m + j].x;
-      ay += hp[(size_t)b * m + j].y;
-    }
-    h[j] = cd(ax, ay);
-  }
   return VP_OK;
 }
 
@@ -377,19 +403,29 @@ vp_status fgmres_cycle(const Ctx& c, Work& w, const float2* b, float2* x, double
     }
     if ((st = op32(c, w, zj, wv)) != VP_OK) return st;
     ++*matvecs;
-    // classical Gram-Schmidt, twice
-    std::vector<cd> h1(j + 1), h2(j + 1);
-    if ((st = mdot(c, w, j + 1, wv, h1.data())) != VP_OK) return st;
-    if ((st = upload(c, w, h1.data(), j + 1)) != VP_OK) return st;
-    k_mupdate<<<grid_for(n), 256, 0, c.s>>>(wv, w.V, n, j + 1, w.hdev, n);
-    if ((st = mdot(c, w, j + 1, wv, h2.data())) != VP_OK) return st;
-    if ((st = upload(c, w, h2.data(), j + 1)) != VP_OK) return st;
-    k_mupdate<<<grid_for(n), 256, 0, c.s>>>(wv, w.V, n, j + 1, w.hdev, n);
-    for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h1[i] + h2[i];
-    double hn = 0.0;
-    if ((st = norm2(c, w, wv, &hn)) != VP_OK) return st;
+    // classical Gram-Schmidt, twice; coefficients and the norm stay on the
+    // device, and one copy per step brings them to the host for H and Givens
+    double2* h1d = w.hstep;
+    double2* h2d = w.hstep + (kMaxBasis + 1);
+    double2* nd = w.hstep + 2 * (kMaxBasis + 1);
+    double2* part = reinterpret_cast<double2*>(w.red);
+    k_mdot<<<kRedBlocks, kRedThreads, 0, c.s>>>(w.V, n, j + 1, wv, n, part);
+    k_reduce_dots<<<1, 64, 0, c.s>>>(part, j + 1, kRedBlocks, h1d);
+    k_mupdate<<<grid_for(n), 256, 0, c.s>>>(wv, w.V, n, j + 1, h1d, n);
+    k_mdot<<<kRedBlocks, kRedThreads, 0, c.s>>>(w.V, n, j + 1, wv, n, part);
+    k_reduce_dots<<<1, 64, 0, c.s>>>(part, j + 1, kRedBlocks, h2d);
+    k_mupdate<<<grid_for(n), 256, 0, c.s>>>(wv, w.V, n, j + 1, h2d, n);
+    k_norm2<float2><<<kRedBlocks, kRedThreads, 0, c.s>>>(wv, n, reinterpret_cast<double*>(w.red));
+    k_reduce_norm<<<1, kRedThreads, 0, c.s>>>(reinterpret_cast<const double*>(w.red), kRedBlocks, nd);
+    k_scale_by_norm<<<grid_for(n), 256, 0, c.s>>>(wv, nd, n);
+    LS_CUDA(w, cudaGetLastError());
+    LS_CUDA(w, cudaMemcpyAsync(w.hstep_host, w.hstep, kStepWords * sizeof(double2), cudaMemcpyDeviceToHost, c.s));
+    LS_CUDA(w, cudaStreamSynchronize(c.s));
+    const double2* hh = w.hstep_host;
+    for (int i = 0; i <= j; ++i)
+      H[(size_t)i * m + j] = cd(hh[i].x + hh[kMaxBasis + 1 + i].x, hh[i].y + hh[kMaxBasis + 1 + i].y);
+    const double hn = hh[2 * (kMaxBasis + 1)].x;
     H[(size_t)(j + 1) * m + j] = hn;
-    if (hn > 0) k_scale_copy<<<grid_for(n), 256, 0, c.s>>>(wv, wv, 1.0 / hn, n);
     // Givens rotations on the new column
     for (int i = 0; i < j; ++i) {
       const cd a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
@@ -465,6 +501,10 @@ vp_status alloc_work(Work& w, long long n, int m, bool basis) {
   LS_CUDA(w, cudaMalloc(&w.d0, 4 * n * sizeof(double2)));
   LS_CUDA(w, cudaMalloc(&w.red, (size_t)kRedBlocks * (kMaxBasis + 1) * sizeof(double2)));
   LS_CUDA(w, cudaMalloc(&w.hdev, (kMaxBasis + 1) * sizeof(double2)));
+  if (basis) {
+    LS_CUDA(w, cudaMalloc(&w.hstep, kStepWords * sizeof(double2)));
+    LS_CUDA(w, cudaMallocHost(&w.hstep_host, kStepWords * sizeof(double2)));
+  }
   return VP_OK;
 }
 

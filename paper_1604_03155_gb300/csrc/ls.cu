@@ -30,6 +30,7 @@ namespace {
 using cd = std::complex<double>;
 
 constexpr int kRedBlocks = 304;  // 2 x 152 SMs
+constexpr int kDotBlocks = 1216; // 8 x 152 SMs: the batched dots need many loads in flight
 constexpr int kRedThreads = 256;
 constexpr int kMaxBasis = 64;    // restart length limit
 constexpr int kStepWords = 2 * (kMaxBasis + 1) + 1;
@@ -96,12 +97,34 @@ __global__ void __launch_bounds__(kRedThreads) k_mdot(const float2* __restrict__
     float2 acc[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[q] = make_float2(0.f, 0.f);
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const int mq = m - j0 < 8 ? m - j0 : 8;
+    const float2* Vb = V + (long long)j0 * ldv;
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    // four independent elements per trip (more loads in flight), no bounds checks
+    for (; i + 3 * stride < n; i += 4 * stride) {
+      float2 wi[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) wi[u] = w[i + u * stride];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (q < mq) {
+          const float2* Vq = Vb + (long long)q * ldv + i;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float2 v = Vq[u * stride];
+            acc[q].x = fmaf(v.x, wi[u].x, fmaf(v.y, wi[u].y, acc[q].x));
+            acc[q].y = fmaf(v.x, wi[u].y, fmaf(-v.y, wi[u].x, acc[q].y));
+          }
+        }
+      }
+    }
+    for (; i < n; i += stride) {
       const float2 wi = w[i];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        if (j0 + q < m) {
-          const float2 v = V[(long long)(j0 + q) * ldv + i];
+        if (q < mq) {
+          const float2 v = Vb[(long long)q * ldv + i];
           acc[q].x = fmaf(v.x, wi.x, fmaf(v.y, wi.y, acc[q].x));
           acc[q].y = fmaf(v.x, wi.y, fmaf(-v.y, wi.x, acc[q].y));
         }
@@ -182,16 +205,26 @@ __global__ void k_mcombine(float2* __restrict__ x, const float2* __restrict__ Z,
   }
 }
 
-// out[j] = sum over the blocks' partial dots (FP64), j < m
-__global__ void k_reduce_dots(const double2* __restrict__ partial, int m, int blocks, double2* __restrict__ out) {
-  for (int j = threadIdx.x; j < m; j += blockDim.x) {
-    double2 s = make_double2(0.0, 0.0);
-    for (int b = 0; b < blocks; ++b) {
-      s.x += partial[(long long)b * m + j].x;
-      s.y += partial[(long long)b * m + j].y;
-    }
-    out[j] = s;
+// out[j] = sum over the blocks' partial dots (FP64): one thread block per j
+__global__ void __launch_bounds__(kRedThreads) k_reduce_dots(const double2* __restrict__ partial, int m, int blocks,
+                                                             double2* __restrict__ out) {
+  __shared__ double2 red[kRedThreads];
+  const int j = blockIdx.x;
+  double2 s = make_double2(0.0, 0.0);
+  for (int b = threadIdx.x; b < blocks; b += blockDim.x) {
+    s.x += partial[(long long)b * m + j].x;
+    s.y += partial[(long long)b * m + j].y;
   }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      red[threadIdx.x].x += red[threadIdx.x + o].x;
+      red[threadIdx.x].y += red[threadIdx.x + o].y;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[j] = red[0];
 }
 
 // out = (||x||, 1/||x|| or 0) from the blocks' partial sums of |x|^2
@@ -409,11 +442,11 @@ vp_status fgmres_cycle(const Ctx& c, Work& w, const float2* b, float2* x, double
     double2* h2d = w.hstep + (kMaxBasis + 1);
     double2* nd = w.hstep + 2 * (kMaxBasis + 1);
     double2* part = reinterpret_cast<double2*>(w.red);
-    k_mdot<<<kRedBlocks, kRedThreads, 0, c.s>>>(w.V, n, j + 1, wv, n, part);
-    k_reduce_dots<<<1, 64, 0, c.s>>>(part, j + 1, kRedBlocks, h1d);
+    k_mdot<<<kDotBlocks, kRedThreads, 0, c.s>>>(w.V, n, j + 1, wv, n, part);
+    k_reduce_dots<<<j + 1, kRedThreads, 0, c.s>>>(part, j + 1, kDotBlocks, h1d);
     k_mupdate<<<grid_for(n), 256, 0, c.s>>>(wv, w.V, n, j + 1, h1d, n);
-    k_mdot<<<kRedBlocks, kRedThreads, 0, c.s>>>(w.V, n, j + 1, wv, n, part);
-    k_reduce_dots<<<1, 64, 0, c.s>>>(part, j + 1, kRedBlocks, h2d);
+    k_mdot<<<kDotBlocks, kRedThreads, 0, c.s>>>(w.V, n, j + 1, wv, n, part);
+    k_reduce_dots<<<j + 1, kRedThreads, 0, c.s>>>(part, j + 1, kDotBlocks, h2d);
     k_mupdate<<<grid_for(n), 256, 0, c.s>>>(wv, w.V, n, j + 1, h2d, n);
     k_norm2<float2><<<kRedBlocks, kRedThreads, 0, c.s>>>(wv, n, reinterpret_cast<double*>(w.red));
     k_reduce_norm<<<1, kRedThreads, 0, c.s>>>(reinterpret_cast<const double*>(w.red), kRedBlocks, nd);
@@ -499,7 +532,7 @@ vp_status alloc_work(Work& w, long long n, int m, bool basis) {
   LS_CUDA(w, cudaMalloc(&w.t0, n * sizeof(float2)));
   LS_CUDA(w, cudaMalloc(&w.t1, n * sizeof(float2)));
   LS_CUDA(w, cudaMalloc(&w.d0, 4 * n * sizeof(double2)));
-  LS_CUDA(w, cudaMalloc(&w.red, (size_t)kRedBlocks * (kMaxBasis + 1) * sizeof(double2)));
+  LS_CUDA(w, cudaMalloc(&w.red, (size_t)kDotBlocks * (kMaxBasis + 1) * sizeof(double2)));
   LS_CUDA(w, cudaMalloc(&w.hdev, (kMaxBasis + 1) * sizeof(double2)));
   if (basis) {
     LS_CUDA(w, cudaMalloc(&w.hstep, kStepWords * sizeof(double2)));

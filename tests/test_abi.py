@@ -66,3 +66,22 @@ def test_null_safety_and_strings(lib):
         assert lib.vp_fft_length_supported(n2) == 1
     for n2 in (10, 20, 100, 7):
         assert lib.vp_fft_length_supported(n2) == 0
+
+
+def test_null_arguments_of_the_solver_network_and_batch_entry_points(lib):
+    """Every entry point rejects a missing handle with VP_ERR_INVALID_ARG before
+    touching the device."""
+    import ctypes
+    cnt = ctypes.c_int(0)
+    assert lib.vp_plan_set_precision(None, vp.VP_FP32) == vp.VP_ERR_INVALID_ARG
+    assert lib.vp_plan_status(None) == vp.VP_ERR_INVALID_ARG
+    assert lib.vp_ls_operator(None, None, None, None) == vp.VP_ERR_INVALID_ARG
+    assert lib.vp_ls_rhs(None, None, None, None) == vp.VP_ERR_INVALID_ARG
+    assert lib.vp_ls_solve(None, None, None, None, None, None, None) == vp.VP_ERR_INVALID_ARG
+    assert lib.vp_ls_krylov_basis(None, None, None, 4, None, ctypes.byref(cnt)) == vp.VP_ERR_INVALID_ARG
+    assert lib.vp_ls_flexible_basis(None, None, None, 4, None, None, None, ctypes.byref(cnt)) == vp.VP_ERR_INVALID_ARG
+    assert lib.vp_ls_last_error()
+    assert lib.vp_unet_set_slope(None, 0.5) == vp.VP_ERR_INVALID_ARG
+    assert lib.vp_unet_destroy(None) == vp.VP_OK
+    assert lib.vp_batch_apply(None, None, None) == vp.VP_ERR_INVALID_ARG
+    assert lib.vp_batch_destroy(None) == vp.VP_OK

@@ -522,7 +522,10 @@ vp_status check_plan(vp_plan plan, long long* n, double* k2) {
   return VP_OK;
 }
 
-vp_status alloc_work(Work& w, long long n, int m, bool basis) {
+// basis: the Arnoldi and preconditioned-direction vectors; fp64: the FP64
+// scratch of the true residual (also used as plain scratch by the callers
+// that take it)
+vp_status alloc_work(Work& w, long long n, int m, bool basis, bool fp64 = true) {
   w.n = n;
   w.m = m;
   if (basis) {
@@ -531,7 +534,7 @@ vp_status alloc_work(Work& w, long long n, int m, bool basis) {
   }
   LS_CUDA(w, cudaMalloc(&w.t0, n * sizeof(float2)));
   LS_CUDA(w, cudaMalloc(&w.t1, n * sizeof(float2)));
-  LS_CUDA(w, cudaMalloc(&w.d0, 4 * n * sizeof(double2)));
+  if (fp64) LS_CUDA(w, cudaMalloc(&w.d0, 4 * n * sizeof(double2)));
   LS_CUDA(w, cudaMalloc(&w.red, (size_t)kDotBlocks * (kMaxBasis + 1) * sizeof(double2)));
   LS_CUDA(w, cudaMalloc(&w.hdev, (kMaxBasis + 1) * sizeof(double2)));
   if (basis) {
@@ -552,7 +555,7 @@ vp_status vp_ls_operator(vp_plan plan, const float* q, const void* u, void* out)
   if (st != VP_OK) return st;
   if (!q || !u || !out || u == out) return ls_fail(VP_ERR_INVALID_ARG, "q, u, out must be distinct device pointers");
   Work w;
-  if ((st = alloc_work(w, n, 0, false)) != VP_OK) return ls_fail(st, w.err);
+  if ((st = alloc_work(w, n, 0, false, false)) != VP_OK) return ls_fail(st, w.err);
   Ctx c{plan, q, n, k2, get_stream(plan)};
   st = op32(c, w, reinterpret_cast<const float2*>(u), reinterpret_cast<float2*>(out));
   cudaStreamSynchronize(c.s);
@@ -566,7 +569,7 @@ vp_status vp_ls_rhs(vp_plan plan, const float* q, const void* u_inc, void* b) {
   if (st != VP_OK) return st;
   if (!q || !u_inc || !b || u_inc == b) return ls_fail(VP_ERR_INVALID_ARG, "q, u_inc, b must be distinct device pointers");
   Work w;
-  if ((st = alloc_work(w, n, 0, false)) != VP_OK) return ls_fail(st, w.err);
+  if ((st = alloc_work(w, n, 0, false, false)) != VP_OK) return ls_fail(st, w.err);
   Ctx c{plan, q, n, k2, get_stream(plan)};
   k_qmul<<<grid_for(n), 256, 0, c.s>>>(w.t0, q, reinterpret_cast<const float2*>(u_inc), n);
   st = vp_apply(plan, w.t0, w.t1, VP_C64);

@@ -7,10 +7,15 @@ u = k^2 V[q (u + u_inc)] with V the volume potential of the Green's function of
 
     A u := u - k^2 V[q u] = k^2 V[q u_inc] =: b.
 
-(The paper solves the dual density form; the field form has the same operator
-spectrum and is what the solver here uses.)  V is ``oracle.apply.apply_fft2n``
-with the Helmholtz multiplier.  ``dense_solve`` builds A column by column and
-solves it directly (small N only); ``gmres`` is textbook restarted GMRES.
+The paper's dual (density) form of Section 5.3 puts the unknown in the
+source: with s = k^2 q (u + u_inc) the scattered field is u = V[s] and
+
+    B s := s - k^2 q V[s] = k^2 q u_inc,
+
+(``op_density``, ``rhs_density``).  V is ``oracle.apply.apply_fft2n`` with the
+Helmholtz multiplier.  ``dense_solve`` builds A (or B) column by column and
+solves it directly (small N only); ``gmres`` is textbook restarted GMRES and
+``bicgstab`` textbook Bi-CGStab, the paper's iteration.
 """
 from __future__ import annotations
 
@@ -21,9 +26,14 @@ from . import kernel as K
 
 
 class LSProblem:
-    def __init__(self, N: int, k: float, q: np.ndarray, L: float = 1.8):
+    """The field-form operator on an N^d grid (d = q.ndim); L defaults to the
+    paper's 1.8 (3D) or 1.5 (2D)."""
+
+    def __init__(self, N: int, k: float, q: np.ndarray, L: float | None = None):
         self.N, self.k, self.q = N, k, np.asarray(q, dtype=np.float64)
-        T = K.T_octant_by_sums(3, N, "helmholtz", k, L)
+        self.d = self.q.ndim
+        L = (1.8 if self.d == 3 else 1.5) if L is None else L
+        T = K.T_octant_by_sums(self.d, N, "helmholtz", k, L)
         self.G = K.ghat_full_from_octant(K.ghat_octant_by_sums(T, N))
 
     def V(self, f):
@@ -35,18 +45,26 @@ class LSProblem:
     def rhs(self, u_inc):
         return self.k ** 2 * self.V(self.q * u_inc)
 
+    def op_density(self, s):
+        return s - self.k ** 2 * self.q * self.V(s)
+
+    def rhs_density(self, u_inc):
+        return self.k ** 2 * self.q * u_inc
+
     def residual(self, u, b) -> float:
         return float(np.linalg.norm((b - self.op(u)).ravel()) / np.linalg.norm(b.ravel()))
 
 
-def dense_solve(prob: LSProblem, b: np.ndarray) -> np.ndarray:
-    """Builds the N^3 x N^3 matrix of A from unit vectors and solves A u = b."""
-    n = prob.N ** 3
+def dense_solve(prob: LSProblem, b: np.ndarray, form: str = "field") -> np.ndarray:
+    """Builds the N^d x N^d matrix of A (form "field") or B ("density") from
+    unit vectors and solves it against b."""
+    op = prob.op if form == "field" else prob.op_density
+    n = prob.N ** prob.d
     M = np.empty((n, n), dtype=np.complex128)
     e = np.zeros(n, dtype=np.complex128)
     for j in range(n):
         e[j] = 1.0
-        M[:, j] = prob.op(e.reshape((prob.N,) * 3)).ravel()
+        M[:, j] = op(e.reshape((prob.N,) * prob.d)).ravel()
         e[j] = 0.0
     return np.linalg.solve(M, b.ravel()).reshape(b.shape)
 
@@ -121,3 +139,45 @@ def arnoldi(matvec, b: np.ndarray, m: int):
         H[j + 1, j] = np.linalg.norm(w.ravel())
         V.append(w / H[j + 1, j])
     return np.stack(V), H
+
+
+def bicgstab(matvec, b: np.ndarray, tol: float = 1e-12, maxit: int = 5000):
+    """Unpreconditioned Bi-CGStab (van der Vorst 1992; Saad, Iterative Methods
+    for Sparse Linear Systems, Alg. 7.7) from x = 0 with the shadow residual
+    r^ = b; two products with A per iteration.  Stops when the recurrence
+    residual ||r|| / ||b|| < tol, tested after the half step (||s||) and after
+    the full step.  Returns (x, iterations begun, matvecs, relative residual
+    history)."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    rh = b.copy()
+    bn = np.linalg.norm(b.ravel())
+    rho_prev = alpha = omega = 1.0 + 0j
+    v = np.zeros_like(b)
+    p = np.zeros_like(b)
+    hist = [1.0]
+    matvecs = 0
+    for it in range(1, maxit + 1):
+        rho = np.vdot(rh.ravel(), r.ravel())
+        if rho == 0:
+            break
+        beta = (rho / rho_prev) * (alpha / omega)
+        p = r + beta * (p - omega * v)
+        v = matvec(p)
+        matvecs += 1
+        alpha = rho / np.vdot(rh.ravel(), v.ravel())
+        s = r - alpha * v
+        if np.linalg.norm(s.ravel()) / bn < tol:
+            x = x + alpha * p
+            hist.append(np.linalg.norm(s.ravel()) / bn)
+            return x, it, matvecs, hist
+        t = matvec(s)
+        matvecs += 1
+        omega = np.vdot(t.ravel(), s.ravel()) / np.vdot(t.ravel(), t.ravel())
+        x = x + alpha * p + omega * s
+        r = s - omega * t
+        hist.append(np.linalg.norm(r.ravel()) / bn)
+        if hist[-1] < tol or omega == 0:
+            return x, it, matvecs, hist
+        rho_prev = rho
+    return x, it, matvecs, hist

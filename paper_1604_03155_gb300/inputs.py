@@ -210,10 +210,27 @@ def ls_contrast(seed: int, N: int) -> np.ndarray:
     return q
 
 
-def plane_wave(N: int, k: float) -> np.ndarray:
+def plane_wave(N: int, k: float, d: int = 3) -> np.ndarray:
     """u_inc = exp(i k x_0): a plane wave travelling along the first axis."""
     x = grid_coords(N)
-    return np.broadcast_to(np.exp(1j * k * x)[:, None, None], (N, N, N)).astype(np.complex128).copy()
+    shape = (N,) + (1,) * (d - 1)
+    return np.broadcast_to(np.exp(1j * k * x).reshape(shape), (N,) * d).astype(np.complex128).copy()
+
+
+def filtered_disk(N: int) -> np.ndarray:
+    """The smoothly filtered dielectric disk of Section 5.3,
+    q = exp(-1/2 (|x|/0.25)^8), on the N^2 grid (float64)."""
+    x = grid_coords(N)
+    r = np.sqrt(x[:, None] ** 2 + x[None, :] ** 2)
+    return np.exp(-0.5 * (r / 0.25) ** 8)
+
+
+def luneburg_lens(N: int) -> np.ndarray:
+    """The 2D Luneburg lens of Section 5.3, q = 1 - (|x|/0.45)^2 inside the
+    lens (|x| <= 0.45) and 0 outside, on the N^2 grid (float64)."""
+    x = grid_coords(N)
+    r = np.sqrt(x[:, None] ** 2 + x[None, :] ** 2)
+    return np.where(r <= 0.45, 1.0 - (r / 0.45) ** 2, 0.0)
 
 
 LS_TRAIN_SEED = BASE_SEED + 5000     # contrasts LS_TRAIN_SEED + i, i < 2000

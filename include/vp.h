@@ -276,6 +276,31 @@ vp_status vp_ls_krylov_basis(vp_plan plan, const float* q, const void* b, int m,
  * (A z_j, z_j) for the learned preconditioner. */
 vp_status vp_ls_flexible_basis(vp_plan plan, const float* q, const void* b, int m, vp_precond_fn precond,
                                void* precond_ctx, void* Z, int* count);
+/* The paper's solver (Section 5.3): unpreconditioned Bi-CGStab (van der Vorst
+ * 1992; two operator products per iteration, each one apply of V) on either
+ * form of the scattering problem, u the scattered field:
+ *   VP_LS_FIELD:    u - k^2 V[q u] = k^2 V[q u_inc]
+ *   VP_LS_DENSITY:  s - k^2 q V[s] = k^2 q u_inc,  u = V[s]   (the paper's
+ *                   dual equation of Section 5.3)
+ * plan: 2D or 3D Helmholtz plan.  dtype VP_C64: complex64 u_inc/u and a float
+ * contrast q, the plan in VP_FP32; VP_C128: complex128 and double q, the plan
+ * in VP_FP64.  q, u_inc, u: N^d device arrays in the plan's layout (u is
+ * overwritten; it may not alias u_inc).  Starts from zero; stops when the
+ * recurrence residual ||r|| / ||b|| < tol, checked after each half step (as
+ * the paper's counts imply) and each full step, or after maxit iterations
+ * (VP_OK either way: compare stats->estimated_residual with tol).
+ * history: NULL or a host array of maxit + 1 doubles receiving ||r_j|| / ||b||
+ * for j = 0 .. stats->iterations (the last entry ||s|| / ||b|| when the solve
+ * stops at a half step).  stats: iterations (begun), matvecs (operator
+ * products of the iteration; the right-hand side's apply, and the final
+ * u = V[s] of the density form, are not counted), estimated_residual,
+ * true_residual = ||b - M x|| / ||b|| for the solved form with M and b
+ * evaluated in FP64, seconds (right-hand side, iteration and final apply).
+ * Returns VP_ERR_NUMERICAL on a breakdown (a zero inner product) or a
+ * non-finite value, with u the last iterate. */
+enum { VP_LS_FIELD = 0, VP_LS_DENSITY = 1 };
+vp_status vp_ls_bicgstab(vp_plan plan, const void* q, const void* u_inc, void* u, vp_dtype dtype, int form,
+                         double tol, int maxit, double* history, vp_ls_stats* stats);
 const char* vp_ls_last_error(void);
 
 /* ---------------------------------------------------------------------------

@@ -546,6 +546,10 @@ vp_status alloc_work(Work& w, long long n, int m, bool basis, bool fp64 = true) 
 
 }  // namespace
 
+namespace vp {
+void ls_set_error(const char* msg) { g_ls_error = msg; }
+}  // namespace vp
+
 extern "C" {
 
 vp_status vp_ls_operator(vp_plan plan, const float* q, const void* u, void* out) {

@@ -561,6 +561,8 @@ cudaStream_t plan_stream(vp_plan p) { return p ? p->stream : nullptr; }
 
 int plan_is_fp32(vp_plan p) { return p && p->prec == VP_FP32; }
 
+int plan_is_fp64(vp_plan p) { return p && p->prec == VP_FP64; }
+
 int plan_pass_args_f32(vp_plan p, float2* ws, PassArgs<float>* args, int* kinds) {
   FieldDesc field{(const void*)p->G32, -1, -1};
   void* outs[1] = {nullptr};

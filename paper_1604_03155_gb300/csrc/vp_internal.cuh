@@ -67,6 +67,9 @@ cudaError_t launch_tc_fused(int n, int split, const TcFusedArgs& a, cudaStream_t
 int plan_device(vp_plan p);
 cudaStream_t plan_stream(vp_plan p);
 int plan_is_fp32(vp_plan p);
+int plan_is_fp64(vp_plan p);
+// ls.cu: the message vp_ls_last_error returns on this thread
+void ls_set_error(const char* msg);
 // The FP32 potential-only passes of a plan on workspace `ws` (input and output
 // pointers left NULL): fills args/kinds, returns the number of passes.
 int plan_pass_args_f32(vp_plan p, float2* ws, PassArgs<float>* args, int* kinds);

@@ -83,6 +83,8 @@ _SIGNATURES = {
     "vp_ls_last_error": (c_char_p, []),
     "vp_ls_training_pair": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                     ctypes.POINTER(c_double)]),
+    "vp_ls_bicgstab": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_double, c_int, c_void_p,
+                               c_void_p]),
     "vp_ls_krylov_basis": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, ctypes.POINTER(c_int)]),
     "vp_ls_flexible_basis": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p,
                                      ctypes.POINTER(c_int)]),
@@ -439,6 +441,29 @@ def ls_solve(plan: Plan, q, b, u, u_inc=None, tol=1e-6, maxit=1000, restart=30, 
     _lscheck(lib().vp_ls_solve(plan.handle, _ptr(q), _ptr(b), _ptr(u_inc) if u_inc is not None else None, _ptr(u),
                                ctypes.byref(opts), ctypes.byref(st)))
     return {k: getattr(st, k) for k, _ in LSStats._fields_}
+
+
+LS_FORMS = {"field": 0, "density": 1}
+
+
+def ls_bicgstab(plan: Plan, q, u_inc, u=None, form: str = "field", tol: float = 1e-12, maxit: int = 10000,
+                history: bool = False):
+    """The paper's solver: Bi-CGStab on the field form u - k^2 V[q u] = k^2 V[q u_inc]
+    or the density form s - k^2 q V[s] = k^2 q u_inc, u = V[s].  Device tensors:
+    complex64 u_inc with float32 q (plan in fp32) or complex128 with float64 q (plan
+    in fp64).  Returns (u, stats) or (u, stats, residual history) with history=True."""
+    if form not in LS_FORMS:
+        raise VPError(VP_ERR_INVALID_ARG, f"form must be one of {sorted(LS_FORMS)}")
+    u = _empty_like(u_inc, u_inc.shape) if u is None else u
+    st = LSStats()
+    hist = np.zeros(maxit + 1) if history else None
+    plan._sync_stream_to_torch(u_inc)
+    _lscheck(lib().vp_ls_bicgstab(plan.handle, _ptr(q), _ptr(u_inc), _ptr(u), _dtype_code(u_inc), LS_FORMS[form],
+                                  tol, maxit, _ptr(hist) if history else None, ctypes.byref(st)))
+    stats = {k: getattr(st, k) for k, _ in LSStats._fields_}
+    if history:
+        return u, stats, hist[:stats["iterations"] + 1]
+    return u, stats
 
 
 def ls_training_pair(plan: Plan, q, b, u_s, u_star, x_out, t_out) -> float:

@@ -1,0 +1,157 @@
+"""The paper's scattering solver on the GPU (Section 5.3): Bi-CGStab over the
+FP64 and FP32 applies, field and density forms, against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import ls as OLS
+from paper_1604_03155_gb300 import inputs as I
+from paper_1604_03155_gb300 import vp
+from paper_1604_03155_gb300.vp import Plan
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+CONTRAST = {"disk": I.filtered_disk, "lens": I.luneburg_lens, "cube": I.cube_bump}
+
+
+def _case(name, N, size):
+    q = CONTRAST[name](N)
+    k = 2 * np.pi * size
+    return q, k, I.plane_wave(N, k, q.ndim)
+
+
+def _gpu_solve(q, k, uinc, form, precision, tol, maxit=4000, history=False):
+    d, N = q.ndim, q.shape[0]
+    plan = Plan(d, N, "helmholtz", k, 0.0, precision=precision)
+    rdt, cdt = (torch.float64, torch.complex128) if precision == "fp64" else (torch.float32, torch.complex64)
+    qd = torch.from_numpy(q).to(DEV, rdt)
+    ud = torch.from_numpy(uinc).to(DEV, cdt)
+    out = vp.ls_bicgstab(plan, qd, ud, form=form, tol=tol, maxit=maxit, history=history)
+    plan.close()
+    return (out[0].cpu().numpy(),) + tuple(out[1:])
+
+
+def _rel2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+_ORACLE = {}
+
+
+def _oracle(name, N, size, form):
+    """The oracle's problem and its Bi-CGStab solve at tol 1e-13 (cached):
+    (problem, u_inc, iterations, history, scattered field)."""
+    key = (name, N, size, form)
+    if key not in _ORACLE:
+        q, k, uinc = _case(name, N, size)
+        prob = OLS.LSProblem(N, k, q)
+        op = prob.op if form == "field" else prob.op_density
+        b = prob.rhs(uinc) if form == "field" else prob.rhs_density(uinc)
+        x, its, mv, hist = OLS.bicgstab(op, b, tol=1e-13)
+        _ORACLE[key] = (prob, uinc, its, hist, x if form == "field" else prob.V(x))
+    return _ORACLE[key]
+
+
+@pytest.mark.parametrize("name,N,size", [("disk", 48, 2.0), ("lens", 48, 2.0), ("cube", 12, 1.0)])
+@pytest.mark.parametrize("form", ["field", "density"])
+def test_fp64_bicgstab_matches_oracle(name, N, size, form):
+    """FP64: the oracle's iterates (recurrence residuals equal until the stop,
+    iteration counts equal up to the last step) and its solution to 1e-10."""
+    q, k, uinc = _case(name, N, size)
+    prob, _, its, ohist, u_ref = _oracle(name, N, size, form)
+    u_gpu, st, hist = _gpu_solve(q, k, uinc, form, "fp64", 1e-13, history=True)
+    assert st["estimated_residual"] < 1e-13 and st["true_residual"] < 1e-12
+    assert abs(st["iterations"] - its) <= 1 and st["matvecs"] in (2 * st["iterations"], 2 * st["iterations"] - 1)
+    assert _rel2(u_gpu, u_ref) < 1e-10
+    # the same iterates: the recurrence residuals agree while they stay well above
+    # the rounding level (different summation orders; Bi-CGStab amplifies the
+    # difference as the residual falls)
+    m = min(len(hist), len(ohist))
+    h, oh = np.asarray(hist[:m]), np.asarray(ohist[:m])
+    big = oh > 1e-9
+    assert big.sum() >= 5
+    assert np.all(np.abs(h[big] - oh[big]) <= 1e-2 * oh[big])
+
+
+@pytest.mark.parametrize("name,N,size", [("disk", 16, 2.0), ("lens", 16, 2.0), ("cube", 8, 1.0)])
+def test_fp64_bicgstab_matches_dense_solve(name, N, size):
+    """Small grids: both forms against the oracle's dense direct solve."""
+    q, k, uinc = _case(name, N, size)
+    prob = OLS.LSProblem(N, k, q)
+    u_dense = OLS.dense_solve(prob, prob.rhs(uinc))
+    for form in ("field", "density"):
+        u_gpu, st = _gpu_solve(q, k, uinc, form, "fp64", 1e-13)
+        assert _rel2(u_gpu, u_dense) < 1e-10, form
+
+
+@pytest.mark.parametrize("name,N,size", [("disk", 48, 2.0), ("cube", 12, 1.0)])
+@pytest.mark.parametrize("form", ["field", "density"])
+def test_fp32_bicgstab_matches_oracle(name, N, size, form):
+    q, k, uinc = _case(name, N, size)
+    u_ref = _oracle(name, N, size, "field")[4]
+    u_gpu, st = _gpu_solve(q, k, uinc, form, "fp32", 1e-5)
+    assert st["estimated_residual"] < 1e-5
+    # FP32 applies carry ~1e-6 relative error per product
+    assert st["true_residual"] < 3e-5
+    assert _rel2(u_gpu, u_ref) < 1e-4
+
+
+def test_forms_agree_and_residual_at_full_size():
+    """2D N = 1024 (2N = 2048) filtered disk, 20 wavelengths, FP64: both forms
+    converge to 1e-12 with a true residual below 1e-11 and give the same field."""
+    q, k, uinc = _case("disk", 1024, 20.0)
+    u_f, st_f = _gpu_solve(q, k, uinc, "field", "fp64", 1e-12)
+    u_d, st_d = _gpu_solve(q, k, uinc, "density", "fp64", 1e-12)
+    for st in (st_f, st_d):
+        assert st["estimated_residual"] < 1e-12 and st["true_residual"] < 1e-11
+        assert 100 < st["matvecs"] < 2000
+    assert _rel2(u_d, u_f) < 1e-10
+
+
+def test_3d_full_size_fp64_residual():
+    """3D N = 128 (2N = 256) smoothed cube, 10 wavelengths, FP64."""
+    q, k, uinc = _case("cube", 128, 10.0)
+    u, st = _gpu_solve(q, k, uinc, "density", "fp64", 1e-12)
+    assert st["estimated_residual"] < 1e-12 and st["true_residual"] < 1e-11
+
+
+def test_deterministic_and_history():
+    q, k, uinc = _case("lens", 64, 4.0)
+    u1, st1, h1 = _gpu_solve(q, k, uinc, "density", "fp64", 1e-12, history=True)
+    u2, st2, h2 = _gpu_solve(q, k, uinc, "density", "fp64", 1e-12, history=True)
+    assert np.array_equal(u1, u2) and np.array_equal(h1, h2) and st1["matvecs"] == st2["matvecs"]
+    assert h1[0] == 1.0 and h1[-1] < 1e-12 and len(h1) == st1["iterations"] + 1
+
+
+def test_edge_cases():
+    N, k = 16, 2 * np.pi
+    plan = Plan(2, N, "helmholtz", k, 0.0, precision="fp64")
+    q = torch.from_numpy(I.filtered_disk(N)).to(DEV)
+    # zero incident field: u = 0 without iterations
+    z = torch.zeros((N, N), dtype=torch.complex128, device=DEV)
+    u, st = vp.ls_bicgstab(plan, q, z, form="field")
+    assert st["iterations"] == 0 and st["matvecs"] == 0 and torch.count_nonzero(u) == 0
+    # zero contrast: b = 0 as well
+    u, st = vp.ls_bicgstab(plan, torch.zeros_like(q), torch.from_numpy(I.plane_wave(N, k, 2)).to(DEV), form="density")
+    assert st["iterations"] == 0 and torch.count_nonzero(u) == 0
+    # maxit reached: VP_OK, residual above tol, exactly maxit iterations
+    ui = torch.from_numpy(I.plane_wave(N, k, 2)).to(DEV)
+    u, st = vp.ls_bicgstab(plan, q, ui, form="field", tol=1e-14, maxit=2)
+    assert st["iterations"] == 2 and st["matvecs"] == 4 and st["estimated_residual"] > 1e-14
+    # dtype and precision mismatches, aliasing, a Laplace plan
+    with pytest.raises(vp.VPError):
+        vp.ls_bicgstab(plan, q.float(), ui.to(torch.complex64))
+    with pytest.raises(vp.VPError):
+        vp.ls_bicgstab(plan, q, ui, u=ui)
+    with pytest.raises(vp.VPError):
+        vp.ls_bicgstab(plan, q, ui, form="other")
+    plan.close()
+    lap = Plan(2, N, "laplace", 0.0, 0.0, precision="fp64")
+    with pytest.raises(vp.VPError):
+        vp.ls_bicgstab(lap, q, ui)
+    lap.close()
+    tc = Plan(3, 128, "helmholtz", 10.0, 0.0, precision="tc_bf16x2")
+    q3 = torch.zeros((128,) * 3, dtype=torch.float32, device=DEV)
+    with pytest.raises(vp.VPError):
+        vp.ls_bicgstab(tc, q3, torch.zeros((128,) * 3, dtype=torch.complex64, device=DEV))
+    tc.close()

@@ -11,6 +11,13 @@ Readings of garbled printed formulas (each checked by ``radial_convolution``):
   finite and correct is E_1 (scipy.special.exp1).
 * eq. (test_helm_2D) misses the factor i of g_k = (i/4) H_0^(1) and writes
   H_0(kr) inside the outer integral where H_0(ky) is meant.
+* eq. (test_biharm_3D) misses the factor e^{-r^2/(2 sigma^2)} on its
+  sigma sqrt(2/pi) term (the printed form tends to r/(8 pi) plus a constant
+  instead of r/(8 pi) + sigma^2/(8 pi r) far from the source).
+* eq. (test_biharm_2D) prints c_1 r where the constant c_1 is meant, and its
+  Ei~(x) = Ei(x) + log x + gamma is finite and correct with E_1 in place of
+  Ei (the entire function Ein(x) = int_0^x (1 - e^{-t})/t dt).
+The biharmonic potentials use g_b of Tables 1-2 (Delta^2 g_b = -delta).
 """
 from __future__ import annotations
 
@@ -88,6 +95,41 @@ def helmholtz2(r, sigma: float, k: float) -> np.ndarray:
     return out
 
 
+def biharmonic3(r, sigma: float) -> np.ndarray:
+    """Eq. (test_biharm_3D), corrected: (1/(8 pi)) [sigma sqrt(2/pi) e^{-r^2/(2 sigma^2)}
+    + erf(r/(sqrt 2 sigma)) (sigma^2/r + r)]; at r = 0 the limit sigma sqrt(2/pi)/(4 pi)."""
+    r = np.asarray(r, dtype=np.float64)
+    out = np.empty(r.shape)
+    z = r == 0
+    out[z] = sigma * math.sqrt(2 / math.pi) / (4 * math.pi)
+    rn = r[~z]
+    out[~z] = (sigma * math.sqrt(2 / math.pi) * np.exp(-rn ** 2 / (2 * sigma * sigma))
+               + special.erf(rn / (math.sqrt(2) * sigma)) * (sigma * sigma / rn + rn)) / (8 * math.pi)
+    return out
+
+
+def biharmonic2(r, sigma: float) -> np.ndarray:
+    """Eq. (test_biharm_2D), corrected: -(sigma^2/(8 pi)) [(x + 1) Ein(x) - e^{-x}] + c_2 r^2 + c_1,
+    x = r^2/(2 sigma^2), Ein(x) = E_1(x) + log x + gamma (the series for small x)."""
+    r = np.asarray(r, dtype=np.float64)
+    x = r ** 2 / (2 * sigma * sigma)
+    ein = np.empty(r.shape)
+    small = x < 1.0
+    xs = x[small]
+    acc = np.zeros_like(xs)
+    term = xs.copy()
+    for n in range(1, 40):  # Ein(x) = sum_{n>=1} (-1)^{n+1} x^n/(n n!)
+        acc += (-1) ** (n + 1) * term / n
+        term = term * xs / (n + 1)
+    ein[small] = acc
+    xb = x[~small]
+    ein[~small] = special.exp1(xb) + np.log(xb) + EULER_GAMMA
+    lg = math.log(1.0 / (2 * sigma * sigma))
+    c1 = sigma * sigma / (8 * math.pi) * (EULER_GAMMA + lg)
+    c2 = (EULER_GAMMA / 2 + lg / 2 + 1.0) / (8 * math.pi)
+    return -sigma * sigma / (8 * math.pi) * ((x + 1.0) * ein - np.exp(-x)) + c2 * r ** 2 + c1
+
+
 def radial_convolution(d: int, kernel: str, k: float, sigma: float, r: float) -> complex:
     """(g_k * rho)(r) by direct 1D quadrature, independent of the closed forms.
     3D: (2 pi/r) int t rho(t) int_{|r-t|}^{r+t} u g(u) du dt with
@@ -97,7 +139,9 @@ def radial_convolution(d: int, kernel: str, k: float, sigma: float, r: float) ->
     top = r + 14 * sigma
     if d == 3:
         def inner(t, part):
-            if kernel == "laplace":
+            if kernel == "biharmonic":  # int u (u/(8 pi)) du
+                v = ((r + t) ** 3 - abs(r - t) ** 3) / (24 * math.pi)
+            elif kernel == "laplace":
                 v = (r + t - abs(r - t)) / (4 * math.pi)
             else:
                 v = (np.exp(1j * k * (r + t)) - np.exp(1j * k * abs(r - t))) / (4j * math.pi * k)
@@ -110,4 +154,14 @@ def radial_convolution(d: int, kernel: str, k: float, sigma: float, r: float) ->
     if kernel == "laplace":
         f = lambda t: 2 * math.pi * t * rho(t) * (-math.log(max(r, t)) / (2 * math.pi))
         return complex(integrate.quad(f, 0, top, points=[r], epsabs=0, epsrel=1e-13, limit=400)[0], 0.0)
+    if kernel == "biharmonic":
+        # the circle mean of g_b(|x - y|) over |y| = t, by quadrature in the angle
+        def g(u):
+            return -u * u * (math.log(u) - 1.0) / (8 * math.pi) if u > 0 else 0.0
+
+        def circle(t):
+            f = lambda th: g(math.sqrt(max(r * r + t * t - 2 * r * t * math.cos(th), 0.0)))
+            return 2 * integrate.quad(f, 0, math.pi, epsabs=0, epsrel=1e-13, limit=200)[0]
+        f = lambda t: t * rho(t) * circle(t)
+        return complex(integrate.quad(f, 0, top, points=[r], epsabs=0, epsrel=1e-12, limit=200)[0], 0.0)
     raise ValueError("2D Helmholtz uses helmholtz2 (Graf addition) directly")

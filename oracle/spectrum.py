@@ -26,6 +26,17 @@ are Tables 1-2 evaluated so that no removable singularity loses digits:
   there it is written as an integral over u in [k, s] of its derivative,
   using d/du[u J_1(Lu)] = L u J_0(Lu) and d/du J_0(Lu) = -L J_1(Lu), and the
   mean of the integrand is taken by Gauss-Legendre quadrature.
+* Biharmonic (Tables 1-2, row Delta^2): g_b = r/(8 pi) (3D) and
+  -r^2 (log r - 1)/(8 pi) (2D), so that Delta^2 g_b = -delta (the sign
+  convention of the other rows: g solves -L g = delta).  3D:
+  ((2 - x^2) cos x + 2 x sin x - 2)/(2 s^4), x = Ls; 2D: (J_0(x) - 1)/s^4
+  - L^3 (log L - 1) J_1(x)/(4s) + L log L J_1(x)/s^3 - L^2 (2 log L - 1) J_0(x)/(4 s^2).
+  Both lose digits to cancellation as x -> 0 (the terms grow like x^-4 and
+  x^-2 while G^L stays O(L^4)); for x < 2 each is summed from the power series
+  of its defining radial integral,
+    3D: (L^4/2) sum_n (-1)^n x^{2n} / ((2n+1)! (2n+4)),
+    2D: -(L^4/4) sum_m (-1)^m (x/2)^{2m}/(m!)^2 [(log L - 1)/(2m+4) - 1/(2m+4)^2],
+  whose first terms are the s = 0 limits L^4/8 and -L^4 (4 log L - 5)/64.
 """
 from __future__ import annotations
 
@@ -34,7 +45,10 @@ import math
 import numpy as np
 from scipy import integrate, special
 
-LAPLACE, HELMHOLTZ = "laplace", "helmholtz"
+LAPLACE, HELMHOLTZ, BIHARMONIC = "laplace", "helmholtz", "biharmonic"
+
+# x = Ls below which the biharmonic spectra are summed from their power series
+BIHARM_SERIES_X = 2.0
 
 # |s - k| below which the 2D Helmholtz numerator is evaluated as a divided difference.
 HELM2D_NEAR_K = 1.0
@@ -156,18 +170,61 @@ def G_helmholtz2_table(s, k: float, L: float) -> np.ndarray:
     return num / (s * s - k * k)
 
 
+def G_biharm3(s, L: float) -> np.ndarray:
+    s = np.asarray(s, dtype=np.float64)
+    x = L * s
+    out = np.empty(s.shape, dtype=np.complex128)
+    small = x < BIHARM_SERIES_X
+    xs = x[small]
+    acc = np.zeros_like(xs)
+    term = np.ones_like(xs)  # x^{2n}/(2n+1)!, n = 0
+    for n in range(30):
+        acc += (-1) ** n * term / (2 * n + 4)
+        term = term * xs * xs / ((2 * n + 2) * (2 * n + 3))
+    out[small] = 0.5 * L ** 4 * acc
+    sb, xb = s[~small], x[~small]
+    out[~small] = ((2.0 - xb * xb) * np.cos(xb) + 2.0 * xb * np.sin(xb) - 2.0) / (2.0 * sb ** 4)
+    return out
+
+
+def G_biharm2(s, L: float) -> np.ndarray:
+    s = np.asarray(s, dtype=np.float64)
+    x = L * s
+    lnL = math.log(L)
+    out = np.empty(s.shape, dtype=np.complex128)
+    small = x < BIHARM_SERIES_X
+    xs = x[small]
+    acc = np.zeros_like(xs)
+    term = np.ones_like(xs)  # (x/2)^{2m}/(m!)^2, m = 0
+    for m in range(30):
+        p = 2 * m + 4
+        acc += (-1) ** m * term * ((lnL - 1.0) / p - 1.0 / p ** 2)
+        term = term * (xs / 2) ** 2 / ((m + 1) ** 2)
+    out[small] = -0.25 * L ** 4 * acc
+    sb, xb = s[~small], x[~small]
+    j0, j1 = special.j0(xb), special.j1(xb)
+    out[~small] = ((j0 - 1.0) / sb ** 4 - L ** 3 * (lnL - 1.0) * j1 / (4.0 * sb)
+                   + L * lnL * j1 / sb ** 3 - L ** 2 * (2.0 * lnL - 1.0) * j0 / (4.0 * sb ** 2))
+    return out
+
+
 def G_truncated(d: int, kernel: str, k: float, L: float, s) -> np.ndarray:
-    """G^L(s) for the four supported kernels."""
+    """G^L(s) for the six supported kernels (three operators, two dimensions)."""
+    if d not in (2, 3):
+        raise ValueError("d must be 2 or 3")
+    if kernel == BIHARMONIC:
+        return G_biharm3(s, L) if d == 3 else G_biharm2(s, L)
     if d == 3:
         return G_laplace3(s, L) if kernel == LAPLACE else G_helmholtz3(s, k, L)
-    if d == 2:
-        return G_laplace2(s, L) if kernel == LAPLACE else G_helmholtz2(s, k, L)
-    raise ValueError("d must be 2 or 3")
+    return G_laplace2(s, L) if kernel == LAPLACE else G_helmholtz2(s, k, L)
 
 
 def green(d: int, kernel: str, k: float, r):
-    """Free-space Green's function of -(Delta + k^2) (Tables 1-2, column 2)."""
+    """Free-space Green's function (Tables 1-2, column 2): of -(Delta + k^2)
+    (k = 0: Laplace), or of -Delta^2 (biharmonic)."""
     r = np.asarray(r, dtype=np.float64)
+    if kernel == BIHARMONIC:
+        return (r / (8 * np.pi) if d == 3 else -r * r * (np.log(r) - 1.0) / (8 * np.pi)) + 0j
     if d == 3:
         return (1.0 / (4 * np.pi * r)) * (np.exp(1j * k * r) if kernel == HELMHOLTZ else 1.0)
     if kernel == LAPLACE:
@@ -179,7 +236,9 @@ def G_quadrature(d: int, kernel: str, k: float, L: float, s: float) -> complex:
     """The radial transform of the truncated kernel (Section 2) by adaptive
     quadrature, independent of the closed forms."""
     def integrand(r, part):
-        if d == 3:
+        if d == 3 and kernel == BIHARMONIC:
+            v = 4 * np.pi * (np.sin(s * r) / (s * r) if s > 0 else 1.0) * green(3, kernel, k, r) * r * r
+        elif d == 3:
             # 4 pi sin(sr)/(sr) g(r) r^2 with g = e^{ikr}/(4 pi r): sin(sr)/s e^{ikr}
             kern = (np.sin(s * r) / s) if s > 0 else r
             v = kern * (np.exp(1j * k * r) if kernel == HELMHOLTZ else 1.0)

@@ -12,7 +12,7 @@ from oracle import kernel as K
 from paper_1604_03155_gb300 import inputs as I
 
 CASES = [(3, "laplace", 0.0, 1.8, 6), (3, "helmholtz", 13.0, 1.8, 8), (2, "laplace", 0.0, 1.5, 12),
-         (2, "helmholtz", 30.0, 1.5, 16)]
+         (2, "helmholtz", 30.0, 1.5, 16), (3, "biharmonic", 0.0, 1.8, 6), (2, "biharmonic", 0.0, 1.5, 12)]
 
 
 def _setup(d, kernel, k, L, N):
@@ -127,7 +127,8 @@ def test_laplace3d_exact_gradient_vs_analytic():
 
 
 @pytest.mark.parametrize("d,kernel,k,N,tol", [(3, "helmholtz", 2.0, 40, 1e-9), (2, "laplace", 0.0, 64, 1e-9),
-                                              (2, "helmholtz", 2.0, 64, 1e-9)])
+                                              (2, "helmholtz", 2.0, 64, 1e-9), (3, "biharmonic", 0.0, 40, 1e-9),
+                                              (2, "biharmonic", 0.0, 64, 1e-9)])
 def test_convergence_to_corrected_closed_forms(d, kernel, k, N, tol):
     """Fig. 3's test (sigma = 0.05, k = 2) with the corrected closed forms; a
     sign, a missing i or a wrong special function would fail at O(1)."""
@@ -138,7 +139,9 @@ def test_convergence_to_corrected_closed_forms(d, kernel, k, N, tol):
     X, r = _grid_r(N, d)
     rho = (2 * math.pi * sig * sig) ** (-d / 2) * np.exp(-r * r / (2 * sig * sig))
     phi = A.apply_fft2n(G, rho)
-    if d == 3:
+    if kernel == "biharmonic":
+        ex = CF.biharmonic3(r, sig) if d == 3 else CF.biharmonic2(r, sig)
+    elif d == 3:
         ex = CF.helmholtz3(r, sig, k)
     elif kernel == "laplace":
         ex = CF.laplace2(r, sig)

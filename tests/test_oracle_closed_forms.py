@@ -72,3 +72,44 @@ def test_helmholtz2_far_field_and_near_field():
     # continuity at the origin
     a = CF.helmholtz2(np.array([0.0, 1e-6]), s, k)
     assert abs(a[0] - a[1]) < 1e-6 * abs(a[0])
+
+
+@pytest.mark.parametrize("r", RADII)
+def test_biharmonic3_vs_quadrature(r):
+    got = CF.biharmonic3(np.array([r]), 0.05)[0]
+    if r == 0.0:  # the limit: E|Y| = 2 sigma sqrt(2/pi) for Y ~ N(0, sigma^2 I_3), over 8 pi
+        assert got == pytest.approx(2 * 0.05 * math.sqrt(2 / math.pi) / (8 * math.pi), rel=1e-15)
+        return
+    assert got == pytest.approx(CF.radial_convolution(3, "biharmonic", 0.0, 0.05, r).real, rel=1e-12)
+
+
+def test_biharmonic3_printed_form_misses_the_exponential():
+    """As printed (no e^{-r^2/(2 sigma^2)} on sigma sqrt(2/pi)) the far field is
+    off by sigma sqrt(2/pi)/(8 pi); with the factor it matches quadrature."""
+    sig, r = 0.05, 0.45
+    printed = (sig * math.sqrt(2 / math.pi) + special.erf(r / (sig * math.sqrt(2))) * (sig * sig / r + r)) / (8 * math.pi)
+    ref = CF.radial_convolution(3, "biharmonic", 0.0, sig, r).real
+    assert abs(printed - ref) == pytest.approx(sig * math.sqrt(2 / math.pi) / (8 * math.pi), rel=1e-6)
+    assert CF.biharmonic3(np.array([r]), sig)[0] == pytest.approx(ref, rel=1e-12)
+
+
+@pytest.mark.parametrize("r", [0.0, 0.03, 0.1, 0.3])
+def test_biharmonic2_vs_quadrature(r):
+    got = CF.biharmonic2(np.array([r]), 0.05)[0]
+    ref = CF.radial_convolution(2, "biharmonic", 0.0, 0.05, r).real if r > 0 else None
+    if r == 0.0:
+        # the limit: -sigma^2/(8 pi) (0 - 1) + c_1, against quadrature just off the origin
+        ref = CF.radial_convolution(2, "biharmonic", 0.0, 0.05, 1e-7).real
+        assert got == pytest.approx(ref, rel=1e-9)
+        return
+    assert got == pytest.approx(ref, rel=1e-11)
+
+
+def test_biharmonic2_printed_linear_term_is_a_constant():
+    """With c_1 r (as printed) the formula misses quadrature by c_1 (r - 1)."""
+    sig = 0.05
+    c1 = sig * sig / (8 * math.pi) * (CF.EULER_GAMMA + math.log(1 / (2 * sig * sig)))
+    r = 0.2
+    ref = CF.radial_convolution(2, "biharmonic", 0.0, sig, r).real
+    assert CF.biharmonic2(np.array([r]), sig)[0] == pytest.approx(ref, rel=1e-11)
+    assert abs((CF.biharmonic2(np.array([r]), sig)[0] - c1 + c1 * r) - ref) > 1e-3 * abs(ref)

@@ -11,7 +11,8 @@ import pytest
 from oracle import spectrum as S
 
 CASES = [(3, "laplace", 0.0, 1.8), (3, "helmholtz", 60.0, 1.8), (3, "helmholtz", 2.0, 1.8),
-         (2, "laplace", 0.0, 1.5), (2, "helmholtz", 40.0, 1.5), (2, "helmholtz", 2.0, 1.5)]
+         (2, "laplace", 0.0, 1.5), (2, "helmholtz", 40.0, 1.5), (2, "helmholtz", 2.0, 1.5),
+         (3, "biharmonic", 0.0, 1.8), (2, "biharmonic", 0.0, 1.5)]
 
 
 @pytest.mark.parametrize("d,kernel,k,L", CASES)
@@ -47,6 +48,27 @@ def test_limits_at_zero():
     assert abs(g3[1] - g3[0]) < 1e-8
     g2 = S.G_helmholtz2(np.array([0.0, 1e-6]), k, L2)
     assert abs(g2[0] - g2[1]) < 1e-9
+
+
+@pytest.mark.parametrize("d,L", [(3, 1.8), (2, 1.5), (3, 2.4), (2, 2.9)])
+def test_biharmonic_limits_series_switch_and_small_s(d, L):
+    """s = 0: the integral of g_b over the ball, L^4/8 (3D) and
+    -L^4 (4 log L - 5)/64 (2D); the series and the closed form agree where they
+    switch (x = Ls = 2), and at small s the series matches quadrature where the
+    closed form has lost its digits to cancellation."""
+    G = S.G_biharm3 if d == 3 else S.G_biharm2
+    g0 = L ** 4 / 8 if d == 3 else -L ** 4 * (4 * math.log(L) - 5) / 64
+    assert G(np.array([0.0]), L)[0].real == pytest.approx(g0, rel=1e-15)
+    assert g0 == pytest.approx(S.G_quadrature(d, "biharmonic", 0.0, L, 0.0).real, rel=1e-12)
+    x0 = S.BIHARM_SERIES_X / L  # s where x = Ls crosses the switch
+    a = G(np.array([np.nextafter(x0, 0.0), np.nextafter(x0, 10.0)]), L)
+    assert abs(a[0] - a[1]) < 2e-14 * abs(g0)
+    for s in (1e-3, 0.05, 0.7):
+        q = S.G_quadrature(d, "biharmonic", 0.0, L, s)
+        assert abs(G(np.array([s]), L)[0] - q) < 1e-12 * abs(q)
+    # the spectrum is real (g_b is real) and decays like s^-3 (3D) / s^-2.5 (2D) envelopes
+    s = np.linspace(0.0, 300.0, 601)
+    assert np.all(G(s, L).imag == 0)
 
 
 def test_helmholtz3_tends_to_laplace_as_k_to_zero():

@@ -9,7 +9,8 @@
  *
  * where g_k is the free-space Green's function of -(Delta + k^2): e^{ikr}/(4 pi r)
  * in 3D, (i/4) H_0^(1)(kr) in 2D, 1/(4 pi r) and -log(r)/(2 pi) for k = 0
- * (Tables 1-2).  The kernel is cut off at r = L (Section 1, g^L) so that its
+ * (Tables 1-2), or the biharmonic g_b of -Delta^2: r/(8 pi) in 3D and
+ * -r^2 (log r - 1)/(8 pi) in 2D (Tables 1-2, row Delta^2).  The kernel is cut off at r = L (Section 1, g^L) so that its
  * Fourier transform G^L is smooth; G^L is sampled on the 4N-oversampled grid
  * and inverse transformed once to the discrete kernel T (Section 4, the
  * "precomputation step"); every apply is then a zero-padded (2N)^d FFT
@@ -52,7 +53,7 @@ typedef enum {
   VP_ERR_NUMERICAL = 6    /* non-finite value where a finite one is required */
 } vp_status;
 
-typedef enum { VP_LAPLACE = 0, VP_HELMHOLTZ = 1 } vp_kernel;
+typedef enum { VP_LAPLACE = 0, VP_HELMHOLTZ = 1, VP_BIHARMONIC = 2 } vp_kernel;
 
 /* Arithmetic of the apply.  The precompute is always FP64.
  *  VP_FP32, VP_FP64   every pass in that precision (FP32 / FP64 data types).
@@ -106,7 +107,7 @@ typedef enum {
  * (2N)^d multiplier, stored as its [0, N]^d octant in FP64 and FP32.
  *   d       2 or 3
  *   N       even, >= 4; 2N must be a supported FFT length (VP_ERR_UNSUPPORTED)
- *   kernel  VP_LAPLACE (k must be 0) or VP_HELMHOLTZ (k > 0)
+ *   kernel  VP_LAPLACE or VP_BIHARMONIC (k must be 0), VP_HELMHOLTZ (k > 0)
  *   L       truncation radius; L <= 0 selects 1.8 (3D) / 1.5 (2D) (Section 2);
  *           otherwise sqrt(d) < L <= 3 (3 keeps the 4N grid alias-free).
  * The plan owns all device memory it allocates; workspace for applies is

@@ -229,6 +229,47 @@ __device__ double2 g_helmholtz2(double s, double k, double L) {
   return make_double2(-hp * ci / (s + k), hp * cr / (s + k));
 }
 
+// Biharmonic (row Delta^2 of Tables 1-2; g_b = r/(8 pi) in 3D,
+// -r^2 (log r - 1)/(8 pi) in 2D).  For x = Ls < 2 the printed closed forms
+// cancel (terms of order x^-4 and x^-2 against an O(L^4) value); there the
+// power series of the defining radial integral is summed instead:
+//   3D: (L^4/2) sum_n (-1)^n x^{2n} / ((2n+1)! (2n+4))
+//   2D: -(L^4/4) sum_m (-1)^m (x/2)^{2m} / (m!)^2 [(log L - 1)/(2m+4) - 1/(2m+4)^2]
+__device__ double2 g_biharm3(double s, double L) {
+  const double x = L * s;
+  if (x < BIHARM_SERIES_X) {
+    double acc = 0.0, term = 1.0;
+    for (int n = 0; n < 30; ++n) {
+      acc += ((n & 1) ? -term : term) / (2 * n + 4);
+      term *= x * x / ((2.0 * n + 2.0) * (2.0 * n + 3.0));
+    }
+    return make_double2(0.5 * L * L * L * L * acc, 0.0);
+  }
+  double sn, cs;
+  sincos(x, &sn, &cs);
+  const double s2 = s * s;
+  return make_double2(((2.0 - x * x) * cs + 2.0 * x * sn - 2.0) / (2.0 * s2 * s2), 0.0);
+}
+
+__device__ double2 g_biharm2(double s, double L) {
+  const double x = L * s;
+  const double lnL = log(L);
+  if (x < BIHARM_SERIES_X) {
+    double acc = 0.0, term = 1.0;
+    for (int m = 0; m < 30; ++m) {
+      const double p = 2.0 * m + 4.0;
+      acc += ((m & 1) ? -term : term) * ((lnL - 1.0) / p - 1.0 / (p * p));
+      term *= 0.25 * x * x / ((m + 1.0) * (m + 1.0));
+    }
+    return make_double2(-0.25 * L * L * L * L * acc, 0.0);
+  }
+  const Bessel01 b = bessel01(x);
+  const double s2 = s * s;
+  return make_double2((b.j0 - 1.0) / (s2 * s2) - L * L * L * (lnL - 1.0) * b.j1 / (4.0 * s) +
+                          L * lnL * b.j1 / (s2 * s) - L * L * (2.0 * lnL - 1.0) * b.j0 / (4.0 * s2),
+                      0.0);
+}
+
 __global__ void spectrum_octant_kernel(double2* __restrict__ G, int d, int N, int kernel, double k, double L) {
   const int M1 = 2 * N + 1;
   const long long total = (d == 3) ? (long long)M1 * M1 * M1 : (long long)M1 * M1;
@@ -243,7 +284,9 @@ __global__ void spectrum_octant_kernel(double2* __restrict__ G, int d, int N, in
     const double msq = (double)m2 * m2 + (double)m1 * m1 + (d == 3 ? (double)m0 * m0 : 0.0);
     const double s = 0.5 * 3.14159265358979323846 * sqrt(msq);
     double2 v;
-    if (d == 3)
+    if (kernel == 2)
+      v = (d == 3) ? g_biharm3(s, L) : g_biharm2(s, L);
+    else if (d == 3)
       v = (kernel == 0) ? g_laplace3(s, L) : g_helmholtz3(s, k, L);
     else
       v = (kernel == 0) ? g_laplace2(s, L) : g_helmholtz2(s, k, L);

@@ -457,8 +457,8 @@ vp_status run_apply_ws(vp_plan p, void* ws, const void* f, void* const* outs, co
 vp_status check_dtype(vp_plan p, vp_dtype dtype, bool* real_io) {
   const bool fp64 = p->prec == VP_FP64;
   if (dtype == VP_R32 || dtype == VP_R64) {
-    if (p->kernel != VP_LAPLACE)
-      return fail(p, VP_ERR_INVALID_ARG, "real data types need the Laplace kernel (a real multiplier)");
+    if (p->kernel == VP_HELMHOLTZ)
+      return fail(p, VP_ERR_INVALID_ARG, "real data types need a real multiplier (the Laplace or biharmonic kernel)");
     *real_io = true;
   } else if (dtype == VP_C64 || dtype == VP_C128) {
     *real_io = false;
@@ -617,9 +617,10 @@ vp_status vp_plan_create(vp_plan* out, int d, int N, vp_kernel kernel, double k,
   *out = nullptr;
   if (d != 2 && d != 3) return fail(nullptr, VP_ERR_INVALID_ARG, "d must be 2 or 3");
   if (N < 4 || N % 2) return fail(nullptr, VP_ERR_INVALID_ARG, "N must be even and >= 4");
-  if (kernel != VP_LAPLACE && kernel != VP_HELMHOLTZ) return fail(nullptr, VP_ERR_INVALID_ARG, "unknown kernel");
-  if (!isfinite(k) || (kernel == VP_LAPLACE && k != 0.0) || (kernel == VP_HELMHOLTZ && !(k > 0.0)))
-    return fail(nullptr, VP_ERR_INVALID_ARG, "k must be 0 for Laplace and > 0 for Helmholtz");
+  if (kernel != VP_LAPLACE && kernel != VP_HELMHOLTZ && kernel != VP_BIHARMONIC)
+    return fail(nullptr, VP_ERR_INVALID_ARG, "unknown kernel");
+  if (!isfinite(k) || (kernel != VP_HELMHOLTZ && k != 0.0) || (kernel == VP_HELMHOLTZ && !(k > 0.0)))
+    return fail(nullptr, VP_ERR_INVALID_ARG, "k must be 0 for Laplace and biharmonic, > 0 for Helmholtz");
   if (!isfinite(L)) return fail(nullptr, VP_ERR_INVALID_ARG, "L must be finite");
   if (L <= 0.0) L = (d == 3) ? 1.8 : 1.5;
   if (!(L > sqrt((double)d)) || L > 3.0) return fail(nullptr, VP_ERR_INVALID_ARG, "L must satisfy sqrt(d) < L <= 3");

@@ -14,6 +14,8 @@ namespace vp {
 constexpr int GL_NODES = 24;
 // |s - k| below which the 2D Helmholtz numerator is a divided difference.
 constexpr double HELM2D_NEAR_K = 1.0;
+// x = Ls below which the biharmonic spectra are summed from their power series
+constexpr double BIHARM_SERIES_X = 2.0;
 
 // precompute.cu
 cudaError_t set_gauss_legendre(const double* x, const double* w);

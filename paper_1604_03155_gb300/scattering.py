@@ -120,9 +120,18 @@ def main(argv=None):
     ap.add_argument("--tol", type=float, default=None, help="default 1e-12 (fp64), 1e-6 (fp32)")
     ap.add_argument("--maxit", type=int, default=20000)
     ap.add_argument("--quick", action="store_true", help="small grids only")
+    ap.add_argument("--single", default=None, metavar="TABLE:SIZE:N",
+                    help="one solve (no reference), e.g. disk:20:512; prints its stats")
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     tol = a.tol if a.tol is not None else (1e-12 if a.precision == "fp64" else 1e-6)
+    if a.single:
+        name, size, N = a.single.split(":")
+        d, contrast, _ = TABLES[name]
+        u, st, pre = solve(d, contrast, int(N), float(size), a.precision, a.form, tol, a.maxit)
+        print(json.dumps(dict(table=name, size=float(size), N=int(N), precision=a.precision, form=a.form,
+                              T_precomp=pre, **st)))
+        return
     specs = QUICK if a.quick else TABLES
     rows = []
     for name in a.tables.split(","):

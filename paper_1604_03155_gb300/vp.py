@@ -20,13 +20,13 @@ import numpy as np
 from . import build as _build
 
 VP_OK, VP_ERR_INVALID_ARG, VP_ERR_UNSUPPORTED, VP_ERR_OOM, VP_ERR_CUDA, VP_ERR_TIMEOUT, VP_ERR_NUMERICAL = range(7)
-VP_LAPLACE, VP_HELMHOLTZ = 0, 1
+VP_LAPLACE, VP_HELMHOLTZ, VP_BIHARMONIC = 0, 1, 2
 VP_FP32, VP_FP64 = 0, 1
 VP_GRAD_EXACT, VP_GRAD_SPECTRAL2N = 0, 1
 VP_R32, VP_C64, VP_R64, VP_C128 = 0, 1, 2, 3
 VP_ARRAY_T, VP_ARRAY_GHAT, VP_ARRAY_TJ, VP_ARRAY_GHATJ = 0, 1, 2, 3
 
-KERNELS = {"laplace": VP_LAPLACE, "helmholtz": VP_HELMHOLTZ}
+KERNELS = {"laplace": VP_LAPLACE, "helmholtz": VP_HELMHOLTZ, "biharmonic": VP_BIHARMONIC}
 PRECISIONS = {"fp32": VP_FP32, "fp64": VP_FP64, "tc_bf16x2": 2, "tc_fp16x2": 3, "tc_bf16x3": 4}
 GRAD_MODES = {"exact": VP_GRAD_EXACT, "spectral2n": VP_GRAD_SPECTRAL2N}
 

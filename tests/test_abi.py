@@ -51,6 +51,7 @@ def _create(d, N, kernel, k, L):
     ((2, 16, vp.VP_LAPLACE, 0.0, 3.5), vp.VP_ERR_INVALID_ARG),       # L > 3
     ((3, 10, vp.VP_LAPLACE, 0.0, 0.0), vp.VP_ERR_UNSUPPORTED),       # 2N = 20 not built
     ((2, 9, 7, 0.0, 0.0), vp.VP_ERR_INVALID_ARG),                    # kernel enum
+    ((3, 16, vp.VP_BIHARMONIC, 2.0, 0.0), vp.VP_ERR_INVALID_ARG),    # biharmonic with k
 ])
 def test_plan_create_validation(lib, args, status):
     st, handle = _create(*args)

@@ -33,6 +33,7 @@ WORKLOADS = {
     "helmholtz2d_k40_n1024_grad": dict(d=2, N=1024, kernel="helmholtz", k=40.0, L=1.5, grad=True),
     "helmholtz3d_k60_n256": dict(d=3, N=256, kernel="helmholtz", k=60.0, L=1.8, grad=False),
     "laplace3d_single_gaussian": dict(d=3, N=32, kernel="laplace", k=0.0, L=1.8, grad=False),
+    "biharmonic3d_n256": dict(d=3, N=256, kernel="biharmonic", k=0.0, L=1.8, grad=False),
     "batch64": dict(d=3, N=0, kernel="mixed", k=0.0, L=1.8, grad=False),
 }
 FALLBACK_HBM_GBS = 6800.0
@@ -534,7 +535,7 @@ def run_ours(args, wl):
             if wl["grad"]:
                 errs["grad"] = A.rel_l2(grad.cpu().numpy(), np.stack(grads_o))
             line["cpu_baseline"] = {"value": r["value"], "unit": "grid pts/s", "cores": r["cores"], "kind": "oracle",
-                                    "sample": f"one full {args.workload} apply (phi + gradients), FP64 oracle, own FFT"}
+                                    "sample": f"one full {args.workload} apply ({'phi + gradients' if wl['grad'] else 'phi'}), FP64 oracle, own FFT"}
             line["rel_l2_vs_oracle"] = errs
         print(json.dumps(line), flush=True)
     plan.close()

@@ -114,6 +114,24 @@ typedef enum {
  * allocated on first use.  Synchronous: returns after the precompute. */
 vp_status vp_plan_create(vp_plan* out, int d, int N, vp_kernel kernel, double k, double L);
 
+/* Nystrom matrix entries on the fly (Section 4, the remark after the discrete
+ * convolution): T is the matrix of a high-order Nystrom discretisation of the
+ * volume integral, phi_p = sum_{p'} T(p - p') f_{p'} (weight h^d included).
+ *   which, axis: VP_ARRAY_T (the potential; axis ignored) or VP_ARRAY_TJ with
+ *     axis j (the derivative kernel of Section 3, odd in x_j; built on first use)
+ *   vp_kernel_entries: out[i] = T(n_i) for count integer offsets n_i, given as
+ *     count x d int32 (row i = n_i), each |n_ij| <= N
+ *   vp_matrix_block: out[i][j] = T(p(rows[i]) - p(cols[j])), row-major
+ *     nrows x ncols, rows/cols flat C-order grid indices in [0, N^d) (int64)
+ *   dtype: VP_C128 (the FP64 octant as is) or VP_C64 (rounded); out complex.
+ * All arrays are device pointers; asynchronous work on the plan's stream, the
+ * call returns after it.  An offset or index out of range writes zero there
+ * and returns VP_ERR_INVALID_ARG. */
+vp_status vp_kernel_entries(vp_plan plan, int which, int axis, const int* offsets, long long count, void* out,
+                            vp_dtype dtype);
+vp_status vp_matrix_block(vp_plan plan, int which, int axis, const long long* rows, long long nrows,
+                          const long long* cols, long long ncols, void* out, vp_dtype dtype);
+
 /* Stream for subsequent calls (cudaStream_t as void*; NULL = legacy default).
  * One plan serves one stream at a time. */
 vp_status vp_plan_set_stream(vp_plan plan, void* stream);

@@ -205,3 +205,24 @@ def ghat_full_from_octant(G_oct: np.ndarray, odd_axis=None) -> np.ndarray:
         shape[odd_axis] = 2 * N
         out = out * sgn.reshape(shape)
     return out
+
+
+def nystrom_block(T_oct: np.ndarray, rows, cols, odd_axis=None) -> np.ndarray:
+    """The Nystrom matrix of the discretised volume integral (Section 4, the
+    remark after the discrete convolution): A[i][j] = T(p_i - p'_j) for target
+    nodes rows[i] and source nodes cols[j], flat C-order grid indices, by plain
+    loops over the entries."""
+    d = T_oct.ndim
+    N = T_oct.shape[0] - 1
+    shape = (N,) * d
+    out = np.empty((len(rows), len(cols)), dtype=np.complex128)
+    for i, r in enumerate(rows):
+        p = np.unravel_index(int(r), shape)
+        for j, c in enumerate(cols):
+            q = np.unravel_index(int(c), shape)
+            n = [int(a) - int(b) for a, b in zip(p, q)]
+            v = complex(T_oct[tuple(abs(x) for x in n)])
+            if odd_axis is not None:
+                v *= np.sign(n[odd_axis])
+            out[i, j] = v
+    return out

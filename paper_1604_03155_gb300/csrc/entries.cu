@@ -1,0 +1,231 @@
+// entries.cu -- Nystrom matrix entries on the fly (Section 4, the remark after
+// the discrete convolution of Vico, Greengard & Ferrando).
+//
+// The precomputed kernel T is the matrix of a high-order Nystrom discretisation
+// of the volume integral operator: phi_p = sum_{p'} T(p - p') f_{p'}, so the
+// entry for target node p and source node p' is T(p - p') (the quadrature
+// weight h^d included).  T is even in every axis (the potential) or odd in axis
+// j (the derivative kernel T_j of Section 3); the plan holds it as its FP64
+// octant n in [0, N]^d, so an entry is one gather:
+//   T(n) = T_oct[|n_0|][|n_1|]([|n_2|])  (times sign(n_j) for T_j).
+// Two entry points: a list of integer offsets, and a dense block of the matrix
+// for lists of target and source nodes (flat C-order grid indices), the form a
+// hierarchical or block preconditioner consumes.  Out-of-range offsets or
+// indices write zero and raise a flag the host turns into VP_ERR_INVALID_ARG.
+#include <cuda_runtime.h>
+
+#include "../../include/vp.h"
+#include "vp_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxBlocks = 152 * 32;
+
+template <typename C>
+__device__ __forceinline__ C to_c(double2 v);
+template <>
+__device__ __forceinline__ double2 to_c<double2>(double2 v) {
+  return v;
+}
+template <>
+__device__ __forceinline__ float2 to_c<float2>(double2 v) {
+  return make_float2((float)v.x, (float)v.y);
+}
+
+// T(n) for an offset n (|n_j| <= N), from the octant
+__device__ __forceinline__ double2 gather(const double2* __restrict__ oct, int d, int N, int odd_axis, const int* n) {
+  const long long M = N + 1;
+  long long idx = 0;
+  double sgn = 1.0;
+  for (int j = 0; j < d; ++j) {
+    const int a = n[j] < 0 ? -n[j] : n[j];
+    idx = idx * M + a;
+    if (j == odd_axis) sgn = n[j] > 0 ? 1.0 : (n[j] < 0 ? -1.0 : 0.0);
+  }
+  const double2 v = __ldg(oct + idx);
+  return make_double2(sgn * v.x, sgn * v.y);
+}
+
+template <typename C>
+__global__ void __launch_bounds__(kThreads) k_entries(const double2* __restrict__ oct, int d, int N, int odd_axis,
+                                                      const int* __restrict__ off, long long count, C* __restrict__ out,
+                                                      int* __restrict__ bad) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    int n[3] = {0, 0, 0};
+    bool ok = true;
+    for (int j = 0; j < d; ++j) {
+      n[j] = off[i * d + j];
+      ok = ok && n[j] >= -N && n[j] <= N;
+    }
+    if (!ok) {
+      out[i] = to_c<C>(make_double2(0.0, 0.0));
+      atomicExch(bad, 1);
+      continue;
+    }
+    out[i] = to_c<C>(gather(oct, d, N, odd_axis, n));
+  }
+}
+
+// out[i][j] = T(p(rows[i]) - p(cols[j])), row-major.  A block owns a tile of
+// kTileRows rows x kThreads columns: the rows are decoded once into shared
+// memory, each thread decodes its column once and writes that column of every
+// row of the tile (consecutive threads write consecutive entries of one row).
+constexpr int kTileRows = 16;
+
+template <typename C>
+__global__ void __launch_bounds__(kThreads) k_block(const double2* __restrict__ oct, int d, int N, int odd_axis,
+                                                    const long long* __restrict__ rows, long long nr,
+                                                    const long long* __restrict__ cols, long long nc,
+                                                    C* __restrict__ out, int* __restrict__ bad) {
+  __shared__ int srow[kTileRows][3];
+  __shared__ int sok[kTileRows];
+  const long long U = d == 3 ? (long long)N * N * N : (long long)N * N;
+  const long long c = blockIdx.x * (long long)kThreads + threadIdx.x;
+  int q[3] = {0, 0, 0};
+  bool cok = false;
+  if (c < nc) {
+    long long cc = cols[c];
+    cok = cc >= 0 && cc < U;
+    if (cok)
+      for (int a = d - 1; a >= 0; --a) {
+        q[a] = (int)(cc % N);
+        cc /= N;
+      }
+    else
+      atomicExch(bad, 1);
+  }
+  for (long long r0 = blockIdx.y * (long long)kTileRows; r0 < nr; r0 += (long long)gridDim.y * kTileRows) {
+    __syncthreads();  // the previous tile's rows are no longer read
+    if (threadIdx.x < kTileRows) {
+      const long long r = r0 + threadIdx.x;
+      int ok = 0;
+      if (r < nr) {
+        long long rr = rows[r];
+        ok = rr >= 0 && rr < U;
+        if (ok) {
+          for (int a = d - 1; a >= 0; --a) {
+            srow[threadIdx.x][a] = (int)(rr % N);
+            rr /= N;
+          }
+        } else if (blockIdx.x == 0) {
+          atomicExch(bad, 1);
+        }
+      }
+      sok[threadIdx.x] = ok;
+    }
+    __syncthreads();
+    if (c >= nc) continue;
+    const int nrows = nr - r0 < kTileRows ? (int)(nr - r0) : kTileRows;
+    for (int i = 0; i < nrows; ++i) {
+      double2 v = make_double2(0.0, 0.0);
+      if (cok && sok[i]) {
+        int n[3];
+        for (int a = 0; a < d; ++a) n[a] = srow[i][a] - q[a];
+        v = gather(oct, d, N, odd_axis, n);
+      }
+      out[(r0 + i) * nc + c] = to_c<C>(v);
+    }
+  }
+}
+
+unsigned grid_for(long long n) {
+  const long long b = (n + kThreads - 1) / kThreads;
+  return (unsigned)(b < 1 ? 1 : (b > kMaxBlocks ? kMaxBlocks : b));
+}
+
+bool is_device(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// common checks; *oct, *odd_axis, *dflag on success
+vp_status prepare(vp_plan plan, int which, int axis, vp_dtype dtype, const void* const* ptrs, int nptr,
+                  const double2** oct, int* odd_axis, int** dflag) {
+  if (!plan) return vp::entries_fail(nullptr, VP_ERR_INVALID_ARG, "plan is NULL");
+  if (dtype != VP_C64 && dtype != VP_C128)
+    return vp::entries_fail(plan, VP_ERR_INVALID_ARG, "dtype must be VP_C64 or VP_C128");
+  for (int i = 0; i < nptr; ++i) {
+    if (!ptrs[i]) return vp::entries_fail(plan, VP_ERR_INVALID_ARG, "NULL array");
+    if (!is_device(ptrs[i])) return vp::entries_fail(plan, VP_ERR_INVALID_ARG, "arrays must be device pointers");
+  }
+  vp_status st = vp::plan_kernel_octant(plan, which, axis, oct);
+  if (st != VP_OK) return st;
+  *odd_axis = which == VP_ARRAY_TJ ? axis : -1;
+  *dflag = vp::plan_flag_word(plan);
+  if (!*dflag) return vp::entries_fail(plan, VP_ERR_OOM, "flag word allocation failed");
+  return VP_OK;
+}
+
+vp_status finish(vp_plan plan, int* dflag) {
+  cudaStream_t s = vp::plan_stream(plan);
+  int h = 0;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, dflag, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return vp::entries_fail(plan, VP_ERR_CUDA, cudaGetErrorString(e));
+  if (h) return vp::entries_fail(plan, VP_ERR_INVALID_ARG, "an offset or grid index is out of range (zeros written)");
+  return VP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vp_status vp_kernel_entries(vp_plan plan, int which, int axis, const int* offsets, long long count, void* out,
+                            vp_dtype dtype) {
+  if (count < 0) return vp::entries_fail(plan, VP_ERR_INVALID_ARG, "count < 0");
+  if (count == 0) return VP_OK;
+  const void* ptrs[2] = {offsets, out};
+  const double2* oct = nullptr;
+  int odd = -1, *flag = nullptr;
+  vp_status st = prepare(plan, which, axis, dtype, ptrs, 2, &oct, &odd, &flag);
+  if (st != VP_OK) return st;
+  int d = 0, N = 0;
+  vp_plan_info(plan, &d, &N, nullptr, nullptr, nullptr);
+  cudaStream_t s = vp::plan_stream(plan);
+  cudaMemsetAsync(flag, 0, sizeof(int), s);
+  if (dtype == VP_C128)
+    k_entries<double2><<<grid_for(count), kThreads, 0, s>>>(oct, d, N, odd, offsets, count,
+                                                              reinterpret_cast<double2*>(out), flag);
+  else
+    k_entries<float2><<<grid_for(count), kThreads, 0, s>>>(oct, d, N, odd, offsets, count,
+                                                             reinterpret_cast<float2*>(out), flag);
+  return finish(plan, flag);
+}
+
+vp_status vp_matrix_block(vp_plan plan, int which, int axis, const long long* rows, long long nrows,
+                          const long long* cols, long long ncols, void* out, vp_dtype dtype) {
+  if (nrows < 0 || ncols < 0) return vp::entries_fail(plan, VP_ERR_INVALID_ARG, "negative block size");
+  if (nrows == 0 || ncols == 0) return VP_OK;
+  const void* ptrs[3] = {rows, cols, out};
+  const double2* oct = nullptr;
+  int odd = -1, *flag = nullptr;
+  vp_status st = prepare(plan, which, axis, dtype, ptrs, 3, &oct, &odd, &flag);
+  if (st != VP_OK) return st;
+  int d = 0, N = 0;
+  vp_plan_info(plan, &d, &N, nullptr, nullptr, nullptr);
+  cudaStream_t s = vp::plan_stream(plan);
+  cudaMemsetAsync(flag, 0, sizeof(int), s);
+  const long long gx = (ncols + kThreads - 1) / kThreads;
+  if (gx > 0x7fffffffLL) return vp::entries_fail(plan, VP_ERR_INVALID_ARG, "ncols too large");
+  const long long row_tiles = (nrows + kTileRows - 1) / kTileRows;
+  // about 32 resident blocks per SM in all; the row tiles are strided over grid.y
+  long long gy = (152LL * 32 + gx - 1) / gx;
+  gy = gy < 1 ? 1 : (gy > row_tiles ? row_tiles : (gy > 65535 ? 65535 : gy));
+  const dim3 grid((unsigned)gx, (unsigned)gy);
+  if (dtype == VP_C128)
+    k_block<double2><<<grid, kThreads, 0, s>>>(oct, d, N, odd, rows, nrows, cols, ncols,
+                                               reinterpret_cast<double2*>(out), flag);
+  else
+    k_block<float2><<<grid, kThreads, 0, s>>>(oct, d, N, odd, rows, nrows, cols, ncols,
+                                              reinterpret_cast<float2*>(out), flag);
+  return finish(plan, flag);
+}
+
+}  // extern "C"

@@ -55,6 +55,7 @@ struct vp_plan_s {
   uint16_t* tcB = nullptr;
   int tc_split = -1;
   int* d_err = nullptr;
+  int* d_flag = nullptr;  // range flag of the Nystrom entry kernels
 
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -563,6 +564,30 @@ int plan_is_fp32(vp_plan p) { return p && p->prec == VP_FP32; }
 
 int plan_is_fp64(vp_plan p) { return p && p->prec == VP_FP64; }
 
+vp_status entries_fail(vp_plan p, vp_status st, const char* msg) { return fail(p, st, msg); }
+
+vp_status plan_kernel_octant(vp_plan p, int which, int axis, const double2** oct) {
+  VP_CUDA(p, cudaSetDevice(p->device));
+  if (which == VP_ARRAY_T) {
+    *oct = p->T64;
+    return VP_OK;
+  }
+  if (which != VP_ARRAY_TJ) return fail(p, VP_ERR_INVALID_ARG, "which must be VP_ARRAY_T or VP_ARRAY_TJ");
+  if (axis < 0 || axis >= p->d) return fail(p, VP_ERR_INVALID_ARG, "axis out of range");
+  vp_status st = build_grad(p);
+  if (st != VP_OK) return st;
+  *oct = p->Tj64[axis];
+  return VP_OK;
+}
+
+int* plan_flag_word(vp_plan p) {
+  if (!p->d_flag && cudaMalloc(&p->d_flag, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    p->d_flag = nullptr;
+  }
+  return p->d_flag;
+}
+
 int plan_pass_args_f32(vp_plan p, float2* ws, PassArgs<float>* args, int* kinds) {
   FieldDesc field{(const void*)p->G32, -1, -1};
   void* outs[1] = {nullptr};
@@ -839,6 +864,7 @@ vp_status vp_destroy(vp_plan p) {
   cudaFree(p->tw32);
   cudaFree(p->tcB);
   cudaFree(p->d_err);
+  cudaFree(p->d_flag);
   cudaFree(p->ws);
   cudaFree(p->stage);
   for (const TimedLaunch& t : p->timed) {

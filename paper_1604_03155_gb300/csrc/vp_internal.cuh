@@ -70,6 +70,12 @@ int plan_device(vp_plan p);
 cudaStream_t plan_stream(vp_plan p);
 int plan_is_fp32(vp_plan p);
 int plan_is_fp64(vp_plan p);
+// Nystrom entries (entries.cu): the plan's FP64 kernel octant T (which =
+// VP_ARRAY_T) or T_axis (VP_ARRAY_TJ, built on first use), a device flag word
+// owned by the plan, and the plan's error message.
+vp_status plan_kernel_octant(vp_plan p, int which, int axis, const double2** oct);
+int* plan_flag_word(vp_plan p);
+vp_status entries_fail(vp_plan p, vp_status st, const char* msg);
 // ls.cu: the message vp_ls_last_error returns on this thread
 void ls_set_error(const char* msg);
 // The FP32 potential-only passes of a plan on workspace `ws` (input and output

@@ -145,13 +145,15 @@ class Workload:
 
 
 def workload(name: str) -> Workload:
-    """The five benchmark workloads by name."""
+    """The benchmark workloads by name."""
     if name == "laplace3d_single_gaussian":  # 3D Laplace, N=32, one Gaussian sigma=0.08, FP64
         return Workload(name, 3, 32, "laplace", 0.0, 1.8, BASE_SEED + 1, 1, "fp64")
     if name == "helmholtz2d_k40_n1024_grad":  # 2D Helmholtz k=40, N=1024, 8 Gaussians, FP32 + grad
         return Workload(name, 2, 1024, "helmholtz", 40.0, 1.5, BASE_SEED + 2, 8, "fp32", grad=True)
     if name == "helmholtz3d_k60_n256":  # 3D Helmholtz k=60, N=256, 16 Gaussians, FP32
         return Workload(name, 3, 256, "helmholtz", 60.0, 1.8, BASE_SEED + 3, 16, "fp32")
+    if name == "biharmonic3d_n256":  # 3D biharmonic, N=256, 16 Gaussians, FP32
+        return Workload(name, 3, 256, "biharmonic", 0.0, 1.8, BASE_SEED + 6, 16, "fp32")
     raise KeyError(name)
 
 

@@ -53,6 +53,9 @@ _SIGNATURES = {
     "vp_apply": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
     "vp_apply_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int]),
     "vp_plan_get_array": (c_int, [c_void_p, c_int, c_int, ctypes.POINTER(c_double), c_size_t]),
+    "vp_kernel_entries": (c_int, [c_void_p, c_int, c_int, c_void_p, ctypes.c_longlong, c_void_p, c_int]),
+    "vp_matrix_block": (c_int, [c_void_p, c_int, c_int, c_void_p, ctypes.c_longlong, c_void_p, ctypes.c_longlong,
+                                c_void_p, c_int]),
     "vp_plan_info": (c_int, [c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_double),
                              ctypes.POINTER(c_double), ctypes.POINTER(c_size_t)]),
     "vp_plan_set_timing": (c_int, [c_void_p, c_int]),
@@ -276,6 +279,40 @@ class Plan:
         _check(lib().vp_plan_get_array(self.handle, code, axis,
                                        buf.ctypes.data_as(ctypes.POINTER(c_double)), buf.size), self.handle)
         return buf.view(np.complex128).reshape((self.N + 1,) * self.d)
+
+    def kernel_entries(self, offsets, which: str = "T", axis: int = 0, dtype=None):
+        """Nystrom entries T(n) for a (count, d) int32 device tensor of offsets
+        (|n_j| <= N); which 'T' or 'Tj' (derivative along `axis`).  Returns a
+        complex128 (or `dtype`) device tensor of length count."""
+        import torch
+        dtype = torch.complex128 if dtype is None else dtype
+        out = torch.empty(offsets.shape[0], dtype=dtype, device=offsets.device)
+        code = {"T": VP_ARRAY_T, "Tj": VP_ARRAY_TJ}[which]
+        self._sync_stream_to_torch(offsets)
+        _check(lib().vp_kernel_entries(self.handle, code, axis, _ptr(offsets), offsets.shape[0], _ptr(out),
+                                       _dtype_code(out)), self.handle)
+        return out
+
+    def matrix_block(self, rows, cols, which: str = "T", axis: int = 0, dtype=None):
+        """The (len(rows), len(cols)) block of the Nystrom matrix, T(p(row) - p(col)),
+        for int64 device tensors of flat grid indices."""
+        import torch
+        dtype = torch.complex128 if dtype is None else dtype
+        out = torch.empty((rows.shape[0], cols.shape[0]), dtype=dtype, device=rows.device)
+        code = {"T": VP_ARRAY_T, "Tj": VP_ARRAY_TJ}[which]
+        self._sync_stream_to_torch(rows)
+        _check(lib().vp_matrix_block(self.handle, code, axis, _ptr(rows), rows.shape[0], _ptr(cols), cols.shape[0],
+                                     _ptr(out), _dtype_code(out)), self.handle)
+        return out
+
+    def kernel_line(self, axis: int = 0, which: str = "T"):
+        """T along one grid axis through the origin, offsets -N+1 .. N-1 (the
+        paper's Fig. 2 view of the kernel), as a complex128 device tensor."""
+        import torch
+        n = torch.arange(-self.N + 1, self.N, dtype=torch.int32, device="cuda")
+        off = torch.zeros((n.shape[0], self.d), dtype=torch.int32, device="cuda")
+        off[:, axis] = n
+        return self.kernel_entries(off, which, axis)
 
     def info(self) -> dict:
         d, N, k, L, b = c_int(), c_int(), c_double(), c_double(), c_size_t()

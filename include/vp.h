@@ -320,6 +320,28 @@ vp_status vp_ls_flexible_basis(vp_plan plan, const float* q, const void* b, int 
 enum { VP_LS_FIELD = 0, VP_LS_DENSITY = 1 };
 vp_status vp_ls_bicgstab(vp_plan plan, const void* q, const void* u_inc, void* u, vp_dtype dtype, int form,
                          double tol, int maxit, double* history, vp_ls_stats* stats);
+/* The same solve with FP64 accuracy at mostly FP32 cost (a project addition:
+ * GB300 runs FP64 arithmetic at a small fraction of its FP32 rate): Bi-CGStab
+ * with reliable updates (Sleijpen & van der Vorst 1996).  The recurrence runs
+ * on the FP32 apply and accumulates a correction; whenever its residual has
+ * fallen below delta times the largest residual since the last update (or
+ * below tol), the correction is added to the FP64 solution and the true
+ * residual b - M x, formed with the FP64 apply, replaces the recurrence
+ * residual.  The solve stops when the true residual is below tol ||b||.
+ * FP32 products slow Bi-CGStab down on strongly indefinite problems (measured:
+ * the filtered disk at 80 wavelengths); when the FP32 phase has not converged
+ * after maxit iterations, or three consecutive updates each gain less than 2x,
+ * or it breaks down, the solve is rerun in FP64 (vp_ls_bicgstab, at most
+ * maxit iterations) and stats->used_fallback is set.
+ * q: N^d doubles, u_inc/u: complex128 device arrays; the plan's precision may
+ * be VP_FP32 or VP_FP64 (it is switched internally and restored).  delta in
+ * (0, 1), e.g. 0.01.  stats: matvecs = operator products (FP32, plus the
+ * FP64 ones of a fallback), restarts = the number of updates (one FP64 product
+ * each), estimated_residual = the last true residual; other fields as for
+ * vp_ls_bicgstab.  history[j]: the FP32
+ * recurrence residual ||r_j|| / ||b|| after iteration j. */
+vp_status vp_ls_bicgstab_mixed(vp_plan plan, const double* q, const void* u_inc, void* u, int form, double tol,
+                               double delta, int maxit, double* history, vp_ls_stats* stats);
 const char* vp_ls_last_error(void);
 
 /* ---------------------------------------------------------------------------

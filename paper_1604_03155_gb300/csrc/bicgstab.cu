@@ -44,14 +44,26 @@ namespace {
 constexpr int kBlocks = 304;  // 2 x 152 SMs
 constexpr int kThreads = 512;
 constexpr int kScalThreads = 256;
+// mixed precision: consecutive reliable updates that each reduce the true
+// residual by less than 2x before the solve falls back to FP64
+constexpr int kMaxStall = 3;
 
 enum { BCG_RUNNING = 0, BCG_CONVERGED = 1, BCG_CONVERGED_HALF = 2, BCG_BREAKDOWN = 3, BCG_NONFINITE = 4 };
 
 struct BcgState {
   double2 rho, alpha, omega, beta;
   double bnorm2, rnorm2, snorm2, tol, tol2;
-  int done, first, breakdown, iterations, matvecs, pad;
+  // reliable updates (mixed precision): the update threshold delta^2 and the
+  // largest ||r||^2 since the last update
+  double delta2, maxrr2;
+  double best2;  // smallest true ||r||^2 at an update
+  int done, first, breakdown, iterations, matvecs;
+  int mixed, update, epoch, updates, stall;  // stall: consecutive updates gaining less than 2x
 };
+
+// the vector and scalar kernels of an iteration do nothing after the stop or
+// while a reliable update is pending
+__device__ __forceinline__ bool idle(const BcgState* st) { return st->done || st->update; }
 
 template <typename R>
 struct Cx;
@@ -184,7 +196,7 @@ __global__ void __launch_bounds__(kThreads) k_p(const BcgState* __restrict__ st,
                                                 const typename Cx<R>::T* __restrict__ v, const R* __restrict__ q,
                                                 typename Cx<R>::T* __restrict__ t0, long long n) {
   using C = typename Cx<R>::T;
-  if (st->done) return;
+  if (idle(st)) return;
   const R br = (R)st->beta.x, bi = (R)st->beta.y, wr = (R)st->omega.x, wi = (R)st->omega.y;
   GRID_LOOP(i, n) {
     const C pv = p[i], vv = v[i], rv = r[i];
@@ -206,7 +218,7 @@ __global__ void __launch_bounds__(kThreads) k_v(const BcgState* __restrict__ st,
                                                 const typename Cx<R>::T* __restrict__ rh, R k2, long long n,
                                                 double2* __restrict__ part) {
   using C = typename Cx<R>::T;
-  if (st->done) return;
+  if (idle(st)) return;
   R ar = 0, ai = 0;
   GRID_LOOP(i, n) {
     const R f = DENSITY ? k2 * q[i] : k2;
@@ -229,7 +241,7 @@ __global__ void __launch_bounds__(kThreads) k_s(const BcgState* __restrict__ st,
                                                 typename Cx<R>::T* __restrict__ t0, long long n,
                                                 double2* __restrict__ part) {
   using C = typename Cx<R>::T;
-  if (st->done) return;
+  if (idle(st)) return;
   const R ar = (R)st->alpha.x, ai = (R)st->alpha.y;
   R acc = 0;
   GRID_LOOP(i, n) {
@@ -254,7 +266,7 @@ __global__ void __launch_bounds__(kThreads) k_t(const BcgState* __restrict__ st,
                                                 const typename Cx<R>::T* __restrict__ s, const R* __restrict__ q, R k2,
                                                 long long n, double2* __restrict__ part) {
   using C = typename Cx<R>::T;
-  if (st->done) return;
+  if (idle(st)) return;
   R tsr = 0, tsi = 0, tt = 0;
   GRID_LOOP(i, n) {
     const R f = DENSITY ? k2 * q[i] : k2;
@@ -277,7 +289,7 @@ __global__ void __launch_bounds__(kThreads) k_xr(const BcgState* __restrict__ st
                                                  const typename Cx<R>::T* __restrict__ rh, long long n,
                                                  double2* __restrict__ part) {
   using C = typename Cx<R>::T;
-  if (st->done) return;
+  if (idle(st)) return;
   const R wr = (R)st->omega.x, wi = (R)st->omega.y;
   R hr = 0, hi = 0, nn = 0;
   GRID_LOOP(i, n) {
@@ -327,7 +339,7 @@ __global__ void k_widen_r(double* __restrict__ out, const float* __restrict__ in
 
 // after k_start / k_xr: rho_{j+1} = <r^, r>, ||r||^2; stop test; beta
 __global__ void __launch_bounds__(kScalThreads) k_scal_rho(BcgState* __restrict__ st, const double2* __restrict__ part) {
-  if (st->done) return;
+  if (idle(st)) return;
   double2 s[2];
   sum_partials<2>(part, s);
   if (threadIdx.x != 0) return;
@@ -345,11 +357,19 @@ __global__ void __launch_bounds__(kScalThreads) k_scal_rho(BcgState* __restrict_
   } else if (!isfinite(rn2) || !finite2(rho_new)) {
     st->done = BCG_NONFINITE;
     return;
-  } else if (rn2 < st->tol2) {
-    st->done = BCG_CONVERGED;
-    return;
   } else if (st->breakdown) {
     st->done = BCG_BREAKDOWN;
+    return;
+  } else if (st->mixed) {
+    // reliable update when the recurrence residual claims convergence or has
+    // fallen by delta since the last update (rho is kept for the update's beta)
+    if (rn2 < st->tol2 || rn2 < st->delta2 * st->maxrr2) {
+      st->update = 1;
+      return;
+    }
+    st->maxrr2 = fmax(st->maxrr2, rn2);
+  } else if (rn2 < st->tol2) {
+    st->done = BCG_CONVERGED;
     return;
   }
   if (rho_new.x == 0.0 && rho_new.y == 0.0) {
@@ -362,7 +382,7 @@ __global__ void __launch_bounds__(kScalThreads) k_scal_rho(BcgState* __restrict_
 
 // after k_v: alpha = rho / <r^, v>
 __global__ void __launch_bounds__(kScalThreads) k_scal_alpha(BcgState* __restrict__ st, const double2* __restrict__ part) {
-  if (st->done) return;
+  if (idle(st)) return;
   double2 s[1];
   sum_partials<1>(part, s);
   if (threadIdx.x != 0) return;
@@ -379,20 +399,20 @@ __global__ void __launch_bounds__(kScalThreads) k_scal_alpha(BcgState* __restric
 
 // after k_s: ||s||^2 and the half-step stop test
 __global__ void __launch_bounds__(kScalThreads) k_scal_s(BcgState* __restrict__ st, const double2* __restrict__ part) {
-  if (st->done) return;
+  if (idle(st)) return;
   double2 s[1];
   sum_partials<1>(part, s);
   if (threadIdx.x != 0) return;
   st->snorm2 = s[0].x;
   if (!isfinite(s[0].x))
     st->done = BCG_NONFINITE;
-  else if (s[0].x < st->tol2)
+  else if (s[0].x < st->tol2 && !st->mixed)  // mixed precision: the true residual decides
     st->done = BCG_CONVERGED_HALF;
 }
 
 // after k_t: omega = <t, s> / <t, t> (0 with a breakdown flag when t = 0)
 __global__ void __launch_bounds__(kScalThreads) k_scal_omega(BcgState* __restrict__ st, const double2* __restrict__ part) {
-  if (st->done) return;
+  if (idle(st)) return;
   double2 s[2];
   sum_partials<2>(part, s);
   if (threadIdx.x != 0) return;
@@ -404,6 +424,128 @@ __global__ void __launch_bounds__(kScalThreads) k_scal_omega(BcgState* __restric
     st->breakdown = 1;
   } else {
     st->omega = make_double2(s[0].x / s[1].x, s[0].y / s[1].x);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// mixed precision with reliable updates (Sleijpen & van der Vorst 1996): the
+// recurrence runs in FP32 on the correction x_lo; at an update the FP64 solution
+// takes x_lo, the true residual b - M x is formed with the FP64 apply and
+// replaces the recurrence residual, and the recurrence continues from it.
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(kThreads) k_narrow_r(float* __restrict__ out, const double* __restrict__ in,
+                                                       long long n) {
+  GRID_LOOP(i, n) out[i] = (float)in[i];
+}
+
+// r = r^ = (float) b; p = v = x_lo = 0; x = 0; partials (<r^, r>, ||b||^2 in FP64)
+__global__ void __launch_bounds__(kThreads) k_mixed_init(const double2* __restrict__ b, float2* __restrict__ r,
+                                                         float2* __restrict__ rh, float2* __restrict__ p,
+                                                         float2* __restrict__ v, float2* __restrict__ xlo,
+                                                         double2* __restrict__ x, long long n,
+                                                         double2* __restrict__ part) {
+  float acc = 0.f;
+  double bb = 0.0;
+  GRID_LOOP(i, n) {
+    const double2 bv = b[i];
+    const float2 rv = make_float2((float)bv.x, (float)bv.y);
+    r[i] = rv;
+    rh[i] = rv;
+    p[i] = make_float2(0.f, 0.f);
+    v[i] = make_float2(0.f, 0.f);
+    xlo[i] = make_float2(0.f, 0.f);
+    x[i] = make_double2(0.0, 0.0);
+    acc += rv.x * rv.x + rv.y * rv.y;
+    bb += bv.x * bv.x + bv.y * bv.y;
+  }
+  const double re[2] = {(double)acc, bb}, im[2] = {0.0, 0.0};
+  block_partials<2>(re, im, part);
+}
+
+// x += x_lo, x_lo = 0; t0 = q x for the field form's FP64 product
+template <bool DENSITY>
+__global__ void __launch_bounds__(kThreads) k_accumulate(double2* __restrict__ x, float2* __restrict__ xlo,
+                                                         const double* __restrict__ q, double2* __restrict__ t0,
+                                                         long long n) {
+  GRID_LOOP(i, n) {
+    const float2 d = xlo[i];
+    const double2 xv = make_double2(x[i].x + d.x, x[i].y + d.y);
+    x[i] = xv;
+    xlo[i] = make_float2(0.f, 0.f);
+    if (!DENSITY) {
+      const double qi = q[i];
+      t0[i] = make_double2(qi * xv.x, qi * xv.y);
+    }
+  }
+}
+
+// true residual r = b - (x - k^2 (q) t1) in FP64 (t1 = V[q x] or V[x]), its
+// FP32 copy for the recurrence; partials (<r^, r>, ||r||^2 in FP64)
+template <bool DENSITY>
+__global__ void __launch_bounds__(kThreads) k_true_residual(const double2* __restrict__ b,
+                                                            const double2* __restrict__ x,
+                                                            const double2* __restrict__ t1,
+                                                            const double* __restrict__ q, double k2,
+                                                            const float2* __restrict__ rh, float2* __restrict__ r,
+                                                            long long n, double2* __restrict__ part) {
+  float hr = 0.f, hi = 0.f;
+  double nn = 0.0;
+  GRID_LOOP(i, n) {
+    const double f = DENSITY ? k2 * q[i] : k2;
+    const double2 bv = b[i], xv = x[i], tv = t1[i];
+    const double ex = bv.x - (xv.x - f * tv.x), ey = bv.y - (xv.y - f * tv.y);
+    const float2 rv = make_float2((float)ex, (float)ey);
+    r[i] = rv;
+    const float2 h = rh[i];
+    hr += h.x * rv.x + h.y * rv.y;
+    hi += h.x * rv.y - h.y * rv.x;
+    nn += ex * ex + ey * ey;
+  }
+  const double re[2] = {(double)hr, nn}, im[2] = {(double)hi, 0.0};
+  block_partials<2>(re, im, part);
+}
+
+// after k_mixed_init (first) or k_true_residual: the stop test on the true
+// residual, beta from the new residual, the update flag cleared
+__global__ void __launch_bounds__(kScalThreads) k_scal_update(BcgState* __restrict__ st,
+                                                              const double2* __restrict__ part) {
+  if (st->done) return;
+  double2 s[2];
+  sum_partials<2>(part, s);
+  if (threadIdx.x != 0) return;
+  const double2 rho_new = s[0];
+  const double rn2 = s[1].x;
+  st->rnorm2 = rn2;
+  st->update = 0;
+  st->maxrr2 = rn2;
+  if (st->first) {
+    st->first = 0;
+    st->bnorm2 = rn2;
+    st->best2 = rn2;
+    st->tol2 = st->tol * st->tol * rn2;
+    st->rho = rho_new;
+    st->beta = make_double2(0.0, 0.0);
+    if (!(rn2 > 0.0)) st->done = isfinite(rn2) ? BCG_CONVERGED : BCG_NONFINITE;
+    return;
+  }
+  ++st->epoch;
+  ++st->updates;
+  if (rn2 < 0.25 * st->best2) {
+    st->stall = 0;
+  } else {
+    ++st->stall;
+  }
+  st->best2 = fmin(st->best2, rn2);
+  if (!isfinite(rn2) || !finite2(rho_new)) {
+    st->done = BCG_NONFINITE;
+  } else if (rn2 < st->tol2) {
+    st->done = BCG_CONVERGED;
+  } else if (rho_new.x == 0.0 && rho_new.y == 0.0) {
+    st->done = BCG_BREAKDOWN;
+  } else {
+    st->beta = cmul(cdiv(rho_new, st->rho), cdiv(st->alpha, st->omega));
+    st->rho = rho_new;
   }
 }
 
@@ -510,18 +652,19 @@ vp_status enqueue_iteration(vp_plan plan, Work<R>& w, const R* q, R k2, int slot
   return cudaGetLastError() == cudaSuccess ? VP_OK : VP_ERR_CUDA;
 }
 
-// ||b - M x|| / ||b|| with the operator of this precision (w.t0/w.t1 as scratch)
+// ||b - M x|| / ||b|| with the operator of this precision (w.t0/w.t1 as scratch,
+// the plan's stream s, partials in part)
 template <typename R, bool DENSITY>
-vp_status residual(vp_plan plan, Work<R>& w, const typename Cx<R>::T* b, const typename Cx<R>::T* x, const R* q,
-                   R k2, double* out, Err& E) {
+vp_status residual(vp_plan plan, Work<R>& w, cudaStream_t s, double2* part, const typename Cx<R>::T* b,
+                   const typename Cx<R>::T* x, const R* q, R k2, double* out, Err& E) {
   const long long n = w.n;
-  if (!DENSITY) k_qmul<R><<<kBlocks, kThreads, 0, w.s>>>(w.t0, q, x, n);
+  if (!DENSITY) k_qmul<R><<<kBlocks, kThreads, 0, s>>>(w.t0, q, x, n);
   vp_status st = apply_v<R, DENSITY>(plan, w, x);
   if (st != VP_OK) return st;
-  k_resid<R, DENSITY><<<kBlocks, kThreads, 0, w.s>>>(b, x, w.t1, q, k2, n, w.part);
+  k_resid<R, DENSITY><<<kBlocks, kThreads, 0, s>>>(b, x, w.t1, q, k2, n, part);
   double2 h[2 * kBlocks];
-  BCG_CUDA(E, cudaMemcpyAsync(h, w.part, sizeof(h), cudaMemcpyDeviceToHost, w.s));
-  BCG_CUDA(E, cudaStreamSynchronize(w.s));
+  BCG_CUDA(E, cudaMemcpyAsync(h, part, sizeof(h), cudaMemcpyDeviceToHost, s));
+  BCG_CUDA(E, cudaStreamSynchronize(s));
   double rr = 0.0, bb = 0.0;
   for (int i = 0; i < kBlocks; ++i) {
     rr += h[2 * i].x;
@@ -626,7 +769,7 @@ vp_status solve(vp_plan plan, const R* q, const typename Cx<R>::T* uinc, typenam
   // true residual ||b - M x|| / ||b||, the operator and b evaluated in FP64
   double tr = 0.0;
   if constexpr (sizeof(R) == 8) {
-    st = residual<R, DENSITY>(plan, w, w.b, w.x, q, k2, &tr, E);
+    st = residual<R, DENSITY>(plan, w, w.s, w.part, w.b, w.x, q, k2, &tr, E);
     if (st != VP_OK) return st;
   } else {
     Work<double> w64;
@@ -651,7 +794,7 @@ vp_status solve(vp_plan plan, const R* q, const typename Cx<R>::T* uinc, typenam
     }
     double2* x64 = w64.r;
     k_widen_c<<<kBlocks, kThreads, 0, w64.s>>>(x64, reinterpret_cast<const float2*>(w.x), n);
-    st = residual<double, DENSITY>(plan, w64, w64.b, x64, q64, k2d, &tr, E);
+    st = residual<double, DENSITY>(plan, w64, w64.s, w64.part, w64.b, x64, q64, k2d, &tr, E);
     if (st != VP_OK) return st;
   }
   if (stats) {
@@ -675,9 +818,210 @@ vp_status solve(vp_plan plan, const R* q, const typename Cx<R>::T* uinc, typenam
   return VP_OK;
 }
 
+struct GraphHolder {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t x = nullptr;
+  cudaStream_t s = nullptr;  // synchronised before destruction
+  ~GraphHolder() {
+    if (s) cudaStreamSynchronize(s);
+    if (x) cudaGraphExecDestroy(x);
+    if (g) cudaGraphDestroy(g);
+  }
+};
+
+template <bool DENSITY>
+vp_status solve_mixed(vp_plan plan, const double* q64, const double2* uinc, double2* u, double k2d, long long n,
+                      double tol, double delta, int maxit, double* history, vp_ls_stats* stats, Err& E) {
+  const auto t_start = std::chrono::steady_clock::now();
+  PlanGuard guard{plan, vp::plan_stream(plan), vp::plan_is_fp64(plan) ? VP_FP64 : VP_FP32};
+  guard.restore_prec = true;
+  vp_status st = vp_plan_set_precision(plan, VP_FP32);
+  if (st != VP_OK) return st;
+  // FP32 recurrence: r, r^, p, v, t1 (and t0), x_lo, the FP32 workspace, state
+  Work<float> w;
+  if ((st = alloc_work<float>(w, plan, n, true, E)) != VP_OK) return st;
+  if (!DENSITY) BCG_CUDA(E, cudaMalloc(&w.t0, n * sizeof(float2)));
+  float* q32 = nullptr;
+  BCG_CUDA(E, cudaMalloc(&q32, n * sizeof(float)));
+  struct Free {
+    void* p;
+    ~Free() { cudaFree(p); }
+  } free_q32{q32};
+  // FP64 side: b, the solution x (the caller's u for the field form), t1 (and
+  // t0), the FP64 workspace
+  Work<double> w64;
+  w64.n = n;
+  if ((st = vp_plan_set_precision(plan, VP_FP64)) != VP_OK) return st;
+  BCG_CUDA(E, cudaMalloc(&w64.b, n * sizeof(double2)));
+  BCG_CUDA(E, cudaMalloc(&w64.t1, n * sizeof(double2)));
+  if (!DENSITY) {
+    BCG_CUDA(E, cudaMalloc(&w64.t0, n * sizeof(double2)));
+    w64.x = u;
+  } else {
+    BCG_CUDA(E, cudaMalloc(&w64.x_own, n * sizeof(double2)));
+    w64.x = w64.x_own;
+  }
+  w64.ws_bytes = vp::plan_apply_workspace_bytes(plan);
+  BCG_CUDA(E, cudaMalloc(&w64.ws, w64.ws_bytes));
+  BCG_CUDA(E, cudaStreamSynchronize(guard.stream));
+  if ((st = vp_plan_set_stream(plan, w.s)) != VP_OK) return st;
+
+  // FP64 right-hand side (its apply also sets up the FP64 passes before capture)
+  k_narrow_r<<<kBlocks, kThreads, 0, w.s>>>(q32, q64, n);
+  if (!DENSITY) {
+    k_qmul<double><<<kBlocks, kThreads, 0, w.s>>>(w64.t0, q64, uinc, n);
+    if ((st = apply_v<double, false>(plan, w64, uinc)) != VP_OK) return st;
+    k_rhs<double, false><<<kBlocks, kThreads, 0, w.s>>>(w64.t1, q64, k2d, w64.b, n);
+  } else {
+    if ((st = apply_v<double, true>(plan, w64, uinc)) != VP_OK) return st;
+    k_rhs<double, true><<<kBlocks, kThreads, 0, w.s>>>(uinc, q64, k2d, w64.b, n);
+  }
+  k_mixed_init<<<kBlocks, kThreads, 0, w.s>>>(w64.b, w.r, w.rh, w.p, w.v, w.x, w64.x, n, w.part);
+  BcgState init;
+  memset(&init, 0, sizeof(init));
+  init.rho = init.alpha = init.omega = make_double2(1.0, 0.0);
+  init.tol = tol;
+  init.delta2 = delta * delta;
+  init.first = 1;
+  init.mixed = 1;
+  w.host[2] = init;
+  BCG_CUDA(E, cudaMemcpyAsync(w.st, w.host + 2, sizeof(BcgState), cudaMemcpyHostToDevice, w.s));
+  k_scal_update<<<1, kScalThreads, 0, w.s>>>(w.st, w.part);
+  BCG_CUDA(E, cudaGetLastError());
+
+  // the reliable update as one graph (FP64 passes)
+  GraphHolder upd;
+  upd.s = w.s;
+  BCG_CUDA(E, cudaStreamBeginCapture(w.s, cudaStreamCaptureModeThreadLocal));
+  k_accumulate<DENSITY><<<kBlocks, kThreads, 0, w.s>>>(w64.x, w.x, q64, w64.t0, n);
+  st = apply_v<double, DENSITY>(plan, w64, w64.x);
+  k_true_residual<DENSITY><<<kBlocks, kThreads, 0, w.s>>>(w64.b, w64.x, w64.t1, q64, k2d, w.rh, w.r, n, w.part);
+  k_scal_update<<<1, kScalThreads, 0, w.s>>>(w.st, w.part);
+  cudaError_t ce = cudaStreamEndCapture(w.s, &upd.g);
+  if (st != VP_OK) return st;
+  BCG_CUDA(E, ce);
+  BCG_CUDA(E, cudaGraphInstantiate(&upd.x, upd.g, 0));
+
+  // the FP32 iteration as two graphs (an uncaptured apply first sets up the FP32 passes)
+  if ((st = vp_plan_set_precision(plan, VP_FP32)) != VP_OK) return st;
+  if ((st = apply_v<float, DENSITY>(plan, w, w.p)) != VP_OK) return st;
+  const float k2 = (float)k2d;
+  for (int k = 0; k < 2; ++k) {
+    BCG_CUDA(E, cudaStreamBeginCapture(w.s, cudaStreamCaptureModeThreadLocal));
+    vp_status cs = enqueue_iteration<float, DENSITY>(plan, w, q32, k2, k);
+    ce = cudaStreamEndCapture(w.s, &w.g[k]);
+    if (cs != VP_OK) return cs;
+    BCG_CUDA(E, ce);
+    BCG_CUDA(E, cudaGraphInstantiate(&w.gx[k], w.g[k], 0));
+  }
+  BCG_CUDA(E, cudaMemcpyAsync(w.host + 2, w.st, sizeof(BcgState), cudaMemcpyDeviceToHost, w.s));
+  BCG_CUDA(E, cudaStreamSynchronize(w.s));
+  if (history) history[0] = 1.0;
+  BcgState last = w.host[2];
+  if (!last.done) {
+    // iteration j runs while the host reads iteration j-1's state; an update
+    // requested by iteration j-1 runs after iteration j (which then does nothing)
+    int epoch = last.epoch;
+    for (int j = 1; j <= maxit + 1; ++j) {
+      if (j <= maxit) {
+        BCG_CUDA(E, cudaGraphLaunch(w.gx[j & 1], w.s));
+        BCG_CUDA(E, cudaEventRecord(w.ev[j & 1], w.s));
+      }
+      if (j >= 2) {
+        BCG_CUDA(E, cudaEventSynchronize(w.ev[(j - 1) & 1]));
+        last = w.host[(j - 1) & 1];
+        // indexed by completed iterations: the idle iteration after an update request rewrites its entry
+        if (history && last.bnorm2 > 0) history[last.iterations] = sqrt(last.rnorm2 / last.bnorm2);
+        if (last.done || last.stall >= kMaxStall) break;
+        if (last.update && last.epoch == epoch) {
+          BCG_CUDA(E, cudaGraphLaunch(upd.x, w.s));
+          ++epoch;
+        }
+      }
+    }
+    BCG_CUDA(E, cudaStreamSynchronize(w.s));
+    if (last.done != BCG_CONVERGED) {  // fold the last correction into x
+      BCG_CUDA(E, cudaGraphLaunch(upd.x, w.s));
+    }
+    BCG_CUDA(E, cudaMemcpyAsync(w.host + 2, w.st, sizeof(BcgState), cudaMemcpyDeviceToHost, w.s));
+    BCG_CUDA(E, cudaStreamSynchronize(w.s));
+    last = w.host[2];
+  }
+  if ((st = vp_plan_set_precision(plan, VP_FP64)) != VP_OK) return st;
+  if (last.done != BCG_CONVERGED) {
+    // FP32 products did not reach tol within the budget (the iteration count,
+    // a stall or a breakdown): the plain FP64 solve from the start
+    BCG_CUDA(E, cudaStreamSynchronize(w.s));
+    vp_ls_stats s64;
+    memset(&s64, 0, sizeof(s64));
+    st = solve<double, DENSITY>(plan, q64, uinc, u, k2d, n, tol, maxit, nullptr, &s64, E);
+    const auto t_end = std::chrono::steady_clock::now();
+    if (stats) {
+      stats->iterations = last.iterations + s64.iterations;
+      stats->matvecs = last.matvecs + s64.matvecs;
+      stats->restarts = last.updates;
+      stats->used_fallback = 1;
+      stats->estimated_residual = s64.estimated_residual;
+      stats->true_residual = s64.true_residual;
+      stats->seconds = std::chrono::duration<double>(t_end - t_start).count();
+    }
+    return st;
+  }
+  if (DENSITY) {  // u = V[s] in FP64
+    st = vp::apply_with_workspace(plan, w64.x, u, VP_C128, w64.ws, w64.ws_bytes);
+    if (st != VP_OK) return st;
+  }
+  BCG_CUDA(E, cudaStreamSynchronize(w.s));
+  const auto t_end = std::chrono::steady_clock::now();
+  double tr = 0.0;
+  if ((st = residual<double, DENSITY>(plan, w64, w.s, w.part, w64.b, w64.x, q64, k2d, &tr, E)) != VP_OK) return st;
+  if (stats) {
+    stats->iterations = last.iterations;
+    stats->matvecs = last.matvecs;
+    stats->restarts = last.updates;
+    stats->used_fallback = 0;
+    stats->estimated_residual = last.bnorm2 > 0 ? sqrt(last.rnorm2 / last.bnorm2) : 0.0;
+    stats->true_residual = tr;
+    stats->seconds = std::chrono::duration<double>(t_end - t_start).count();
+  }
+  return VP_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+vp_status vp_ls_bicgstab_mixed(vp_plan plan, const double* q, const void* u_inc, void* u, int form, double tol,
+                               double delta, int maxit, double* history, vp_ls_stats* stats) {
+  int d = 0, N = 0;
+  double k = 0.0;
+  if (!plan) {
+    vp::ls_set_error("plan is NULL");
+    return VP_ERR_INVALID_ARG;
+  }
+  vp_status st = vp_plan_info(plan, &d, &N, &k, nullptr, nullptr);
+  if (st != VP_OK) return st;
+  auto bad = [](const char* m) {
+    vp::ls_set_error(m);
+    return VP_ERR_INVALID_ARG;
+  };
+  if (!(k > 0)) return bad("the scattering solve needs a Helmholtz plan");
+  if (!q || !u_inc || !u) return bad("q, u_inc and u are required");
+  if (u == u_inc) return bad("u may not alias u_inc");
+  if (form != VP_LS_FIELD && form != VP_LS_DENSITY) return bad("form must be VP_LS_FIELD or VP_LS_DENSITY");
+  if (!(tol > 0) || maxit < 1) return bad("tol > 0 and maxit >= 1 required");
+  if (!(delta > 0 && delta < 1)) return bad("delta must be in (0, 1)");
+  if (!vp::plan_is_fp32(plan) && !vp::plan_is_fp64(plan)) return bad("the plan's precision must be VP_FP32 or VP_FP64");
+  const long long n = (long long)N * N * (d == 3 ? N : 1);
+  Err E;
+  cudaSetDevice(vp::plan_device(plan));
+  auto ui = reinterpret_cast<const double2*>(u_inc);
+  auto uo = reinterpret_cast<double2*>(u);
+  st = form == VP_LS_DENSITY ? solve_mixed<true>(plan, q, ui, uo, k * k, n, tol, delta, maxit, history, stats, E)
+                             : solve_mixed<false>(plan, q, ui, uo, k * k, n, tol, delta, maxit, history, stats, E);
+  if (st != VP_OK) vp::ls_set_error(E.msg.empty() ? vp_status_string(st) : E.msg.c_str());
+  return st;
+}
 
 vp_status vp_ls_bicgstab(vp_plan plan, const void* q, const void* u_inc, void* u, vp_dtype dtype, int form,
                          double tol, int maxit, double* history, vp_ls_stats* stats) {

@@ -33,12 +33,15 @@ __device__ __forceinline__ float2 to_c<float2>(double2 v) {
   return make_float2((float)v.x, (float)v.y);
 }
 
-// T(n) for an offset n (|n_j| <= N), from the octant
-__device__ __forceinline__ double2 gather(const double2* __restrict__ oct, int d, int N, int odd_axis, const int* n) {
+// T(n) for an offset n (|n_j| <= N), from the octant (D = d: the loops unroll
+// and the index arrays stay in registers)
+template <int D>
+__device__ __forceinline__ double2 gather(const double2* __restrict__ oct, int N, int odd_axis, const int (&n)[3]) {
   const long long M = N + 1;
   long long idx = 0;
   double sgn = 1.0;
-  for (int j = 0; j < d; ++j) {
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
     const int a = n[j] < 0 ? -n[j] : n[j];
     idx = idx * M + a;
     if (j == odd_axis) sgn = n[j] > 0 ? 1.0 : (n[j] < 0 ? -1.0 : 0.0);
@@ -47,16 +50,17 @@ __device__ __forceinline__ double2 gather(const double2* __restrict__ oct, int d
   return make_double2(sgn * v.x, sgn * v.y);
 }
 
-template <typename C>
-__global__ void __launch_bounds__(kThreads) k_entries(const double2* __restrict__ oct, int d, int N, int odd_axis,
+template <typename C, int D>
+__global__ void __launch_bounds__(kThreads) k_entries(const double2* __restrict__ oct, int N, int odd_axis,
                                                       const int* __restrict__ off, long long count, C* __restrict__ out,
                                                       int* __restrict__ bad) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
        i += (long long)gridDim.x * blockDim.x) {
     int n[3] = {0, 0, 0};
     bool ok = true;
-    for (int j = 0; j < d; ++j) {
-      n[j] = off[i * d + j];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      n[j] = off[i * D + j];
       ok = ok && n[j] >= -N && n[j] <= N;
     }
     if (!ok) {
@@ -64,7 +68,7 @@ __global__ void __launch_bounds__(kThreads) k_entries(const double2* __restrict_
       atomicExch(bad, 1);
       continue;
     }
-    out[i] = to_c<C>(gather(oct, d, N, odd_axis, n));
+    out[i] = to_c<C>(gather<D>(oct, N, odd_axis, n));
   }
 }
 
@@ -74,27 +78,29 @@ __global__ void __launch_bounds__(kThreads) k_entries(const double2* __restrict_
 // row of the tile (consecutive threads write consecutive entries of one row).
 constexpr int kTileRows = 16;
 
-template <typename C>
-__global__ void __launch_bounds__(kThreads) k_block(const double2* __restrict__ oct, int d, int N, int odd_axis,
+template <typename C, int D>
+__global__ void __launch_bounds__(kThreads) k_block(const double2* __restrict__ oct, int N, int odd_axis,
                                                     const long long* __restrict__ rows, long long nr,
                                                     const long long* __restrict__ cols, long long nc,
                                                     C* __restrict__ out, int* __restrict__ bad) {
   __shared__ int srow[kTileRows][3];
   __shared__ int sok[kTileRows];
-  const long long U = d == 3 ? (long long)N * N * N : (long long)N * N;
+  const long long U = D == 3 ? (long long)N * N * N : (long long)N * N;
   const long long c = blockIdx.x * (long long)kThreads + threadIdx.x;
   int q[3] = {0, 0, 0};
   bool cok = false;
   if (c < nc) {
     long long cc = cols[c];
     cok = cc >= 0 && cc < U;
-    if (cok)
-      for (int a = d - 1; a >= 0; --a) {
+    if (cok) {
+#pragma unroll
+      for (int a = D - 1; a >= 0; --a) {
         q[a] = (int)(cc % N);
         cc /= N;
       }
-    else
+    } else {
       atomicExch(bad, 1);
+    }
   }
   for (long long r0 = blockIdx.y * (long long)kTileRows; r0 < nr; r0 += (long long)gridDim.y * kTileRows) {
     __syncthreads();  // the previous tile's rows are no longer read
@@ -105,7 +111,8 @@ __global__ void __launch_bounds__(kThreads) k_block(const double2* __restrict__ 
         long long rr = rows[r];
         ok = rr >= 0 && rr < U;
         if (ok) {
-          for (int a = d - 1; a >= 0; --a) {
+#pragma unroll
+          for (int a = D - 1; a >= 0; --a) {
             srow[threadIdx.x][a] = (int)(rr % N);
             rr /= N;
           }
@@ -118,15 +125,21 @@ __global__ void __launch_bounds__(kThreads) k_block(const double2* __restrict__ 
     __syncthreads();
     if (c >= nc) continue;
     const int nrows = nr - r0 < kTileRows ? (int)(nr - r0) : kTileRows;
-    for (int i = 0; i < nrows; ++i) {
-      double2 v = make_double2(0.0, 0.0);
-      if (cok && sok[i]) {
-        int n[3];
-        for (int a = 0; a < d; ++a) n[a] = srow[i][a] - q[a];
-        v = gather(oct, d, N, odd_axis, n);
+    // all gathers of the tile in flight before the stores
+    double2 v[kTileRows];
+#pragma unroll
+    for (int i = 0; i < kTileRows; ++i) {
+      v[i] = make_double2(0.0, 0.0);
+      if (i < nrows && cok && sok[i]) {
+        int n[3] = {0, 0, 0};
+#pragma unroll
+        for (int a = 0; a < D; ++a) n[a] = srow[i][a] - q[a];
+        v[i] = gather<D>(oct, N, odd_axis, n);
       }
-      out[(r0 + i) * nc + c] = to_c<C>(v);
     }
+#pragma unroll
+    for (int i = 0; i < kTileRows; ++i)
+      if (i < nrows) out[(r0 + i) * nc + c] = to_c<C>(v[i]);
   }
 }
 
@@ -190,12 +203,20 @@ vp_status vp_kernel_entries(vp_plan plan, int which, int axis, const int* offset
   vp_plan_info(plan, &d, &N, nullptr, nullptr, nullptr);
   cudaStream_t s = vp::plan_stream(plan);
   cudaMemsetAsync(flag, 0, sizeof(int), s);
-  if (dtype == VP_C128)
-    k_entries<double2><<<grid_for(count), kThreads, 0, s>>>(oct, d, N, odd, offsets, count,
-                                                              reinterpret_cast<double2*>(out), flag);
-  else
-    k_entries<float2><<<grid_for(count), kThreads, 0, s>>>(oct, d, N, odd, offsets, count,
-                                                             reinterpret_cast<float2*>(out), flag);
+  const unsigned g = grid_for(count);
+  if (dtype == VP_C128) {
+    auto o = reinterpret_cast<double2*>(out);
+    if (d == 3)
+      k_entries<double2, 3><<<g, kThreads, 0, s>>>(oct, N, odd, offsets, count, o, flag);
+    else
+      k_entries<double2, 2><<<g, kThreads, 0, s>>>(oct, N, odd, offsets, count, o, flag);
+  } else {
+    auto o = reinterpret_cast<float2*>(out);
+    if (d == 3)
+      k_entries<float2, 3><<<g, kThreads, 0, s>>>(oct, N, odd, offsets, count, o, flag);
+    else
+      k_entries<float2, 2><<<g, kThreads, 0, s>>>(oct, N, odd, offsets, count, o, flag);
+  }
   return finish(plan, flag);
 }
 
@@ -219,12 +240,19 @@ vp_status vp_matrix_block(vp_plan plan, int which, int axis, const long long* ro
   long long gy = (152LL * 32 + gx - 1) / gx;
   gy = gy < 1 ? 1 : (gy > row_tiles ? row_tiles : (gy > 65535 ? 65535 : gy));
   const dim3 grid((unsigned)gx, (unsigned)gy);
-  if (dtype == VP_C128)
-    k_block<double2><<<grid, kThreads, 0, s>>>(oct, d, N, odd, rows, nrows, cols, ncols,
-                                               reinterpret_cast<double2*>(out), flag);
-  else
-    k_block<float2><<<grid, kThreads, 0, s>>>(oct, d, N, odd, rows, nrows, cols, ncols,
-                                              reinterpret_cast<float2*>(out), flag);
+  if (dtype == VP_C128) {
+    auto o = reinterpret_cast<double2*>(out);
+    if (d == 3)
+      k_block<double2, 3><<<grid, kThreads, 0, s>>>(oct, N, odd, rows, nrows, cols, ncols, o, flag);
+    else
+      k_block<double2, 2><<<grid, kThreads, 0, s>>>(oct, N, odd, rows, nrows, cols, ncols, o, flag);
+  } else {
+    auto o = reinterpret_cast<float2*>(out);
+    if (d == 3)
+      k_block<float2, 3><<<grid, kThreads, 0, s>>>(oct, N, odd, rows, nrows, cols, ncols, o, flag);
+    else
+      k_block<float2, 2><<<grid, kThreads, 0, s>>>(oct, N, odd, rows, nrows, cols, ncols, o, flag);
+  }
   return finish(plan, flag);
 }
 

@@ -37,6 +37,10 @@ TABLES = {
                                   (40, 2048, [256, 512, 1024]), (60, 2048, [512, 1024])]),
     "cube": (3, I.cube_bump, [(1, 384, [32, 48, 64]), (20, 384, [64, 96, 128]), (40, 384, [128, 192])]),
 }
+DELTA = 1e-2  # reliable-update threshold of the mixed-precision solver
+REF_PRECISION = "fp64"  # precision of the reference solves
+MIXED_MAXIT = 3000  # FP32 iteration budget of a mixed solve before the FP64 rerun
+
 QUICK = {
     "disk": (2, I.filtered_disk, [(1, 256, [16, 32]), (20, 256, [64, 128])]),
     "lens": (2, I.luneburg_lens, [(1, 512, [128, 256])]),
@@ -51,13 +55,16 @@ def solve(d: int, contrast, N: int, size: float, precision: str, form: str, tol:
     dev = torch.device("cuda", torch.cuda.current_device())
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    plan = vp.Plan(d, N, "helmholtz", k, 0.0, precision=precision)
+    plan = vp.Plan(d, N, "helmholtz", k, 0.0, precision="fp32" if precision == "mixed" else precision)
     torch.cuda.synchronize()
     t_pre = time.perf_counter() - t0
-    rdt, cdt = (torch.float64, torch.complex128) if precision == "fp64" else (torch.float32, torch.complex64)
+    rdt, cdt = (torch.float32, torch.complex64) if precision == "fp32" else (torch.float64, torch.complex128)
     q = torch.from_numpy(contrast(N)).to(dev, rdt)
     uinc = torch.from_numpy(I.plane_wave(N, k, d)).to(dev, cdt)
-    u, stats = vp.ls_bicgstab(plan, q, uinc, form=form, tol=tol, maxit=maxit)
+    if precision == "mixed":  # FP32 iterations, FP64 reliable updates (FP64 rerun after MIXED_MAXIT)
+        u, stats = vp.ls_bicgstab_mixed(plan, q, uinc, form=form, tol=tol, delta=DELTA, maxit=min(maxit, MIXED_MAXIT))
+    else:
+        u, stats = vp.ls_bicgstab(plan, q, uinc, form=form, tol=tol, maxit=maxit)
     plan.close()
     return u, stats, t_pre
 
@@ -81,9 +88,10 @@ def run_table(name: str, spec, precision: str, form: str, tol: float, maxit: int
     d, contrast, rows = spec
     out = []
     for size, n_ref, grids in rows:
-        u_ref, st_ref, pre_ref = solve(d, contrast, n_ref, size, "fp64", form, 1e-12, maxit)
-        rec = dict(table=name, size=size, N=n_ref, N_tot=n_ref ** d, reference=True, precision="fp64", form=form,
-                   matvecs=st_ref["matvecs"], T_solve=st_ref["seconds"], T_precomp=pre_ref,
+        u_ref, st_ref, pre_ref = solve(d, contrast, n_ref, size, REF_PRECISION, form, 1e-12, maxit)
+        rec = dict(table=name, size=size, N=n_ref, N_tot=n_ref ** d, reference=True, precision=REF_PRECISION, form=form,
+                   matvecs=st_ref["matvecs"], updates=st_ref["restarts"], fallback=st_ref["used_fallback"],
+                   T_solve=st_ref["seconds"], T_precomp=pre_ref,
                    residual=st_ref["estimated_residual"], true_residual=st_ref["true_residual"])
         out.append(rec)
         log(json.dumps(rec))
@@ -92,7 +100,8 @@ def run_table(name: str, spec, precision: str, form: str, tol: float, maxit: int
             u, st, pre = solve(d, contrast, N, size, precision, form, tol, maxit)
             e2, einf = errors(u, nested(u_ref, N))
             rec = dict(table=name, size=size, N=N, N_tot=N ** d, reference=False, precision=precision, form=form,
-                       E2=e2, Einf=einf, matvecs=st["matvecs"], T_solve=st["seconds"], T_precomp=pre,
+                       E2=e2, Einf=einf, matvecs=st["matvecs"], updates=st["restarts"],
+                       fallback=st["used_fallback"], T_solve=st["seconds"], T_precomp=pre,
                        residual=st["estimated_residual"], true_residual=st["true_residual"])
             out.append(rec)
             log(json.dumps(rec))
@@ -115,7 +124,10 @@ def markdown(rows) -> str:
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--tables", default="disk,lens,cube")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "mixed"],
+                    help="mixed: FP32 iterations with FP64 reliable updates (FP64 accuracy)")
+    ap.add_argument("--delta", type=float, default=None, help="reliable-update threshold (mixed), default 1e-2")
+    ap.add_argument("--reference-precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--form", default="density", choices=["density", "field"])
     ap.add_argument("--tol", type=float, default=None, help="default 1e-12 (fp64), 1e-6 (fp32)")
     ap.add_argument("--maxit", type=int, default=20000)
@@ -124,7 +136,10 @@ def main(argv=None):
                     help="one solve (no reference), e.g. disk:20:512; prints its stats")
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
-    tol = a.tol if a.tol is not None else (1e-12 if a.precision == "fp64" else 1e-6)
+    global DELTA, REF_PRECISION
+    DELTA = DELTA if a.delta is None else a.delta
+    REF_PRECISION = a.reference_precision
+    tol = a.tol if a.tol is not None else (1e-6 if a.precision == "fp32" else 1e-12)
     if a.single:
         name, size, N = a.single.split(":")
         d, contrast, _ = TABLES[name]

@@ -88,6 +88,8 @@ _SIGNATURES = {
                                     ctypes.POINTER(c_double)]),
     "vp_ls_bicgstab": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_double, c_int, c_void_p,
                                c_void_p]),
+    "vp_ls_bicgstab_mixed": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_double, c_double, c_int,
+                                     c_void_p, c_void_p]),
     "vp_ls_krylov_basis": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, ctypes.POINTER(c_int)]),
     "vp_ls_flexible_basis": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p,
                                      ctypes.POINTER(c_int)]),
@@ -497,6 +499,27 @@ def ls_bicgstab(plan: Plan, q, u_inc, u=None, form: str = "field", tol: float = 
     plan._sync_stream_to_torch(u_inc)
     _lscheck(lib().vp_ls_bicgstab(plan.handle, _ptr(q), _ptr(u_inc), _ptr(u), _dtype_code(u_inc), LS_FORMS[form],
                                   tol, maxit, _ptr(hist) if history else None, ctypes.byref(st)))
+    stats = {k: getattr(st, k) for k, _ in LSStats._fields_}
+    if history:
+        return u, stats, hist[:stats["iterations"] + 1]
+    return u, stats
+
+
+def ls_bicgstab_mixed(plan: Plan, q, u_inc, u=None, form: str = "field", tol: float = 1e-12, delta: float = 1e-2,
+                      maxit: int = 10000, history: bool = False):
+    """Bi-CGStab with FP32 iterations and FP64 reliable updates: FP64 accuracy
+    (complex128 u_inc/u, float64 q) at mostly FP32 cost.  Returns (u, stats) or
+    (u, stats, history); stats["restarts"] counts the FP64 updates, and
+    stats["used_fallback"] is 1 when the FP32 phase gave up (after maxit
+    iterations or a stall) and the solve was rerun in FP64."""
+    if form not in LS_FORMS:
+        raise VPError(VP_ERR_INVALID_ARG, f"form must be one of {sorted(LS_FORMS)}")
+    u = _empty_like(u_inc, u_inc.shape) if u is None else u
+    st = LSStats()
+    hist = np.zeros(maxit + 1) if history else None
+    plan._sync_stream_to_torch(u_inc)
+    _lscheck(lib().vp_ls_bicgstab_mixed(plan.handle, _ptr(q), _ptr(u_inc), _ptr(u), LS_FORMS[form], tol, delta,
+                                        maxit, _ptr(hist) if history else None, ctypes.byref(st)))
     stats = {k: getattr(st, k) for k, _ in LSStats._fields_}
     if history:
         return u, stats, hist[:stats["iterations"] + 1]

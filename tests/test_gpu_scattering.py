@@ -155,3 +155,74 @@ def test_edge_cases():
     with pytest.raises(vp.VPError):
         vp.ls_bicgstab(tc, q3, torch.zeros((128,) * 3, dtype=torch.complex64, device=DEV))
     tc.close()
+
+
+def _gpu_mixed(q, k, uinc, form, tol=1e-12, delta=1e-2, history=False):
+    d, N = q.ndim, q.shape[0]
+    plan = Plan(d, N, "helmholtz", k, 0.0, precision="fp32")
+    qd = torch.from_numpy(q).to(DEV, torch.float64)
+    ud = torch.from_numpy(uinc).to(DEV, torch.complex128)
+    out = vp.ls_bicgstab_mixed(plan, qd, ud, form=form, tol=tol, delta=delta, history=history)
+    plan.close()
+    return (out[0].cpu().numpy(),) + tuple(out[1:])
+
+
+@pytest.mark.parametrize("name,N,size", [("disk", 48, 2.0), ("lens", 48, 2.0), ("cube", 12, 1.0)])
+@pytest.mark.parametrize("form", ["field", "density"])
+def test_mixed_precision_reaches_fp64_accuracy(name, N, size, form):
+    """FP32 iterations with FP64 reliable updates reach the oracle's FP64
+    solution to 1e-10 with a true FP64 residual below 1e-12."""
+    q, k, uinc = _case(name, N, size)
+    u_ref = _oracle(name, N, size, "field")[4]
+    u, st, hist = _gpu_mixed(q, k, uinc, form, history=True)
+    assert st["estimated_residual"] < 1e-12 and st["true_residual"] < 1e-12
+    assert st["restarts"] >= 2  # FP64 updates happened
+    assert _rel2(u, u_ref) < 1e-10
+    assert hist[0] == 1.0 and len(hist) == st["iterations"] + 1
+
+
+def test_mixed_precision_full_size_matches_fp64_solver():
+    """2D N = 1024 filtered disk, 20 wavelengths: the mixed solve agrees with the
+    FP64 solve to 1e-10 in both forms."""
+    q, k, uinc = _case("disk", 1024, 20.0)
+    u64, st64 = _gpu_solve(q, k, uinc, "density", "fp64", 1e-12)
+    for form in ("density", "field"):
+        u, st = _gpu_mixed(q, k, uinc, form)
+        assert st["true_residual"] < 1e-12, form
+        assert _rel2(u, u64) < 1e-10, form
+        assert st["matvecs"] < 3 * st64["matvecs"], form
+
+
+def test_mixed_precision_edge_cases():
+    N, k = 16, 2 * np.pi
+    plan = Plan(2, N, "helmholtz", k, 0.0, precision="fp64")
+    q = torch.from_numpy(I.filtered_disk(N)).to(DEV)
+    z = torch.zeros((N, N), dtype=torch.complex128, device=DEV)
+    u, st = vp.ls_bicgstab_mixed(plan, q, z)
+    assert st["iterations"] == 0 and torch.count_nonzero(u) == 0
+    ui = torch.from_numpy(I.plane_wave(N, k, 2)).to(DEV)
+    for bad in (0.0, 1.0, -0.5):
+        with pytest.raises(vp.VPError):
+            vp.ls_bicgstab_mixed(plan, q, ui, delta=bad)
+    # the plan's precision is restored
+    u, st = vp.ls_bicgstab_mixed(plan, q, ui)
+    phi = plan.apply(ui)  # complex128 input works only if the plan is back in FP64
+    assert phi.dtype == torch.complex128 and st["true_residual"] < 1e-12
+    plan.close()
+
+
+def test_mixed_precision_fallback_mechanics():
+    """An FP32 phase that cannot finish within maxit hands over to the FP64 solve:
+    used_fallback is set and the products of both phases are counted."""
+    q, k, uinc = _case("disk", 48, 2.0)
+    plan = Plan(2, 48, "helmholtz", k, 0.0, precision="fp32")
+    qd = torch.from_numpy(q).to(DEV)
+    ud = torch.from_numpy(uinc).to(DEV)
+    u, st = vp.ls_bicgstab_mixed(plan, qd, ud, tol=1e-12, maxit=3)
+    assert st["used_fallback"] == 1
+    assert st["iterations"] == 6 and st["matvecs"] == 12
+    # an update after every iteration that gains little stalls the FP32 phase
+    # early; the FP64 rerun still converges
+    u, st = vp.ls_bicgstab_mixed(plan, qd, ud, tol=1e-12, maxit=60, delta=0.999999)
+    assert st["true_residual"] < 1e-12
+    plan.close()

@@ -266,3 +266,72 @@ def bf16_round(x: np.ndarray) -> np.ndarray:
     u = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
     u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
     return u.astype(np.uint32).view(np.float32)
+
+
+# ---------------------------------------------------------------------------
+# Variable-coefficient Poisson (Section 5.2): a synthetic molecule standing in
+# for the paper's 1235-atom protein (whose coordinates are not available)
+# ---------------------------------------------------------------------------
+
+PB_ATOMS = 1235
+PB_RADIUS = 0.022  # van der Waals radius R_i of every atom
+PB_MU2 = 2.0  # mu^2
+PB_EPS_IN, PB_EPS_OUT = 2.0, 4.0
+PB_BALL = 0.2  # atom centres uniform in the ball |x| < 0.2
+PB_CUTOFF = 6.0  # alpha_i is taken as 0 beyond r = 6 mu R (exp(-36) = 2.3e-16)
+
+
+def pb_molecule(seed: int = BASE_SEED + 7000, M: int = PB_ATOMS):
+    """M atom centres uniform in a ball of radius 0.2 (splitmix64 rejection
+    sampling) and charges uniform in [-1, 1]: (centres (M, 3), charges (M,))."""
+    out = []
+    off = 0
+    while len(out) < M:
+        u = uniform(seed, 3 * 4096, off) * 2 - 1
+        off += 3 * 4096
+        c = u.reshape(-1, 3) * PB_BALL
+        out.extend(c[np.sum(c * c, axis=1) < PB_BALL ** 2])
+    centres = np.array(out[:M])
+    charges = uniform(seed + 1, M) * 2 - 1
+    return centres, charges
+
+
+def pb_fields(mol, N: int, device="cpu", dtype=None, eps_in: float = PB_EPS_IN, eps_out: float = PB_EPS_OUT):
+    """The smooth dielectric of Section 5.2 on the N^3 grid: alpha_i =
+    exp(-r_i^2/(mu^2 R^2)) (cut off at r = 6 mu R), q = 1 - prod_i (1 - alpha_i),
+    eps = q eps_in + (1 - q) eps_out; its exact gradient, and the charge density
+    rho = sum_i c_i alpha_i.  Returns torch tensors (eps (N,N,N), grad_eps
+    (3,N,N,N), rho (N,N,N)) on `device` (float64 by default).  The product and
+    its gradient are accumulated atom by atom over each atom's box:
+    P <- P (1 - alpha), G <- G (1 - alpha) - P grad(alpha)."""
+    import torch
+    dt = torch.float64 if dtype is None else dtype
+    x = torch.tensor(grid_coords(N), dtype=dt, device=device)
+    h = 1.0 / N
+    w2 = PB_MU2 * PB_RADIUS ** 2
+    rc = PB_CUTOFF * np.sqrt(w2)
+    P = torch.ones((N, N, N), dtype=dt, device=device)
+    G = torch.zeros((3, N, N, N), dtype=dt, device=device)
+    rho = torch.zeros((N, N, N), dtype=dt, device=device)
+    centres, charges = mol
+    lo_idx = lambda c: max(0, int(np.ceil((c - rc) / h + N // 2 - 1)))
+    hi_idx = lambda c: min(N, int(np.floor((c + rc) / h + N // 2 - 1)) + 1)
+    for (cx, cy, cz), ch in zip(centres, charges):
+        sl = [slice(lo_idx(c), hi_idx(c)) for c in (cx, cy, cz)]
+        if any(s.stop <= s.start for s in sl):
+            continue
+        dx = (x[sl[0]] - cx).view(-1, 1, 1)
+        dy = (x[sl[1]] - cy).view(1, -1, 1)
+        dz = (x[sl[2]] - cz).view(1, 1, -1)
+        r2 = dx * dx + dy * dy + dz * dz
+        a = torch.where(r2 <= rc * rc, torch.exp(-r2 / w2), torch.zeros_like(r2))
+        Pb = P[sl[0], sl[1], sl[2]]
+        for j, dj in enumerate((dx, dy, dz)):
+            ga = -2.0 * dj / w2 * a  # d alpha / d x_j
+            G[j, sl[0], sl[1], sl[2]] = G[j, sl[0], sl[1], sl[2]] * (1 - a) - Pb * ga
+        P[sl[0], sl[1], sl[2]] = Pb * (1 - a)
+        rho[sl[0], sl[1], sl[2]] += float(ch) * a
+    q = 1 - P
+    eps = q * eps_in + (1 - q) * eps_out
+    grad_eps = (eps_in - eps_out) * (-G)  # grad q = -grad P
+    return eps, grad_eps, rho

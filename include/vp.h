@@ -342,6 +342,23 @@ vp_status vp_ls_bicgstab(vp_plan plan, const void* q, const void* u_inc, void* u
  * recurrence residual ||r_j|| / ||b|| after iteration j. */
 vp_status vp_ls_bicgstab_mixed(vp_plan plan, const double* q, const void* u_inc, void* u, int form, double tol,
                                double delta, int maxit, double* history, vp_ls_stats* stats);
+/* Variable-coefficient Poisson (linearised Poisson-Boltzmann with lambda = 0,
+ * Section 5.2): div(eps grad phi) = rho with phi = V[sigma], V the Laplace
+ * volume potential, gives the second-kind equation (eq. pbeq)
+ *     -eps sigma + grad(eps) . grad V[sigma] = rho,
+ * whose operator products use the exact-gradient apply (Section 3).  Solved
+ * with the Bi-CGStab iteration of vp_ls_bicgstab (the paper uses GMRES).
+ *   plan: 2D or 3D Laplace plan (derivative multipliers built on first use)
+ *   eps: N^d reals; grad_eps: d blocks of N^d reals (d eps / d x_j); rho,
+ *   sigma: N^d complex (real data: zero imaginary parts); device pointers.
+ *   vp_pb_solve: dtype VP_C64 (float eps, FP32 plan) or VP_C128 (double, FP64);
+ *   vp_pb_solve_mixed: FP64 data, FP32 iterations with FP64 reliable updates
+ *   (as vp_ls_bicgstab_mixed).  The potential is phi = V[sigma] (vp_apply).
+ * tol, maxit, history, stats and errors as for vp_ls_bicgstab. */
+vp_status vp_pb_solve(vp_plan plan, const void* eps, const void* grad_eps, const void* rho, void* sigma,
+                      vp_dtype dtype, double tol, int maxit, double* history, vp_ls_stats* stats);
+vp_status vp_pb_solve_mixed(vp_plan plan, const double* eps, const double* grad_eps, const void* rho, void* sigma,
+                            double tol, double delta, int maxit, double* history, vp_ls_stats* stats);
 const char* vp_ls_last_error(void);
 
 /* ---------------------------------------------------------------------------

@@ -153,20 +153,63 @@ __global__ void __launch_bounds__(kThreads) k_qmul(typename Cx<R>::T* __restrict
   }
 }
 
-// b = k^2 src (field: src = V[q u_inc]) or k^2 q src (density: src = u_inc);
-// r = r^ = b; x = p = v = 0; partials (<r^, r>, ||r||^2) = (||b||^2, ||b||^2)
-template <typename R, bool DENSITY>
-__global__ void __launch_bounds__(kThreads) k_start(const typename Cx<R>::T* __restrict__ src, const R* __restrict__ q,
-                                                    R k2, typename Cx<R>::T* __restrict__ b,
+// The operator M of each form, applied at node i given t1 = the apply's
+// output (V[q x] for the field form, V[x] for the density form, the d
+// components of grad V[x] for the Poisson-Boltzmann form, d blocks of n):
+//   field:    M x = x - k^2 V[q x]
+//   density:  M x = x - k^2 q V[x]
+//   pb:       M x = -eps x + grad(eps) . grad V[x]        (Section 5.2, eq. pbeq)
+enum { F_FIELD = 0, F_DENSITY = 1, F_PB = 2 };
+
+template <typename R>
+struct OpArgs {
+  const R* q;   // contrast q, or eps for the Poisson-Boltzmann form
+  const R* ge;  // grad eps (d blocks of n), Poisson-Boltzmann form only
+  R k2;
+  int d;
+  long long n;
+};
+
+template <typename R, int FORM>
+__device__ __forceinline__ typename Cx<R>::T op_at(const typename Cx<R>::T xv, const typename Cx<R>::T* __restrict__ t1,
+                                                   const OpArgs<R>& a, long long i) {
+  using C = typename Cx<R>::T;
+  if (FORM == F_PB) {
+    const R e = a.q[i];
+    C acc = {-e * xv.x, -e * xv.y};
+    for (int j = 0; j < a.d; ++j) {
+      const R g = a.ge[j * a.n + i];
+      const C tj = t1[j * a.n + i];
+      acc.x += g * tj.x;
+      acc.y += g * tj.y;
+    }
+    return acc;
+  }
+  const R f = FORM == F_DENSITY ? a.k2 * a.q[i] : a.k2;
+  const C tv = t1[i];
+  return {xv.x - f * tv.x, xv.y - f * tv.y};
+}
+
+// the right-hand side: k^2 src (field, src = V[q u_inc]), k^2 q src (density,
+// src = u_inc), src (Poisson-Boltzmann, src = rho)
+template <typename R, int FORM>
+__device__ __forceinline__ typename Cx<R>::T rhs_at(const typename Cx<R>::T sv, const OpArgs<R>& a, long long i) {
+  if (FORM == F_PB) return sv;
+  const R f = FORM == F_DENSITY ? a.k2 * a.q[i] : a.k2;
+  return {f * sv.x, f * sv.y};
+}
+
+// b from src; r = r^ = b; x = p = v = 0; partials (<r^, r>, ||r||^2) = (||b||^2, ||b||^2)
+template <typename R, int FORM>
+__global__ void __launch_bounds__(kThreads) k_start(const typename Cx<R>::T* __restrict__ src, OpArgs<R> a,
+                                                    typename Cx<R>::T* __restrict__ b,
                                                     typename Cx<R>::T* __restrict__ r, typename Cx<R>::T* __restrict__ rh,
                                                     typename Cx<R>::T* __restrict__ x, typename Cx<R>::T* __restrict__ p,
-                                                    typename Cx<R>::T* __restrict__ v, long long n,
-                                                    double2* __restrict__ part) {
+                                                    typename Cx<R>::T* __restrict__ v, double2* __restrict__ part) {
   using C = typename Cx<R>::T;
   R acc = 0;
-  GRID_LOOP(i, n) {
-    const R f = DENSITY ? k2 * q[i] : k2;
-    const C bi = {f * src[i].x, f * src[i].y};
+  GRID_LOOP(i, a.n) {
+    const C bi = rhs_at<R, FORM>(src[i], a, i);
     b[i] = bi;
     r[i] = bi;
     rh[i] = bi;
@@ -179,51 +222,46 @@ __global__ void __launch_bounds__(kThreads) k_start(const typename Cx<R>::T* __r
   block_partials<2>(re, im, part);
 }
 
-// b = k^2 src (field) or k^2 q src (density)
-template <typename R, bool DENSITY>
-__global__ void __launch_bounds__(kThreads) k_rhs(const typename Cx<R>::T* __restrict__ src, const R* __restrict__ q,
-                                                  R k2, typename Cx<R>::T* __restrict__ b, long long n) {
-  GRID_LOOP(i, n) {
-    const R f = DENSITY ? k2 * q[i] : k2;
-    b[i] = {f * src[i].x, f * src[i].y};
-  }
+// b from src only
+template <typename R, int FORM>
+__global__ void __launch_bounds__(kThreads) k_rhs(const typename Cx<R>::T* __restrict__ src, OpArgs<R> a,
+                                                  typename Cx<R>::T* __restrict__ b) {
+  GRID_LOOP(i, a.n) b[i] = rhs_at<R, FORM>(src[i], a, i);
 }
 
 // p = r + beta (p - omega v); t0 = q p (field form)
-template <typename R, bool DENSITY>
+template <typename R, int FORM>
 __global__ void __launch_bounds__(kThreads) k_p(const BcgState* __restrict__ st, typename Cx<R>::T* __restrict__ p,
                                                 const typename Cx<R>::T* __restrict__ r,
-                                                const typename Cx<R>::T* __restrict__ v, const R* __restrict__ q,
-                                                typename Cx<R>::T* __restrict__ t0, long long n) {
+                                                const typename Cx<R>::T* __restrict__ v, OpArgs<R> a,
+                                                typename Cx<R>::T* __restrict__ t0) {
   using C = typename Cx<R>::T;
   if (idle(st)) return;
   const R br = (R)st->beta.x, bi = (R)st->beta.y, wr = (R)st->omega.x, wi = (R)st->omega.y;
-  GRID_LOOP(i, n) {
+  GRID_LOOP(i, a.n) {
     const C pv = p[i], vv = v[i], rv = r[i];
     const R dx = pv.x - (wr * vv.x - wi * vv.y), dy = pv.y - (wr * vv.y + wi * vv.x);
     const C np = {rv.x + br * dx - bi * dy, rv.y + br * dy + bi * dx};
     p[i] = np;
-    if (!DENSITY) {
-      const R qi = q[i];
+    if (FORM == F_FIELD) {
+      const R qi = a.q[i];
       t0[i] = {qi * np.x, qi * np.y};
     }
   }
 }
 
-// v = p - k^2 t1 (field) or p - k^2 q t1 (density); partial <r^, v>
-template <typename R, bool DENSITY>
+// v = M p; partial <r^, v>
+template <typename R, int FORM>
 __global__ void __launch_bounds__(kThreads) k_v(const BcgState* __restrict__ st, typename Cx<R>::T* __restrict__ v,
                                                 const typename Cx<R>::T* __restrict__ p,
-                                                const typename Cx<R>::T* __restrict__ t1, const R* __restrict__ q,
-                                                const typename Cx<R>::T* __restrict__ rh, R k2, long long n,
-                                                double2* __restrict__ part) {
+                                                const typename Cx<R>::T* __restrict__ t1, OpArgs<R> a,
+                                                const typename Cx<R>::T* __restrict__ rh, double2* __restrict__ part) {
   using C = typename Cx<R>::T;
   if (idle(st)) return;
   R ar = 0, ai = 0;
-  GRID_LOOP(i, n) {
-    const R f = DENSITY ? k2 * q[i] : k2;
-    const C tv = t1[i], pv = p[i], h = rh[i];
-    const C vv = {pv.x - f * tv.x, pv.y - f * tv.y};
+  GRID_LOOP(i, a.n) {
+    const C vv = op_at<R, FORM>(p[i], t1, a, i);
+    const C h = rh[i];
     v[i] = vv;
     ar += h.x * vv.x + h.y * vv.y;
     ai += h.x * vv.y - h.y * vv.x;
@@ -233,24 +271,23 @@ __global__ void __launch_bounds__(kThreads) k_v(const BcgState* __restrict__ st,
 }
 
 // s = r - alpha v (written over r); x += alpha p; t0 = q s (field form); partial ||s||^2
-template <typename R, bool DENSITY>
+template <typename R, int FORM>
 __global__ void __launch_bounds__(kThreads) k_s(const BcgState* __restrict__ st, typename Cx<R>::T* __restrict__ r,
                                                 const typename Cx<R>::T* __restrict__ v,
                                                 typename Cx<R>::T* __restrict__ x,
-                                                const typename Cx<R>::T* __restrict__ p, const R* __restrict__ q,
-                                                typename Cx<R>::T* __restrict__ t0, long long n,
-                                                double2* __restrict__ part) {
+                                                const typename Cx<R>::T* __restrict__ p, OpArgs<R> a,
+                                                typename Cx<R>::T* __restrict__ t0, double2* __restrict__ part) {
   using C = typename Cx<R>::T;
   if (idle(st)) return;
   const R ar = (R)st->alpha.x, ai = (R)st->alpha.y;
   R acc = 0;
-  GRID_LOOP(i, n) {
+  GRID_LOOP(i, a.n) {
     const C rv = r[i], vv = v[i], pv = p[i], xv = x[i];
     const C s = {rv.x - (ar * vv.x - ai * vv.y), rv.y - (ar * vv.y + ai * vv.x)};
     r[i] = s;
     x[i] = {xv.x + ar * pv.x - ai * pv.y, xv.y + ar * pv.y + ai * pv.x};
-    if (!DENSITY) {
-      const R qi = q[i];
+    if (FORM == F_FIELD) {
+      const R qi = a.q[i];
       t0[i] = {qi * s.x, qi * s.y};
     }
     acc += s.x * s.x + s.y * s.y;
@@ -259,19 +296,17 @@ __global__ void __launch_bounds__(kThreads) k_s(const BcgState* __restrict__ st,
   block_partials<1>(re, im, part);
 }
 
-// t = s - k^2 t1 (field) or s - k^2 q t1 (density), written over t1;
-// partials <t, s>, <t, t>
-template <typename R, bool DENSITY>
+// t = M s, written over the first n entries of t1; partials <t, s>, <t, t>
+template <typename R, int FORM>
 __global__ void __launch_bounds__(kThreads) k_t(const BcgState* __restrict__ st, typename Cx<R>::T* __restrict__ t1,
-                                                const typename Cx<R>::T* __restrict__ s, const R* __restrict__ q, R k2,
-                                                long long n, double2* __restrict__ part) {
+                                                const typename Cx<R>::T* __restrict__ s, OpArgs<R> a,
+                                                double2* __restrict__ part) {
   using C = typename Cx<R>::T;
   if (idle(st)) return;
   R tsr = 0, tsi = 0, tt = 0;
-  GRID_LOOP(i, n) {
-    const R f = DENSITY ? k2 * q[i] : k2;
-    const C tv = t1[i], sv = s[i];
-    const C t = {sv.x - f * tv.x, sv.y - f * tv.y};
+  GRID_LOOP(i, a.n) {
+    const C sv = s[i];
+    const C t = op_at<R, FORM>(sv, t1, a, i);  // reads every component of t1 at i before the write
     t1[i] = t;
     tsr += t.x * sv.x + t.y * sv.y;
     tsi += t.x * sv.y - t.y * sv.x;
@@ -305,19 +340,18 @@ __global__ void __launch_bounds__(kThreads) k_xr(const BcgState* __restrict__ st
   block_partials<2>(re, im, part);
 }
 
-// partials of ||b - M x||^2 and ||b||^2 from t1 = V[q x] (field) or V[x] (density)
-template <typename R, bool DENSITY>
+// partials of ||b - M x||^2 and ||b||^2 (t1: the apply of x's operand)
+template <typename R, int FORM>
 __global__ void __launch_bounds__(kThreads) k_resid(const typename Cx<R>::T* __restrict__ b,
                                                     const typename Cx<R>::T* __restrict__ x,
-                                                    const typename Cx<R>::T* __restrict__ t1, const R* __restrict__ q,
-                                                    R k2, long long n, double2* __restrict__ part) {
+                                                    const typename Cx<R>::T* __restrict__ t1, OpArgs<R> a,
+                                                    double2* __restrict__ part) {
   using C = typename Cx<R>::T;
   double rr = 0.0, bb = 0.0;
-  GRID_LOOP(i, n) {
-    const R f = DENSITY ? k2 * q[i] : k2;
-    const C bv = b[i], xv = x[i], tv = t1[i];
-    const double ex = (double)bv.x - ((double)xv.x - (double)f * tv.x);
-    const double ey = (double)bv.y - ((double)xv.y - (double)f * tv.y);
+  GRID_LOOP(i, a.n) {
+    const C bv = b[i];
+    const C mx = op_at<R, FORM>(x[i], t1, a, i);
+    const double ex = (double)bv.x - (double)mx.x, ey = (double)bv.y - (double)mx.y;
     rr += ex * ex + ey * ey;
     bb += (double)bv.x * bv.x + (double)bv.y * bv.y;
   }
@@ -464,7 +498,7 @@ __global__ void __launch_bounds__(kThreads) k_mixed_init(const double2* __restri
 }
 
 // x += x_lo, x_lo = 0; t0 = q x for the field form's FP64 product
-template <bool DENSITY>
+template <int FORM>
 __global__ void __launch_bounds__(kThreads) k_accumulate(double2* __restrict__ x, float2* __restrict__ xlo,
                                                          const double* __restrict__ q, double2* __restrict__ t0,
                                                          long long n) {
@@ -473,28 +507,27 @@ __global__ void __launch_bounds__(kThreads) k_accumulate(double2* __restrict__ x
     const double2 xv = make_double2(x[i].x + d.x, x[i].y + d.y);
     x[i] = xv;
     xlo[i] = make_float2(0.f, 0.f);
-    if (!DENSITY) {
+    if (FORM == F_FIELD) {
       const double qi = q[i];
       t0[i] = make_double2(qi * xv.x, qi * xv.y);
     }
   }
 }
 
-// true residual r = b - (x - k^2 (q) t1) in FP64 (t1 = V[q x] or V[x]), its
+// true residual r = b - M x in FP64 (t1: the FP64 apply of x's operand), its
 // FP32 copy for the recurrence; partials (<r^, r>, ||r||^2 in FP64)
-template <bool DENSITY>
+template <int FORM>
 __global__ void __launch_bounds__(kThreads) k_true_residual(const double2* __restrict__ b,
                                                             const double2* __restrict__ x,
-                                                            const double2* __restrict__ t1,
-                                                            const double* __restrict__ q, double k2,
+                                                            const double2* __restrict__ t1, OpArgs<double> a,
                                                             const float2* __restrict__ rh, float2* __restrict__ r,
-                                                            long long n, double2* __restrict__ part) {
+                                                            double2* __restrict__ part) {
   float hr = 0.f, hi = 0.f;
   double nn = 0.0;
-  GRID_LOOP(i, n) {
-    const double f = DENSITY ? k2 * q[i] : k2;
-    const double2 bv = b[i], xv = x[i], tv = t1[i];
-    const double ex = bv.x - (xv.x - f * tv.x), ey = bv.y - (xv.y - f * tv.y);
+  GRID_LOOP(i, a.n) {
+    const double2 bv = b[i];
+    const double2 mx = op_at<double, FORM>(x[i], t1, a, i);
+    const double ex = bv.x - mx.x, ey = bv.y - mx.y;
     const float2 rv = make_float2((float)ex, (float)ey);
     r[i] = rv;
     const float2 h = rh[i];
@@ -624,28 +657,29 @@ vp_dtype cdtype() {
   return sizeof(R) == 8 ? VP_C128 : VP_C64;
 }
 
-// one operator product's apply of V: field form V[t0], density form V[in]
-template <typename R, bool DENSITY>
+// one operator product's apply: V[t0] (field), V[in] (density), grad V[in]
+// (Poisson-Boltzmann: d fields into t1)
+template <typename R, int FORM>
 vp_status apply_v(vp_plan plan, Work<R>& w, const typename Cx<R>::T* in) {
-  return vp::apply_with_workspace(plan, DENSITY ? (const void*)in : (const void*)w.t0, w.t1, cdtype<R>(), w.ws,
-                                  w.ws_bytes);
+  if (FORM == F_PB) return vp::apply_grad_with_workspace(plan, in, w.t1, cdtype<R>(), w.ws, w.ws_bytes);
+  return vp::apply_with_workspace(plan, FORM == F_DENSITY ? (const void*)in : (const void*)w.t0, w.t1, cdtype<R>(),
+                                  w.ws, w.ws_bytes);
 }
 
 // one iteration on w.s, its state copied to host slot `slot`
-template <typename R, bool DENSITY>
-vp_status enqueue_iteration(vp_plan plan, Work<R>& w, const R* q, R k2, int slot) {
-  const long long n = w.n;
-  k_p<R, DENSITY><<<kBlocks, kThreads, 0, w.s>>>(w.st, w.p, w.r, w.v, q, w.t0, n);
-  vp_status st = apply_v<R, DENSITY>(plan, w, w.p);
+template <typename R, int FORM>
+vp_status enqueue_iteration(vp_plan plan, Work<R>& w, const OpArgs<R>& a, int slot) {
+  k_p<R, FORM><<<kBlocks, kThreads, 0, w.s>>>(w.st, w.p, w.r, w.v, a, w.t0);
+  vp_status st = apply_v<R, FORM>(plan, w, w.p);
   if (st != VP_OK) return st;
-  k_v<R, DENSITY><<<kBlocks, kThreads, 0, w.s>>>(w.st, w.v, w.p, w.t1, q, w.rh, k2, n, w.part);
+  k_v<R, FORM><<<kBlocks, kThreads, 0, w.s>>>(w.st, w.v, w.p, w.t1, a, w.rh, w.part);
   k_scal_alpha<<<1, kScalThreads, 0, w.s>>>(w.st, w.part);
-  k_s<R, DENSITY><<<kBlocks, kThreads, 0, w.s>>>(w.st, w.r, w.v, w.x, w.p, q, w.t0, n, w.part);
+  k_s<R, FORM><<<kBlocks, kThreads, 0, w.s>>>(w.st, w.r, w.v, w.x, w.p, a, w.t0, w.part);
   k_scal_s<<<1, kScalThreads, 0, w.s>>>(w.st, w.part);
-  if ((st = apply_v<R, DENSITY>(plan, w, w.r)) != VP_OK) return st;
-  k_t<R, DENSITY><<<kBlocks, kThreads, 0, w.s>>>(w.st, w.t1, w.r, q, k2, n, w.part);
+  if ((st = apply_v<R, FORM>(plan, w, w.r)) != VP_OK) return st;
+  k_t<R, FORM><<<kBlocks, kThreads, 0, w.s>>>(w.st, w.t1, w.r, a, w.part);
   k_scal_omega<<<1, kScalThreads, 0, w.s>>>(w.st, w.part);
-  k_xr<R><<<kBlocks, kThreads, 0, w.s>>>(w.st, w.x, w.r, w.t1, w.rh, n, w.part);
+  k_xr<R><<<kBlocks, kThreads, 0, w.s>>>(w.st, w.x, w.r, w.t1, w.rh, a.n, w.part);
   k_scal_rho<<<1, kScalThreads, 0, w.s>>>(w.st, w.part);
   if (cudaMemcpyAsync(w.host + slot, w.st, sizeof(BcgState), cudaMemcpyDeviceToHost, w.s) != cudaSuccess)
     return VP_ERR_CUDA;
@@ -654,14 +688,13 @@ vp_status enqueue_iteration(vp_plan plan, Work<R>& w, const R* q, R k2, int slot
 
 // ||b - M x|| / ||b|| with the operator of this precision (w.t0/w.t1 as scratch,
 // the plan's stream s, partials in part)
-template <typename R, bool DENSITY>
+template <typename R, int FORM>
 vp_status residual(vp_plan plan, Work<R>& w, cudaStream_t s, double2* part, const typename Cx<R>::T* b,
-                   const typename Cx<R>::T* x, const R* q, R k2, double* out, Err& E) {
-  const long long n = w.n;
-  if (!DENSITY) k_qmul<R><<<kBlocks, kThreads, 0, s>>>(w.t0, q, x, n);
-  vp_status st = apply_v<R, DENSITY>(plan, w, x);
+                   const typename Cx<R>::T* x, const OpArgs<R>& a, double* out, Err& E) {
+  if (FORM == F_FIELD) k_qmul<R><<<kBlocks, kThreads, 0, s>>>(w.t0, a.q, x, a.n);
+  vp_status st = apply_v<R, FORM>(plan, w, x);
   if (st != VP_OK) return st;
-  k_resid<R, DENSITY><<<kBlocks, kThreads, 0, s>>>(b, x, w.t1, q, k2, n, part);
+  k_resid<R, FORM><<<kBlocks, kThreads, 0, s>>>(b, x, w.t1, a, part);
   double2 h[2 * kBlocks];
   BCG_CUDA(E, cudaMemcpyAsync(h, part, sizeof(h), cudaMemcpyDeviceToHost, s));
   BCG_CUDA(E, cudaStreamSynchronize(s));
@@ -674,20 +707,27 @@ vp_status residual(vp_plan plan, Work<R>& w, cudaStream_t s, double2* part, cons
   return VP_OK;
 }
 
+// the apply workspace of the form (the Poisson-Boltzmann form takes d gradient fields)
+size_t form_workspace_bytes(vp_plan plan, int form) {
+  return form == F_PB ? vp::plan_grad_workspace_bytes(plan) : vp::plan_apply_workspace_bytes(plan);
+}
+
+// vectors of one recurrence; x_own only when the iterate is not the caller's u
 template <typename R>
-vp_status alloc_work(Work<R>& w, vp_plan plan, long long n, bool density, Err& E) {
+vp_status alloc_work(Work<R>& w, vp_plan plan, long long n, int form, int d, bool own_x, Err& E) {
   using C = typename Cx<R>::T;
   w.n = n;
   BCG_CUDA(E, cudaStreamCreateWithFlags(&w.s, cudaStreamNonBlocking));
   for (int i = 0; i < 2; ++i) BCG_CUDA(E, cudaEventCreateWithFlags(&w.ev[i], cudaEventDisableTiming));
-  C** vecs[] = {&w.b, &w.r, &w.rh, &w.p, &w.v, &w.t1};
+  C** vecs[] = {&w.b, &w.r, &w.rh, &w.p, &w.v};
   for (C** pp : vecs) BCG_CUDA(E, cudaMalloc(pp, n * sizeof(C)));
-  if (!density) BCG_CUDA(E, cudaMalloc(&w.t0, n * sizeof(C)));
-  if (density) {
+  BCG_CUDA(E, cudaMalloc(&w.t1, (form == F_PB ? d : 1) * n * sizeof(C)));
+  if (form == F_FIELD) BCG_CUDA(E, cudaMalloc(&w.t0, n * sizeof(C)));
+  if (own_x) {
     BCG_CUDA(E, cudaMalloc(&w.x_own, n * sizeof(C)));
     w.x = w.x_own;
   }
-  w.ws_bytes = vp::plan_apply_workspace_bytes(plan);
+  w.ws_bytes = form_workspace_bytes(plan, form);
   BCG_CUDA(E, cudaMalloc(&w.ws, w.ws_bytes));
   BCG_CUDA(E, cudaMalloc(&w.part, 2 * kBlocks * sizeof(double2)));
   BCG_CUDA(E, cudaMalloc(&w.st, sizeof(BcgState)));
@@ -695,28 +735,29 @@ vp_status alloc_work(Work<R>& w, vp_plan plan, long long n, bool density, Err& E
   return VP_OK;
 }
 
-template <typename R, bool DENSITY>
-vp_status solve(vp_plan plan, const R* q, const typename Cx<R>::T* uinc, typename Cx<R>::T* u, double k2d,
-                long long n, double tol, int maxit, double* history, vp_ls_stats* stats, Err& E) {
-  using C = typename Cx<R>::T;
+// The solve in one precision R.  src: u_inc (field, density) or rho (PB);
+// q: contrast or eps; ge: grad eps (PB).  u: the scattered field or sigma.
+template <typename R, int FORM>
+vp_status solve(vp_plan plan, const R* q, const R* ge, const typename Cx<R>::T* src, typename Cx<R>::T* u,
+                double k2d, int d, long long n, double tol, int maxit, double* history, vp_ls_stats* stats, Err& E) {
   const auto t_start = std::chrono::steady_clock::now();
   Work<R> w;
-  vp_status st = alloc_work<R>(w, plan, n, DENSITY, E);
+  vp_status st = alloc_work<R>(w, plan, n, FORM, d, FORM == F_DENSITY, E);
   if (st != VP_OK) return st;
-  if (!DENSITY) w.x = u;  // the field form iterates on u itself
-  const R k2 = (R)k2d;
+  if (FORM != F_DENSITY) w.x = u;  // the field and PB forms iterate on u itself
+  const OpArgs<R> a{q, ge, (R)k2d, d, n};
   PlanGuard guard{plan, vp::plan_stream(plan), VP_FP32};
   BCG_CUDA(E, cudaStreamSynchronize(guard.stream));  // inputs produced on the plan's stream
   if ((st = vp_plan_set_stream(plan, w.s)) != VP_OK) return st;
 
   // right-hand side (an uncaptured apply also sets up every pass kernel before capture)
-  if (!DENSITY) {
-    k_qmul<R><<<kBlocks, kThreads, 0, w.s>>>(w.t0, q, uinc, n);
-    if ((st = apply_v<R, false>(plan, w, uinc)) != VP_OK) return st;
-    k_start<R, false><<<kBlocks, kThreads, 0, w.s>>>(w.t1, q, k2, w.b, w.r, w.rh, w.x, w.p, w.v, n, w.part);
+  if (FORM == F_FIELD) {
+    k_qmul<R><<<kBlocks, kThreads, 0, w.s>>>(w.t0, q, src, n);
+    if ((st = apply_v<R, FORM>(plan, w, src)) != VP_OK) return st;
+    k_start<R, FORM><<<kBlocks, kThreads, 0, w.s>>>(w.t1, a, w.b, w.r, w.rh, w.x, w.p, w.v, w.part);
   } else {
-    if ((st = apply_v<R, true>(plan, w, uinc)) != VP_OK) return st;
-    k_start<R, true><<<kBlocks, kThreads, 0, w.s>>>(uinc, q, k2, w.b, w.r, w.rh, w.x, w.p, w.v, n, w.part);
+    if ((st = apply_v<R, FORM>(plan, w, src)) != VP_OK) return st;
+    k_start<R, FORM><<<kBlocks, kThreads, 0, w.s>>>(src, a, w.b, w.r, w.rh, w.x, w.p, w.v, w.part);
   }
   BcgState init;
   memset(&init, 0, sizeof(init));
@@ -736,7 +777,7 @@ vp_status solve(vp_plan plan, const R* q, const typename Cx<R>::T* uinc, typenam
     // the iteration as two graphs (state copied to host slot 0 or 1)
     for (int k = 0; k < 2; ++k) {
       BCG_CUDA(E, cudaStreamBeginCapture(w.s, cudaStreamCaptureModeThreadLocal));
-      vp_status cs = enqueue_iteration<R, DENSITY>(plan, w, q, k2, k);
+      vp_status cs = enqueue_iteration<R, FORM>(plan, w, a, k);
       cudaError_t ce = cudaStreamEndCapture(w.s, &w.g[k]);
       if (cs != VP_OK) return cs;
       BCG_CUDA(E, ce);
@@ -758,7 +799,7 @@ vp_status solve(vp_plan plan, const R* q, const typename Cx<R>::T* uinc, typenam
     }
     BCG_CUDA(E, cudaStreamSynchronize(w.s));
   }
-  if (DENSITY) {  // u = V[s]
+  if (FORM == F_DENSITY) {  // u = V[s]
     BCG_CUDA(E, cudaGetLastError());
     st = vp::apply_with_workspace(plan, w.x, u, cdtype<R>(), w.ws, w.ws_bytes);
     if (st != VP_OK) return st;
@@ -769,32 +810,42 @@ vp_status solve(vp_plan plan, const R* q, const typename Cx<R>::T* uinc, typenam
   // true residual ||b - M x|| / ||b||, the operator and b evaluated in FP64
   double tr = 0.0;
   if constexpr (sizeof(R) == 8) {
-    st = residual<R, DENSITY>(plan, w, w.s, w.part, w.b, w.x, q, k2, &tr, E);
+    st = residual<R, FORM>(plan, w, w.s, w.part, w.b, w.x, a, &tr, E);
     if (st != VP_OK) return st;
   } else {
     Work<double> w64;
-    if ((st = alloc_work<double>(w64, plan, n, DENSITY, E)) != VP_OK) return st;
+    if ((st = alloc_work<double>(w64, plan, n, FORM, d, false, E)) != VP_OK) return st;
     guard.restore_prec = true;
     if ((st = vp_plan_set_precision(plan, VP_FP64)) != VP_OK) return st;
     cudaFree(w64.ws);  // resize for the FP64 passes
     w64.ws = nullptr;
-    w64.ws_bytes = vp::plan_apply_workspace_bytes(plan);
+    w64.ws_bytes = form_workspace_bytes(plan, FORM);
     BCG_CUDA(E, cudaMalloc(&w64.ws, w64.ws_bytes));
     BCG_CUDA(E, cudaStreamSynchronize(w.s));
     if ((st = vp_plan_set_stream(plan, w64.s)) != VP_OK) return st;
     double* q64 = reinterpret_cast<double*>(w64.rh);  // n doubles fit in n complex
     k_widen_r<<<kBlocks, kThreads, 0, w64.s>>>(q64, reinterpret_cast<const float*>(q), n);
-    k_widen_c<<<kBlocks, kThreads, 0, w64.s>>>(w64.p, reinterpret_cast<const float2*>(uinc), n);
-    if (!DENSITY) {  // b = k^2 V[q u_inc] in FP64
-      k_qmul<double><<<kBlocks, kThreads, 0, w64.s>>>(w64.t0, q64, w64.p, n);
-      if ((st = apply_v<double, false>(plan, w64, w64.p)) != VP_OK) return st;
-      k_rhs<double, false><<<kBlocks, kThreads, 0, w64.s>>>(w64.t1, q64, k2d, w64.b, n);
-    } else {  // b = k^2 q u_inc
-      k_rhs<double, true><<<kBlocks, kThreads, 0, w64.s>>>(w64.p, q64, k2d, w64.b, n);
+    struct FreeGe {
+      double* p = nullptr;
+      ~FreeGe() { cudaFree(p); }
+    } ge64;
+    if (FORM == F_PB) {
+      BCG_CUDA(E, cudaMalloc(&ge64.p, (size_t)d * n * sizeof(double)));
+      k_widen_r<<<kBlocks, kThreads, 0, w64.s>>>(ge64.p, reinterpret_cast<const float*>(ge), (long long)d * n);
+    }
+    double2* src64 = w64.p;
+    k_widen_c<<<kBlocks, kThreads, 0, w64.s>>>(src64, reinterpret_cast<const float2*>(src), n);
+    const OpArgs<double> a64{q64, ge64.p, k2d, d, n};
+    if (FORM == F_FIELD) {  // b = k^2 V[q u_inc] in FP64
+      k_qmul<double><<<kBlocks, kThreads, 0, w64.s>>>(w64.t0, q64, src64, n);
+      if ((st = apply_v<double, FORM>(plan, w64, src64)) != VP_OK) return st;
+      k_rhs<double, FORM><<<kBlocks, kThreads, 0, w64.s>>>(w64.t1, a64, w64.b);
+    } else {
+      k_rhs<double, FORM><<<kBlocks, kThreads, 0, w64.s>>>(src64, a64, w64.b);
     }
     double2* x64 = w64.r;
     k_widen_c<<<kBlocks, kThreads, 0, w64.s>>>(x64, reinterpret_cast<const float2*>(w.x), n);
-    st = residual<double, DENSITY>(plan, w64, w64.s, w64.part, w64.b, x64, q64, k2d, &tr, E);
+    st = residual<double, FORM>(plan, w64, w64.s, w64.part, w64.b, x64, a64, &tr, E);
     if (st != VP_OK) return st;
   }
   if (stats) {
@@ -829,9 +880,11 @@ struct GraphHolder {
   }
 };
 
-template <bool DENSITY>
-vp_status solve_mixed(vp_plan plan, const double* q64, const double2* uinc, double2* u, double k2d, long long n,
-                      double tol, double delta, int maxit, double* history, vp_ls_stats* stats, Err& E) {
+// Mixed precision: q, ge (PB), src, u in FP64; the recurrence in FP32.
+template <int FORM>
+vp_status solve_mixed(vp_plan plan, const double* q64, const double* ge64, const double2* src, double2* u, double k2d,
+                      int d, long long n, double tol, double delta, int maxit, double* history, vp_ls_stats* stats,
+                      Err& E) {
   const auto t_start = std::chrono::steady_clock::now();
   PlanGuard guard{plan, vp::plan_stream(plan), vp::plan_is_fp64(plan) ? VP_FP64 : VP_FP32};
   guard.restore_prec = true;
@@ -839,42 +892,46 @@ vp_status solve_mixed(vp_plan plan, const double* q64, const double2* uinc, doub
   if (st != VP_OK) return st;
   // FP32 recurrence: r, r^, p, v, t1 (and t0), x_lo, the FP32 workspace, state
   Work<float> w;
-  if ((st = alloc_work<float>(w, plan, n, true, E)) != VP_OK) return st;
-  if (!DENSITY) BCG_CUDA(E, cudaMalloc(&w.t0, n * sizeof(float2)));
-  float* q32 = nullptr;
-  BCG_CUDA(E, cudaMalloc(&q32, n * sizeof(float)));
+  if ((st = alloc_work<float>(w, plan, n, FORM, d, true, E)) != VP_OK) return st;
   struct Free {
-    void* p;
+    void* p = nullptr;
     ~Free() { cudaFree(p); }
-  } free_q32{q32};
-  // FP64 side: b, the solution x (the caller's u for the field form), t1 (and
-  // t0), the FP64 workspace
+  } q32, ge32;
+  BCG_CUDA(E, cudaMalloc(&q32.p, n * sizeof(float)));
+  if (FORM == F_PB) BCG_CUDA(E, cudaMalloc(&ge32.p, (size_t)d * n * sizeof(float)));
+  // FP64 side: b, the solution x (the caller's u unless the density form),
+  // t1 (and t0), the FP64 workspace
   Work<double> w64;
   w64.n = n;
   if ((st = vp_plan_set_precision(plan, VP_FP64)) != VP_OK) return st;
   BCG_CUDA(E, cudaMalloc(&w64.b, n * sizeof(double2)));
-  BCG_CUDA(E, cudaMalloc(&w64.t1, n * sizeof(double2)));
-  if (!DENSITY) {
-    BCG_CUDA(E, cudaMalloc(&w64.t0, n * sizeof(double2)));
-    w64.x = u;
-  } else {
+  BCG_CUDA(E, cudaMalloc(&w64.t1, (FORM == F_PB ? d : 1) * n * sizeof(double2)));
+  if (FORM == F_FIELD) BCG_CUDA(E, cudaMalloc(&w64.t0, n * sizeof(double2)));
+  if (FORM == F_DENSITY) {
     BCG_CUDA(E, cudaMalloc(&w64.x_own, n * sizeof(double2)));
     w64.x = w64.x_own;
+  } else {
+    w64.x = u;
   }
-  w64.ws_bytes = vp::plan_apply_workspace_bytes(plan);
+  w64.ws_bytes = form_workspace_bytes(plan, FORM);
   BCG_CUDA(E, cudaMalloc(&w64.ws, w64.ws_bytes));
   BCG_CUDA(E, cudaStreamSynchronize(guard.stream));
   if ((st = vp_plan_set_stream(plan, w.s)) != VP_OK) return st;
+  const OpArgs<double> a64{q64, ge64, k2d, d, n};
+  const OpArgs<float> a32{reinterpret_cast<const float*>(q32.p), reinterpret_cast<const float*>(ge32.p), (float)k2d,
+                          d, n};
 
   // FP64 right-hand side (its apply also sets up the FP64 passes before capture)
-  k_narrow_r<<<kBlocks, kThreads, 0, w.s>>>(q32, q64, n);
-  if (!DENSITY) {
-    k_qmul<double><<<kBlocks, kThreads, 0, w.s>>>(w64.t0, q64, uinc, n);
-    if ((st = apply_v<double, false>(plan, w64, uinc)) != VP_OK) return st;
-    k_rhs<double, false><<<kBlocks, kThreads, 0, w.s>>>(w64.t1, q64, k2d, w64.b, n);
+  k_narrow_r<<<kBlocks, kThreads, 0, w.s>>>(reinterpret_cast<float*>(q32.p), q64, n);
+  if (FORM == F_PB)
+    k_narrow_r<<<kBlocks, kThreads, 0, w.s>>>(reinterpret_cast<float*>(ge32.p), ge64, (long long)d * n);
+  if (FORM == F_FIELD) {
+    k_qmul<double><<<kBlocks, kThreads, 0, w.s>>>(w64.t0, q64, src, n);
+    if ((st = apply_v<double, FORM>(plan, w64, src)) != VP_OK) return st;
+    k_rhs<double, FORM><<<kBlocks, kThreads, 0, w.s>>>(w64.t1, a64, w64.b);
   } else {
-    if ((st = apply_v<double, true>(plan, w64, uinc)) != VP_OK) return st;
-    k_rhs<double, true><<<kBlocks, kThreads, 0, w.s>>>(uinc, q64, k2d, w64.b, n);
+    if ((st = apply_v<double, FORM>(plan, w64, src)) != VP_OK) return st;
+    k_rhs<double, FORM><<<kBlocks, kThreads, 0, w.s>>>(src, a64, w64.b);
   }
   k_mixed_init<<<kBlocks, kThreads, 0, w.s>>>(w64.b, w.r, w.rh, w.p, w.v, w.x, w64.x, n, w.part);
   BcgState init;
@@ -893,9 +950,9 @@ vp_status solve_mixed(vp_plan plan, const double* q64, const double2* uinc, doub
   GraphHolder upd;
   upd.s = w.s;
   BCG_CUDA(E, cudaStreamBeginCapture(w.s, cudaStreamCaptureModeThreadLocal));
-  k_accumulate<DENSITY><<<kBlocks, kThreads, 0, w.s>>>(w64.x, w.x, q64, w64.t0, n);
-  st = apply_v<double, DENSITY>(plan, w64, w64.x);
-  k_true_residual<DENSITY><<<kBlocks, kThreads, 0, w.s>>>(w64.b, w64.x, w64.t1, q64, k2d, w.rh, w.r, n, w.part);
+  k_accumulate<FORM><<<kBlocks, kThreads, 0, w.s>>>(w64.x, w.x, q64, w64.t0, n);
+  st = apply_v<double, FORM>(plan, w64, w64.x);
+  k_true_residual<FORM><<<kBlocks, kThreads, 0, w.s>>>(w64.b, w64.x, w64.t1, a64, w.rh, w.r, w.part);
   k_scal_update<<<1, kScalThreads, 0, w.s>>>(w.st, w.part);
   cudaError_t ce = cudaStreamEndCapture(w.s, &upd.g);
   if (st != VP_OK) return st;
@@ -904,11 +961,10 @@ vp_status solve_mixed(vp_plan plan, const double* q64, const double2* uinc, doub
 
   // the FP32 iteration as two graphs (an uncaptured apply first sets up the FP32 passes)
   if ((st = vp_plan_set_precision(plan, VP_FP32)) != VP_OK) return st;
-  if ((st = apply_v<float, DENSITY>(plan, w, w.p)) != VP_OK) return st;
-  const float k2 = (float)k2d;
+  if ((st = apply_v<float, FORM>(plan, w, w.p)) != VP_OK) return st;
   for (int k = 0; k < 2; ++k) {
     BCG_CUDA(E, cudaStreamBeginCapture(w.s, cudaStreamCaptureModeThreadLocal));
-    vp_status cs = enqueue_iteration<float, DENSITY>(plan, w, q32, k2, k);
+    vp_status cs = enqueue_iteration<float, FORM>(plan, w, a32, k);
     ce = cudaStreamEndCapture(w.s, &w.g[k]);
     if (cs != VP_OK) return cs;
     BCG_CUDA(E, ce);
@@ -954,7 +1010,7 @@ vp_status solve_mixed(vp_plan plan, const double* q64, const double2* uinc, doub
     BCG_CUDA(E, cudaStreamSynchronize(w.s));
     vp_ls_stats s64;
     memset(&s64, 0, sizeof(s64));
-    st = solve<double, DENSITY>(plan, q64, uinc, u, k2d, n, tol, maxit, nullptr, &s64, E);
+    st = solve<double, FORM>(plan, q64, ge64, src, u, k2d, d, n, tol, maxit, nullptr, &s64, E);
     const auto t_end = std::chrono::steady_clock::now();
     if (stats) {
       stats->iterations = last.iterations + s64.iterations;
@@ -967,14 +1023,14 @@ vp_status solve_mixed(vp_plan plan, const double* q64, const double2* uinc, doub
     }
     return st;
   }
-  if (DENSITY) {  // u = V[s] in FP64
+  if (FORM == F_DENSITY) {  // u = V[s] in FP64
     st = vp::apply_with_workspace(plan, w64.x, u, VP_C128, w64.ws, w64.ws_bytes);
     if (st != VP_OK) return st;
   }
   BCG_CUDA(E, cudaStreamSynchronize(w.s));
   const auto t_end = std::chrono::steady_clock::now();
   double tr = 0.0;
-  if ((st = residual<double, DENSITY>(plan, w64, w.s, w.part, w64.b, w64.x, q64, k2d, &tr, E)) != VP_OK) return st;
+  if ((st = residual<double, FORM>(plan, w64, w.s, w.part, w64.b, w64.x, a64, &tr, E)) != VP_OK) return st;
   if (stats) {
     stats->iterations = last.iterations;
     stats->matvecs = last.matvecs;
@@ -989,85 +1045,156 @@ vp_status solve_mixed(vp_plan plan, const double* q64, const double2* uinc, doub
 
 }  // namespace
 
-extern "C" {
+namespace {
 
-vp_status vp_ls_bicgstab_mixed(vp_plan plan, const double* q, const void* u_inc, void* u, int form, double tol,
-                               double delta, int maxit, double* history, vp_ls_stats* stats) {
-  int d = 0, N = 0;
-  double k = 0.0;
-  if (!plan) {
-    vp::ls_set_error("plan is NULL");
-    return VP_ERR_INVALID_ARG;
-  }
-  vp_status st = vp_plan_info(plan, &d, &N, &k, nullptr, nullptr);
-  if (st != VP_OK) return st;
+// common argument checks of the entry points; *n and *d on success
+vp_status check_args(vp_plan plan, bool pb, const void* q, const void* ge, const void* src, const void* u, int form,
+                     double tol, int maxit, long long* n, int* d, double* k) {
+  int N = 0;
   auto bad = [](const char* m) {
     vp::ls_set_error(m);
     return VP_ERR_INVALID_ARG;
   };
-  if (!(k > 0)) return bad("the scattering solve needs a Helmholtz plan");
-  if (!q || !u_inc || !u) return bad("q, u_inc and u are required");
-  if (u == u_inc) return bad("u may not alias u_inc");
-  if (form != VP_LS_FIELD && form != VP_LS_DENSITY) return bad("form must be VP_LS_FIELD or VP_LS_DENSITY");
+  if (!plan) return bad("plan is NULL");
+  vp_status st = vp_plan_info(plan, d, &N, k, nullptr, nullptr);
+  if (st != VP_OK) return st;
+  if (pb) {
+    if (vp::plan_kernel(plan) != VP_LAPLACE) return bad("the Poisson-Boltzmann solve needs a Laplace plan");
+    if (!q || !ge || !src || !u) return bad("eps, grad_eps, rho and sigma are required");
+    if (u == src) return bad("sigma may not alias rho");
+  } else {
+    if (!(*k > 0)) return bad("the scattering solve needs a Helmholtz plan");
+    if (!q || !src || !u) return bad("q, u_inc and u are required");
+    if (u == src) return bad("u may not alias u_inc");
+    if (form != VP_LS_FIELD && form != VP_LS_DENSITY) return bad("form must be VP_LS_FIELD or VP_LS_DENSITY");
+  }
   if (!(tol > 0) || maxit < 1) return bad("tol > 0 and maxit >= 1 required");
-  if (!(delta > 0 && delta < 1)) return bad("delta must be in (0, 1)");
-  if (!vp::plan_is_fp32(plan) && !vp::plan_is_fp64(plan)) return bad("the plan's precision must be VP_FP32 or VP_FP64");
-  const long long n = (long long)N * N * (d == 3 ? N : 1);
-  Err E;
-  cudaSetDevice(vp::plan_device(plan));
-  auto ui = reinterpret_cast<const double2*>(u_inc);
+  *n = (long long)N * N * (*d == 3 ? N : 1);
+  return VP_OK;
+}
+
+template <typename R>
+vp_status run_one(vp_plan plan, int FORMv, const void* q, const void* ge, const void* src, void* u, double k2, int d,
+                  long long n, double tol, int maxit, double* history, vp_ls_stats* stats, Err& E) {
+  using C = typename Cx<R>::T;
+  auto qq = reinterpret_cast<const R*>(q);
+  auto gg = reinterpret_cast<const R*>(ge);
+  auto ss = reinterpret_cast<const C*>(src);
+  auto uo = reinterpret_cast<C*>(u);
+  if (FORMv == F_FIELD) return solve<R, F_FIELD>(plan, qq, gg, ss, uo, k2, d, n, tol, maxit, history, stats, E);
+  if (FORMv == F_DENSITY) return solve<R, F_DENSITY>(plan, qq, gg, ss, uo, k2, d, n, tol, maxit, history, stats, E);
+  return solve<R, F_PB>(plan, qq, gg, ss, uo, k2, d, n, tol, maxit, history, stats, E);
+}
+
+vp_status run_mixed(vp_plan plan, int FORMv, const double* q, const double* ge, const void* src, void* u, double k2,
+                    int d, long long n, double tol, double delta, int maxit, double* history, vp_ls_stats* stats,
+                    Err& E) {
+  auto ss = reinterpret_cast<const double2*>(src);
   auto uo = reinterpret_cast<double2*>(u);
-  st = form == VP_LS_DENSITY ? solve_mixed<true>(plan, q, ui, uo, k * k, n, tol, delta, maxit, history, stats, E)
-                             : solve_mixed<false>(plan, q, ui, uo, k * k, n, tol, delta, maxit, history, stats, E);
+  if (FORMv == F_FIELD)
+    return solve_mixed<F_FIELD>(plan, q, ge, ss, uo, k2, d, n, tol, delta, maxit, history, stats, E);
+  if (FORMv == F_DENSITY)
+    return solve_mixed<F_DENSITY>(plan, q, ge, ss, uo, k2, d, n, tol, delta, maxit, history, stats, E);
+  return solve_mixed<F_PB>(plan, q, ge, ss, uo, k2, d, n, tol, delta, maxit, history, stats, E);
+}
+
+vp_status finish(vp_status st, const Err& E) {
   if (st != VP_OK) vp::ls_set_error(E.msg.empty() ? vp_status_string(st) : E.msg.c_str());
   return st;
 }
 
-vp_status vp_ls_bicgstab(vp_plan plan, const void* q, const void* u_inc, void* u, vp_dtype dtype, int form,
-                         double tol, int maxit, double* history, vp_ls_stats* stats) {
-  int d = 0, N = 0;
-  double k = 0.0;
-  if (!plan) {
-    vp::ls_set_error("plan is NULL");
+vp_status check_mixed(vp_plan plan, double delta) {
+  if (!(delta > 0 && delta < 1)) {
+    vp::ls_set_error("delta must be in (0, 1)");
     return VP_ERR_INVALID_ARG;
   }
-  vp_status st = vp_plan_info(plan, &d, &N, &k, nullptr, nullptr);
-  if (st != VP_OK) return st;
-  auto bad = [](const char* m) {
+  if (!vp::plan_is_fp32(plan) && !vp::plan_is_fp64(plan)) {
+    vp::ls_set_error("the plan's precision must be VP_FP32 or VP_FP64");
+    return VP_ERR_INVALID_ARG;
+  }
+  return VP_OK;
+}
+
+vp_status check_dtype_prec(vp_plan plan, vp_dtype dtype) {
+  const char* m = nullptr;
+  if (dtype == VP_C64) {
+    if (!vp::plan_is_fp32(plan)) m = "VP_C64 iterates with the FP32 apply: set the plan's precision to VP_FP32";
+  } else if (dtype == VP_C128) {
+    if (!vp::plan_is_fp64(plan)) m = "VP_C128 iterates with the FP64 apply: set the plan's precision to VP_FP64";
+  } else {
+    m = "dtype must be VP_C64 or VP_C128";
+  }
+  if (m) {
     vp::ls_set_error(m);
     return VP_ERR_INVALID_ARG;
-  };
-  if (!(k > 0)) return bad("the scattering solve needs a Helmholtz plan");
-  if (!q || !u_inc || !u) return bad("q, u_inc and u are required");
-  if (u == u_inc) return bad("u may not alias u_inc");
-  if (form != VP_LS_FIELD && form != VP_LS_DENSITY) return bad("form must be VP_LS_FIELD or VP_LS_DENSITY");
-  if (!(tol > 0) || maxit < 1) return bad("tol > 0 and maxit >= 1 required");
-  if (dtype == VP_C64) {
-    if (!vp::plan_is_fp32(plan)) return bad("VP_C64 iterates with the FP32 apply: set the plan's precision to VP_FP32");
-  } else if (dtype == VP_C128) {
-    if (!vp::plan_is_fp64(plan)) return bad("VP_C128 iterates with the FP64 apply: set the plan's precision to VP_FP64");
-  } else {
-    return bad("dtype must be VP_C64 or VP_C128");
   }
-  const long long n = (long long)N * N * (d == 3 ? N : 1);
+  return VP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vp_status vp_ls_bicgstab(vp_plan plan, const void* q, const void* u_inc, void* u, vp_dtype dtype, int form,
+                         double tol, int maxit, double* history, vp_ls_stats* stats) {
+  long long n = 0;
+  int d = 0;
+  double k = 0.0;
+  vp_status st = check_args(plan, false, q, nullptr, u_inc, u, form, tol, maxit, &n, &d, &k);
+  if (st == VP_OK) st = check_dtype_prec(plan, dtype);
+  if (st != VP_OK) return st;
   Err E;
   cudaSetDevice(vp::plan_device(plan));
-  const bool dens = form == VP_LS_DENSITY;
-  if (dtype == VP_C64) {
-    auto qq = reinterpret_cast<const float*>(q);
-    auto ui = reinterpret_cast<const float2*>(u_inc);
-    auto uo = reinterpret_cast<float2*>(u);
-    st = dens ? solve<float, true>(plan, qq, ui, uo, k * k, n, tol, maxit, history, stats, E)
-              : solve<float, false>(plan, qq, ui, uo, k * k, n, tol, maxit, history, stats, E);
-  } else {
-    auto qq = reinterpret_cast<const double*>(q);
-    auto ui = reinterpret_cast<const double2*>(u_inc);
-    auto uo = reinterpret_cast<double2*>(u);
-    st = dens ? solve<double, true>(plan, qq, ui, uo, k * k, n, tol, maxit, history, stats, E)
-              : solve<double, false>(plan, qq, ui, uo, k * k, n, tol, maxit, history, stats, E);
-  }
-  if (st != VP_OK) vp::ls_set_error(E.msg.empty() ? vp_status_string(st) : E.msg.c_str());
-  return st;
+  const int f = form == VP_LS_DENSITY ? F_DENSITY : F_FIELD;
+  st = dtype == VP_C64 ? run_one<float>(plan, f, q, nullptr, u_inc, u, k * k, d, n, tol, maxit, history, stats, E)
+                       : run_one<double>(plan, f, q, nullptr, u_inc, u, k * k, d, n, tol, maxit, history, stats, E);
+  return finish(st, E);
+}
+
+vp_status vp_ls_bicgstab_mixed(vp_plan plan, const double* q, const void* u_inc, void* u, int form, double tol,
+                               double delta, int maxit, double* history, vp_ls_stats* stats) {
+  long long n = 0;
+  int d = 0;
+  double k = 0.0;
+  vp_status st = check_args(plan, false, q, nullptr, u_inc, u, form, tol, maxit, &n, &d, &k);
+  if (st == VP_OK) st = check_mixed(plan, delta);
+  if (st != VP_OK) return st;
+  Err E;
+  cudaSetDevice(vp::plan_device(plan));
+  const int f = form == VP_LS_DENSITY ? F_DENSITY : F_FIELD;
+  st = run_mixed(plan, f, q, nullptr, u_inc, u, k * k, d, n, tol, delta, maxit, history, stats, E);
+  return finish(st, E);
+}
+
+vp_status vp_pb_solve(vp_plan plan, const void* eps, const void* grad_eps, const void* rho, void* sigma,
+                      vp_dtype dtype, double tol, int maxit, double* history, vp_ls_stats* stats) {
+  long long n = 0;
+  int d = 0;
+  double k = 0.0;
+  vp_status st = check_args(plan, true, eps, grad_eps, rho, sigma, 0, tol, maxit, &n, &d, &k);
+  if (st == VP_OK) st = check_dtype_prec(plan, dtype);
+  if (st == VP_OK) st = vp::plan_prepare_grad(plan);
+  if (st != VP_OK) return st;
+  Err E;
+  cudaSetDevice(vp::plan_device(plan));
+  st = dtype == VP_C64 ? run_one<float>(plan, F_PB, eps, grad_eps, rho, sigma, 0.0, d, n, tol, maxit, history, stats, E)
+                       : run_one<double>(plan, F_PB, eps, grad_eps, rho, sigma, 0.0, d, n, tol, maxit, history, stats, E);
+  return finish(st, E);
+}
+
+vp_status vp_pb_solve_mixed(vp_plan plan, const double* eps, const double* grad_eps, const void* rho, void* sigma,
+                            double tol, double delta, int maxit, double* history, vp_ls_stats* stats) {
+  long long n = 0;
+  int d = 0;
+  double k = 0.0;
+  vp_status st = check_args(plan, true, eps, grad_eps, rho, sigma, 0, tol, maxit, &n, &d, &k);
+  if (st == VP_OK) st = check_mixed(plan, delta);
+  if (st == VP_OK) st = vp::plan_prepare_grad(plan);
+  if (st != VP_OK) return st;
+  Err E;
+  cudaSetDevice(vp::plan_device(plan));
+  st = run_mixed(plan, F_PB, eps, grad_eps, rho, sigma, 0.0, d, n, tol, delta, maxit, history, stats, E);
+  return finish(st, E);
 }
 
 }  // extern "C"

@@ -566,6 +566,42 @@ int plan_is_fp64(vp_plan p) { return p && p->prec == VP_FP64; }
 
 vp_status entries_fail(vp_plan p, vp_status st, const char* msg) { return fail(p, st, msg); }
 
+int plan_kernel(vp_plan p) { return p ? p->kernel : -1; }
+
+vp_status plan_prepare_grad(vp_plan p) {
+  VP_CUDA(p, cudaSetDevice(p->device));
+  return build_grad(p);
+}
+
+size_t plan_grad_workspace_bytes(vp_plan p) {
+  const size_t csize = p->prec == VP_FP64 ? sizeof(double2) : sizeof(float2);
+  return workspace_bytes(p->d, p->N, p->d, csize);
+}
+
+vp_status apply_grad_with_workspace(vp_plan p, const void* f, void* grad, vp_dtype dtype, void* ws, size_t ws_bytes) {
+  if (!p) return fail(nullptr, VP_ERR_INVALID_ARG, "plan is NULL");
+  if (!f || !grad) return fail(p, VP_ERR_INVALID_ARG, "f and grad must be non-NULL");
+  bool real_io = false;
+  vp_status st = check_dtype(p, dtype, &real_io);
+  if (st != VP_OK) return st;
+  if (!p->grad_built) return fail(p, VP_ERR_INVALID_ARG, "the derivative multipliers are not built");
+  if (ws_bytes < plan_grad_workspace_bytes(p)) return fail(p, VP_ERR_UNSUPPORTED, "gradient workspace too small");
+  const bool fp64 = p->prec == VP_FP64;
+  const size_t U = (size_t)p->N * p->N * (p->d == 3 ? p->N : 1);
+  FieldDesc fields[3];
+  void* outs[3];
+  for (int j = 0; j < p->d; ++j) {
+    fields[j] = FieldDesc{fp64 ? (const void*)p->Gj64[j] : (const void*)p->Gj32[j], j, -1};
+    outs[j] = reinterpret_cast<char*>(grad) + (size_t)j * U * elem_bytes(dtype);
+  }
+  const bool timing = p->timing;
+  p->timing = false;
+  st = fp64 ? run_apply_ws<double>(p, ws, f, outs, fields, p->d, real_io)
+            : run_apply_ws<float>(p, ws, f, outs, fields, p->d, real_io);
+  p->timing = timing;
+  return st;
+}
+
 vp_status plan_kernel_octant(vp_plan p, int which, int axis, const double2** oct) {
   VP_CUDA(p, cudaSetDevice(p->device));
   if (which == VP_ARRAY_T) {

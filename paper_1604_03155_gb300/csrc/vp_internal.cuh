@@ -83,5 +83,12 @@ void ls_set_error(const char* msg);
 int plan_pass_args_f32(vp_plan p, float2* ws, PassArgs<float>* args, int* kinds);
 size_t plan_apply_workspace_bytes(vp_plan p);
 vp_status apply_with_workspace(vp_plan p, const void* f, void* phi, vp_dtype dtype, void* ws, size_t ws_bytes);
+// The exact gradient (d fields, d blocks of N^d) on a caller workspace of
+// plan_grad_workspace_bytes; the derivative multipliers must have been built
+// (plan_prepare_grad) before, e.g. outside a stream capture.
+int plan_kernel(vp_plan p);
+vp_status plan_prepare_grad(vp_plan p);
+size_t plan_grad_workspace_bytes(vp_plan p);
+vp_status apply_grad_with_workspace(vp_plan p, const void* f, void* grad, vp_dtype dtype, void* ws, size_t ws_bytes);
 
 }  // namespace vp

@@ -90,6 +90,10 @@ _SIGNATURES = {
                                c_void_p]),
     "vp_ls_bicgstab_mixed": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_double, c_double, c_int,
                                      c_void_p, c_void_p]),
+    "vp_pb_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_double, c_int, c_void_p,
+                            c_void_p]),
+    "vp_pb_solve_mixed": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_double, c_int,
+                                  c_void_p, c_void_p]),
     "vp_ls_krylov_basis": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, ctypes.POINTER(c_int)]),
     "vp_ls_flexible_basis": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p,
                                      ctypes.POINTER(c_int)]),
@@ -524,6 +528,30 @@ def ls_bicgstab_mixed(plan: Plan, q, u_inc, u=None, form: str = "field", tol: fl
     if history:
         return u, stats, hist[:stats["iterations"] + 1]
     return u, stats
+
+
+def pb_solve(plan: Plan, eps, grad_eps, rho, sigma=None, tol: float = 1e-12, maxit: int = 1000,
+             mixed: bool = False, delta: float = 1e-2, history: bool = False):
+    """-eps sigma + grad(eps) . grad V[sigma] = rho on a Laplace plan (Section 5.2).
+    eps (N^d), grad_eps (d, N^d...) real and rho complex device tensors of the
+    plan's precision (mixed=True: FP64 data, FP32 iterations with FP64 reliable
+    updates).  Returns (sigma, stats) or (sigma, stats, history)."""
+    sigma = _empty_like(rho, rho.shape) if sigma is None else sigma
+    st = LSStats()
+    hist = np.zeros(maxit + 1) if history else None
+    plan._sync_stream_to_torch(rho)
+    hp = _ptr(hist) if history else None
+    if mixed:
+        code = lib().vp_pb_solve_mixed(plan.handle, _ptr(eps), _ptr(grad_eps), _ptr(rho), _ptr(sigma), tol, delta,
+                                       maxit, hp, ctypes.byref(st))
+    else:
+        code = lib().vp_pb_solve(plan.handle, _ptr(eps), _ptr(grad_eps), _ptr(rho), _ptr(sigma), _dtype_code(rho),
+                                 tol, maxit, hp, ctypes.byref(st))
+    _lscheck(code)
+    stats = {k: getattr(st, k) for k, _ in LSStats._fields_}
+    if history:
+        return sigma, stats, hist[:stats["iterations"] + 1]
+    return sigma, stats
 
 
 def ls_training_pair(plan: Plan, q, b, u_s, u_star, x_out, t_out) -> float:

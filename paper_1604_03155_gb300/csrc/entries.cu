@@ -77,9 +77,10 @@ __global__ void __launch_bounds__(kThreads) k_entries(const double2* __restrict_
 // memory, each thread decodes its column once and writes that column of every
 // row of the tile (consecutive threads write consecutive entries of one row).
 constexpr int kTileRows = 16;
+constexpr int kGroup = 8;
 
 template <typename C, int D>
-__global__ void __launch_bounds__(kThreads) k_block(const double2* __restrict__ oct, int N, int odd_axis,
+__global__ void __launch_bounds__(kThreads, 4) k_block(const double2* __restrict__ oct, int N, int odd_axis,
                                                     const long long* __restrict__ rows, long long nr,
                                                     const long long* __restrict__ cols, long long nc,
                                                     C* __restrict__ out, int* __restrict__ bad) {
@@ -125,21 +126,25 @@ __global__ void __launch_bounds__(kThreads) k_block(const double2* __restrict__ 
     __syncthreads();
     if (c >= nc) continue;
     const int nrows = nr - r0 < kTileRows ? (int)(nr - r0) : kTileRows;
-    // all gathers of the tile in flight before the stores
-    double2 v[kTileRows];
+    // the gathers of kGroup rows in flight before their stores (kGroup bounds
+    // the registers, and so keeps four CTAs resident per SM)
+    for (int i0 = 0; i0 < kTileRows; i0 += kGroup) {
+      double2 v[kGroup];
 #pragma unroll
-    for (int i = 0; i < kTileRows; ++i) {
-      v[i] = make_double2(0.0, 0.0);
-      if (i < nrows && cok && sok[i]) {
-        int n[3] = {0, 0, 0};
+      for (int g = 0; g < kGroup; ++g) {
+        const int i = i0 + g;
+        v[g] = make_double2(0.0, 0.0);
+        if (i < nrows && cok && sok[i]) {
+          int n[3] = {0, 0, 0};
 #pragma unroll
-        for (int a = 0; a < D; ++a) n[a] = srow[i][a] - q[a];
-        v[i] = gather<D>(oct, N, odd_axis, n);
+          for (int a = 0; a < D; ++a) n[a] = srow[i][a] - q[a];
+          v[g] = gather<D>(oct, N, odd_axis, n);
+        }
       }
-    }
 #pragma unroll
-    for (int i = 0; i < kTileRows; ++i)
-      if (i < nrows) out[(r0 + i) * nc + c] = to_c<C>(v[i]);
+      for (int g = 0; g < kGroup; ++g)
+        if (i0 + g < nrows) out[(r0 + i0 + g) * nc + c] = to_c<C>(v[g]);
+    }
   }
 }
 

@@ -26,14 +26,31 @@ def main(argv=None):
     ap.add_argument("--cols", type=int, default=8192)
     ap.add_argument("--dtype", default="c128", choices=["c64", "c128"])
     ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--boxes", action="store_true",
+                    help="rows and columns are the nodes of two sub-boxes of the grid (the index sets of a "
+                         "hierarchical solver) instead of random nodes")
     a = ap.parse_args(argv)
     dev = torch.device("cuda", 0)
     dt = torch.complex128 if a.dtype == "c128" else torch.complex64
     plan = vp.Plan(a.d, a.N, a.kernel, a.k if a.kernel == "helmholtz" else 0.0, 0.0)
     U = a.N ** a.d
     g = torch.Generator(device="cpu").manual_seed(1)
-    rows = torch.randint(0, U, (a.rows,), generator=g).to(dev)
-    cols = torch.randint(0, U, (a.cols,), generator=g).to(dev)
+    if a.boxes:
+        def box(count, corner):
+            # the first `count` nodes of a sub-box whose last axis spans 32 nodes, in C order
+            side = int(round((count / 32) ** (1.0 / (a.d - 1))))
+            shape = [side] * (a.d - 1) + [32]
+            idx = torch.stack(torch.meshgrid(*[torch.arange(n) for n in shape], indexing="ij"), -1).reshape(-1, a.d)
+            idx = idx + torch.tensor(corner)
+            flat = torch.zeros(idx.shape[0], dtype=torch.int64)
+            for j in range(a.d):
+                flat = flat * a.N + idx[:, j]
+            return flat[:count].to(dev)
+        rows = box(a.rows, [a.N // 8] * a.d)
+        cols = box(a.cols, [a.N // 2] * a.d)
+    else:
+        rows = torch.randint(0, U, (a.rows,), generator=g).to(dev)
+        cols = torch.randint(0, U, (a.cols,), generator=g).to(dev)
     off = torch.randint(-a.N + 1, a.N, (a.rows * 64, a.d), generator=g, dtype=torch.int32).to(dev)
     out = {}
     for name, fn, count in [("matrix_block", lambda: plan.matrix_block(rows, cols, dtype=dt), a.rows * a.cols),
@@ -53,7 +70,7 @@ def main(argv=None):
         esize = 16 if dt == torch.complex128 else 8
         out[name] = {"entries": count, "ms": ms, "entries_per_s": count / (ms * 1e-3),
                      "output_GBps": count * esize / (ms * 1e-3) / 1e9}
-    print(json.dumps({"d": a.d, "N": a.N, "kernel": a.kernel, "dtype": a.dtype, **out}))
+    print(json.dumps({"d": a.d, "N": a.N, "kernel": a.kernel, "dtype": a.dtype, "boxes": a.boxes, **out}))
     plan.close()
 
 

@@ -22,36 +22,29 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kMaxBlocks = 152 * 32;
 
-template <typename C>
-__device__ __forceinline__ C to_c(double2 v);
-template <>
-__device__ __forceinline__ double2 to_c<double2>(double2 v) {
-  return v;
-}
-template <>
-__device__ __forceinline__ float2 to_c<float2>(double2 v) {
-  return make_float2((float)v.x, (float)v.y);
-}
-
-// T(n) for an offset n (|n_j| <= N), from the octant (D = d: the loops unroll
-// and the index arrays stay in registers)
-template <int D>
-__device__ __forceinline__ double2 gather(const double2* __restrict__ oct, int N, int odd_axis, const int (&n)[3]) {
+// T(n) for an offset n (|n_j| <= N), from the octant of the output's precision
+// (D = d: the loops unroll and the index arrays stay in registers)
+template <typename C, int D>
+__device__ __forceinline__ C gather(const C* __restrict__ oct, int N, int odd_axis, const int (&n)[3]) {
   const long long M = N + 1;
   long long idx = 0;
-  double sgn = 1.0;
+  int sgn = 1;
 #pragma unroll
   for (int j = 0; j < D; ++j) {
     const int a = n[j] < 0 ? -n[j] : n[j];
     idx = idx * M + a;
-    if (j == odd_axis) sgn = n[j] > 0 ? 1.0 : (n[j] < 0 ? -1.0 : 0.0);
+    if (j == odd_axis) sgn = n[j] > 0 ? 1 : (n[j] < 0 ? -1 : 0);
   }
-  const double2 v = __ldg(oct + idx);
-  return make_double2(sgn * v.x, sgn * v.y);
+  C v = __ldg(oct + idx);
+  if (sgn != 1) {
+    v.x = sgn ? -v.x : 0;
+    v.y = sgn ? -v.y : 0;
+  }
+  return v;
 }
 
 template <typename C, int D>
-__global__ void __launch_bounds__(kThreads) k_entries(const double2* __restrict__ oct, int N, int odd_axis,
+__global__ void __launch_bounds__(kThreads) k_entries(const C* __restrict__ oct, int N, int odd_axis,
                                                       const int* __restrict__ off, long long count, C* __restrict__ out,
                                                       int* __restrict__ bad) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
@@ -64,11 +57,11 @@ __global__ void __launch_bounds__(kThreads) k_entries(const double2* __restrict_
       ok = ok && n[j] >= -N && n[j] <= N;
     }
     if (!ok) {
-      out[i] = to_c<C>(make_double2(0.0, 0.0));
+      out[i] = C{0, 0};
       atomicExch(bad, 1);
       continue;
     }
-    out[i] = to_c<C>(gather<D>(oct, N, odd_axis, n));
+    out[i] = gather<C, D>(oct, N, odd_axis, n);
   }
 }
 
@@ -80,7 +73,7 @@ constexpr int kTileRows = 16;
 constexpr int kGroup = 8;
 
 template <typename C, int D>
-__global__ void __launch_bounds__(kThreads, 4) k_block(const double2* __restrict__ oct, int N, int odd_axis,
+__global__ void __launch_bounds__(kThreads, 4) k_block(const C* __restrict__ oct, int N, int odd_axis,
                                                     const long long* __restrict__ rows, long long nr,
                                                     const long long* __restrict__ cols, long long nc,
                                                     C* __restrict__ out, int* __restrict__ bad) {
@@ -129,21 +122,21 @@ __global__ void __launch_bounds__(kThreads, 4) k_block(const double2* __restrict
     // the gathers of kGroup rows in flight before their stores (kGroup bounds
     // the registers, and so keeps four CTAs resident per SM)
     for (int i0 = 0; i0 < kTileRows; i0 += kGroup) {
-      double2 v[kGroup];
+      C v[kGroup];
 #pragma unroll
       for (int g = 0; g < kGroup; ++g) {
         const int i = i0 + g;
-        v[g] = make_double2(0.0, 0.0);
+        v[g] = C{0, 0};
         if (i < nrows && cok && sok[i]) {
           int n[3] = {0, 0, 0};
 #pragma unroll
           for (int a = 0; a < D; ++a) n[a] = srow[i][a] - q[a];
-          v[g] = gather<D>(oct, N, odd_axis, n);
+          v[g] = gather<C, D>(oct, N, odd_axis, n);
         }
       }
 #pragma unroll
       for (int g = 0; g < kGroup; ++g)
-        if (i0 + g < nrows) out[(r0 + i0 + g) * nc + c] = to_c<C>(v[g]);
+        if (i0 + g < nrows) out[(r0 + i0 + g) * nc + c] = v[g];
     }
   }
 }
@@ -162,9 +155,9 @@ bool is_device(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// common checks; *oct, *odd_axis, *dflag on success
+// common checks; *oct (FP64 or FP32 per dtype), *odd_axis, *dflag on success
 vp_status prepare(vp_plan plan, int which, int axis, vp_dtype dtype, const void* const* ptrs, int nptr,
-                  const double2** oct, int* odd_axis, int** dflag) {
+                  const void** oct, int* odd_axis, int** dflag) {
   if (!plan) return vp::entries_fail(nullptr, VP_ERR_INVALID_ARG, "plan is NULL");
   if (dtype != VP_C64 && dtype != VP_C128)
     return vp::entries_fail(plan, VP_ERR_INVALID_ARG, "dtype must be VP_C64 or VP_C128");
@@ -172,7 +165,16 @@ vp_status prepare(vp_plan plan, int which, int axis, vp_dtype dtype, const void*
     if (!ptrs[i]) return vp::entries_fail(plan, VP_ERR_INVALID_ARG, "NULL array");
     if (!is_device(ptrs[i])) return vp::entries_fail(plan, VP_ERR_INVALID_ARG, "arrays must be device pointers");
   }
-  vp_status st = vp::plan_kernel_octant(plan, which, axis, oct);
+  vp_status st;
+  if (dtype == VP_C128) {
+    const double2* o = nullptr;
+    st = vp::plan_kernel_octant(plan, which, axis, &o);
+    *oct = o;
+  } else {
+    const float2* o = nullptr;
+    st = vp::plan_kernel_octant32(plan, which, axis, &o);
+    *oct = o;
+  }
   if (st != VP_OK) return st;
   *odd_axis = which == VP_ARRAY_TJ ? axis : -1;
   *dflag = vp::plan_flag_word(plan);
@@ -200,7 +202,7 @@ vp_status vp_kernel_entries(vp_plan plan, int which, int axis, const int* offset
   if (count < 0) return vp::entries_fail(plan, VP_ERR_INVALID_ARG, "count < 0");
   if (count == 0) return VP_OK;
   const void* ptrs[2] = {offsets, out};
-  const double2* oct = nullptr;
+  const void* oct = nullptr;
   int odd = -1, *flag = nullptr;
   vp_status st = prepare(plan, which, axis, dtype, ptrs, 2, &oct, &odd, &flag);
   if (st != VP_OK) return st;
@@ -211,16 +213,18 @@ vp_status vp_kernel_entries(vp_plan plan, int which, int axis, const int* offset
   const unsigned g = grid_for(count);
   if (dtype == VP_C128) {
     auto o = reinterpret_cast<double2*>(out);
+    auto t = reinterpret_cast<const double2*>(oct);
     if (d == 3)
-      k_entries<double2, 3><<<g, kThreads, 0, s>>>(oct, N, odd, offsets, count, o, flag);
+      k_entries<double2, 3><<<g, kThreads, 0, s>>>(t, N, odd, offsets, count, o, flag);
     else
-      k_entries<double2, 2><<<g, kThreads, 0, s>>>(oct, N, odd, offsets, count, o, flag);
+      k_entries<double2, 2><<<g, kThreads, 0, s>>>(t, N, odd, offsets, count, o, flag);
   } else {
     auto o = reinterpret_cast<float2*>(out);
+    auto t = reinterpret_cast<const float2*>(oct);
     if (d == 3)
-      k_entries<float2, 3><<<g, kThreads, 0, s>>>(oct, N, odd, offsets, count, o, flag);
+      k_entries<float2, 3><<<g, kThreads, 0, s>>>(t, N, odd, offsets, count, o, flag);
     else
-      k_entries<float2, 2><<<g, kThreads, 0, s>>>(oct, N, odd, offsets, count, o, flag);
+      k_entries<float2, 2><<<g, kThreads, 0, s>>>(t, N, odd, offsets, count, o, flag);
   }
   return finish(plan, flag);
 }
@@ -230,7 +234,7 @@ vp_status vp_matrix_block(vp_plan plan, int which, int axis, const long long* ro
   if (nrows < 0 || ncols < 0) return vp::entries_fail(plan, VP_ERR_INVALID_ARG, "negative block size");
   if (nrows == 0 || ncols == 0) return VP_OK;
   const void* ptrs[3] = {rows, cols, out};
-  const double2* oct = nullptr;
+  const void* oct = nullptr;
   int odd = -1, *flag = nullptr;
   vp_status st = prepare(plan, which, axis, dtype, ptrs, 3, &oct, &odd, &flag);
   if (st != VP_OK) return st;
@@ -247,16 +251,18 @@ vp_status vp_matrix_block(vp_plan plan, int which, int axis, const long long* ro
   const dim3 grid((unsigned)gx, (unsigned)gy);
   if (dtype == VP_C128) {
     auto o = reinterpret_cast<double2*>(out);
+    auto t = reinterpret_cast<const double2*>(oct);
     if (d == 3)
-      k_block<double2, 3><<<grid, kThreads, 0, s>>>(oct, N, odd, rows, nrows, cols, ncols, o, flag);
+      k_block<double2, 3><<<grid, kThreads, 0, s>>>(t, N, odd, rows, nrows, cols, ncols, o, flag);
     else
-      k_block<double2, 2><<<grid, kThreads, 0, s>>>(oct, N, odd, rows, nrows, cols, ncols, o, flag);
+      k_block<double2, 2><<<grid, kThreads, 0, s>>>(t, N, odd, rows, nrows, cols, ncols, o, flag);
   } else {
     auto o = reinterpret_cast<float2*>(out);
+    auto t = reinterpret_cast<const float2*>(oct);
     if (d == 3)
-      k_block<float2, 3><<<grid, kThreads, 0, s>>>(oct, N, odd, rows, nrows, cols, ncols, o, flag);
+      k_block<float2, 3><<<grid, kThreads, 0, s>>>(t, N, odd, rows, nrows, cols, ncols, o, flag);
     else
-      k_block<float2, 2><<<grid, kThreads, 0, s>>>(oct, N, odd, rows, nrows, cols, ncols, o, flag);
+      k_block<float2, 2><<<grid, kThreads, 0, s>>>(t, N, odd, rows, nrows, cols, ncols, o, flag);
   }
   return finish(plan, flag);
 }

@@ -459,6 +459,19 @@ cudaError_t launch_axis_transform(const double2* in, double2* out, const double*
   return cudaGetLastError();
 }
 
+// out = in rounded to FP32 (the FP32 copy of a kernel octant)
+__global__ void narrow_kernel(const double2* __restrict__ in, float2* __restrict__ out, long long count) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
+    out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+
+cudaError_t launch_narrow(const double2* in, float2* out, long long count, cudaStream_t s) {
+  long long blocks = (count + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  narrow_kernel<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, s>>>(in, out, count);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_finalize(const double2* in, double2* out_u, double2* out64, float2* out32, long long count,
                             double scale, int times_minus_i, cudaStream_t s) {
   long long blocks = (count + 255) / 256;

@@ -45,6 +45,9 @@ struct vp_plan_s {
   double2* G64 = nullptr;   // scaled by 1/(2N)^d
   float2* G32 = nullptr;
   double2* Tj64[3] = {nullptr, nullptr, nullptr};
+  // FP32 copies of T and T_j for FP32 Nystrom entries (built on first use)
+  float2* T32 = nullptr;
+  float2* Tj32[3] = {nullptr, nullptr, nullptr};
   double2* Gj64u[3] = {nullptr, nullptr, nullptr};
   double2* Gj64[3] = {nullptr, nullptr, nullptr};
   float2* Gj32[3] = {nullptr, nullptr, nullptr};
@@ -616,6 +619,19 @@ vp_status plan_kernel_octant(vp_plan p, int which, int axis, const double2** oct
   return VP_OK;
 }
 
+vp_status plan_kernel_octant32(vp_plan p, int which, int axis, const float2** oct) {
+  const double2* o64 = nullptr;
+  vp_status st = plan_kernel_octant(p, which, axis, &o64);
+  if (st != VP_OK) return st;
+  float2** slot = which == VP_ARRAY_T ? &p->T32 : &p->Tj32[axis];
+  if (!*slot) {
+    VP_CUDA(p, dalloc(p, slot, p->oct));
+    VP_CUDA(p, launch_narrow(o64, *slot, p->oct, p->stream));
+  }
+  *oct = *slot;
+  return VP_OK;
+}
+
 int* plan_flag_word(vp_plan p) {
   if (!p->d_flag && cudaMalloc(&p->d_flag, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
@@ -887,11 +903,13 @@ vp_status vp_destroy(vp_plan p) {
   cudaSetDevice(p->device);
   if (p->stream) cudaStreamSynchronize(p->stream);
   cudaFree(p->T64);
+  cudaFree(p->T32);
   cudaFree(p->G64u);
   cudaFree(p->G64);
   cudaFree(p->G32);
   for (int j = 0; j < 3; ++j) {
     cudaFree(p->Tj64[j]);
+    cudaFree(p->Tj32[j]);
     cudaFree(p->Gj64u[j]);
     cudaFree(p->Gj64[j]);
     cudaFree(p->Gj32[j]);

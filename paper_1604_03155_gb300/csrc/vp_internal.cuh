@@ -23,6 +23,7 @@ cudaError_t launch_spectrum(double2* G, int d, int N, int kernel, double k, doub
 cudaError_t launch_matrix(double* M, int N, int type, cudaStream_t s);
 cudaError_t launch_axis_transform(const double2* in, double2* out, const double* M, long long O, int P, int Q,
                                   long long I, cudaStream_t s);
+cudaError_t launch_narrow(const double2* in, float2* out, long long count, cudaStream_t s);
 cudaError_t launch_finalize(const double2* in, double2* out_u, double2* out64, float2* out32, long long count,
                             double scale, int times_minus_i, cudaStream_t s);
 cudaError_t launch_twiddles(double2* tw64, float2* tw32, int n, cudaStream_t s);
@@ -74,6 +75,7 @@ int plan_is_fp64(vp_plan p);
 // VP_ARRAY_T) or T_axis (VP_ARRAY_TJ, built on first use), a device flag word
 // owned by the plan, and the plan's error message.
 vp_status plan_kernel_octant(vp_plan p, int which, int axis, const double2** oct);
+vp_status plan_kernel_octant32(vp_plan p, int which, int axis, const float2** oct);
 int* plan_flag_word(vp_plan p);
 vp_status entries_fail(vp_plan p, vp_status st, const char* msg);
 // ls.cu: the message vp_ls_last_error returns on this thread

@@ -1,15 +1,20 @@
-// bicgstab.cu -- the scattering solver of Section 5.3 (Vico, Greengard &
-// Ferrando): unpreconditioned Bi-CGStab (van der Vorst 1992) on the
-// Lippmann-Schwinger equation, two operator products per iteration, each one
-// apply of the plan's volume potential V (the Green's function of
-// -(Delta + k^2)).
+// bicgstab.cu -- the integral-equation solvers of Sections 5.2 and 5.3 (Vico,
+// Greengard & Ferrando): unpreconditioned Bi-CGStab (van der Vorst 1992), two
+// operator products per iteration, each one apply of the plan's volume
+// potential V (or of its exact gradient).
 //
-// Two forms of one problem (u the scattered field, q the real contrast):
+// Lippmann-Schwinger scattering (Section 5.3; V the Green's function of
+// -(Delta + k^2)), two forms of one problem (u the scattered field, q the real
+// contrast):
 //   field:    A u = u - k^2 V[q u]   = k^2 V[q u_inc]
 //   density:  B s = s - k^2 q V[s]   = k^2 q u_inc,      u = V[s]
 // The density form is the paper's dual equation of Section 5.3 (s is the
 // source density whose potential is the scattered field); the field form is
 // the one the GMRES solver of ls.cu uses.  Both give the same u.
+// Variable-coefficient Poisson (Section 5.2, eq. pbeq; V the Laplace potential):
+//   P s = -eps s + grad(eps) . grad V[s] = rho,            phi = V[s]
+// Mixed precision (FP32 products, FP64 reliable updates) is described further
+// down, before solve_mixed.
 //
 // The recurrence (Saad, Iterative Methods for Sparse Linear Systems, Alg. 7.7,
 // with the early exit at the half step): x_0 = 0, r_0 = r^ = b, p_0 = r_0;

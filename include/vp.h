@@ -114,6 +114,19 @@ typedef enum {
  * allocated on first use.  Synchronous: returns after the precompute. */
 vp_status vp_plan_create(vp_plan* out, int d, int N, vp_kernel kernel, double k, double L);
 
+/* The same on a grid with N[j] points along axis j (axis 0 slowest; each N[j]
+ * even, >= 4, 2 N[j] a built length): h_j = 1/N[j] on the same unit box.  The
+ * spectrum is sampled at s_m = (pi/2) m on the per-axis 4 N[j] grids (the
+ * frequency step is pi/2 on every axis) and every transform of Section 4 runs
+ * per axis with that axis's length; arrays are C order [N0][N1]([N2]), octants
+ * [N0+1][N1+1]([N2+1]).  Serves vp_apply, vp_apply_grad, vp_apply_noalloc, the
+ * Nystrom entries and the Bi-CGStab solvers; the tensor-core precisions, the
+ * batch and the FGMRES/U-Net solver take cubic plans only (VP_ERR_UNSUPPORTED /
+ * VP_ERR_INVALID_ARG). */
+vp_status vp_plan_create_aniso(vp_plan* out, int d, const int* N, vp_kernel kernel, double k, double L);
+/* Points per axis (d ints). */
+vp_status vp_plan_dims(vp_plan plan, int* N);
+
 /* Nystrom matrix entries on the fly (Section 4, the remark after the discrete
  * convolution): T is the matrix of a high-order Nystrom discretisation of the
  * volume integral, phi_p = sum_{p'} T(p - p') f_{p'} (weight h^d included).
@@ -152,12 +165,13 @@ vp_status vp_apply(vp_plan plan, const void* f, void* phi, vp_dtype dtype);
  * ... at the cost of an additional FFT").  grad: d * N^d elements. */
 vp_status vp_apply_grad(vp_plan plan, const void* f, void* phi, void* grad, vp_dtype dtype);
 
-/* Copies a precomputed FP64 octant ((N+1)^d complex128 = 2 (N+1)^d doubles) to
+/* Copies a precomputed FP64 octant (prod_j (N_j+1) complex128 = 2 prod_j (N_j+1) doubles) to
  * host memory.  `axis` selects j for the gradient arrays (ignored otherwise);
  * `count` is the number of doubles available at host_dst. */
 vp_status vp_plan_get_array(vp_plan plan, vp_array which, int axis, double* host_dst, size_t count);
 
-/* Plan parameters and the device bytes it currently holds. */
+/* Plan parameters and the device bytes it currently holds (N: the points of
+ * axis 0; vp_plan_dims gives every axis). */
 vp_status vp_plan_info(vp_plan plan, int* d, int* N, double* k, double* L, size_t* device_bytes);
 
 /* Per-pass device timing with CUDA events recorded on the plan's stream

@@ -498,7 +498,7 @@ vp_status vp_batch_create(vp_batch* out, int count, const vp_plan* plans) {
   size_t ws_elems = 0;
   std::vector<size_t> ws_off(count);
   for (int i = 0; i < count; ++i) {
-    if (!plans[i] || !plan_is_fp32(plans[i])) {
+    if (!plans[i] || !plan_is_fp32(plans[i]) || plan_is_aniso(plans[i])) {  // cubic FP32 plans
       delete b;
       return VP_ERR_INVALID_ARG;
     }

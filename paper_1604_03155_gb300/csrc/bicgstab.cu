@@ -1074,7 +1074,7 @@ vp_status check_args(vp_plan plan, bool pb, const void* q, const void* ge, const
     if (form != VP_LS_FIELD && form != VP_LS_DENSITY) return bad("form must be VP_LS_FIELD or VP_LS_DENSITY");
   }
   if (!(tol > 0) || maxit < 1) return bad("tol > 0 and maxit >= 1 required");
-  *n = (long long)N * N * (*d == 3 ? N : 1);
+  *n = vp::plan_points(plan);  // prod_j N_j
   return VP_OK;
 }
 

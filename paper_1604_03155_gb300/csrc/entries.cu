@@ -24,15 +24,18 @@ constexpr int kMaxBlocks = 152 * 32;
 
 // T(n) for an offset n (|n_j| <= N), from the octant of the output's precision
 // (D = d: the loops unroll and the index arrays stay in registers)
+struct Dims {
+  int N[3];  // points per axis (N_j; 1 beyond d)
+};
+
 template <typename C, int D>
-__device__ __forceinline__ C gather(const C* __restrict__ oct, int N, int odd_axis, const int (&n)[3]) {
-  const long long M = N + 1;
+__device__ __forceinline__ C gather(const C* __restrict__ oct, const Dims& g, int odd_axis, const int (&n)[3]) {
   long long idx = 0;
   int sgn = 1;
 #pragma unroll
   for (int j = 0; j < D; ++j) {
     const int a = n[j] < 0 ? -n[j] : n[j];
-    idx = idx * M + a;
+    idx = idx * (g.N[j] + 1) + a;
     if (j == odd_axis) sgn = n[j] > 0 ? 1 : (n[j] < 0 ? -1 : 0);
   }
   C v = __ldg(oct + idx);
@@ -44,7 +47,7 @@ __device__ __forceinline__ C gather(const C* __restrict__ oct, int N, int odd_ax
 }
 
 template <typename C, int D>
-__global__ void __launch_bounds__(kThreads) k_entries(const C* __restrict__ oct, int N, int odd_axis,
+__global__ void __launch_bounds__(kThreads) k_entries(const C* __restrict__ oct, Dims g, int odd_axis,
                                                       const int* __restrict__ off, long long count, C* __restrict__ out,
                                                       int* __restrict__ bad) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
@@ -54,14 +57,14 @@ __global__ void __launch_bounds__(kThreads) k_entries(const C* __restrict__ oct,
 #pragma unroll
     for (int j = 0; j < D; ++j) {
       n[j] = off[i * D + j];
-      ok = ok && n[j] >= -N && n[j] <= N;
+      ok = ok && n[j] >= -g.N[j] && n[j] <= g.N[j];
     }
     if (!ok) {
       out[i] = C{0, 0};
       atomicExch(bad, 1);
       continue;
     }
-    out[i] = gather<C, D>(oct, N, odd_axis, n);
+    out[i] = gather<C, D>(oct, g, odd_axis, n);
   }
 }
 
@@ -73,13 +76,13 @@ constexpr int kTileRows = 16;
 constexpr int kGroup = 8;
 
 template <typename C, int D>
-__global__ void __launch_bounds__(kThreads, 4) k_block(const C* __restrict__ oct, int N, int odd_axis,
+__global__ void __launch_bounds__(kThreads, 4) k_block(const C* __restrict__ oct, Dims g, int odd_axis,
                                                     const long long* __restrict__ rows, long long nr,
                                                     const long long* __restrict__ cols, long long nc,
                                                     C* __restrict__ out, int* __restrict__ bad) {
   __shared__ int srow[kTileRows][3];
   __shared__ int sok[kTileRows];
-  const long long U = D == 3 ? (long long)N * N * N : (long long)N * N;
+  const long long U = D == 3 ? (long long)g.N[0] * g.N[1] * g.N[2] : (long long)g.N[0] * g.N[1];
   const long long c = blockIdx.x * (long long)kThreads + threadIdx.x;
   int q[3] = {0, 0, 0};
   bool cok = false;
@@ -89,8 +92,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_block(const C* __restrict__ oct
     if (cok) {
 #pragma unroll
       for (int a = D - 1; a >= 0; --a) {
-        q[a] = (int)(cc % N);
-        cc /= N;
+        q[a] = (int)(cc % g.N[a]);
+        cc /= g.N[a];
       }
     } else {
       atomicExch(bad, 1);
@@ -107,8 +110,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_block(const C* __restrict__ oct
         if (ok) {
 #pragma unroll
           for (int a = D - 1; a >= 0; --a) {
-            srow[threadIdx.x][a] = (int)(rr % N);
-            rr /= N;
+            srow[threadIdx.x][a] = (int)(rr % g.N[a]);
+            rr /= g.N[a];
           }
         } else if (blockIdx.x == 0) {
           atomicExch(bad, 1);
@@ -124,19 +127,19 @@ __global__ void __launch_bounds__(kThreads, 4) k_block(const C* __restrict__ oct
     for (int i0 = 0; i0 < kTileRows; i0 += kGroup) {
       C v[kGroup];
 #pragma unroll
-      for (int g = 0; g < kGroup; ++g) {
-        const int i = i0 + g;
-        v[g] = C{0, 0};
+      for (int k = 0; k < kGroup; ++k) {
+        const int i = i0 + k;
+        v[k] = C{0, 0};
         if (i < nrows && cok && sok[i]) {
           int n[3] = {0, 0, 0};
 #pragma unroll
           for (int a = 0; a < D; ++a) n[a] = srow[i][a] - q[a];
-          v[g] = gather<C, D>(oct, N, odd_axis, n);
+          v[k] = gather<C, D>(oct, g, odd_axis, n);
         }
       }
 #pragma unroll
-      for (int g = 0; g < kGroup; ++g)
-        if (i0 + g < nrows) out[(r0 + i0 + g) * nc + c] = v[g];
+      for (int k = 0; k < kGroup; ++k)
+        if (i0 + k < nrows) out[(r0 + i0 + k) * nc + c] = v[k];
     }
   }
 }
@@ -208,6 +211,8 @@ vp_status vp_kernel_entries(vp_plan plan, int which, int axis, const int* offset
   if (st != VP_OK) return st;
   int d = 0, N = 0;
   vp_plan_info(plan, &d, &N, nullptr, nullptr, nullptr);
+  Dims dims;
+  vp::plan_dims(plan, dims.N);
   cudaStream_t s = vp::plan_stream(plan);
   cudaMemsetAsync(flag, 0, sizeof(int), s);
   const unsigned g = grid_for(count);
@@ -215,16 +220,16 @@ vp_status vp_kernel_entries(vp_plan plan, int which, int axis, const int* offset
     auto o = reinterpret_cast<double2*>(out);
     auto t = reinterpret_cast<const double2*>(oct);
     if (d == 3)
-      k_entries<double2, 3><<<g, kThreads, 0, s>>>(t, N, odd, offsets, count, o, flag);
+      k_entries<double2, 3><<<g, kThreads, 0, s>>>(t, dims, odd, offsets, count, o, flag);
     else
-      k_entries<double2, 2><<<g, kThreads, 0, s>>>(t, N, odd, offsets, count, o, flag);
+      k_entries<double2, 2><<<g, kThreads, 0, s>>>(t, dims, odd, offsets, count, o, flag);
   } else {
     auto o = reinterpret_cast<float2*>(out);
     auto t = reinterpret_cast<const float2*>(oct);
     if (d == 3)
-      k_entries<float2, 3><<<g, kThreads, 0, s>>>(t, N, odd, offsets, count, o, flag);
+      k_entries<float2, 3><<<g, kThreads, 0, s>>>(t, dims, odd, offsets, count, o, flag);
     else
-      k_entries<float2, 2><<<g, kThreads, 0, s>>>(t, N, odd, offsets, count, o, flag);
+      k_entries<float2, 2><<<g, kThreads, 0, s>>>(t, dims, odd, offsets, count, o, flag);
   }
   return finish(plan, flag);
 }
@@ -240,6 +245,8 @@ vp_status vp_matrix_block(vp_plan plan, int which, int axis, const long long* ro
   if (st != VP_OK) return st;
   int d = 0, N = 0;
   vp_plan_info(plan, &d, &N, nullptr, nullptr, nullptr);
+  Dims dims;
+  vp::plan_dims(plan, dims.N);
   cudaStream_t s = vp::plan_stream(plan);
   cudaMemsetAsync(flag, 0, sizeof(int), s);
   const long long gx = (ncols + kThreads - 1) / kThreads;
@@ -253,16 +260,16 @@ vp_status vp_matrix_block(vp_plan plan, int which, int axis, const long long* ro
     auto o = reinterpret_cast<double2*>(out);
     auto t = reinterpret_cast<const double2*>(oct);
     if (d == 3)
-      k_block<double2, 3><<<grid, kThreads, 0, s>>>(t, N, odd, rows, nrows, cols, ncols, o, flag);
+      k_block<double2, 3><<<grid, kThreads, 0, s>>>(t, dims, odd, rows, nrows, cols, ncols, o, flag);
     else
-      k_block<double2, 2><<<grid, kThreads, 0, s>>>(t, N, odd, rows, nrows, cols, ncols, o, flag);
+      k_block<double2, 2><<<grid, kThreads, 0, s>>>(t, dims, odd, rows, nrows, cols, ncols, o, flag);
   } else {
     auto o = reinterpret_cast<float2*>(out);
     auto t = reinterpret_cast<const float2*>(oct);
     if (d == 3)
-      k_block<float2, 3><<<grid, kThreads, 0, s>>>(t, N, odd, rows, nrows, cols, ncols, o, flag);
+      k_block<float2, 3><<<grid, kThreads, 0, s>>>(t, dims, odd, rows, nrows, cols, ncols, o, flag);
     else
-      k_block<float2, 2><<<grid, kThreads, 0, s>>>(t, N, odd, rows, nrows, cols, ncols, o, flag);
+      k_block<float2, 2><<<grid, kThreads, 0, s>>>(t, dims, odd, rows, nrows, cols, ncols, o, flag);
   }
   return finish(plan, flag);
 }

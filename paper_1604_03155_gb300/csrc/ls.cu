@@ -515,7 +515,8 @@ vp_status check_plan(vp_plan plan, long long* n, double* k2) {
   if (!plan) return ls_fail(VP_ERR_INVALID_ARG, "plan is NULL");
   vp_status st = vp_plan_info(plan, &d, &N, &k, nullptr, nullptr);
   if (st != VP_OK) return st;
-  if (d != 3 || !(k > 0)) return ls_fail(VP_ERR_INVALID_ARG, "the scattering solve needs a 3D Helmholtz plan");
+  if (d != 3 || !(k > 0) || vp::plan_is_aniso(plan))
+    return ls_fail(VP_ERR_INVALID_ARG, "the scattering solve needs a cubic 3D Helmholtz plan");
   if (!vp::plan_is_fp32(plan)) return ls_fail(VP_ERR_INVALID_ARG, "the scattering solve iterates in FP32: set the plan's precision to VP_FP32");
   *n = (long long)N * N * N;
   *k2 = k * k;

@@ -311,7 +311,9 @@ template <typename Real> struct PassArgs {
   // fused pass only
   int nfields;
   int d;
-  int Nh;  // N = n/2
+  int Nh;      // N = n/2 of the fused axis (axis 0)
+  int nn[3];   // transform length 2 N_j of every axis (the grid may differ per axis)
+  int Nhs[3];  // N_j
   FieldDesc fields[4];
 };
 
@@ -580,18 +582,20 @@ __device__ __forceinline__ void process_tile(const PassArgs<Real>& a, long long 
         }
     }
   } else {
-    // frequencies of the other axes (fused axis = axis 0, the slowest)
-    const int Nh = a.Nh;
-    const int np1 = Nh + 1;
+    // frequencies of the other axes (fused axis = axis 0, the slowest); the
+    // multiplier octant is [N_0 + 1][N_1 + 1]([N_2 + 1])
+    const int n1 = a.nn[1], n2 = a.nn[2];
     int m1 = 0, m2 = 0;
     if (a.d == 3) {
-      m1 = inner / n;
-      m2 = inner % n;
+      m1 = inner / n2;
+      m2 = inner % n2;
     } else {
       m1 = inner;
     }
-    const long long oct_rest = (a.d == 3) ? (long long)fold_freq(m1, n) * np1 + fold_freq(m2, n) : fold_freq(m1, n);
-    const long long oct_pitch0 = (a.d == 3) ? (long long)np1 * np1 : np1;
+    const long long np1_1 = a.Nhs[1] + 1, np1_2 = a.Nhs[2] + 1;
+    const long long oct_rest =
+        (a.d == 3) ? (long long)fold_freq(m1, n1) * np1_2 + fold_freq(m2, n2) : fold_freq(m1, n1);
+    const long long oct_pitch0 = (a.d == 3) ? np1_1 * np1_2 : np1_1;
     constexpr int RL = stage_radix(n, E, false, NS - 1);  // == first inverse radix
     // multiplier of field 0, issued before the forward transform to hide its latency
     C g[E];
@@ -629,11 +633,15 @@ __device__ __forceinline__ void process_tile(const PassArgs<Real>& a, long long 
           C gg = g[q * RL + r];
           if (fd.odd_axis >= 0) {
             const int mj = fd.odd_axis == 0 ? m0 : (fd.odd_axis == 1 ? m1 : m2);
-            if (mj > Nh) gg = C{-gg.x, -gg.y};
+            const int Nj = fd.odd_axis == 0 ? a.Nhs[0] : (fd.odd_axis == 1 ? a.Nhs[1] : a.Nhs[2]);
+            if (mj > Nj) gg = C{-gg.x, -gg.y};
           }
           if (fd.spectral_axis >= 0) {
-            const int mj = fd.spectral_axis == 0 ? m0 : (fd.spectral_axis == 1 ? m1 : m2);
-            const int ms = mj < Nh ? mj : (mj == Nh ? 0 : mj - n);
+            const int j = fd.spectral_axis;
+            const int mj = j == 0 ? m0 : (j == 1 ? m1 : m2);
+            const int Nj = j == 0 ? a.Nhs[0] : (j == 1 ? a.Nhs[1] : a.Nhs[2]);
+            const int nj = j == 0 ? a.nn[0] : (j == 1 ? a.nn[1] : a.nn[2]);
+            const int ms = mj < Nj ? mj : (mj == Nj ? 0 : mj - nj);
             const Real f = (Real)3.14159265358979323846 * (Real)ms;
             gg = C{-gg.y * f, gg.x * f};  // i pi m_j * g
           }

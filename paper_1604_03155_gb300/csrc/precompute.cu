@@ -270,18 +270,19 @@ __device__ double2 g_biharm2(double s, double L) {
                       0.0);
 }
 
-__global__ void spectrum_octant_kernel(double2* __restrict__ G, int d, int N, int kernel, double k, double L) {
-  const int M1 = 2 * N + 1;
-  const long long total = (d == 3) ? (long long)M1 * M1 * M1 : (long long)M1 * M1;
+// G at m in prod_j [0, 2N_j]: extents e0 x e1 (x e2), e_j = 2 N_j + 1 (e2 = 1 in 2D),
+// the last axis fastest
+__global__ void spectrum_octant_kernel(double2* __restrict__ G, int d, int e0, int e1, int e2, int kernel, double k,
+                                       double L) {
+  const long long total = (long long)e0 * e1 * e2;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
     long long r = idx;
-    const int m2 = (int)(r % M1);
-    r /= M1;
-    const int m1 = (int)(r % M1);
-    r /= M1;
-    const int m0 = (int)r;
-    const double msq = (double)m2 * m2 + (double)m1 * m1 + (d == 3 ? (double)m0 * m0 : 0.0);
+    const int m2 = (int)(r % e2);
+    r /= e2;
+    const int m1 = (int)(r % e1);
+    const int m0 = (int)(r / e1);
+    const double msq = (double)m0 * m0 + (double)m1 * m1 + (double)m2 * m2;
     const double s = 0.5 * 3.14159265358979323846 * sqrt(msq);
     double2 v;
     if (kernel == 2)
@@ -430,12 +431,12 @@ cudaError_t set_gauss_legendre(const double* x, const double* w) {
   return cudaMemcpyToSymbol(c_gl_w, w, sizeof(double) * GL_NODES);
 }
 
-cudaError_t launch_spectrum(double2* G, int d, int N, int kernel, double k, double L, cudaStream_t s) {
-  const long long M1 = 2LL * N + 1;
-  const long long total = d == 3 ? M1 * M1 * M1 : M1 * M1;
+cudaError_t launch_spectrum(double2* G, int d, const int* M1s, int kernel, double k, double L, cudaStream_t s) {
+  const int e0 = M1s[0], e1 = M1s[1], e2 = d == 3 ? M1s[2] : 1;
+  const long long total = (long long)e0 * e1 * e2;
   long long blocks = (total + 255) / 256;
   if (blocks > 152LL * 64) blocks = 152LL * 64;
-  spectrum_octant_kernel<<<(unsigned)blocks, 256, 0, s>>>(G, d, N, kernel, k, L);
+  spectrum_octant_kernel<<<(unsigned)blocks, 256, 0, s>>>(G, d, e0, e1, e2, kernel, k, L);
   return cudaGetLastError();
 }
 

@@ -31,6 +31,9 @@ enum { P_FWD_ROWS = 0, P_FWD_AX1 = 1, P_FUSED = 2, P_INV_AX1 = 3, P_INV_ROWS = 4
 
 struct vp_plan_s {
   int d = 0, N = 0, kernel = 0;
+  // points per axis (all N for a cubic grid; axis 0 slowest); aniso: not all equal
+  int Nv[3] = {0, 0, 0};
+  int aniso = 0;
   double k = 0.0, L = 0.0;
   int n2 = 0;  // FFT length 2N
   int device = 0;
@@ -52,8 +55,10 @@ struct vp_plan_s {
   double2* Gj64[3] = {nullptr, nullptr, nullptr};
   float2* Gj32[3] = {nullptr, nullptr, nullptr};
   bool grad_built = false;
-  double2* tw64 = nullptr;
+  double2* tw64 = nullptr;  // twiddles of axis 0 (every axis of a cubic grid)
   float2* tw32 = nullptr;
+  double2* twv64[3] = {nullptr, nullptr, nullptr};  // per axis; twv[j] may alias an earlier axis's table
+  float2* twv32[3] = {nullptr, nullptr, nullptr};
   // tensor-core fused pass (VP_TC_*): DFT matrices of the current split, error word
   uint16_t* tcB = nullptr;
   int tc_split = -1;
@@ -147,60 +152,84 @@ struct Scratch {
   double2* t0 = nullptr;
   double2* t1 = nullptr;
   double2* Traw = nullptr;
-  double* C4 = nullptr;
-  double* S4 = nullptr;
-  double* C2 = nullptr;
-  double* S2 = nullptr;
+  // per-axis transform matrices; an axis with the same N as an earlier one shares them
+  double* C4[3] = {nullptr, nullptr, nullptr};
+  double* S4[3] = {nullptr, nullptr, nullptr};
+  double* C2[3] = {nullptr, nullptr, nullptr};
+  double* S2[3] = {nullptr, nullptr, nullptr};
+  bool own[3] = {false, false, false};
   void release() {
     cudaFree(G);
     cudaFree(t0);
     cudaFree(t1);
     cudaFree(Traw);
-    cudaFree(C4);
-    cudaFree(S4);
-    cudaFree(C2);
-    cudaFree(S2);
+    for (int a = 0; a < 3; ++a)
+      if (own[a]) {
+        cudaFree(C4[a]);
+        cudaFree(S4[a]);
+        cudaFree(C2[a]);
+        cudaFree(S2[a]);
+      }
     *this = Scratch();
   }
 };
 
 cudaError_t scratch_alloc(vp_plan p, Scratch& sc) {
-  const long long M1 = 2LL * p->N + 1, Np1 = p->N + 1;
-  const long long gsz = p->d == 3 ? M1 * M1 * M1 : M1 * M1;
-  const long long tsz = p->d == 3 ? Np1 * M1 * M1 : Np1 * M1;
+  long long gsz = 1, tsz = 1;
+  int M1s[3] = {1, 1, 1};
+  for (int a = 0; a < p->d; ++a) {
+    M1s[a] = 2 * p->Nv[a] + 1;
+    gsz *= M1s[a];
+    tsz *= (a == 0) ? p->Nv[a] + 1 : M1s[a];  // the chain's largest intermediate (after axis 0)
+  }
   cudaError_t e;
   if ((e = cudaMalloc(&sc.G, gsz * sizeof(double2))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&sc.t0, tsz * sizeof(double2))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&sc.t1, tsz * sizeof(double2))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&sc.Traw, p->oct * sizeof(double2))) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&sc.C4, Np1 * M1 * sizeof(double))) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&sc.S4, Np1 * M1 * sizeof(double))) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&sc.C2, Np1 * Np1 * sizeof(double))) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&sc.S2, Np1 * Np1 * sizeof(double))) != cudaSuccess) return e;
-  if ((e = launch_matrix(sc.C4, p->N, 0, 0)) != cudaSuccess) return e;
-  if ((e = launch_matrix(sc.S4, p->N, 1, 0)) != cudaSuccess) return e;
-  if ((e = launch_matrix(sc.C2, p->N, 2, 0)) != cudaSuccess) return e;
-  if ((e = launch_matrix(sc.S2, p->N, 3, 0)) != cudaSuccess) return e;
-  return launch_spectrum(sc.G, p->d, p->N, p->kernel, p->k, p->L, 0);
+  for (int a = 0; a < p->d; ++a) {
+    int same = -1;
+    for (int b = 0; b < a; ++b)
+      if (p->Nv[b] == p->Nv[a]) same = b;
+    if (same >= 0) {
+      sc.C4[a] = sc.C4[same];
+      sc.S4[a] = sc.S4[same];
+      sc.C2[a] = sc.C2[same];
+      sc.S2[a] = sc.S2[same];
+      continue;
+    }
+    const long long M1 = 2LL * p->Nv[a] + 1, Np1 = p->Nv[a] + 1;
+    sc.own[a] = true;
+    if ((e = cudaMalloc(&sc.C4[a], Np1 * M1 * sizeof(double))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&sc.S4[a], Np1 * M1 * sizeof(double))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&sc.C2[a], Np1 * Np1 * sizeof(double))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&sc.S2[a], Np1 * Np1 * sizeof(double))) != cudaSuccess) return e;
+    if ((e = launch_matrix(sc.C4[a], p->Nv[a], 0, 0)) != cudaSuccess) return e;
+    if ((e = launch_matrix(sc.S4[a], p->Nv[a], 1, 0)) != cudaSuccess) return e;
+    if ((e = launch_matrix(sc.C2[a], p->Nv[a], 2, 0)) != cudaSuccess) return e;
+    if ((e = launch_matrix(sc.S2[a], p->Nv[a], 3, 0)) != cudaSuccess) return e;
+  }
+  return launch_spectrum(sc.G, p->d, M1s, p->kernel, p->k, p->L, 0);
 }
 
 // T (odd_axis < 0) or T_j, then the multiplier, into the plan's arrays.
 cudaError_t build_kernel(vp_plan p, Scratch& sc, int odd_axis, double2* Tout, double2* Gu, double2* G64, float2* G32) {
-  const int M1 = 2 * p->N + 1, Np1 = p->N + 1;
-  int dims4[3] = {M1, M1, M1};
-  int qs[3] = {Np1, Np1, Np1};
+  int dims4[3], qs[3];
   double* m4[3];
   double* m2[3];
+  double scale = 1.0;
   for (int a = 0; a < 3; ++a) {
-    m4[a] = (a == odd_axis) ? sc.S4 : sc.C4;
-    m2[a] = (a == odd_axis) ? sc.S2 : sc.C2;
+    const int N = a < p->d ? p->Nv[a] : 1;
+    dims4[a] = 2 * N + 1;
+    qs[a] = N + 1;
+    m4[a] = (a == odd_axis) ? sc.S4[a] : sc.C4[a];
+    m2[a] = (a == odd_axis) ? sc.S2[a] : sc.C2[a];
+    if (a < p->d) scale /= 2.0 * N;
   }
   cudaError_t e = run_chain(sc.G, Tout, sc.t0, sc.t1, p->d, dims4, m4, qs, 0);
   if (e != cudaSuccess) return e;
-  int dims2[3] = {Np1, Np1, Np1};
-  e = run_chain(Tout, sc.Traw, sc.t0, sc.t1, p->d, dims2, m2, qs, 0);
+  e = run_chain(Tout, sc.Traw, sc.t0, sc.t1, p->d, qs, m2, qs, 0);
   if (e != cudaSuccess) return e;
-  const double scale = 1.0 / pow(2.0 * p->N, p->d);
   return launch_finalize(sc.Traw, Gu, G64, G32, p->oct, scale, odd_axis >= 0 ? 1 : 0, 0);
 }
 
@@ -267,7 +296,7 @@ void set_async(PassArgs<Real>& a, bool contig, int nin) {
 bool is_tc(vp_precision pr) { return pr == VP_TC_BF16X2 || pr == VP_TC_FP16X2 || pr == VP_TC_BF16X3; }
 
 template <typename Real>
-cudaError_t launch_pass(vp_plan p, int pass, PassKind kind, const PassArgs<Real>& a) {
+cudaError_t launch_pass(vp_plan p, int pass, PassKind kind, const PassArgs<Real>& a, int len) {
   TimedLaunch tl{pass, nullptr, nullptr};
   if (p->timing && p->timed.size() < 100000) {
     tl.start = pool_event(p);
@@ -286,11 +315,11 @@ cudaError_t launch_pass(vp_plan p, int pass, PassKind kind, const PassArgs<Real>
     t.tw = p->tw32;
     t.bmat = p->tcB;
     t.err = p->d_err;
-    e = launch_tc_fused(p->n2, p->tc_split, t, p->stream);
+    e = launch_tc_fused(len, p->tc_split, t, p->stream);
   } else if (sizeof(Real) == 4)
-    e = launch_pass_f32(kind, p->n2, reinterpret_cast<const PassArgs<float>&>(a), p->stream);
+    e = launch_pass_f32(kind, len, reinterpret_cast<const PassArgs<float>&>(a), p->stream);
   else
-    e = launch_pass_f64(kind, p->n2, reinterpret_cast<const PassArgs<double>&>(a), p->stream);
+    e = launch_pass_f64(kind, len, reinterpret_cast<const PassArgs<double>&>(a), p->stream);
   if (tl.start) {
     cudaEventRecord(tl.stop, p->stream);
     p->timed.push_back(tl);
@@ -300,9 +329,19 @@ cudaError_t launch_pass(vp_plan p, int pass, PassKind kind, const PassArgs<Real>
 
 // Workspace (complex Real elements, U = N^d): 3D: F x 2U (rows) + F x 4U
 // (two-axis spectra); 2D: F x 2U.
-size_t workspace_bytes(int d, int N, int F, size_t csize) {
-  const size_t U = (size_t)N * N * (d == 3 ? N : 1);
-  return (d == 3 ? (size_t)F * 6 * U : (size_t)F * 2 * U) * csize;
+// grid points of the plan
+size_t grid_points(vp_plan p) {
+  size_t U = 1;
+  for (int a = 0; a < p->d; ++a) U *= (size_t)p->Nv[a];
+  return U;
+}
+
+// scratch of one apply with F output fields: 3D rows F x [N0][N1][2N2] and
+// two-axis spectra F x [N0][2N1][2N2]; 2D F x [N0][2N1]
+size_t workspace_bytes(vp_plan p, int F, size_t csize) {
+  const size_t U = grid_points(p);
+  if (p->d == 3) return (size_t)F * (U * 2 + U * 4) * csize;
+  return (size_t)F * 2 * U * csize;
 }
 
 vp_status ensure_workspace(vp_plan p, size_t bytes) {
@@ -328,7 +367,7 @@ vp_status run_apply_ws(vp_plan p, void* ws, const void* f, void* const* outs, co
 template <typename Real>
 vp_status run_apply(vp_plan p, const void* f, void* const* outs, const FieldDesc* fields, int F, bool real_io) {
   using C = typename CxT<Real>::T;
-  vp_status st = ensure_workspace(p, workspace_bytes(p->d, p->N, F, sizeof(C)));
+  vp_status st = ensure_workspace(p, workspace_bytes(p, F, sizeof(C)));
   if (st != VP_OK) return st;
   return run_apply_ws<Real>(p, p->ws, f, outs, fields, F, real_io);
 }
@@ -339,6 +378,7 @@ template <typename Real>
 struct PassLaunch {
   int pass;
   PassKind kind;
+  int len;  // transform length of the pass's axis
   PassArgs<Real> a;
 };
 
@@ -346,101 +386,115 @@ template <typename Real>
 int build_pass_list(vp_plan p, void* ws, const void* f, void* const* outs, const FieldDesc* fields, int F,
                     bool real_io, PassLaunch<Real>* list) {
   using C = typename CxT<Real>::T;
-  const int N = p->N, n = p->n2, d = p->d;
-  const long long U = (long long)N * N * (d == 3 ? N : 1);
+  const int d = p->d;
+  // grid N0 x N1 (x N2), axis 0 slowest; transform lengths n_j = 2 N_j
+  const int N0 = p->Nv[0], N1 = p->Nv[1], N2 = d == 3 ? p->Nv[2] : 1;
+  const int n0 = 2 * N0, n1 = 2 * N1, n2 = 2 * N2;
+  const long long U = (long long)grid_points(p);
   C* wsA = reinterpret_cast<C*>(ws);    // rows: F x 2U
   C* wsB = wsA + (long long)F * 2 * U;  // 3D spectra: F x 4U
-  const C* tw = sizeof(Real) == 4 ? reinterpret_cast<const C*>(p->tw32) : reinterpret_cast<const C*>(p->tw64);
+  auto tw_of = [&](int axis) -> const C* {
+    return sizeof(Real) == 4 ? reinterpret_cast<const C*>(p->twv32[axis]) : reinterpret_cast<const C*>(p->twv64[axis]);
+  };
   int np = 0;
   PassArgs<Real> a;
   memset(&a, 0, sizeof(a));
-  a.tw = tw;
   a.d = d;
-  a.Nh = N;
-  auto push = [&](int pass, PassKind kind, bool contig, int nin) {
+  a.Nh = N0;
+  for (int j = 0; j < 3; ++j) {
+    a.Nhs[j] = j < d ? p->Nv[j] : 1;
+    a.nn[j] = 2 * a.Nhs[j];
+  }
+  auto push = [&](int pass, PassKind kind, bool contig, int nin, int axis) {
+    a.tw = tw_of(axis);
     set_async(a, contig, nin);
     list[np].pass = pass;
     list[np].kind = kind;
+    list[np].len = 2 * p->Nv[axis];
     list[np].a = a;
     ++np;
   };
-  // first pass: rows along the last axis, N -> 2N
+  const int last = d - 1;       // the contiguous axis
+  const int Nl = p->Nv[last];   // its points and transform length
+  const int nl = 2 * Nl;
+  // first pass: rows along the last axis, N_l -> 2N_l
   a.in = f;
   a.out = wsA;
-  a.O = (d == 3) ? N * N : N;
+  a.O = (int)(U / Nl);
   a.I = 1;
-  a.in_pitch_o = N;
+  a.in_pitch_o = Nl;
   a.in_pitch_pos = 1;
-  a.out_pitch_o = n;
+  a.out_pitch_o = nl;
   a.out_pitch_pos = 1;
   a.in_real = real_io;
-  push(P_FWD_ROWS, FWD_CONTIG, true, N);
+  push(P_FWD_ROWS, FWD_CONTIG, true, Nl, last);
   a.in_real = 0;
   if (d == 3) {
-    // axis 1, N -> 2N, slabs i0
+    // axis 1, N1 -> 2N1, slabs i0: [N0][N1][n2] -> [N0][n1][n2]
     a.in = wsA;
     a.out = wsB;
-    a.O = N;
-    a.I = n;
-    a.in_pitch_o = (long long)N * n;
-    a.in_pitch_pos = n;
-    a.out_pitch_o = (long long)n * n;
-    a.out_pitch_pos = n;
-    push(P_FWD_AX1, FWD_STRIDED, false, N);
-    // axis 0 fused, N -> N per field (field 0 in place)
+    a.O = N0;
+    a.I = n2;
+    a.in_pitch_o = (long long)N1 * n2;
+    a.in_pitch_pos = n2;
+    a.out_pitch_o = (long long)n1 * n2;
+    a.out_pitch_pos = n2;
+    push(P_FWD_AX1, FWD_STRIDED, false, N1, 1);
+    // axis 0 fused, N0 -> N0 per field (field 0 in place): [N0][n1][n2]
     a.in = wsB;
     a.out = wsB;
     a.O = 1;
-    a.I = n * n;
+    a.I = n1 * n2;
     a.in_pitch_o = 0;
-    a.in_pitch_pos = (long long)n * n;
+    a.in_pitch_pos = (long long)n1 * n2;
     a.out_pitch_o = 0;
-    a.out_pitch_pos = (long long)n * n;
-    a.out_field_stride = 4 * U;
+    a.out_pitch_pos = (long long)n1 * n2;
+    a.out_field_stride = (long long)N0 * n1 * n2;
     a.nfields = F;
     for (int i = 0; i < F; ++i) a.fields[i] = fields[i];
-    push(P_FUSED, FUSED_STRIDED, false, N);
+    push(P_FUSED, FUSED_STRIDED, false, N0, 0);
     a.nfields = 0;
-    // axis 1 inverse, 2N -> N, all fields as slabs
+    // axis 1 inverse, 2N1 -> N1, all fields as slabs: [F N0][n1][n2] -> [F N0][N1][n2]
     a.in = wsB;
     a.out = wsA;
-    a.O = F * N;
-    a.I = n;
-    a.in_pitch_o = (long long)n * n;
-    a.in_pitch_pos = n;
-    a.out_pitch_o = (long long)N * n;
-    a.out_pitch_pos = n;
-    push(P_INV_AX1, INV_STRIDED, false, n);
+    a.O = F * N0;
+    a.I = n2;
+    a.in_pitch_o = (long long)n1 * n2;
+    a.in_pitch_pos = n2;
+    a.out_pitch_o = (long long)N1 * n2;
+    a.out_pitch_pos = n2;
+    push(P_INV_AX1, INV_STRIDED, false, n1, 1);
   } else {
-    // axis 0 fused (field 0 in place)
+    // axis 0 fused (field 0 in place): [N0][n1]
     a.in = wsA;
     a.out = wsA;
     a.O = 1;
-    a.I = n;
+    a.I = n1;
     a.in_pitch_o = 0;
-    a.in_pitch_pos = n;
+    a.in_pitch_pos = n1;
     a.out_pitch_o = 0;
-    a.out_pitch_pos = n;
-    a.out_field_stride = 2 * U;
+    a.out_pitch_pos = n1;
+    a.out_field_stride = (long long)N0 * n1;
     a.nfields = F;
     for (int i = 0; i < F; ++i) a.fields[i] = fields[i];
-    push(P_FUSED, FUSED_STRIDED, false, N);
+    push(P_FUSED, FUSED_STRIDED, false, N0, 0);
     a.nfields = 0;
   }
-  // rows inverse, 2N -> N, all fields in one launch
+  (void)n0;
+  // rows inverse, 2N_l -> N_l, all fields in one launch
   a.in = wsA;
   a.out = outs[0];
-  a.O = F * ((d == 3) ? N * N : N);
+  a.O = (int)(F * (U / Nl));
   a.I = 1;
-  a.in_pitch_o = n;
+  a.in_pitch_o = nl;
   a.in_pitch_pos = 1;
-  a.out_pitch_o = N;
+  a.out_pitch_o = Nl;
   a.out_pitch_pos = 1;
   a.out_real = real_io;
   a.nout = F;
-  a.rows_per_field = (d == 3) ? (long long)N * N : N;
+  a.rows_per_field = (long long)(U / Nl);
   for (int i = 0; i < F; ++i) a.outs[i] = outs[i];
-  push(P_INV_ROWS, INV_CONTIG, true, n);
+  push(P_INV_ROWS, INV_CONTIG, true, nl, last);
   return np;
 }
 
@@ -452,7 +506,7 @@ vp_status run_apply_ws(vp_plan p, void* ws, const void* f, void* const* outs, co
   static const char* what[NPASS] = {"pass fwd_rows", "pass fwd_axis1", "pass fused_axis0", "pass inv_axis1",
                                     "pass inv_rows"};
   for (int i = 0; i < np; ++i) {
-    cudaError_t e = launch_pass<Real>(p, list[i].pass, list[i].kind, list[i].a);
+    cudaError_t e = launch_pass<Real>(p, list[i].pass, list[i].kind, list[i].a, list[i].len);
     if (e != cudaSuccess) return cuda_fail(p, e, what[list[i].pass]);
   }
   return VP_OK;
@@ -492,7 +546,7 @@ vp_status apply_common(vp_plan p, const void* f, void* phi, void* grad, vp_dtype
   }
   const bool fp64 = p->prec == VP_FP64;
   const size_t eb = elem_bytes(dtype);
-  const size_t U = (size_t)p->N * p->N * (p->d == 3 ? p->N : 1);
+  const size_t U = grid_points(p);
 
   FieldDesc fields[4];
   int F = 0;
@@ -571,6 +625,14 @@ vp_status entries_fail(vp_plan p, vp_status st, const char* msg) { return fail(p
 
 int plan_kernel(vp_plan p) { return p ? p->kernel : -1; }
 
+int plan_is_aniso(vp_plan p) { return p ? p->aniso : 0; }
+
+long long plan_points(vp_plan p) { return p ? (long long)grid_points(p) : 0; }
+
+void plan_dims(vp_plan p, int* N) {
+  for (int a = 0; a < 3; ++a) N[a] = a < p->d ? p->Nv[a] : 1;
+}
+
 vp_status plan_prepare_grad(vp_plan p) {
   VP_CUDA(p, cudaSetDevice(p->device));
   return build_grad(p);
@@ -578,7 +640,7 @@ vp_status plan_prepare_grad(vp_plan p) {
 
 size_t plan_grad_workspace_bytes(vp_plan p) {
   const size_t csize = p->prec == VP_FP64 ? sizeof(double2) : sizeof(float2);
-  return workspace_bytes(p->d, p->N, p->d, csize);
+  return workspace_bytes(p, p->d, csize);
 }
 
 vp_status apply_grad_with_workspace(vp_plan p, const void* f, void* grad, vp_dtype dtype, void* ws, size_t ws_bytes) {
@@ -590,7 +652,7 @@ vp_status apply_grad_with_workspace(vp_plan p, const void* f, void* grad, vp_dty
   if (!p->grad_built) return fail(p, VP_ERR_INVALID_ARG, "the derivative multipliers are not built");
   if (ws_bytes < plan_grad_workspace_bytes(p)) return fail(p, VP_ERR_UNSUPPORTED, "gradient workspace too small");
   const bool fp64 = p->prec == VP_FP64;
-  const size_t U = (size_t)p->N * p->N * (p->d == 3 ? p->N : 1);
+  const size_t U = grid_points(p);
   FieldDesc fields[3];
   void* outs[3];
   for (int j = 0; j < p->d; ++j) {
@@ -654,7 +716,7 @@ int plan_pass_args_f32(vp_plan p, float2* ws, PassArgs<float>* args, int* kinds)
 
 size_t plan_apply_workspace_bytes(vp_plan p) {
   const size_t csize = p->prec == VP_FP64 ? sizeof(double2) : sizeof(float2);
-  return workspace_bytes(p->d, p->N, 1, csize);
+  return workspace_bytes(p, 1, csize);
 }
 
 vp_status apply_with_workspace(vp_plan p, const void* f, void* phi, vp_dtype dtype, void* ws, size_t ws_bytes) {
@@ -689,11 +751,14 @@ extern "C" {
 
 int vp_fft_length_supported(int n2) { return fft_length_built(n2) ? 1 : 0; }
 
-vp_status vp_plan_create(vp_plan* out, int d, int N, vp_kernel kernel, double k, double L) {
+namespace {
+
+vp_status plan_create_common(vp_plan* out, int d, const int* Ns, vp_kernel kernel, double k, double L) {
   if (!out) return fail(nullptr, VP_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (d != 2 && d != 3) return fail(nullptr, VP_ERR_INVALID_ARG, "d must be 2 or 3");
-  if (N < 4 || N % 2) return fail(nullptr, VP_ERR_INVALID_ARG, "N must be even and >= 4");
+  for (int a = 0; a < d; ++a)
+    if (Ns[a] < 4 || Ns[a] % 2) return fail(nullptr, VP_ERR_INVALID_ARG, "N must be even and >= 4");
   if (kernel != VP_LAPLACE && kernel != VP_HELMHOLTZ && kernel != VP_BIHARMONIC)
     return fail(nullptr, VP_ERR_INVALID_ARG, "unknown kernel");
   if (!isfinite(k) || (kernel != VP_HELMHOLTZ && k != 0.0) || (kernel == VP_HELMHOLTZ && !(k > 0.0)))
@@ -701,16 +766,23 @@ vp_status vp_plan_create(vp_plan* out, int d, int N, vp_kernel kernel, double k,
   if (!isfinite(L)) return fail(nullptr, VP_ERR_INVALID_ARG, "L must be finite");
   if (L <= 0.0) L = (d == 3) ? 1.8 : 1.5;
   if (!(L > sqrt((double)d)) || L > 3.0) return fail(nullptr, VP_ERR_INVALID_ARG, "L must satisfy sqrt(d) < L <= 3");
-  if (!fft_length_built(2 * N)) return fail(nullptr, VP_ERR_UNSUPPORTED, "2N is not a built FFT length");
-  const long long oct = d == 3 ? (long long)(N + 1) * (N + 1) * (N + 1) : (long long)(N + 1) * (N + 1);
+  long long oct = 1;
+  for (int a = 0; a < d; ++a) {
+    if (!fft_length_built(2 * Ns[a])) return fail(nullptr, VP_ERR_UNSUPPORTED, "2N is not a built FFT length");
+    oct *= Ns[a] + 1;
+  }
 
   vp_plan p = new vp_plan_s();
   p->d = d;
-  p->N = N;
+  p->N = Ns[0];
+  for (int a = 0; a < d; ++a) {
+    p->Nv[a] = Ns[a];
+    if (Ns[a] != Ns[0]) p->aniso = 1;
+  }
   p->kernel = kernel;
   p->k = k;
   p->L = L;
-  p->n2 = 2 * N;
+  p->n2 = 2 * Ns[0];
   p->oct = oct;
   cudaError_t e = cudaGetDevice(&p->device);
   if (e == cudaSuccess) {
@@ -722,9 +794,22 @@ vp_status vp_plan_create(vp_plan* out, int d, int N, vp_kernel kernel, double k,
   if (e == cudaSuccess) e = dalloc(p, &p->G64u, oct);
   if (e == cudaSuccess) e = dalloc(p, &p->G64, oct);
   if (e == cudaSuccess) e = dalloc(p, &p->G32, oct);
-  if (e == cudaSuccess) e = dalloc(p, &p->tw64, 2 * N);
-  if (e == cudaSuccess) e = dalloc(p, &p->tw32, 2 * N);
-  if (e == cudaSuccess) e = launch_twiddles(p->tw64, p->tw32, 2 * N, 0);
+  // twiddles per distinct axis length (axis 0's are the plan's tw64/tw32)
+  for (int a = 0; a < d && e == cudaSuccess; ++a) {
+    int same = -1;
+    for (int b = 0; b < a; ++b)
+      if (Ns[b] == Ns[a]) same = b;
+    if (same >= 0) {
+      p->twv64[a] = p->twv64[same];
+      p->twv32[a] = p->twv32[same];
+      continue;
+    }
+    e = dalloc(p, &p->twv64[a], 2 * Ns[a]);
+    if (e == cudaSuccess) e = dalloc(p, &p->twv32[a], 2 * Ns[a]);
+    if (e == cudaSuccess) e = launch_twiddles(p->twv64[a], p->twv32[a], 2 * Ns[a], 0);
+  }
+  p->tw64 = p->twv64[0];
+  p->tw32 = p->twv32[0];
   Scratch sc;
   if (e == cudaSuccess) e = scratch_alloc(p, sc);
   if (e == cudaSuccess) e = build_kernel(p, sc, -1, p->T64, p->G64u, p->G64, p->G32);
@@ -740,6 +825,28 @@ vp_status vp_plan_create(vp_plan* out, int d, int N, vp_kernel kernel, double k,
   return VP_OK;
 }
 
+}  // namespace
+
+vp_status vp_plan_create(vp_plan* out, int d, int N, vp_kernel kernel, double k, double L) {
+  const int Ns[3] = {N, N, N};
+  return plan_create_common(out, d, Ns, kernel, k, L);
+}
+
+vp_status vp_plan_create_aniso(vp_plan* out, int d, const int* N, vp_kernel kernel, double k, double L) {
+  if (!N) {
+    if (out) *out = nullptr;
+    return fail(nullptr, VP_ERR_INVALID_ARG, "N is NULL");
+  }
+  return plan_create_common(out, d, N, kernel, k, L);
+}
+
+vp_status vp_plan_dims(vp_plan p, int* N) {
+  if (!p) return fail(nullptr, VP_ERR_INVALID_ARG, "plan is NULL");
+  if (!N) return fail(p, VP_ERR_INVALID_ARG, "N is NULL");
+  for (int a = 0; a < p->d; ++a) N[a] = p->Nv[a];
+  return VP_OK;
+}
+
 vp_status vp_plan_set_stream(vp_plan p, void* stream) {
   if (!p) return fail(nullptr, VP_ERR_INVALID_ARG, "plan is NULL");
   p->stream = reinterpret_cast<cudaStream_t>(stream);
@@ -751,8 +858,8 @@ vp_status vp_plan_set_precision(vp_plan p, vp_precision precision) {
   if (precision != VP_FP32 && precision != VP_FP64 && !is_tc(precision))
     return fail(p, VP_ERR_INVALID_ARG, "unknown precision");
   if (is_tc(precision)) {
-    if (p->d != 3 || !tc_length_supported(p->n2))
-      return fail(p, VP_ERR_UNSUPPORTED, "tensor-core precisions need a 3D plan with N = 128 or 256");
+    if (p->d != 3 || p->aniso || !tc_length_supported(p->n2))
+      return fail(p, VP_ERR_UNSUPPORTED, "tensor-core precisions need a cubic 3D plan with N = 128 or 256");
     const int split = precision == VP_TC_BF16X2 ? 0 : (precision == VP_TC_FP16X2 ? 1 : 2);
     if (p->tc_split != split) {
       VP_CUDA(p, cudaSetDevice(p->device));
@@ -914,8 +1021,14 @@ vp_status vp_destroy(vp_plan p) {
     cudaFree(p->Gj64[j]);
     cudaFree(p->Gj32[j]);
   }
-  cudaFree(p->tw64);
-  cudaFree(p->tw32);
+  for (int a = 0; a < 3; ++a) {
+    bool dup = false;
+    for (int b = 0; b < a; ++b) dup = dup || p->twv64[b] == p->twv64[a];
+    if (!dup) {
+      cudaFree(p->twv64[a]);
+      cudaFree(p->twv32[a]);
+    }
+  }
   cudaFree(p->tcB);
   cudaFree(p->d_err);
   cudaFree(p->d_flag);

@@ -19,7 +19,7 @@ constexpr double BIHARM_SERIES_X = 2.0;
 
 // precompute.cu
 cudaError_t set_gauss_legendre(const double* x, const double* w);
-cudaError_t launch_spectrum(double2* G, int d, int N, int kernel, double k, double L, cudaStream_t s);
+cudaError_t launch_spectrum(double2* G, int d, const int* M1s, int kernel, double k, double L, cudaStream_t s);
 cudaError_t launch_matrix(double* M, int N, int type, cudaStream_t s);
 cudaError_t launch_axis_transform(const double2* in, double2* out, const double* M, long long O, int P, int Q,
                                   long long I, cudaStream_t s);
@@ -89,6 +89,10 @@ vp_status apply_with_workspace(vp_plan p, const void* f, void* phi, vp_dtype dty
 // plan_grad_workspace_bytes; the derivative multipliers must have been built
 // (plan_prepare_grad) before, e.g. outside a stream capture.
 int plan_kernel(vp_plan p);
+// per-axis grids: not all N_j equal; N_0 N_1 (N_2) points; N_j per axis (1 beyond d)
+int plan_is_aniso(vp_plan p);
+long long plan_points(vp_plan p);
+void plan_dims(vp_plan p, int* N);
 vp_status plan_prepare_grad(vp_plan p);
 size_t plan_grad_workspace_bytes(vp_plan p);
 vp_status apply_grad_with_workspace(vp_plan p, const void* f, void* grad, vp_dtype dtype, void* ws, size_t ws_bytes);

@@ -53,6 +53,9 @@ _SIGNATURES = {
     "vp_apply": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
     "vp_apply_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int]),
     "vp_plan_get_array": (c_int, [c_void_p, c_int, c_int, ctypes.POINTER(c_double), c_size_t]),
+    "vp_plan_create_aniso": (c_int, [ctypes.POINTER(c_void_p), c_int, ctypes.POINTER(c_int), c_int, c_double,
+                                     c_double]),
+    "vp_plan_dims": (c_int, [c_void_p, ctypes.POINTER(c_int)]),
     "vp_kernel_entries": (c_int, [c_void_p, c_int, c_int, c_void_p, ctypes.c_longlong, c_void_p, c_int]),
     "vp_matrix_block": (c_int, [c_void_p, c_int, c_int, c_void_p, ctypes.c_longlong, c_void_p, ctypes.c_longlong,
                                 c_void_p, c_int]),
@@ -229,13 +232,23 @@ def _empty_like(f, shape):
 
 
 class Plan:
-    """A precomputed volume-potential operator (one d, N, kernel, k, L)."""
+    """A precomputed volume-potential operator (one d, N, kernel, k, L).  N is an
+    int (N^d grid) or a tuple of d per-axis sizes (an N_0 x N_1 [x N_2] grid)."""
 
-    def __init__(self, d: int, N: int, kernel: str = "laplace", k: float = 0.0, L: float = 0.0,
+    def __init__(self, d: int, N, kernel: str = "laplace", k: float = 0.0, L: float = 0.0,
                  precision: str = "fp32", grad_mode: str = "exact", stream=None):
         self.d, self.N = d, N
+        self.dims = tuple(N) if isinstance(N, (tuple, list)) else (N,) * d
         self.kernel = kernel
-        self.handle = vp_plan_create(d, N, KERNELS[kernel], k, L)
+        if isinstance(N, (tuple, list)):
+            if len(N) != d:
+                raise VPError(VP_ERR_INVALID_ARG, "N needs d entries")
+            out = c_void_p()
+            arr = (c_int * d)(*N)
+            _check(lib().vp_plan_create_aniso(ctypes.byref(out), d, arr, KERNELS[kernel], float(k), float(L)))
+            self.handle = out.value
+        else:
+            self.handle = vp_plan_create(d, N, KERNELS[kernel], k, L)
         self.precision = precision
         vp_plan_set_precision(self.handle, PRECISIONS[precision])
         vp_plan_set_grad_mode(self.handle, GRAD_MODES[grad_mode])
@@ -280,11 +293,11 @@ class Plan:
     def get_array(self, which: str, axis: int = 0) -> np.ndarray:
         """An FP64 octant ((N+1)^d complex128): 'T', 'ghat', 'Tj', 'ghatj'."""
         code = {"T": VP_ARRAY_T, "ghat": VP_ARRAY_GHAT, "Tj": VP_ARRAY_TJ, "ghatj": VP_ARRAY_GHATJ}[which]
-        n = (self.N + 1) ** self.d
-        buf = np.empty(2 * n, dtype=np.float64)
+        shape = tuple(n + 1 for n in self.dims)
+        buf = np.empty(2 * int(np.prod(shape)), dtype=np.float64)
         _check(lib().vp_plan_get_array(self.handle, code, axis,
                                        buf.ctypes.data_as(ctypes.POINTER(c_double)), buf.size), self.handle)
-        return buf.view(np.complex128).reshape((self.N + 1,) * self.d)
+        return buf.view(np.complex128).reshape(shape)
 
     def kernel_entries(self, offsets, which: str = "T", axis: int = 0, dtype=None):
         """Nystrom entries T(n) for a (count, d) int32 device tensor of offsets
@@ -315,7 +328,8 @@ class Plan:
         """T along one grid axis through the origin, offsets -N+1 .. N-1 (the
         paper's Fig. 2 view of the kernel), as a complex128 device tensor."""
         import torch
-        n = torch.arange(-self.N + 1, self.N, dtype=torch.int32, device="cuda")
+        Na = self.dims[axis]
+        n = torch.arange(-Na + 1, Na, dtype=torch.int32, device="cuda")
         off = torch.zeros((n.shape[0], self.d), dtype=torch.int32, device="cuda")
         off[:, axis] = n
         return self.kernel_entries(off, which, axis)

@@ -35,6 +35,7 @@ WORKLOADS = {
     "laplace3d_single_gaussian": dict(d=3, N=32, kernel="laplace", k=0.0, L=1.8, grad=False),
     "biharmonic3d_n256": dict(d=3, N=256, kernel="biharmonic", k=0.0, L=1.8, grad=False),
     "batch64": dict(d=3, N=0, kernel="mixed", k=0.0, L=1.8, grad=False),
+    "batch64_grids": dict(d=3, N=0, kernel="mixed", k=0.0, L=1.8, grad=False),
 }
 FALLBACK_HBM_GBS = 6800.0
 FALLBACK_BF16_TFLOPS = 1900.0
@@ -553,19 +554,23 @@ def run_batch(args):
     from paper_1604_03155_gb300 import vp
 
     dev = torch.device("cuda", 0)
-    recipe = I.batch_recipe()
+    grids = args.workload == "batch64_grids"
+    if grids:  # per-axis sizes: (Ns, kernel, k, density) per density
+        recipe = [(Ns, kern, k, h) for Ns, kern, k, h in I.batch_recipe_grids()]
+    else:
+        recipe = [((w.N,) * 3, w.kernel, w.k, w.density()) for w in I.batch_recipe()]
     t0 = time.perf_counter()
-    plans = [vp.Plan(3, w.N, w.kernel, w.k, 1.8, precision="fp32") for w in recipe]
+    plans = [vp.Plan(3, Ns if grids else Ns[0], kern, k, 1.8, precision="fp32") for Ns, kern, k, _ in recipe]
     precompute_s = time.perf_counter() - t0
-    hs = [w.density().astype(np.complex64) for w in recipe]
+    hs = [h.astype(np.complex64) for _, _, _, h in recipe]
     fs = [torch.from_numpy(h).to(dev) for h in hs]
     outs = [torch.empty_like(f) for f in fs]
     stream = torch.cuda.Stream(device=dev)
     b = vp.Batch(plans, stream=stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    pts = sum(w.N ** 3 for w in recipe)
-    U_bytes = sum(8 * w.N ** 3 for w in recipe)
-    oct_bytes = sum(8 * (w.N + 1) ** 3 for w in recipe)
+    pts = sum(int(np.prod(Ns)) for Ns, _, _, _ in recipe)
+    U_bytes = 8 * pts
+    oct_bytes = sum(8 * int(np.prod([n + 1 for n in Ns])) for Ns, _, _, _ in recipe)
     algo = 27 * U_bytes + oct_bytes - 0  # 3+6+(4+4)+6+3 U and one multiplier octant per density
 
     def timed(strategy, steps):
@@ -600,8 +605,9 @@ def run_batch(args):
         "value": pts / (ms / 1000.0), "unit": "grid pts/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "batch64", "densities": len(recipe), "sizes": sorted({w.N for w in recipe}),
-                   "sum_N3": pts, "l2": "flushed before every timed step (256 MB write)"},
+        "config": {"workload": args.workload, "densities": len(recipe),
+                   "sizes": sorted({n for Ns, _, _, _ in recipe for n in Ns}), "per_axis_sizes": grids,
+                   "sum_points": pts, "l2": "flushed before every timed step (256 MB write)"},
         "roofline": {"bound": "hbm", "kernel": "batch_kernel", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
                      "algorithmic_bytes_per_launch": algo, "avg_launch_ms": ms},
@@ -620,7 +626,7 @@ def main():
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, wl)
-    elif args.workload == "batch64":
+    elif args.workload in ("batch64", "batch64_grids"):
         run_batch(args)
     else:
         run_ours(args, wl)

@@ -120,9 +120,9 @@ vp_status vp_plan_create(vp_plan* out, int d, int N, vp_kernel kernel, double k,
  * frequency step is pi/2 on every axis) and every transform of Section 4 runs
  * per axis with that axis's length; arrays are C order [N0][N1]([N2]), octants
  * [N0+1][N1+1]([N2+1]).  Serves vp_apply, vp_apply_grad, vp_apply_noalloc, the
- * Nystrom entries and the Bi-CGStab solvers; the tensor-core precisions, the
- * batch and the FGMRES/U-Net solver take cubic plans only (VP_ERR_UNSUPPORTED /
- * VP_ERR_INVALID_ARG). */
+ * batch, the Nystrom entries and the Bi-CGStab solvers; the tensor-core
+ * precisions and the FGMRES/U-Net solver take cubic plans only
+ * (VP_ERR_UNSUPPORTED / VP_ERR_INVALID_ARG). */
 vp_status vp_plan_create_aniso(vp_plan* out, int d, const int* N, vp_kernel kernel, double k, double L);
 /* Points per axis (d ints). */
 vp_status vp_plan_dims(vp_plan plan, int* N);

@@ -367,8 +367,7 @@ vp_status run_streams(vp_batch b, const void* const* f, void* const* phi) {
     std::vector<double> work(b->count, 1.0);
     for (int i = 0; i < b->count; ++i) {
       order[i] = i;
-      int d = 0, N = 0;
-      if (vp_plan_info(b->plans[i], &d, &N, nullptr, nullptr, nullptr) == VP_OK) work[i] = std::pow((double)N, d);
+      work[i] = (double)plan_points(b->plans[i]);
     }
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work[x] > work[y]; });
     double load[kSideStreams] = {0.0};
@@ -498,17 +497,19 @@ vp_status vp_batch_create(vp_batch* out, int count, const vp_plan* plans) {
   size_t ws_elems = 0;
   std::vector<size_t> ws_off(count);
   for (int i = 0; i < count; ++i) {
-    if (!plans[i] || !plan_is_fp32(plans[i]) || plan_is_aniso(plans[i])) {  // cubic FP32 plans
+    if (!plans[i] || !plan_is_fp32(plans[i])) {
       delete b;
       return VP_ERR_INVALID_ARG;
     }
-    int d, N;
+    int d, N, dims[3];
     vp_plan_info(plans[i], &d, &N, nullptr, nullptr, nullptr);
-    if (!batch_length_built(2 * N)) {
-      delete b;
-      return VP_ERR_UNSUPPORTED;
-    }
-    const size_t U = (size_t)N * N * (d == 3 ? N : 1);
+    plan_dims(plans[i], dims);
+    for (int a = 0; a < d; ++a)
+      if (!batch_length_built(2 * dims[a])) {
+        delete b;
+        return VP_ERR_UNSUPPORTED;
+      }
+    const size_t U = (size_t)plan_points(plans[i]);
     ws_off[i] = ws_elems;
     ws_elems += (d == 3 ? 6 : 2) * U;
   }
@@ -523,15 +524,13 @@ vp_status vp_batch_create(vp_batch* out, int count, const vp_plan* plans) {
   int counter = 0;
   for (int i = 0; i < count; ++i) {
     PassArgs<float> args[5];
-    int kinds[5];
-    int np = plan_pass_args_f32(plans[i], reinterpret_cast<float2*>(b->ws) + ws_off[i], args, kinds);
-    int d, N;
-    vp_plan_info(plans[i], &d, &N, nullptr, nullptr, nullptr);
+    int kinds[5], lens[5];
+    int np = plan_pass_args_f32(plans[i], reinterpret_cast<float2*>(b->ws) + ws_off[i], args, kinds, lens);
     for (int p = 0; p < np; ++p) {
       BatchPass bp;
       memset(&bp, 0, sizeof(bp));
       bp.a = args[p];
-      bp.n = 2 * N;
+      bp.n = lens[p];
       bp.kind = kinds[p];
       bp.density = i;
       bp.io = (p == 0) ? 1 : (p == np - 1 ? 2 : 0);
@@ -551,10 +550,8 @@ vp_status vp_batch_create(vp_batch* out, int count, const vp_plan* plans) {
   std::vector<int> order(count);
   std::vector<double> work(count);
   for (int i = 0; i < count; ++i) {
-    int d, N;
-    vp_plan_info(plans[i], &d, &N, nullptr, nullptr, nullptr);
     order[i] = i;
-    work[i] = std::pow((double)N, d);
+    work[i] = (double)plan_points(plans[i]);
   }
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work[x] > work[y]; });
   long long base = 0;
@@ -597,9 +594,12 @@ vp_status vp_batch_create(vp_batch* out, int count, const vp_plan* plans) {
   cudaDriverGetVersion(&drv);
   std::vector<std::string> parts;
   for (int i = 0; i < count; ++i) {
-    int d, N;
+    int d, N, dims[3];
     vp_plan_info(plans[i], &d, &N, nullptr, nullptr, nullptr);
-    parts.push_back(std::to_string(d) + "x" + std::to_string(N));
+    plan_dims(plans[i], dims);
+    std::string g = std::to_string(dims[0]);
+    for (int a = 1; a < d; ++a) g += "x" + std::to_string(dims[a]);
+    parts.push_back(std::to_string(d) + "d" + g);
   }
   std::sort(parts.begin(), parts.end());
   std::string sig = std::string(prop.name) + "|drv" + std::to_string(drv) + "|";

@@ -702,7 +702,7 @@ int* plan_flag_word(vp_plan p) {
   return p->d_flag;
 }
 
-int plan_pass_args_f32(vp_plan p, float2* ws, PassArgs<float>* args, int* kinds) {
+int plan_pass_args_f32(vp_plan p, float2* ws, PassArgs<float>* args, int* kinds, int* lens) {
   FieldDesc field{(const void*)p->G32, -1, -1};
   void* outs[1] = {nullptr};
   PassLaunch<float> list[6];
@@ -710,6 +710,7 @@ int plan_pass_args_f32(vp_plan p, float2* ws, PassArgs<float>* args, int* kinds)
   for (int i = 0; i < np; ++i) {
     args[i] = list[i].a;
     kinds[i] = (int)list[i].kind;
+    lens[i] = list[i].len;
   }
   return np;
 }

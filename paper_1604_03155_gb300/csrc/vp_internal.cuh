@@ -81,8 +81,9 @@ vp_status entries_fail(vp_plan p, vp_status st, const char* msg);
 // ls.cu: the message vp_ls_last_error returns on this thread
 void ls_set_error(const char* msg);
 // The FP32 potential-only passes of a plan on workspace `ws` (input and output
-// pointers left NULL): fills args/kinds, returns the number of passes.
-int plan_pass_args_f32(vp_plan p, float2* ws, PassArgs<float>* args, int* kinds);
+// pointers left NULL): fills args/kinds and each pass's transform length,
+// returns the number of passes.
+int plan_pass_args_f32(vp_plan p, float2* ws, PassArgs<float>* args, int* kinds, int* lens);
 size_t plan_apply_workspace_bytes(vp_plan p);
 vp_status apply_with_workspace(vp_plan p, const void* f, void* phi, vp_dtype dtype, void* ws, size_t ws_bytes);
 // The exact gradient (d fields, d blocks of N^d) on a caller workspace of

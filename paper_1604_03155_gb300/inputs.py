@@ -173,6 +173,38 @@ def batch_recipe(seed: int = BASE_SEED + 4, count: int = 64):
     return out
 
 
+def sample_gaussians_grid(src: GaussianSources, Ns) -> np.ndarray:
+    """The sources on a grid with Ns[j] points along axis j (complex128)."""
+    d = src.d
+    xs = [grid_coords(N) for N in Ns]
+    f = np.zeros(tuple(Ns), dtype=np.complex128)
+    for c, s, a in zip(src.centres, src.sigmas, src.amps):
+        g = np.ones((1,) * d)
+        for j in range(d):
+            shape = [1] * d
+            shape[j] = Ns[j]
+            g = g * np.exp(-((xs[j] - c[j]) ** 2) / (s * s)).reshape(shape)
+        f += a * g
+    return f
+
+
+def batch_recipe_grids(seed: int = BASE_SEED + 8, count: int = 64):
+    """The batch with per-axis sizes: 64 densities, each axis's N drawn
+    uniformly from {48, 64, 96, 128}; half Laplace and half Helmholtz with
+    k ~ U[5, 40]; four Gaussians each (3D, FP32).  Returns (Ns, kernel, k,
+    density) tuples."""
+    u = uniform(seed, 4 * count)
+    sizes = np.array([48, 64, 96, 128])
+    out = []
+    for i in range(count):
+        Ns = tuple(int(sizes[min(3, int(u[3 * i + j] * 4))]) for j in range(3))
+        helm = i >= count // 2
+        k = 5.0 + 35.0 * u[3 * count + i] if helm else 0.0
+        src = random_gaussians(seed * 1000 + i, 4, 3)
+        out.append((Ns, "helmholtz" if helm else "laplace", k, sample_gaussians_grid(src, Ns)))
+    return out
+
+
 def to_device_dtype(f: np.ndarray, precision: str) -> np.ndarray:
     """The array both sides consume: complex64 for the FP32 path, complex128 for FP64."""
     return f.astype(np.complex64 if precision == "fp32" else np.complex128)

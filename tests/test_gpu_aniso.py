@@ -85,8 +85,6 @@ def test_cubic_case_and_cubic_only_features():
     p = Plan(3, (128, 128, 64), "helmholtz", 9.0, 0.0)
     with pytest.raises(VPError):
         p.set_precision("tc_bf16x2")
-    with pytest.raises(VPError):
-        vp.Batch([p])
     q = torch.zeros((128, 128, 64), dtype=torch.float32, device=DEV)
     u = torch.zeros((128, 128, 64), dtype=torch.complex64, device=DEV)
     with pytest.raises(VPError):
@@ -120,3 +118,30 @@ def test_scattering_on_a_per_axis_grid():
     ref = AN.apply_fft2n(G, x)
     assert A.rel_l2(u.cpu().numpy(), ref) < 1e-10
     plan.close()
+
+
+@pytest.mark.parametrize("strategy", [vp.VP_BATCH_PERSISTENT, vp.VP_BATCH_GRAPH_STREAMS])
+def test_batch_of_per_axis_grids(strategy):
+    """The batch configuration's other reading: per-axis sizes drawn from
+    {48, 64, 96, 128} (here smaller, for the oracle); every density of a mixed
+    batch against the per-axis oracle."""
+    specs = [((8, 12, 16), "helmholtz", 9.0), ((16, 8, 12), "laplace", 0.0), ((12, 16), "helmholtz", 20.0),
+             ((24, 16, 8), "helmholtz", 15.0), ((8, 8, 8), "laplace", 0.0)]
+    plans, fs, hs = [], [], []
+    for i, (Ns, kern, k) in enumerate(specs):
+        plans.append(Plan(len(Ns), Ns, kern, k, 0.0, precision="fp32"))
+        h = I.random_complex_field(900 + i, Ns).astype(np.complex64)
+        hs.append(h)
+        fs.append(torch.from_numpy(h).to(DEV))
+    b = vp.Batch(plans)
+    b.set_strategy(strategy)
+    outs = b.apply(fs)
+    b.status()
+    for (Ns, kern, k), h, o in zip(specs, hs, outs):
+        L = 1.8 if len(Ns) == 3 else 1.5
+        G = AN.ghat_full_from_octant(AN.ghat_octant_by_sums(AN.T_octant_by_sums(Ns, kern, k, L)))
+        ref = AN.apply_fft2n(G, h.astype(np.complex128))
+        assert A.rel_l2(o.cpu().numpy(), ref) < 1e-4, Ns
+    b.close()
+    for p in plans:
+        p.close()

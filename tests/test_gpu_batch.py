@@ -99,7 +99,7 @@ def test_autotuner_chooses_and_caches(tmp_path, monkeypatch):
     s = b.strategy()
     assert s in (1, 2, 3, 4)
     text = cache.read_text()
-    assert text.strip().endswith(f" {s}") and "3x8" in text
+    assert text.strip().endswith(f" {s}") and "3d8x8x8" in text  # the key names every axis's size
     b.close()
     b2 = Batch(plans)  # a new batch of the same sizes reads the cached choice
     assert b2.strategy() == s

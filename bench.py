@@ -274,6 +274,9 @@ def density_sample(wl: dict, N: int):
     name = wl["name"]
     if name == "laplace3d_single_gaussian":
         return I.workload(name).density(N).astype(np.complex128)
+    if name.startswith("batch64"):  # the batch's first Helmholtz density stands for the batch
+        base = I.batch_recipe()[32]
+        return I.sample_gaussians(I.random_gaussians(base.seed, base.n_gauss, 3), N).astype(np.complex128)
     base = I.workload(name)
     return I.sample_gaussians(I.random_gaussians(base.seed, base.n_gauss, base.d), N).astype(np.complex128)
 
@@ -284,6 +287,11 @@ def run_reference(args, wl):
         return
     steps = max(1, args.steps)
     wl = dict(wl, name=args.workload)
+    if args.workload.startswith("batch64"):
+        # per step one density of the batch (its first Helmholtz one: N, k), in grid points per second
+        from paper_1604_03155_gb300 import inputs as I
+        w = I.batch_recipe()[32]
+        wl = dict(wl, N=w.N, kernel=w.kernel, k=w.k)
     Ns = reference_sample_N(wl, steps)
     sw = dict(wl, N=Ns)
     f = density_sample(wl, Ns)

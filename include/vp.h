@@ -25,8 +25,10 @@
  * Result: phi_p = sum_{p'} T(p - p') f_{p'}, the quadrature weight h^d included,
  *   so phi approximates the integral above to spectral accuracy for smooth f.
  * Pointers: f, phi and grad may be device pointers (asynchronous on the
- *   plan's stream) or host pointers (the call stages through device memory
- *   and returns when the host result is written).  phi may not alias f.
+ *   plan's stream) or host pointers (pinned buffers are read and written in
+ *   place through their device mappings, others are staged through device
+ *   memory; the call returns when the host result is written).  phi may not
+ *   alias f.
  * Complex data is interleaved (re, im).  grad holds d contiguous N^d blocks,
  *   block j = d phi / d x_j.
  * Errors: every call returns a vp_status and never aborts; argument errors are
@@ -144,6 +146,13 @@ vp_status vp_kernel_entries(vp_plan plan, int which, int axis, const int* offset
                             vp_dtype dtype);
 vp_status vp_matrix_block(vp_plan plan, int which, int axis, const long long* rows, long long nrows,
                           const long long* cols, long long ncols, void* out, vp_dtype dtype);
+
+/* Host pointers to page-locked (pinned) memory: direct = 1 (default) lets the
+ * first pass read f and the last pass write phi/grad in host memory through
+ * their device mappings (over the CPU-GPU link, no staging copies); direct = 0
+ * stages them through a plan-owned device buffer, as for pageable memory.
+ * The call returns after the host result is written either way. */
+vp_status vp_plan_set_host_access(vp_plan plan, int direct);
 
 /* Stream for subsequent calls (cudaStream_t as void*; NULL = legacy default).
  * One plan serves one stream at a time. */

@@ -72,6 +72,7 @@ struct vp_plan_s {
   size_t device_bytes = 0;
 
   bool timing = false;
+  int host_direct = 1;  // pinned host buffers: access them in place (0: stage through device memory)
   std::vector<TimedLaunch> timed;
   std::vector<cudaEvent_t> event_pool;
 
@@ -260,6 +261,16 @@ size_t elem_bytes(vp_dtype t) {
     case VP_C128: return 16;
   }
   return 0;
+}
+
+// The device mapping of page-locked (pinned) host memory, else NULL.
+void* mapped_host_ptr(const void* ptr) {
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return attr.type == cudaMemoryTypeHost ? attr.devicePointer : nullptr;
 }
 
 bool is_device_ptr(const void* ptr) {
@@ -560,10 +571,28 @@ vp_status apply_common(vp_plan p, const void* f, void* phi, void* grad, vp_dtype
     }
   }
 
-  // host pointers are staged through device memory
   const bool host_io = !is_device_ptr(f);
-  const void* fd = f;
   void* outs[4];
+  if (host_io && p->host_direct) {
+    // page-locked host buffers: the first pass reads f and the last pass writes
+    // the outputs through their device mappings, across the CPU-GPU link,
+    // with no staging copies (the result is in host memory after the sync)
+    const void* fm = mapped_host_ptr(f);
+    void* pm = phi ? mapped_host_ptr(phi) : nullptr;
+    void* gm = want_grad ? mapped_host_ptr(grad) : nullptr;
+    if (fm && (!phi || pm) && (!want_grad || gm)) {
+      int i = 0;
+      if (phi) outs[i++] = pm;
+      if (want_grad)
+        for (int j = 0; j < p->d; ++j) outs[i++] = reinterpret_cast<char*>(gm) + (size_t)j * U * eb;
+      st = fp64 ? run_apply<double>(p, fm, outs, fields, F, real_io) : run_apply<float>(p, fm, outs, fields, F, real_io);
+      if (st != VP_OK) return st;
+      VP_CUDA(p, cudaStreamSynchronize(p->stream));
+      return VP_OK;
+    }
+  }
+  // other host pointers are staged through device memory
+  const void* fd = f;
   char* out_base = nullptr;
   if (host_io) {
     const size_t need = (1 + (size_t)F) * U * eb;
@@ -845,6 +874,12 @@ vp_status vp_plan_dims(vp_plan p, int* N) {
   if (!p) return fail(nullptr, VP_ERR_INVALID_ARG, "plan is NULL");
   if (!N) return fail(p, VP_ERR_INVALID_ARG, "N is NULL");
   for (int a = 0; a < p->d; ++a) N[a] = p->Nv[a];
+  return VP_OK;
+}
+
+vp_status vp_plan_set_host_access(vp_plan p, int direct) {
+  if (!p) return fail(nullptr, VP_ERR_INVALID_ARG, "plan is NULL");
+  p->host_direct = direct ? 1 : 0;
   return VP_OK;
 }
 

@@ -56,6 +56,7 @@ _SIGNATURES = {
     "vp_plan_create_aniso": (c_int, [ctypes.POINTER(c_void_p), c_int, ctypes.POINTER(c_int), c_int, c_double,
                                      c_double]),
     "vp_plan_dims": (c_int, [c_void_p, ctypes.POINTER(c_int)]),
+    "vp_plan_set_host_access": (c_int, [c_void_p, c_int]),
     "vp_kernel_entries": (c_int, [c_void_p, c_int, c_int, c_void_p, ctypes.c_longlong, c_void_p, c_int]),
     "vp_matrix_block": (c_int, [c_void_p, c_int, c_int, c_void_p, ctypes.c_longlong, c_void_p, ctypes.c_longlong,
                                 c_void_p, c_int]),
@@ -270,6 +271,10 @@ class Plan:
     def set_precision(self, precision: str):
         vp_plan_set_precision(self.handle, PRECISIONS[precision])
         self.precision = precision
+
+    def set_host_access(self, direct: bool):
+        """Pinned host buffers: access them in place (True) or stage them (False)."""
+        _check(lib().vp_plan_set_host_access(self.handle, int(direct)), self.handle)
 
     def set_grad_mode(self, mode: str):
         vp_plan_set_grad_mode(self.handle, GRAD_MODES[mode])

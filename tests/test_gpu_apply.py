@@ -205,3 +205,22 @@ def test_workload_helmholtz3d_n256_sampled():
     phi2 = plan.apply(ft * (2 - 1j)).cpu().numpy()
     assert A.rel_l2(phi2, (2 - 1j) * phi) < 1e-6
     plan.close()
+
+
+@pytest.mark.parametrize("d,N,prec", [(2, 64, "fp32"), (3, 32, "fp64")])
+def test_pinned_host_buffers_in_place_and_staged_match_device_path(d, N, prec):
+    """Pinned host buffers are read and written in place by the first and last
+    pass (or staged with host_access off): both give the device path's bits."""
+    plan = Plan(d, N, "helmholtz", 11.0, 0.0, precision=prec)
+    plan.set_grad_mode("exact")
+    f = _density(d, N, 6000 + N, prec)
+    phi_d, g_d = plan.apply_grad(torch.from_numpy(f).to(DEV))
+    torch.cuda.synchronize()
+    fp = torch.from_numpy(f).pin_memory()
+    for direct in (True, False):
+        plan.set_host_access(direct)
+        phi_h = torch.empty_like(fp).pin_memory()
+        g_h = torch.empty((d,) + fp.shape, dtype=fp.dtype).pin_memory()
+        plan.apply_grad(fp, phi_h, g_h)
+        assert torch.equal(phi_h, phi_d.cpu()) and torch.equal(g_h, g_d.cpu()), direct
+    plan.close()

@@ -354,8 +354,10 @@ vp_status vp_ls_bicgstab(vp_plan plan, const void* q, const void* u_inc, void* u
  * FP32 products slow Bi-CGStab down on strongly indefinite problems (measured:
  * the filtered disk at 80 wavelengths); when the FP32 phase has not converged
  * after maxit iterations, or three consecutive updates each gain less than 2x,
- * or it breaks down, the solve is rerun in FP64 (vp_ls_bicgstab, at most
- * maxit iterations) and stats->used_fallback is set.
+ * or it breaks down, FP64 Bi-CGStab (vp_ls_bicgstab's iteration, at most
+ * maxit iterations) solves the correction equation M e = b - M x from the
+ * mixed iterate x to the same tol ||b||, u is x + e (field) or V[s + e]
+ * (density), and stats->used_fallback is set.
  * q: N^d doubles, u_inc/u: complex128 device arrays; the plan's precision may
  * be VP_FP32 or VP_FP64 (it is switched internally and restored).  delta in
  * (0, 1), e.g. 0.01.  stats: matvecs = operator products (FP32, plus the

@@ -544,6 +544,30 @@ __global__ void __launch_bounds__(kThreads) k_true_residual(const double2* __res
   block_partials<2>(re, im, part);
 }
 
+// out = b - M x in FP64 (t1: the FP64 apply of x's operand); partials (||out||^2, ||b||^2)
+template <int FORM>
+__global__ void __launch_bounds__(kThreads) k_residual_vec(const double2* __restrict__ b,
+                                                           const double2* __restrict__ x,
+                                                           const double2* __restrict__ t1, OpArgs<double> a,
+                                                           double2* __restrict__ out, double2* __restrict__ part) {
+  double rr = 0.0, bb = 0.0;
+  GRID_LOOP(i, a.n) {
+    const double2 bv = b[i];
+    const double2 mx = op_at<double, FORM>(x[i], t1, a, i);
+    const double2 r = make_double2(bv.x - mx.x, bv.y - mx.y);
+    out[i] = r;
+    rr += r.x * r.x + r.y * r.y;
+    bb += bv.x * bv.x + bv.y * bv.y;
+  }
+  const double re[2] = {rr, bb}, im[2] = {0.0, 0.0};
+  block_partials<2>(re, im, part);
+}
+
+// u += e
+__global__ void __launch_bounds__(kThreads) k_add(double2* __restrict__ u, const double2* __restrict__ e, long long n) {
+  GRID_LOOP(i, n) u[i] = make_double2(u[i].x + e[i].x, u[i].y + e[i].y);
+}
+
 // after k_mixed_init (first) or k_true_residual: the stop test on the true
 // residual, beta from the new residual, the update flag cleared
 __global__ void __launch_bounds__(kScalThreads) k_scal_update(BcgState* __restrict__ st,
@@ -742,9 +766,12 @@ vp_status alloc_work(Work<R>& w, vp_plan plan, long long n, int form, int d, boo
 
 // The solve in one precision R.  src: u_inc (field, density) or rho (PB);
 // q: contrast or eps; ge: grad eps (PB).  u: the scattered field or sigma.
+// rhs_given: src is the right-hand side b itself (a correction equation), not
+// the incident field or rho it is formed from.
 template <typename R, int FORM>
 vp_status solve(vp_plan plan, const R* q, const R* ge, const typename Cx<R>::T* src, typename Cx<R>::T* u,
-                double k2d, int d, long long n, double tol, int maxit, double* history, vp_ls_stats* stats, Err& E) {
+                double k2d, int d, long long n, double tol, int maxit, double* history, vp_ls_stats* stats, Err& E,
+                bool rhs_given = false) {
   const auto t_start = std::chrono::steady_clock::now();
   Work<R> w;
   vp_status st = alloc_work<R>(w, plan, n, FORM, d, FORM == F_DENSITY, E);
@@ -759,11 +786,15 @@ vp_status solve(vp_plan plan, const R* q, const R* ge, const typename Cx<R>::T* 
   if (FORM == F_FIELD) {
     k_qmul<R><<<kBlocks, kThreads, 0, w.s>>>(w.t0, q, src, n);
     if ((st = apply_v<R, FORM>(plan, w, src)) != VP_OK) return st;
-    k_start<R, FORM><<<kBlocks, kThreads, 0, w.s>>>(w.t1, a, w.b, w.r, w.rh, w.x, w.p, w.v, w.part);
   } else {
     if ((st = apply_v<R, FORM>(plan, w, src)) != VP_OK) return st;
-    k_start<R, FORM><<<kBlocks, kThreads, 0, w.s>>>(src, a, w.b, w.r, w.rh, w.x, w.p, w.v, w.part);
   }
+  if (rhs_given)  // b = src (the Poisson-Boltzmann form's right-hand side is src itself)
+    k_start<R, F_PB><<<kBlocks, kThreads, 0, w.s>>>(src, a, w.b, w.r, w.rh, w.x, w.p, w.v, w.part);
+  else if (FORM == F_FIELD)
+    k_start<R, FORM><<<kBlocks, kThreads, 0, w.s>>>(w.t1, a, w.b, w.r, w.rh, w.x, w.p, w.v, w.part);
+  else
+    k_start<R, FORM><<<kBlocks, kThreads, 0, w.s>>>(src, a, w.b, w.r, w.rh, w.x, w.p, w.v, w.part);
   BcgState init;
   memset(&init, 0, sizeof(init));
   init.rho = init.alpha = init.omega = make_double2(1.0, 0.0);
@@ -841,7 +872,9 @@ vp_status solve(vp_plan plan, const R* q, const R* ge, const typename Cx<R>::T* 
     double2* src64 = w64.p;
     k_widen_c<<<kBlocks, kThreads, 0, w64.s>>>(src64, reinterpret_cast<const float2*>(src), n);
     const OpArgs<double> a64{q64, ge64.p, k2d, d, n};
-    if (FORM == F_FIELD) {  // b = k^2 V[q u_inc] in FP64
+    if (rhs_given) {
+      k_rhs<double, F_PB><<<kBlocks, kThreads, 0, w64.s>>>(src64, a64, w64.b);
+    } else if (FORM == F_FIELD) {  // b = k^2 V[q u_inc] in FP64
       k_qmul<double><<<kBlocks, kThreads, 0, w64.s>>>(w64.t0, q64, src64, n);
       if ((st = apply_v<double, FORM>(plan, w64, src64)) != VP_OK) return st;
       k_rhs<double, FORM><<<kBlocks, kThreads, 0, w64.s>>>(w64.t1, a64, w64.b);
@@ -1011,19 +1044,52 @@ vp_status solve_mixed(vp_plan plan, const double* q64, const double* ge64, const
   if ((st = vp_plan_set_precision(plan, VP_FP64)) != VP_OK) return st;
   if (last.done != BCG_CONVERGED) {
     // FP32 products did not reach tol within the budget (the iteration count,
-    // a stall or a breakdown): the plain FP64 solve from the start
+    // a stall or a breakdown): FP64 Bi-CGStab on the correction equation
+    // M e = r = b - M x from the mixed iterate x (M x + M e = b), to tol ||b||
+    struct Buf {
+      double2* p = nullptr;
+      ~Buf() { cudaFree(p); }
+    } r64, e64;
+    BCG_CUDA(E, cudaMalloc(&r64.p, n * sizeof(double2)));
+    BCG_CUDA(E, cudaMalloc(&e64.p, n * sizeof(double2)));
+    if (FORM == F_FIELD) k_qmul<double><<<kBlocks, kThreads, 0, w.s>>>(w64.t0, q64, w64.x, n);
+    if ((st = apply_v<double, FORM>(plan, w64, w64.x)) != VP_OK) return st;
+    k_residual_vec<FORM><<<kBlocks, kThreads, 0, w.s>>>(w64.b, w64.x, w64.t1, a64, r64.p, w.part);
+    double2 h[2 * kBlocks];
+    BCG_CUDA(E, cudaMemcpyAsync(h, w.part, sizeof(h), cudaMemcpyDeviceToHost, w.s));
     BCG_CUDA(E, cudaStreamSynchronize(w.s));
+    double rr = 0.0, bb = 0.0;
+    for (int i = 0; i < kBlocks; ++i) {
+      rr += h[2 * i].x;
+      bb += h[2 * i + 1].x;
+    }
+    const double rn = sqrt(rr), bn = sqrt(bb);
     vp_ls_stats s64;
     memset(&s64, 0, sizeof(s64));
-    st = solve<double, FORM>(plan, q64, ge64, src, u, k2d, d, n, tol, maxit, nullptr, &s64, E);
+    if (rn > 0.0) {
+      st = solve<double, FORM>(plan, q64, ge64, r64.p, e64.p, k2d, d, n, tol * bn / rn, maxit, nullptr, &s64, E,
+                               true);
+      if (st != VP_OK && st != VP_ERR_NUMERICAL) return st;
+    } else {
+      BCG_CUDA(E, cudaMemsetAsync(e64.p, 0, n * sizeof(double2), w.s));
+    }
+    // u = x + e (field, Poisson-Boltzmann); u = V[s] + V[e_s] (density: the
+    // correction solve returns V[e_s])
+    if (FORM == F_DENSITY) {
+      vp_status sa = vp::apply_with_workspace(plan, w64.x, u, VP_C128, w64.ws, w64.ws_bytes);
+      if (sa != VP_OK) return sa;
+    }
+    k_add<<<kBlocks, kThreads, 0, w.s>>>(u, e64.p, n);
+    BCG_CUDA(E, cudaStreamSynchronize(w.s));
     const auto t_end = std::chrono::steady_clock::now();
     if (stats) {
       stats->iterations = last.iterations + s64.iterations;
       stats->matvecs = last.matvecs + s64.matvecs;
       stats->restarts = last.updates;
       stats->used_fallback = 1;
-      stats->estimated_residual = s64.estimated_residual;
-      stats->true_residual = s64.true_residual;
+      // the correction solve's residuals are relative to ||r||
+      stats->estimated_residual = s64.estimated_residual * rn / bn;
+      stats->true_residual = s64.true_residual * rn / bn;
       stats->seconds = std::chrono::duration<double>(t_end - t_start).count();
     }
     return st;

@@ -39,7 +39,7 @@ TABLES = {
 }
 DELTA = 1e-2  # reliable-update threshold of the mixed-precision solver
 REF_PRECISION = "fp64"  # precision of the reference solves
-MIXED_MAXIT = 3000  # FP32 iteration budget of a mixed solve before the FP64 rerun
+MIXED_MAXIT = 3000  # FP32 iteration budget of a mixed solve before its FP64 phase
 
 QUICK = {
     "disk": (2, I.filtered_disk, [(1, 256, [16, 32]), (20, 256, [64, 128])]),
@@ -61,7 +61,7 @@ def solve(d: int, contrast, N: int, size: float, precision: str, form: str, tol:
     rdt, cdt = (torch.float32, torch.complex64) if precision == "fp32" else (torch.float64, torch.complex128)
     q = torch.from_numpy(contrast(N)).to(dev, rdt)
     uinc = torch.from_numpy(I.plane_wave(N, k, d)).to(dev, cdt)
-    if precision == "mixed":  # FP32 iterations, FP64 reliable updates (FP64 rerun after MIXED_MAXIT)
+    if precision == "mixed":  # FP32 iterations, FP64 reliable updates (an FP64 phase after MIXED_MAXIT)
         u, stats = vp.ls_bicgstab_mixed(plan, q, uinc, form=form, tol=tol, delta=DELTA, maxit=min(maxit, MIXED_MAXIT))
     else:
         u, stats = vp.ls_bicgstab(plan, q, uinc, form=form, tol=tol, maxit=maxit)
@@ -122,12 +122,15 @@ def markdown(rows) -> str:
 
 
 def main(argv=None):
+    global DELTA, REF_PRECISION, MIXED_MAXIT
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--tables", default="disk,lens,cube")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "mixed"],
                     help="mixed: FP32 iterations with FP64 reliable updates (FP64 accuracy)")
     ap.add_argument("--delta", type=float, default=None, help="reliable-update threshold (mixed), default 1e-2")
     ap.add_argument("--reference-precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--mixed-maxit", type=int, default=None,
+                    help=f"FP32 iteration budget of a mixed solve, default {MIXED_MAXIT}")
     ap.add_argument("--form", default="density", choices=["density", "field"])
     ap.add_argument("--tol", type=float, default=None, help="default 1e-12 (fp64), 1e-6 (fp32)")
     ap.add_argument("--maxit", type=int, default=20000)
@@ -136,8 +139,8 @@ def main(argv=None):
                     help="one solve (no reference), e.g. disk:20:512; prints its stats")
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
-    global DELTA, REF_PRECISION
     DELTA = DELTA if a.delta is None else a.delta
+    MIXED_MAXIT = MIXED_MAXIT if a.mixed_maxit is None else a.mixed_maxit
     REF_PRECISION = a.reference_precision
     tol = a.tol if a.tol is not None else (1e-6 if a.precision == "fp32" else 1e-12)
     if a.single:

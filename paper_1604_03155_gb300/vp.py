@@ -534,7 +534,8 @@ def ls_bicgstab_mixed(plan: Plan, q, u_inc, u=None, form: str = "field", tol: fl
     (complex128 u_inc/u, float64 q) at mostly FP32 cost.  Returns (u, stats) or
     (u, stats, history); stats["restarts"] counts the FP64 updates, and
     stats["used_fallback"] is 1 when the FP32 phase gave up (after maxit
-    iterations or a stall) and the solve was rerun in FP64."""
+    iterations or a stall) and FP64 Bi-CGStab finished the solve from the
+    mixed iterate (on the correction equation M e = b - M x)."""
     if form not in LS_FORMS:
         raise VPError(VP_ERR_INVALID_ARG, f"form must be one of {sorted(LS_FORMS)}")
     u = _empty_like(u_inc, u_inc.shape) if u is None else u

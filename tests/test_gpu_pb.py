@@ -71,6 +71,23 @@ def test_manufactured_solution_fp64_accuracy(mixed):
     assert st["true_residual"] < 1e-12 and st["used_fallback"] == 0
 
 
+def test_mixed_fallback_continues_from_mixed_iterate():
+    """An FP32 phase cut off by maxit hands over to FP64 Bi-CGStab on the
+    correction equation from the mixed iterate: the analytic sigma to 1e-10."""
+    N = 48
+    eps, ge, rho, sig = _manufactured(N)
+    _, st64 = _solve(N, eps, ge, rho, "fp64", 1e-13)
+    plan = Plan(3, N, "laplace", 0.0, 0.0, precision="fp32")
+    e = torch.as_tensor(eps).to(DEV).contiguous()
+    g = torch.as_tensor(ge).to(DEV).contiguous()
+    b = torch.as_tensor(rho).to(DEV, torch.complex128).contiguous()
+    maxit = max(2, (2 * st64["iterations"]) // 3)
+    got, st = vp.pb_solve(plan, e, g, b, tol=1e-13, maxit=maxit, mixed=True)
+    plan.close()
+    assert st["used_fallback"] == 1 and st["true_residual"] < 1e-12
+    assert _rel2(got.cpu().numpy(), sig) < 1e-10
+
+
 def test_fp32_against_oracle():
     N = 24
     eps, ge, rho, sig = _manufactured(N)

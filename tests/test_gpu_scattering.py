@@ -222,7 +222,33 @@ def test_mixed_precision_fallback_mechanics():
     assert st["used_fallback"] == 1
     assert st["iterations"] == 6 and st["matvecs"] == 12
     # an update after every iteration that gains little stalls the FP32 phase
-    # early; the FP64 rerun still converges
+    # early; the FP64 solve that continues from the mixed iterate converges
     u, st = vp.ls_bicgstab_mixed(plan, qd, ud, tol=1e-12, maxit=60, delta=0.999999)
     assert st["true_residual"] < 1e-12
     plan.close()
+
+
+@pytest.mark.parametrize("form", ["field", "density"])
+def test_mixed_precision_fallback_continues_from_mixed_iterate(form):
+    """An FP32 phase cut off by maxit = the FP64 solve's iteration count (the
+    FP32 phase needs about 1.5x that, with one idle launch per update) hands
+    over to an FP64 solve of the correction equation M e = b - M x from the
+    mixed iterate x: u = x + e (field) or V[s + e] (density) is the oracle's
+    solution to 1e-10, and that FP64 phase takes fewer products than the FP64
+    solve from zero."""
+    q, k, uinc = _case("disk", 48, 2.0)
+    u_ref = _oracle("disk", 48, 2.0, "field")[4]
+    _, st64 = _gpu_solve(q, k, uinc, form, "fp64", 1e-12)
+    maxit = st64["iterations"]
+    plan = Plan(2, 48, "helmholtz", k, 0.0, precision="fp32")
+    qd = torch.from_numpy(q).to(DEV)
+    ud = torch.from_numpy(uinc).to(DEV)
+    u, st = vp.ls_bicgstab_mixed(plan, qd, ud, form=form, tol=1e-12, maxit=maxit)
+    plan.close()
+    assert st["used_fallback"] == 1, (st, st64)
+    assert st["true_residual"] < 1e-12, (st, st64)
+    assert _rel2(u.cpu().numpy(), u_ref) < 1e-10
+    # the FP32 phase ran maxit graph launches, each an iteration of two products
+    # except the one idle launch after each update
+    mixed_products = 2 * (maxit - st["restarts"])
+    assert st["matvecs"] - mixed_products < st64["matvecs"], (st, st64)

@@ -384,6 +384,28 @@ vp_status vp_pb_solve(vp_plan plan, const void* eps, const void* grad_eps, const
                       vp_dtype dtype, double tol, int maxit, double* history, vp_ls_stats* stats);
 vp_status vp_pb_solve_mixed(vp_plan plan, const double* eps, const double* grad_eps, const void* rho, void* sigma,
                             double tol, double delta, int maxit, double* history, vp_ls_stats* stats);
+/* The same equation solved with restarted GMRES(m), the paper's solver for it
+ * (Section 5.2; Saad & Schultz 1986), in FP64 on an FP64 plan: eps, grad_eps
+ * as above (doubles), rho and sigma complex128 device arrays.  Arnoldi with
+ * classical Gram-Schmidt applied twice (inner products summed in FP64 in a
+ * fixed order: repeated solves are bit-identical), Givens rotations on the
+ * host; each cycle restarts from the explicit residual rho - P sigma.
+ *   restart: m in [1, 512] (the basis holds m + 1 vectors of N^d complex128;
+ *            m is capped at maxit); maxit: the budget of Arnoldi steps.
+ *   history[0..iterations] (maxit + 1 doubles, or NULL): |g_{j+1}| / ||rho||
+ *            after step j + 1 (the GMRES residual estimate), replaced at a
+ *            restart by the explicit residual.
+ *   stats: iterations = Arnoldi steps, matvecs = operator products (one per
+ *          step, plus one per restart), restarts (cycles begun from an
+ *          explicit residual), estimated_residual (the last
+ *          estimate), true_residual = ||rho - P sigma|| / ||rho|| (FP64),
+ *          seconds.
+ * Stops when the estimate (or the explicit residual at a restart) is below
+ * tol, or after maxit steps (VP_OK; see stats).  rho = 0 gives sigma = 0 and
+ * no iterations.  VP_ERR_NUMERICAL on a non-finite value or a breakdown
+ * without convergence (a zero column of H), sigma the last iterate. */
+vp_status vp_pb_gmres(vp_plan plan, const double* eps, const double* grad_eps, const void* rho, void* sigma,
+                      double tol, int restart, int maxit, double* history, vp_ls_stats* stats);
 const char* vp_ls_last_error(void);
 
 /* ---------------------------------------------------------------------------

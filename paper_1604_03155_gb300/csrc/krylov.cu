@@ -1,7 +1,8 @@
-// bicgstab.cu -- the integral-equation solvers of Sections 5.2 and 5.3 (Vico,
+// krylov.cu -- the integral-equation solvers of Sections 5.2 and 5.3 (Vico,
 // Greengard & Ferrando): unpreconditioned Bi-CGStab (van der Vorst 1992), two
 // operator products per iteration, each one apply of the plan's volume
-// potential V (or of its exact gradient).
+// potential V (or of its exact gradient); and restarted GMRES, the paper's
+// solver for the Section 5.2 equation (at the end of the file).
 //
 // Lippmann-Schwinger scattering (Section 5.3; V the Green's function of
 // -(Delta + k^2)), two forms of one problem (u the scattered field, q the real
@@ -38,7 +39,11 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
+#include <cmath>
+#include <complex>
+#include <vector>
 #include <string>
 
 #include "../../include/vp.h"
@@ -1118,6 +1123,295 @@ vp_status solve_mixed(vp_plan plan, const double* q64, const double* ge64, const
 
 namespace {
 
+// ---------------------------------------------------------------------------
+// Restarted GMRES(m) in FP64: the paper's solver for the Section 5.2 equation
+// P s = -eps s + grad(eps) . grad V[s] = rho (Saad & Schultz 1986; Saad,
+// Iterative Methods for Sparse Linear Systems, Alg. 6.9, with the Givens
+// rotations of Section 6.5.3).  Each cycle starts from v_0 = r / ||r||,
+// r = b - P x (r = b in the first cycle, x = 0).  Arnoldi step j:
+//   w = P v_j (one exact-gradient apply), then classical Gram-Schmidt applied
+//   twice ("twice is enough"): per pass one kernel of all the inner products
+//   h_i = <v_i, w>, i <= j (FP64, per-block partials summed in a fixed order)
+//   and one kernel w -= sum_i h_i v_i; h_{j+1,j} = ||w||, v_{j+1} = w / ||w||.
+// The column of H (j + 2 values) goes to the host, which applies the earlier
+// rotations, forms the new one and updates g; |g_{j+1}| / ||b|| is the
+// residual estimate.  The cycle ends after m steps or when the estimate is
+// below tol (or the step budget is spent); the host solves the triangular
+// system R y = g and x += sum_i y_i v_i runs on the device.
+// ---------------------------------------------------------------------------
+constexpr int kGmDots = 4;            // inner products per block row of k_gm_dots
+constexpr int kGmMaxRestart = 512;    // the largest restart length m accepted
+
+// part[(blockIdx.y * kBlocks + blockIdx.x) * kGmDots + k] = this block's share
+// of <v_i, w>, i = blockIdx.y * kGmDots + k < count (zero for i >= count)
+__global__ void __launch_bounds__(kThreads) k_gm_dots(const double2* __restrict__ V, long long n, int count,
+                                                      const double2* __restrict__ w, double2* __restrict__ part) {
+  const int i0 = blockIdx.y * kGmDots;
+  double re[kGmDots], im[kGmDots];
+#pragma unroll
+  for (int k = 0; k < kGmDots; ++k) re[k] = im[k] = 0.0;
+  GRID_LOOP(e, n) {
+    const double2 wv = w[e];
+#pragma unroll
+    for (int k = 0; k < kGmDots; ++k)
+      if (i0 + k < count) {
+        const double2 v = V[(long long)(i0 + k) * n + e];
+        re[k] += v.x * wv.x + v.y * wv.y;
+        im[k] += v.x * wv.y - v.y * wv.x;
+      }
+  }
+  block_partials<kGmDots>(re, im, part + (size_t)blockIdx.y * kBlocks * kGmDots);
+}
+
+// h[i] = <v_i, w> from the partials (one block per row of kGmDots products);
+// col[i] = h[i] (first pass) or col[i] + h[i] (second pass)
+__global__ void __launch_bounds__(kScalThreads) k_gm_reduce(const double2* __restrict__ part, int count,
+                                                            double2* __restrict__ h, double2* __restrict__ col,
+                                                            int accumulate) {
+  double2 s[kGmDots];
+  sum_partials<kGmDots>(part + (size_t)blockIdx.x * kBlocks * kGmDots, s);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < kGmDots; ++k) {
+      const int i = blockIdx.x * kGmDots + k;
+      if (i < count) {
+        h[i] = s[k];
+        col[i] = accumulate ? make_double2(col[i].x + s[k].x, col[i].y + s[k].y) : s[k];
+      }
+    }
+}
+
+// w += sign * sum_{i < count} c_i v_i   (sign -1: a Gram-Schmidt pass; +1: x += V y)
+__global__ void __launch_bounds__(kThreads) k_gm_axpy(double2* __restrict__ w, const double2* __restrict__ V,
+                                                      long long n, int count, const double2* __restrict__ c,
+                                                      double sign) {
+  __shared__ double2 cs[kGmMaxRestart + 1];
+  for (int i = threadIdx.x; i < count; i += blockDim.x) cs[i] = make_double2(sign * c[i].x, sign * c[i].y);
+  __syncthreads();
+  GRID_LOOP(e, n) {
+    double2 acc = w[e];
+    for (int i = 0; i < count; ++i) {
+      const double2 v = V[(long long)i * n + e];
+      acc.x += cs[i].x * v.x - cs[i].y * v.y;
+      acc.y += cs[i].x * v.y + cs[i].y * v.x;
+    }
+    w[e] = acc;
+  }
+}
+
+// partials of ||w||^2
+__global__ void __launch_bounds__(kThreads) k_gm_norm(const double2* __restrict__ w, long long n,
+                                                      double2* __restrict__ part) {
+  double s = 0.0;
+  GRID_LOOP(e, n) s += w[e].x * w[e].x + w[e].y * w[e].y;
+  const double re[1] = {s}, im[1] = {0.0};
+  block_partials<1>(re, im, part);
+}
+
+// *entry = (||w||, 0); *inv = 1 / ||w|| (0 when w = 0)
+__global__ void __launch_bounds__(kScalThreads) k_gm_norm_reduce(const double2* __restrict__ part,
+                                                                 double2* __restrict__ entry, double* __restrict__ inv) {
+  double2 s[1];
+  sum_partials<1>(part, s);
+  if (threadIdx.x == 0) {
+    const double nr = sqrt(s[0].x);
+    *entry = make_double2(nr, 0.0);
+    *inv = nr > 0.0 ? 1.0 / nr : 0.0;
+  }
+}
+
+// w *= *inv (device scalar) or w *= c (host scalar, inv == nullptr)
+__global__ void __launch_bounds__(kThreads) k_gm_scale(double2* __restrict__ w, long long n,
+                                                       const double* __restrict__ inv, double c) {
+  const double f = inv ? *inv : c;
+  GRID_LOOP(e, n) w[e] = make_double2(w[e].x * f, w[e].y * f);
+}
+
+// w = P v (t1: the d components of grad V[v])
+__global__ void __launch_bounds__(kThreads) k_gm_op(const double2* __restrict__ v, const double2* __restrict__ t1,
+                                                    OpArgs<double> a, double2* __restrict__ w) {
+  GRID_LOOP(i, a.n) w[i] = op_at<double, F_PB>(v[i], t1, a, i);
+}
+
+struct DevBuf {
+  void* p = nullptr;
+  ~DevBuf() { cudaFree(p); }
+};
+
+// The GMRES(m) solve of the Poisson-Boltzmann form; the plan is FP64.
+vp_status gmres_pb(vp_plan plan, const double* eps, const double* ge, const double2* rho, double2* x, int d,
+                   long long n, double tol, int m, int maxit, double* history, vp_ls_stats* stats, Err& E) {
+  using cd = std::complex<double>;
+  const auto t_start = std::chrono::steady_clock::now();
+  m = m < maxit ? m : maxit;
+  const int rows = (m + 1 + kGmDots - 1) / kGmDots;
+  Work<double> w;  // stream, t1 (d gradient fields), apply workspace, partials
+  w.n = n;
+  BCG_CUDA(E, cudaStreamCreateWithFlags(&w.s, cudaStreamNonBlocking));
+  BCG_CUDA(E, cudaMalloc(&w.t1, (size_t)d * n * sizeof(double2)));
+  w.ws_bytes = form_workspace_bytes(plan, F_PB);
+  BCG_CUDA(E, cudaMalloc(&w.ws, w.ws_bytes));
+  BCG_CUDA(E, cudaMalloc(&w.part, 2 * kBlocks * sizeof(double2)));
+  DevBuf V, partg, h, col, inv;
+  BCG_CUDA(E, cudaMalloc(&V.p, (size_t)(m + 1) * n * sizeof(double2)));
+  BCG_CUDA(E, cudaMalloc(&partg.p, (size_t)rows * kBlocks * kGmDots * sizeof(double2)));
+  BCG_CUDA(E, cudaMalloc(&h.p, (m + 1) * sizeof(double2)));
+  BCG_CUDA(E, cudaMalloc(&col.p, (m + 2) * sizeof(double2)));
+  BCG_CUDA(E, cudaMalloc(&inv.p, sizeof(double)));
+  struct HostBuf {
+    double2* p = nullptr;
+    ~HostBuf() { cudaFreeHost(p); }
+  } hc;
+  BCG_CUDA(E, cudaMallocHost(&hc.p, (m + 2) * sizeof(double2)));
+  double2* const Vb = static_cast<double2*>(V.p);
+  double2* const hd = static_cast<double2*>(h.p);
+  double2* const cold = static_cast<double2*>(col.p);
+  double* const invd = static_cast<double*>(inv.p);
+  double2* const pg = static_cast<double2*>(partg.p);
+  PlanGuard guard{plan, vp::plan_stream(plan), VP_FP64};
+  BCG_CUDA(E, cudaStreamSynchronize(guard.stream));  // inputs produced on the plan's stream
+  vp_status st = vp_plan_set_stream(plan, w.s);
+  if (st != VP_OK) return st;
+  const OpArgs<double> a{eps, ge, 0.0, d, n};
+  auto host_sum = [&](int K, double* out) -> vp_status {  // out[k] = sum of the kBlocks partials' .x
+    std::vector<double2> hp((size_t)K * kBlocks);
+    BCG_CUDA(E, cudaMemcpyAsync(hp.data(), w.part, hp.size() * sizeof(double2), cudaMemcpyDeviceToHost, w.s));
+    BCG_CUDA(E, cudaStreamSynchronize(w.s));
+    for (int k = 0; k < K; ++k) {
+      out[k] = 0.0;
+      for (int b = 0; b < kBlocks; ++b) out[k] += hp[(size_t)b * K + k].x;
+    }
+    return VP_OK;
+  };
+
+  BCG_CUDA(E, cudaMemsetAsync(x, 0, n * sizeof(double2), w.s));
+  k_gm_norm<<<kBlocks, kThreads, 0, w.s>>>(rho, n, w.part);
+  double bn2 = 0.0;
+  if ((st = host_sum(1, &bn2)) != VP_OK) return st;
+  const double bn = sqrt(bn2);
+  if (history) history[0] = 1.0;
+  int it = 0, cycles = 0, matvecs = 0, restarts = 0;
+  double est = bn > 0 ? 1.0 : 0.0;
+  bool breakdown = false;
+  std::vector<cd> H((size_t)(m + 1) * m), g(m + 1), sn(m), y(m);
+  std::vector<double> cs(m);
+  auto Hc = [&](int i, int j) -> cd& { return H[(size_t)j * (m + 1) + i]; };
+  while (bn > 0) {
+    // v_0 = r / ||r||
+    double beta = bn;
+    if (cycles == 0) {
+      BCG_CUDA(E, cudaMemcpyAsync(Vb, rho, n * sizeof(double2), cudaMemcpyDeviceToDevice, w.s));
+    } else {
+      if ((st = apply_v<double, F_PB>(plan, w, x)) != VP_OK) return st;
+      k_residual_vec<F_PB><<<kBlocks, kThreads, 0, w.s>>>(rho, x, w.t1, a, Vb, w.part);
+      double sums[2];
+      if ((st = host_sum(2, sums)) != VP_OK) return st;
+      ++matvecs;
+      ++restarts;
+      beta = sqrt(sums[0]);
+      est = beta / bn;
+      if (history) history[it] = est;  // the explicit residual replaces the estimate
+      if (est < tol || !std::isfinite(est)) break;
+    }
+    if (it >= maxit) break;
+    if (beta == 0.0) break;
+    k_gm_scale<<<kBlocks, kThreads, 0, w.s>>>(Vb, n, nullptr, 1.0 / beta);
+    std::fill(g.begin(), g.end(), cd(0.0));
+    g[0] = beta;
+    int jend = 0;
+    for (int j = 0; j < m; ++j) {
+      double2* const vj = Vb + (size_t)j * n;
+      double2* const wv = Vb + (size_t)(j + 1) * n;
+      if ((st = apply_v<double, F_PB>(plan, w, vj)) != VP_OK) return st;
+      k_gm_op<<<kBlocks, kThreads, 0, w.s>>>(vj, w.t1, a, wv);
+      ++matvecs;
+      const int cnt = j + 1, rws = (cnt + kGmDots - 1) / kGmDots;
+      for (int pass = 0; pass < 2; ++pass) {
+        k_gm_dots<<<dim3(kBlocks, rws), kThreads, 0, w.s>>>(Vb, n, cnt, wv, pg);
+        k_gm_reduce<<<rws, kScalThreads, 0, w.s>>>(pg, cnt, hd, cold, pass);
+        k_gm_axpy<<<kBlocks, kThreads, 0, w.s>>>(wv, Vb, n, cnt, hd, -1.0);
+      }
+      k_gm_norm<<<kBlocks, kThreads, 0, w.s>>>(wv, n, w.part);
+      k_gm_norm_reduce<<<1, kScalThreads, 0, w.s>>>(w.part, cold + j + 1, invd);
+      k_gm_scale<<<kBlocks, kThreads, 0, w.s>>>(wv, n, invd, 0.0);
+      BCG_CUDA(E, cudaMemcpyAsync(hc.p, cold, (j + 2) * sizeof(double2), cudaMemcpyDeviceToHost, w.s));
+      BCG_CUDA(E, cudaStreamSynchronize(w.s));
+      BCG_CUDA(E, cudaGetLastError());
+      bool finite = true;
+      for (int i = 0; i <= j + 1; ++i) {
+        Hc(i, j) = cd(hc.p[i].x, hc.p[i].y);
+        finite = finite && std::isfinite(hc.p[i].x) && std::isfinite(hc.p[i].y);
+      }
+      if (!finite) {
+        E.msg = "GMRES produced a non-finite value";
+        return E.st = VP_ERR_NUMERICAL;
+      }
+      for (int i = 0; i < j; ++i) {  // the earlier rotations
+        const cd t = cs[i] * Hc(i, j) + sn[i] * Hc(i + 1, j);
+        Hc(i + 1, j) = -std::conj(sn[i]) * Hc(i, j) + cs[i] * Hc(i + 1, j);
+        Hc(i, j) = t;
+      }
+      const double a0 = std::abs(Hc(j, j)), a1 = std::abs(Hc(j + 1, j)), den = std::hypot(a0, a1);
+      if (den == 0.0) {  // P v_j = 0 within the basis: no progress is possible
+        breakdown = true;
+        break;
+      }
+      if (a0 == 0.0) {
+        cs[j] = 0.0;
+        sn[j] = std::conj(Hc(j + 1, j)) / den;
+      } else {
+        cs[j] = a0 / den;
+        sn[j] = (Hc(j, j) / a0) * std::conj(Hc(j + 1, j)) / den;
+      }
+      Hc(j, j) = cs[j] * Hc(j, j) + sn[j] * Hc(j + 1, j);
+      Hc(j + 1, j) = 0.0;
+      g[j + 1] = -std::conj(sn[j]) * g[j];
+      g[j] = cs[j] * g[j];
+      ++it;
+      jend = j + 1;
+      est = std::abs(g[j + 1]) / bn;
+      if (history) history[it] = est;
+      if (est < tol || it >= maxit) break;
+    }
+    // x += V y with R y = g (back substitution on the rotated H)
+    for (int i = jend - 1; i >= 0; --i) {
+      cd acc = g[i];
+      for (int k = i + 1; k < jend; ++k) acc -= Hc(i, k) * y[k];
+      y[i] = acc / Hc(i, i);
+    }
+    if (jend > 0) {
+      for (int i = 0; i < jend; ++i) hc.p[i] = make_double2(y[i].real(), y[i].imag());
+      BCG_CUDA(E, cudaMemcpyAsync(hd, hc.p, jend * sizeof(double2), cudaMemcpyHostToDevice, w.s));
+      k_gm_axpy<<<kBlocks, kThreads, 0, w.s>>>(x, Vb, n, jend, hd, 1.0);
+      BCG_CUDA(E, cudaStreamSynchronize(w.s));  // hc.p is rewritten by the next step's copy
+    }
+    ++cycles;
+    if (breakdown || est < tol || it >= maxit) break;
+  }
+  BCG_CUDA(E, cudaStreamSynchronize(w.s));
+  BCG_CUDA(E, cudaGetLastError());
+  const auto t_end = std::chrono::steady_clock::now();
+  double tr = 0.0;
+  if (bn > 0 && (st = residual<double, F_PB>(plan, w, w.s, w.part, rho, x, a, &tr, E)) != VP_OK) return st;
+  if (stats) {
+    stats->iterations = it;
+    stats->matvecs = matvecs;
+    stats->restarts = restarts;  // explicit residuals formed at the start of a cycle
+    stats->used_fallback = 0;
+    stats->estimated_residual = est;
+    stats->true_residual = tr;
+    stats->seconds = std::chrono::duration<double>(t_end - t_start).count();
+  }
+  if (breakdown) {
+    E.msg = "GMRES breakdown (a zero Hessenberg column) before convergence";
+    return E.st = VP_ERR_NUMERICAL;
+  }
+  return VP_OK;
+}
+
+}  // namespace
+
+namespace {
+
 // common argument checks of the entry points; *n and *d on success
 vp_status check_args(vp_plan plan, bool pb, const void* q, const void* ge, const void* src, const void* u, int form,
                      double tol, int maxit, long long* n, int* d, double* k) {
@@ -1250,6 +1544,26 @@ vp_status vp_pb_solve(vp_plan plan, const void* eps, const void* grad_eps, const
   cudaSetDevice(vp::plan_device(plan));
   st = dtype == VP_C64 ? run_one<float>(plan, F_PB, eps, grad_eps, rho, sigma, 0.0, d, n, tol, maxit, history, stats, E)
                        : run_one<double>(plan, F_PB, eps, grad_eps, rho, sigma, 0.0, d, n, tol, maxit, history, stats, E);
+  return finish(st, E);
+}
+
+vp_status vp_pb_gmres(vp_plan plan, const double* eps, const double* grad_eps, const void* rho, void* sigma,
+                      double tol, int restart, int maxit, double* history, vp_ls_stats* stats) {
+  long long n = 0;
+  int d = 0;
+  double k = 0.0;
+  vp_status st = check_args(plan, true, eps, grad_eps, rho, sigma, 0, tol, maxit, &n, &d, &k);
+  if (st == VP_OK) st = check_dtype_prec(plan, VP_C128);
+  if (st == VP_OK && (restart < 1 || restart > kGmMaxRestart)) {
+    vp::ls_set_error("restart must be in [1, 512]");
+    st = VP_ERR_INVALID_ARG;
+  }
+  if (st == VP_OK) st = vp::plan_prepare_grad(plan);
+  if (st != VP_OK) return st;
+  Err E;
+  cudaSetDevice(vp::plan_device(plan));
+  st = gmres_pb(plan, eps, grad_eps, static_cast<const double2*>(rho), static_cast<double2*>(sigma), d, n, tol,
+                restart, maxit, history, stats, E);
   return finish(st, E);
 }
 

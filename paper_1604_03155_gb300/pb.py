@@ -1,9 +1,10 @@
 """The variable-coefficient Poisson experiment of Section 5.2 (the paper's
 Table 3) on the GPU, with a seeded synthetic 1235-atom molecule standing in for
 the paper's protein: -eps sigma + grad(eps) . grad V[sigma] = rho solved with
-vp_pb_solve (Bi-CGStab over the exact-gradient apply, tolerance 1e-12), the
-potential phi = V[sigma] compared with a reference solve on a finer grid that
-contains the coarse nodes (N_ref / N an integer).
+restarted GMRES, the paper's solver (vp_pb_gmres, FP64), or with Bi-CGStab
+(vp_pb_solve, FP64 or mixed precision), over the exact-gradient apply at
+tolerance 1e-12; the potential phi = V[sigma] compared with a reference solve
+on a finer grid that contains the coarse nodes (N_ref / N an integer).
 
     E2   = ||phi_N - phi_ref||_2 / ||phi_ref||_2 over the coarse nodes
     Einf = max |phi_N - phi_ref| / max |phi_ref|
@@ -11,7 +12,7 @@ contains the coarse nodes (N_ref / N an integer).
 with the iteration count, the operator products, T_solve (seconds) and
 T_precomp (plan creation with the derivative multipliers, seconds).
 
-    python -m paper_1604_03155_gb300.pb --out pb.json
+    python -m paper_1604_03155_gb300.pb --solver gmres --out pb.json
 """
 from __future__ import annotations
 
@@ -26,7 +27,7 @@ GRIDS = [64, 96, 128, 192]
 N_REF = 384
 
 
-def solve(N: int, mol, precision: str, tol: float, maxit: int):
+def solve(N: int, mol, precision: str, tol: float, maxit: int, solver: str = "gmres", restart: int = 40):
     """One solve on the N^3 grid: (phi on the device, stats, T_precomp)."""
     import torch
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -37,8 +38,12 @@ def solve(N: int, mol, precision: str, tol: float, maxit: int):
     plan.get_array("ghatj", 0)  # builds the derivative multipliers
     torch.cuda.synchronize()
     t_pre = time.perf_counter() - t0
-    sigma, st = vp.pb_solve(plan, eps, ge.contiguous(), rho.to(torch.complex128), tol=tol, maxit=maxit,
-                            mixed=precision == "mixed")
+    if solver == "gmres":
+        sigma, st = vp.pb_gmres(plan, eps, ge.contiguous(), rho.to(torch.complex128), tol=tol, restart=restart,
+                                maxit=maxit)
+    else:
+        sigma, st = vp.pb_solve(plan, eps, ge.contiguous(), rho.to(torch.complex128), tol=tol, maxit=maxit,
+                                mixed=precision == "mixed")
     plan.set_precision("fp64")
     phi = plan.apply(sigma)
     plan.close()
@@ -57,24 +62,30 @@ def errors(phi, ref):
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--solver", default="gmres", choices=["gmres", "bicgstab"])
+    ap.add_argument("--restart", type=int, default=40, help="GMRES restart length")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"], help="mixed: Bi-CGStab only")
     ap.add_argument("--tol", type=float, default=1e-12)
     ap.add_argument("--maxit", type=int, default=2000)
     ap.add_argument("--grids", default=",".join(str(n) for n in GRIDS))
     ap.add_argument("--ref", type=int, default=N_REF)
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
+    if a.solver == "gmres" and a.precision != "fp64":
+        ap.error("GMRES runs in FP64")
     mol = I.pb_molecule()
     rows = []
-    ref, st, pre = solve(a.ref, mol, a.precision, a.tol, a.maxit)
-    rows.append(dict(N=a.ref, N_tot=a.ref ** 3, reference=True, precision=a.precision, iterations=st["iterations"],
+    ref, st, pre = solve(a.ref, mol, a.precision, a.tol, a.maxit, a.solver, a.restart)
+    rows.append(dict(N=a.ref, N_tot=a.ref ** 3, reference=True, solver=a.solver, precision=a.precision,
+                     iterations=st["iterations"],
                      matvecs=st["matvecs"], T_solve=st["seconds"], T_precomp=pre, residual=st["true_residual"]))
     print(json.dumps(rows[-1]), flush=True)
     for N in [int(v) for v in a.grids.split(",")]:
         assert a.ref % N == 0
-        phi, st, pre = solve(N, mol, a.precision, a.tol, a.maxit)
+        phi, st, pre = solve(N, mol, a.precision, a.tol, a.maxit, a.solver, a.restart)
         e2, einf = errors(phi, ref)
-        rows.append(dict(N=N, N_tot=N ** 3, reference=False, precision=a.precision, E2=e2, Einf=einf,
+        rows.append(dict(N=N, N_tot=N ** 3, reference=False, solver=a.solver, precision=a.precision, E2=e2,
+                         Einf=einf,
                          iterations=st["iterations"], matvecs=st["matvecs"], T_solve=st["seconds"], T_precomp=pre,
                          residual=st["true_residual"]))
         print(json.dumps(rows[-1]), flush=True)

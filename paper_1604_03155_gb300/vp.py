@@ -98,6 +98,8 @@ _SIGNATURES = {
                             c_void_p]),
     "vp_pb_solve_mixed": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_double, c_int,
                                   c_void_p, c_void_p]),
+    "vp_pb_gmres": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_int, c_int, c_void_p,
+                            c_void_p]),
     "vp_ls_krylov_basis": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, ctypes.POINTER(c_int)]),
     "vp_ls_flexible_basis": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p,
                                      ctypes.POINTER(c_int)]),
@@ -568,6 +570,24 @@ def pb_solve(plan: Plan, eps, grad_eps, rho, sigma=None, tol: float = 1e-12, max
         code = lib().vp_pb_solve(plan.handle, _ptr(eps), _ptr(grad_eps), _ptr(rho), _ptr(sigma), _dtype_code(rho),
                                  tol, maxit, hp, ctypes.byref(st))
     _lscheck(code)
+    stats = {k: getattr(st, k) for k, _ in LSStats._fields_}
+    if history:
+        return sigma, stats, hist[:stats["iterations"] + 1]
+    return sigma, stats
+
+
+def pb_gmres(plan: Plan, eps, grad_eps, rho, sigma=None, tol: float = 1e-12, restart: int = 40,
+             maxit: int = 1000, history: bool = False):
+    """The Section 5.2 equation with restarted GMRES(restart), the paper's
+    solver for it, in FP64 (an FP64 plan; float64 eps and grad_eps, complex128
+    rho).  Returns (sigma, stats) or (sigma, stats, history); history[j] is the
+    GMRES residual estimate after step j (the explicit residual at a restart)."""
+    sigma = _empty_like(rho, rho.shape) if sigma is None else sigma
+    st = LSStats()
+    hist = np.zeros(maxit + 1) if history else None
+    plan._sync_stream_to_torch(rho)
+    _lscheck(lib().vp_pb_gmres(plan.handle, _ptr(eps), _ptr(grad_eps), _ptr(rho), _ptr(sigma), tol, restart, maxit,
+                               _ptr(hist) if history else None, ctypes.byref(st)))
     stats = {k: getattr(st, k) for k, _ in LSStats._fields_}
     if history:
         return sigma, stats, hist[:stats["iterations"] + 1]

@@ -82,6 +82,7 @@ def test_null_arguments_of_the_solver_network_and_batch_entry_points(lib):
     assert lib.vp_ls_krylov_basis(None, None, None, 4, None, ctypes.byref(cnt)) == vp.VP_ERR_INVALID_ARG
     assert lib.vp_ls_flexible_basis(None, None, None, 4, None, None, None, ctypes.byref(cnt)) == vp.VP_ERR_INVALID_ARG
     assert lib.vp_ls_bicgstab(None, None, None, None, vp.VP_C128, 0, 1e-12, 10, None, None) == vp.VP_ERR_INVALID_ARG
+    assert lib.vp_pb_gmres(None, None, None, None, None, 1e-12, 40, 10, None, None) == vp.VP_ERR_INVALID_ARG
     assert lib.vp_ls_last_error()
     assert lib.vp_kernel_entries(None, vp.VP_ARRAY_T, 0, None, 4, None, vp.VP_C128) == vp.VP_ERR_INVALID_ARG
     assert lib.vp_matrix_block(None, vp.VP_ARRAY_T, 0, None, 2, None, 2, None, vp.VP_C128) == vp.VP_ERR_INVALID_ARG

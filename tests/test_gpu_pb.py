@@ -127,10 +127,7 @@ def test_pb_edge_cases():
     hel.close()
 
 
-def test_manufactured_solution_2d():
-    """2D Laplace plan, N = 256: the analytic sigma (Gauss's-law gradient) to
-    1e-10 in FP64 and mixed precision."""
-    N, s = 256, 0.08
+def _manufactured_2d(N, s=0.08):
     x = I.grid_coords(N)
     X = np.meshgrid(x, x, indexing="ij")
     r = np.sqrt(X[0] ** 2 + X[1] ** 2)
@@ -142,6 +139,14 @@ def test_manufactured_solution_2d():
     eps = 2.0 + g
     ge = np.stack([-2 * (X[j] - c[j]) / w ** 2 * g for j in range(2)])
     rho = -eps * sig + sum(ge[j] * dphi * X[j] / rs for j in range(2))
+    return eps, ge, rho, sig
+
+
+def test_manufactured_solution_2d():
+    """2D Laplace plan, N = 256: the analytic sigma (Gauss's-law gradient) to
+    1e-10 in FP64 and mixed precision."""
+    N = 256
+    eps, ge, rho, sig = _manufactured_2d(N)
     for mixed in (False, True):
         plan = Plan(2, N, "laplace", 0.0, 0.0, precision="fp32" if mixed else "fp64")
         e = torch.from_numpy(eps).to(DEV)
@@ -150,3 +155,104 @@ def test_manufactured_solution_2d():
         got, st = vp.pb_solve(plan, e, gg, b, tol=1e-13, mixed=mixed)
         assert _rel2(got.cpu().numpy(), sig) < 1e-10, mixed
         plan.close()
+
+
+def _gmres(d, N, eps, ge, rho, tol, restart=40, maxit=1000, history=False):
+    plan = Plan(d, N, "laplace", 0.0, 0.0, precision="fp64")
+    e = torch.as_tensor(np.asarray(eps)).to(DEV, torch.float64).contiguous()
+    g = torch.as_tensor(np.asarray(ge)).to(DEV, torch.float64).contiguous()
+    b = torch.as_tensor(np.asarray(rho)).to(DEV, torch.complex128).contiguous()
+    out = vp.pb_gmres(plan, e, g, b, tol=tol, restart=restart, maxit=maxit, history=history)
+    plan.close()
+    return (out[0].cpu().numpy(),) + tuple(out[1:])
+
+
+def test_gmres_follows_the_oracle_gmres():
+    """GMRES(40) on the molecule at N = 16 (no restart): the oracle's GMRES
+    residual estimates step by step (within 1% while above 1e-9), its step count
+    within one, and its solution to 1e-10."""
+    N = 16
+    eps, ge, rho = (t.numpy() for t in I.pb_fields(I.pb_molecule(), N))
+    prob = OPB.PBProblem(N, eps, ge)
+    x, its, ohist = OLS.gmres(prob.op, rho.astype(np.complex128), tol=1e-13, restart=40)
+    assert its < 40
+    sig, st, hist = _gmres(3, N, eps, ge, rho, 1e-13, history=True)
+    assert abs(st["iterations"] - its) <= 1 and st["restarts"] == 0
+    assert st["matvecs"] == st["iterations"]
+    assert st["true_residual"] < 1e-12
+    assert _rel2(sig, x) < 1e-10
+    m = min(len(hist), len(ohist))
+    big = np.asarray(ohist[:m]) > 1e-9
+    assert np.all(np.abs(np.asarray(hist[:m])[big] - np.asarray(ohist[:m])[big]) <= 1e-2 * np.asarray(ohist[:m])[big])
+
+
+def test_gmres_restarted_matches_the_oracle():
+    """GMRES(4) with restarts from the explicit residual: the oracle's GMRES(4)
+    solution to 1e-10 and its step count within two."""
+    N = 16
+    eps, ge, rho = (t.numpy() for t in I.pb_fields(I.pb_molecule(), N))
+    prob = OPB.PBProblem(N, eps, ge)
+    x, its, _ = OLS.gmres(prob.op, rho.astype(np.complex128), tol=1e-13, restart=4)
+    sig, st = _gmres(3, N, eps, ge, rho, 1e-13, restart=4)
+    assert st["restarts"] >= 1 and st["matvecs"] == st["iterations"] + st["restarts"]
+    assert abs(st["iterations"] - its) <= 2
+    assert st["true_residual"] < 1e-12
+    assert _rel2(sig, x) < 1e-10
+
+
+def test_gmres_manufactured_solutions():
+    """The analytic sigma to 1e-10: 3D N = 64 and 2D N = 256."""
+    eps, ge, rho, sig = _manufactured(64)
+    got, st = _gmres(3, 64, eps, ge, rho, 1e-13)
+    assert _rel2(got, sig) < 1e-10 and st["true_residual"] < 1e-12
+    eps, ge, rho, sig = _manufactured_2d(256)
+    got, st = _gmres(2, 256, eps, ge, rho, 1e-13)
+    assert _rel2(got, sig) < 1e-10 and st["true_residual"] < 1e-12
+
+
+def test_gmres_full_size_molecule_matches_bicgstab():
+    """N = 128, the 1235-atom molecule: GMRES and Bi-CGStab give the same sigma
+    to 1e-10; repeated GMRES solves are bit-identical."""
+    N = 128
+    eps, ge, rho = I.pb_fields(I.pb_molecule(), N, device=DEV)
+    plan = Plan(3, N, "laplace", 0.0, 0.0, precision="fp64")
+    b = rho.to(torch.complex128)
+    g = ge.contiguous()
+    s1, st1 = vp.pb_gmres(plan, eps, g, b, tol=1e-12)
+    s2, _ = vp.pb_gmres(plan, eps, g, b, tol=1e-12)
+    sb, stb = vp.pb_solve(plan, eps, g, b, tol=1e-12)
+    plan.close()
+    assert st1["true_residual"] < 1e-12 and st1["iterations"] < 40
+    assert torch.equal(s1, s2)
+    assert float((s1 - sb).norm() / sb.norm()) < 1e-10
+
+
+def test_gmres_edge_cases():
+    N = 8
+    plan = Plan(3, N, "laplace", 0.0, 0.0, precision="fp64")
+    eps = torch.full((N, N, N), 2.0, dtype=torch.float64, device=DEV)
+    ge = torch.zeros((3, N, N, N), dtype=torch.float64, device=DEV)
+    z = torch.zeros((N, N, N), dtype=torch.complex128, device=DEV)
+    s, st = vp.pb_gmres(plan, eps, ge, z)
+    assert st["iterations"] == 0 and torch.count_nonzero(s) == 0
+    # constant eps, grad eps = 0: P = -2 I, one step solves it
+    rho = torch.randn((N, N, N), dtype=torch.float64, device=DEV).to(torch.complex128)
+    s, st = vp.pb_gmres(plan, eps, ge, rho)
+    assert st["iterations"] == 1 and torch.allclose(s, -rho / 2, rtol=1e-14, atol=0)
+    for bad in (0, 513):
+        with pytest.raises(vp.VPError):
+            vp.pb_gmres(plan, eps, ge, rho, restart=bad)
+    with pytest.raises(vp.VPError):
+        vp.pb_gmres(plan, eps, ge, rho, sigma=rho)
+    # the step budget: VP_OK with the residual reached so far
+    e2 = eps + 0.5 * torch.rand_like(eps)
+    g2 = 0.3 * torch.randn_like(ge)
+    s, st = vp.pb_gmres(plan, e2, g2, rho, tol=1e-14, maxit=2)
+    assert st["iterations"] == 2 and st["true_residual"] > 1e-14
+    # GMRES(1) still converges on this near-identity operator
+    s1, st1 = vp.pb_gmres(plan, e2, g2, rho, tol=1e-12, restart=1, maxit=500)
+    assert st1["true_residual"] < 1e-12 and st1["restarts"] >= 1
+    plan.set_precision("fp32")
+    with pytest.raises(vp.VPError):
+        vp.pb_gmres(plan, eps, ge, rho)
+    plan.close()

@@ -28,6 +28,42 @@ def test_dense_solve_and_gmres_agree(small_problem):
     assert hist[-1] < 1e-12 and its < 200
 
 
+def test_gmres_estimates_are_the_minimal_krylov_residuals():
+    """GMRES's defining property (Saad & Schultz 1986): after k steps from x = 0
+    the residual is the smallest ||b - A x|| over x in span{b, A b, ..., A^{k-1} b},
+    computed here by least squares on an orthonormalised Krylov matrix.  With a
+    restart after m steps, the next cycle begins from the explicit residual,
+    which equals the last estimate, and the minimisation restarts from there."""
+    rng = np.random.default_rng(7)
+    n = 40
+    A = np.eye(n) + 0.4 * (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(n)
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    mv = lambda x: A @ x
+    bn = np.linalg.norm(b)
+
+    def minres(r0, k):
+        K = np.empty((n, k), dtype=np.complex128)
+        v = r0.copy()
+        for j in range(k):
+            K[:, j] = v
+            v = A @ v
+        Q, _ = np.linalg.qr(K)
+        y = np.linalg.lstsq(A @ Q, r0, rcond=None)[0]
+        return np.linalg.norm(r0 - A @ Q @ y), Q @ y
+
+    _, its, hist = LS.gmres(mv, b, tol=1e-14, restart=60, maxit=12)
+    assert its == 12 and hist[0] == 1.0
+    for k in range(1, 13):
+        assert abs(hist[k] - minres(b, k)[0] / bn) <= 1e-9 * hist[k], k
+    x, _, hist = LS.gmres(mv, b, tol=1e-14, restart=3, maxit=6)
+    r3, x3 = minres(b, 3)
+    assert abs(hist[3] - r3 / bn) <= 1e-9 * hist[3]
+    assert abs(hist[4] - hist[3]) <= 1e-9 * hist[3]  # the explicit residual of the restart
+    r6, e3 = minres(b - A @ x3, 3)
+    assert abs(hist[-1] - r6 / bn) <= 1e-9 * hist[-1]
+    assert np.linalg.norm(x - (x3 + e3)) <= 1e-9 * np.linalg.norm(x)
+
+
 def test_arnoldi_basis_pinned_by_qr_of_the_krylov_matrix(small_problem):
     """The Arnoldi vectors are the Q factor of [b, A b, ..., A^m b] (unique up to
     a unit phase per column, fixed by h_{j+1,j} > 0) and satisfy A V_m = V_{m+1} H."""

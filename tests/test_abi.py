@@ -19,7 +19,8 @@ def _declared():
     names = set()
     for fn in os.listdir(os.path.join(ROOT, "include")):
         if fn.endswith(".h"):
-            text = open(os.path.join(ROOT, "include", fn)).read()
+            with open(os.path.join(ROOT, "include", fn)) as fh:
+                text = fh.read()
             text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
             # function declarations: "<return type> vp_name(" at the start of a line
             names |= set(re.findall(r"^\s*(?:vp_status|const char\*|int)\s+(vp_\w+)\s*\(", text, flags=re.M))

@@ -36,7 +36,8 @@ def _rank_main(rank, world, port, out_dir):
 def test_max_over_ranks_with_two_gloo_ranks(tmp_path):
     mp.start_processes(_rank_main, args=(2, _free_port(), str(tmp_path)), nprocs=2, start_method="spawn")
     for r in range(2):
-        assert json.load(open(tmp_path / f"r{r}.json"))["max"] == 15.0
+        with open(tmp_path / f"r{r}.json") as fh:
+            assert json.load(fh)["max"] == 15.0
 
 
 def test_max_over_ranks_single_process_is_identity():

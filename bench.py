@@ -1,16 +1,22 @@
 """Benchmark of the volume-potential apply on GB300.
 
-Default workload: 2D Helmholtz, k = 40, N = 1024 (2N = 2048 FFTs), eight random
-Gaussian sources, FP32 complex apply with exact gradients (phi + 2 gradient
-fields from one forward transform), FP64 precompute done once before timing.
+Default workload: 3D Helmholtz, k = 60, N = 256 (the apply runs on 512^3
+complex64), sixteen random Gaussian sources, FP32 complex apply, FP64
+precompute done once before timing.  The FP64 form, the three split-operand
+tensor-core forms and cuFFT are timed beside it on the same plan and input,
+each with its relative L2 error against the FP64 oracle at sampled nodes.
+--workload selects the others (e.g. helmholtz2d_k40_n1024_grad: 2D Helmholtz,
+k = 40, N = 1024, phi + 2 exact gradient fields).
 
-One step = one vp_apply_grad on inputs resident in HBM; L2 (129 MB) is flushed
-by writing a 256 MB buffer before every timed step, outside the timed events.
-The metric is grid points per second per potential, N^d / t_step (a gradient
-call counts once).  Printed as one JSON line on rank 0.
+One step = one vp_apply (vp_apply_grad) on inputs resident in HBM; L2 (129 MB)
+is flushed by writing a 256 MB buffer before every timed step, outside the
+timed events.  The metric is grid points per second per potential, N^d / t_step
+(a gradient call counts once).  Printed as one JSON line on rank 0.
 
---impl reference times the CPU oracle (float64, its own FFT) on the same
-workload instead; it is a deliberately slow correctness reference.
+--impl reference times the CPU oracle (float64, its own FFT) on the host cores
+instead: one worker process per core, each running one apply of the workload's
+sources on a smaller grid per step; it is a deliberately slow correctness
+reference.
 """
 from __future__ import annotations
 
@@ -50,7 +56,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="helmholtz2d_k40_n1024_grad", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="helmholtz3d_k60_n256", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"] + TC_PRECISIONS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -223,6 +229,151 @@ def time_oracle(wl: dict, f: np.ndarray, steps: int, Gf=None, Gjf=None):
     return {"value": pts / wall, "seconds": wall, "cores": round(cpu / wall, 2), "out": out}
 
 
+def _oracle_worker(wl: dict, N: int, barrier, cmd, res):
+    """One host core's share of the oracle timing (a spawned process: numpy and
+    the oracle only): set up the workload's kernel on an N^d grid once, then per
+    command one full apply, started together with the other workers."""
+    sw = dict(wl, N=N)
+    f = density_sample(wl, N)
+    Gf, Gjf = oracle_setup(sw)
+    res.put("ready")
+    while cmd.get() is not None:
+        barrier.wait()
+        t0, c0 = time.perf_counter(), time.process_time()
+        oracle_step(sw, f, Gf, Gjf)
+        res.put((t0, time.perf_counter(), time.process_time() - c0))
+
+
+class OraclePool:
+    """`procs` worker processes (spawn start method, so they are safe beside a
+    CUDA context) that run the oracle apply concurrently, one per core."""
+
+    def __init__(self, wl: dict, N: int, procs: int):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        self.N, self.d, self.procs = N, wl["d"], procs
+        self.barrier = ctx.Barrier(procs)
+        self.cmds = [ctx.Queue() for _ in range(procs)]
+        self.res = ctx.Queue()
+        self.ps = [ctx.Process(target=_oracle_worker, args=(wl, N, self.barrier, c, self.res), daemon=True)
+                   for c in self.cmds]
+        for p in self.ps:
+            p.start()
+        for _ in self.ps:
+            assert self.res.get(timeout=600) == "ready"
+
+    def step(self) -> dict:
+        """One apply on every worker at once: points/s of the whole host, wall
+        seconds and the cores actually busy (CPU seconds / wall seconds)."""
+        for c in self.cmds:
+            c.put(1)
+        r = [self.res.get(timeout=1800) for _ in self.ps]
+        wall = max(x[1] for x in r) - min(x[0] for x in r)
+        cpu = sum(x[2] for x in r)
+        return {"value": self.procs * self.N ** self.d / wall, "seconds": wall, "cores": round(cpu / wall, 2)}
+
+    def close(self):
+        for c in self.cmds:
+            c.put(None)
+        for p in self.ps:
+            p.join(timeout=60)
+
+
+def host_cpu() -> dict:
+    """nproc and the CPU model of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        import platform
+        model = platform.processor() or platform.machine()
+    return {"nproc": os.cpu_count() or 1, "cpu_model": model}
+
+
+def cpu_baseline_sample_N(wl: dict) -> int:
+    """Grid size of the oracle sample: the workload's own N when the apply is
+    small (2D, or 3D N <= 64), else 64 (a 128^3 FFT convolution, a few seconds
+    per core)."""
+    if wl["d"] == 2 or wl["N"] <= 64:
+        return min(wl["N"], 512) if wl["d"] == 2 else wl["N"]
+    return 64
+
+
+def cpu_baseline(wl: dict, name: str) -> dict:
+    """The FP64 oracle as it stands on this host: all cores (one worker process
+    each, one apply each, at once) and a single core, on the workload's sources,
+    k and L sampled on a grid of cpu_baseline_sample_N points per axis."""
+    hc = host_cpu()
+    Ns = cpu_baseline_sample_N(dict(wl, name=name))
+    w = dict(wl, name=name)
+    pool = OraclePool(w, Ns, hc["nproc"])
+    allc = pool.step()
+    pool.close()
+    one = OraclePool(w, Ns, 1)
+    single = one.step()
+    one.close()
+    return {"value": allc["value"], "unit": "grid pts/s", "cores": allc["cores"], "kind": "oracle",
+            "sample": (f"{hc['nproc']} worker processes at once, each one full apply "
+                       f"({'phi + gradients' if wl['grad'] else 'phi'}) of the {name} workload's sources, k and L "
+                       f"on an N={Ns} grid ({Ns ** wl['d']} points; the workload's N is {wl['N']}), FP64 oracle "
+                       f"with its own FFT, {allc['seconds']:.1f} s wall"),
+            "nproc": hc["nproc"], "cpu_model": hc["cpu_model"],
+            "single_thread": {"value": single["value"], "unit": "grid pts/s", "cores": single["cores"],
+                              "seconds": single["seconds"]}}
+
+
+def oracle_reference(wl: dict, f_host: np.ndarray, npts: int = 40, seed: int = 1604) -> dict:
+    """The FP64 oracle's values the forms are compared with: its full result
+    (2N FFT form) on grids of at most 2^21 points, else its direct sums at
+    sampled nodes (the 2^d corners and seeded random nodes; each value is the
+    full sum over the grid)."""
+    from oracle import apply as A
+    from oracle import kernel as K
+    d, N = wl["d"], wl["N"]
+    f64 = np.asarray(f_host, dtype=np.complex128)
+    if N ** d <= 2 ** 21:
+        Gf, Gjf = oracle_setup(wl)
+        phi_o, grads_o = oracle_step(wl, f64, Gf, Gjf)
+        return {"kind": "full", "phi": phi_o, "grad": np.stack(grads_o) if grads_o else None,
+                "what": "every output of the FP64 oracle (2N FFT form)"}
+    T = K.T_octant_by_sums(d, N, wl["kernel"], wl["k"], wl["L"])
+    corners = [tuple(c) for c in np.ndindex(*(2,) * d)]
+    corners = [tuple((N - 1) * v for v in c) for c in corners]
+    rng = np.random.default_rng(seed)
+    pts = corners + [tuple(int(v) for v in rng.integers(0, N, d)) for _ in range(npts - len(corners))]
+    vals = A.apply_direct_at_octant(T, f64, pts)
+    grads = None
+    if wl["grad"]:
+        grads = np.stack([A.apply_direct_at_octant(K.T_octant_by_sums(d, N, wl["kernel"], wl["k"], wl["L"],
+                                                                       deriv_axis=j), f64, pts, odd_axis=j)
+                          for j in range(d)])
+    return {"kind": "sampled", "points": pts, "phi": vals, "grad": grads,
+            "what": f"the FP64 oracle's direct sums at {len(pts)} nodes (the {len(corners)} corners and "
+                    f"{len(pts) - len(corners)} seeded random nodes), relative L2 over those nodes"}
+
+
+def form_errors(ref: dict, phi, grad=None) -> dict:
+    """Relative L2 of one form's phi (and gradient) against the oracle reference."""
+    from oracle import apply as A
+    if ref["kind"] == "full":
+        e = {"phi": A.rel_l2(phi.cpu().numpy(), ref["phi"])}
+        if grad is not None and ref["grad"] is not None:
+            e["grad"] = A.rel_l2(grad.cpu().numpy(), ref["grad"])
+        return e
+    import torch
+    idx = tuple(torch.tensor(c, device=phi.device) for c in zip(*ref["points"]))
+    e = {"phi": A.rel_l2(phi[idx].cpu().numpy(), ref["phi"])}
+    if grad is not None and ref["grad"] is not None:
+        e["grad"] = A.rel_l2(np.stack([grad[j][idx].cpu().numpy() for j in range(grad.shape[0])]), ref["grad"])
+    return e
+
+
 def max_over_ranks(value: float, device) -> float:
     """The maximum of `value` over the ranks of the default process group (the
     slowest rank sets the job's time); `value` itself with one rank."""
@@ -293,25 +444,30 @@ def run_reference(args, wl):
         w = I.batch_recipe()[32]
         wl = dict(wl, N=w.N, kernel=w.kernel, k=w.k)
     Ns = reference_sample_N(wl, steps)
-    sw = dict(wl, N=Ns)
-    f = density_sample(wl, Ns)
-    Gf, Gjf = oracle_setup(sw)
+    hc = host_cpu()
+    pool = OraclePool(wl, Ns, hc["nproc"])
     for _ in range(max(0, min(args.warmup, 1))):
-        oracle_step(sw, f, Gf, Gjf)
-    r = time_oracle(sw, f, steps, Gf, Gjf)
+        pool.step()
+    rs = [pool.step() for _ in range(steps)]
+    pool.close()
+    wall = sum(r["seconds"] for r in rs)
+    value = hc["nproc"] * Ns ** wl["d"] * steps / wall
+    cores = round(sum(r["cores"] * r["seconds"] for r in rs) / wall, 2)
     unit = "grid pts/s"
-    sample = (f"per step one full apply (phi{' + gradients' if wl['grad'] else ''}) of the {args.workload} "
-              f"workload (same sources, k, L) on an N={Ns} grid ({Ns ** wl['d']} points; the workload's N is "
-              f"{wl['N']}), FP64 oracle with its own FFT; N chosen so that {steps} steps take about two minutes")
+    sample = (f"per step {hc['nproc']} worker processes at once (one per host core), each one full apply "
+              f"(phi{' + gradients' if wl['grad'] else ''}) of the {args.workload} workload's sources, k and L on "
+              f"an N={Ns} grid ({Ns ** wl['d']} points; the workload's N is {wl['N']}), FP64 oracle with its own "
+              f"FFT; N chosen so that {steps} steps take about two minutes")
     line = {
         "impl": "reference",
         "metric": "grid pts/s per potential (N^d/s), % HBM roofline, vs plain FP64 at stated rel err",
-        "value": r["value"], "unit": unit, "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup,
-        "ms_per_step": 1000 * r["seconds"] / steps, "higher_is_better": True, "scaling": "weak",
+        "value": value, "unit": unit, "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * wall / steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, **{k: v for k, v in wl.items() if k != "name"}},
-        "cpu_baseline": {"value": r["value"], "unit": unit, "cores": r["cores"], "kind": "oracle", "sample": sample},
-        "e2e": {"value": r["value"], "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle", "sample": sample,
+                         "nproc": hc["nproc"], "cpu_model": hc["cpu_model"]},
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
@@ -324,7 +480,6 @@ def run_ours(args, wl):
     import torch
     import torch.distributed as dist
 
-    from oracle import apply as OA  # noqa: F401  (cpu_baseline leg only)
     from paper_1604_03155_gb300.vp import Plan
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -427,8 +582,9 @@ def run_ours(args, wl):
     e2e_s = e2e_time(True)
     U_b = (N ** d) * csize
 
-    def time_form(form: str, reps: int = 20) -> float:
-        """ms per step of the same apply in another precision on this plan."""
+    def time_form(form: str, reps: int = 20):
+        """ms per step of the same apply in another precision on this plan, the
+        per-pass timings of those steps and the outputs of the last one."""
         plan.set_precision(form)
         ff = f.to(torch.complex128) if form == "fp64" else f
         pp = torch.empty_like(ff)
@@ -438,14 +594,20 @@ def run_ours(args, wl):
         with torch.cuda.stream(stream):
             for _ in range(3):
                 plan.apply_grad(ff, pp, gg) if wl["grad"] else plan.apply(ff, pp)
+            torch.cuda.synchronize(dev)
+            plan.get_timing()
+            plan.set_timing(True)
             for i in range(reps):
                 flush.fill_(float(i))
                 s_[i].record(stream)
                 plan.apply_grad(ff, pp, gg) if wl["grad"] else plan.apply(ff, pp)
                 e_[i].record(stream)
         torch.cuda.synchronize(dev)
+        plan.set_timing(False)
+        tim = plan.get_timing()
+        plan.status()
         plan.set_precision(prec)
-        return sum(a.elapsed_time(b) for a, b in zip(s_, e_)) / reps
+        return sum(a.elapsed_time(b) for a, b in zip(s_, e_)) / reps, tim, pp, gg
 
     def cufft_form(reps: int = 20) -> dict:
         """The same apply with cuFFT (torch.fft) for comparison only: f zero-padded to
@@ -499,16 +661,38 @@ def run_ours(args, wl):
 
     cufft = cufft_form() if f32io else None
 
+    # the FP64 oracle's reference values for the error of every form (rank 0, N = 1)
+    ref = oracle_reference(dict(wl, name=args.workload), f_host) if (rank == 0 and world == 1) else None
+    errs = form_errors(ref, phi, grad) if ref is not None else None
+
+    def form_line(form: str, reps: int) -> dict:
+        ms_f, tim, pp, gg = time_form(form, reps)
+        out = {"value": (N ** d) / (ms_f / 1000.0), "ms_per_step": ms_f, "speedup_of_this_form": ms_f / ms_per_step}
+        if ref is not None:
+            out["rel_l2_vs_oracle"] = form_errors(ref, pp, gg)
+        if form in TC_PRECISIONS:
+            fl_, fms = tim.get("fused_axis0", (0, 0.0))
+            if fl_:
+                t_s = fms / fl_ / 1000.0
+                fl = tc_flops_per_launch(N, form)
+                tpk, tkind = measured_peak_bf16(sustained=False)
+                out["fused_axis0_ms"] = t_s * 1000.0
+                out["tensor"] = {"kernel": "fused_axis0 (tcgen05)", "flops_per_launch": fl,
+                                 "achieved_tflops": fl / t_s / 1e12, "peak_tflops": tpk, "peak_source": tkind,
+                                 "frac": fl / t_s / 1e12 / tpk}
+        del pp, gg
+        torch.cuda.empty_cache()
+        return out
+
     # FP64 form on the same grid (same kernels in double), for "vs plain FP64";
-    # the tensor-core forms are also compared with the FP32 form
-    fp64 = None
-    fp32_form = None
-    if prec != "fp64":
-        ms64 = time_form("fp64", 10)
-        fp64 = {"value": (N ** d) / (ms64 / 1000.0), "ms_per_step": ms64, "speedup_of_this_form": ms64 / ms_per_step}
-    if prec in TC_PRECISIONS:
-        ms32 = time_form("fp32")
-        fp32_form = {"value": (N ** d) / (ms32 / 1000.0), "ms_per_step": ms32, "speedup_of_this_form": ms32 / ms_per_step}
+    # the split tensor-core forms of the fused pass (3D, 2N = 256 or 512) beside
+    # the FP32 form; with a tensor-core --precision the FP32 form is the extra
+    fp64 = form_line("fp64", 10) if prec != "fp64" else None
+    extras = {}
+    if prec == "fp32" and d == 3 and N in (128, 256) and not wl["grad"]:
+        for form in TC_PRECISIONS:
+            extras[form] = form_line(form, 20)
+    fp32_form = form_line("fp32", 20) if prec in TC_PRECISIONS else None
 
     line = None
     if rank == 0:
@@ -520,11 +704,18 @@ def run_ours(args, wl):
             "data": "synthetic",
             "config": {"workload": args.workload, "d": d, "N": N, "kernel": wl["kernel"], "k": wl["k"],
                        "L": wl["L"], "fields": F, "grad_mode": "exact" if wl["grad"] else None,
+                       "precision": prec,
                        "l2": "flushed before every timed step (256 MB write)", "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic,
                          "algorithmic_bytes_per_launch": pb[dom], "avg_launch_ms": dom_avg_s * 1000.0},
-            "passes": {k: {"launches": v[0], "avg_ms": (v[1] / v[0] if v[0] else None)} for k, v in passes.items()},
+            "step_roofline": {"algorithmic_bytes_per_step": sum(pb[k] for k in passes if passes[k][0] > 0),
+                              "achieved": sum(pb[k] for k in passes if passes[k][0] > 0) / (ms_per_step / 1000.0) / 1e9,
+                              "peak": peak, "unit": "GB/s",
+                              "frac": sum(pb[k] for k in passes if passes[k][0] > 0) / (ms_per_step / 1000.0) / 1e9 / peak},
+            "passes": {k: {"launches": v[0], "avg_ms": (v[1] / v[0] if v[0] else None),
+                           "frac_of_hbm": (pb[k] / (v[1] / v[0] / 1000.0) / 1e9 / peak) if v[0] else None}
+                       for k, v in passes.items()},
             "clocks": clk,
             "e2e": {"value": (N ** d) / e2e_s, "unit": "grid pts/s", "h2d_bytes_per_step": U_b,
                     "d2h_bytes_per_step": U_b * F,
@@ -535,9 +726,13 @@ def run_ours(args, wl):
             "fp64_form": fp64,
             "cufft_form": cufft,
         }
+        if extras:
+            line["tensor_core_forms"] = extras
+        if errs is not None:
+            line["rel_l2_vs_oracle"] = errs
+            line["oracle_reference"] = ref["what"]
         if fp32_form is not None:
             line["fp32_form"] = fp32_form
-            line["config"]["precision"] = prec
             fused_launches, fused_ms = passes.get("fused_axis0", (0, 0.0))
             if fused_launches:
                 t_s = fused_ms / fused_launches / 1000.0
@@ -547,15 +742,7 @@ def run_ours(args, wl):
                                   "achieved_tflops": fl / t_s / 1e12, "peak_tflops": tpk, "peak_source": tkind,
                                   "frac": fl / t_s / 1e12 / tpk}
         if not args.no_cpu_baseline and world == 1:
-            r = time_oracle(wl, f_host.astype(np.complex128), 1)
-            phi_o, grads_o = r["out"]
-            from oracle import apply as A
-            errs = {"phi": A.rel_l2(phi.cpu().numpy(), phi_o)}
-            if wl["grad"]:
-                errs["grad"] = A.rel_l2(grad.cpu().numpy(), np.stack(grads_o))
-            line["cpu_baseline"] = {"value": r["value"], "unit": "grid pts/s", "cores": r["cores"], "kind": "oracle",
-                                    "sample": f"one full {args.workload} apply ({'phi + gradients' if wl['grad'] else 'phi'}), FP64 oracle, own FFT"}
-            line["rel_l2_vs_oracle"] = errs
+            line["cpu_baseline"] = cpu_baseline(wl, args.workload)
         print(json.dumps(line), flush=True)
     plan.close()
     if world > 1:

@@ -61,6 +61,25 @@ def apply_direct_at(T_full: np.ndarray, f: np.ndarray, points) -> np.ndarray:
     return np.array(out)
 
 
+def apply_direct_at_octant(T_oct: np.ndarray, f: np.ndarray, points, odd_axis=None) -> np.ndarray:
+    """phi at the listed storage points, each by its full sum over the grid, with
+    T(n) read from its octant [0, N]^d by evenness in every n_j (oddness along
+    ``odd_axis``): T(p - p') = T_oct[|p_0 - p'_0|, ...] (times sign(p_j - p'_j)
+    on the odd axis).  Needs no (2N+1)^d array, so it serves full-size grids."""
+    d = f.ndim
+    out = []
+    for p in points:
+        a = [np.abs(int(pj) - np.arange(f.shape[j])) for j, pj in enumerate(p)]
+        Tw = T_oct[np.ix_(*a)]
+        if odd_axis is not None:
+            sgn = np.sign(int(p[odd_axis]) - np.arange(f.shape[odd_axis])).astype(np.float64)
+            shape = [1] * d
+            shape[odd_axis] = f.shape[odd_axis]
+            Tw = Tw * sgn.reshape(shape)
+        out.append(np.sum(Tw * f))
+    return np.array(out)
+
+
 def apply_fft2n(ghat_full: np.ndarray, f: np.ndarray) -> np.ndarray:
     N = f.shape[0]
     X = offt.fftn(_pad(f, 2 * N))

@@ -54,3 +54,26 @@ def condition(d, N, kernel, k, L, f, odd_axis=None):
     phi = A.apply_fft2n(K.ghat_full_from_octant(octants(d, N, kernel, k, L)[1]) if odd_axis is None else
                         K.ghat_full_from_octant(grad_octants(d, N, kernel, k, L, odd_axis)[1], odd_axis), f)
     return max(1.0, top / np.linalg.norm(phi.ravel()))
+
+
+# Relative-L2 bars of the parity sweeps.  A discrete convolution computed in
+# floating point with unit roundoff u has forward error of order
+# u * log(n) * || |T| * |f| ||, i.e. a relative error of order u * log(n) * kappa.
+# Where kappa < KAPPA_FLAT the plain bar (1e-5 FP32, 1e-12 FP64) is asserted
+# as it stands; above it the bar is tol * min(kappa, KAPPA_CAP), and a case with
+# kappa beyond the cap is still held to tol * KAPPA_CAP.
+KAPPA_FLAT = 1.5
+KAPPA_CAP = 12.0
+
+
+def bar(tol, kappa):
+    """The relative-L2 bar of a sweep case of condition number kappa."""
+    return tol if kappa < KAPPA_FLAT else tol * min(kappa, KAPPA_CAP)
+
+
+def check(name, err, tol, kappa):
+    """Prints the case's error, kappa and bar (pytest -s / -rP shows it) and
+    returns whether the error is under the bar."""
+    b = bar(tol, kappa)
+    print(f"PARITY {name} rel_l2={err:.3e} kappa={kappa:.2f} bar={b:.1e} flat={tol:.0e}")
+    return err < b

@@ -11,7 +11,7 @@ import torch
 from oracle import apply as A
 from oracle import closed_forms as CF
 from oracle import kernel as K
-from oracle_cases import condition, octants, potential
+from oracle_cases import check, condition, potential
 from paper_1604_03155_gb300 import inputs as I
 from paper_1604_03155_gb300.vp import Plan, VPError
 
@@ -52,7 +52,7 @@ def test_apply_3d(prec, N, kernel, k):
     f = _density(3, N, 1000 + N, prec)
     phi, _ = _run(plan, f)
     ref, _ = potential(3, N, kernel, k, 1.8, f)
-    assert A.rel_l2(phi, ref) < TOL[prec] * condition(3, N, kernel, k, 1.8, f)
+    assert check(f"3d {kernel} k={k} N={N} {prec}", A.rel_l2(phi, ref), TOL[prec], condition(3, N, kernel, k, 1.8, f))
     plan.close()
 
 
@@ -64,7 +64,7 @@ def test_apply_2d(prec, N, kernel, k):
     f = _density(2, N, 2000 + N, prec)
     phi, _ = _run(plan, f)
     ref, _ = potential(2, N, kernel, k, 1.5, f)
-    assert A.rel_l2(phi, ref) < TOL[prec] * condition(2, N, kernel, k, 1.5, f)
+    assert check(f"2d {kernel} k={k} N={N} {prec}", A.rel_l2(phi, ref), TOL[prec], condition(2, N, kernel, k, 1.5, f))
     plan.close()
 
 
@@ -80,15 +80,15 @@ def test_apply_grad(prec, mode, d, N, kernel, k):
     L = 1.8 if d == 3 else 1.5
     ref_phi, ref_g = potential(d, N, kernel, k, L, f, mode)
     kap = condition(d, N, kernel, k, L, f)
-    if mode == "exact":
-        kap = max([kap] + [condition(d, N, kernel, k, L, f, j) for j in range(d)])
-    assert A.rel_l2(phi, ref_phi) < TOL[prec] * kap
-    assert A.rel_l2(g, ref_g) < TOL[prec] * kap
+    kap_g = max([kap] + [condition(d, N, kernel, k, L, f, j) for j in range(d)]) if mode == "exact" else kap
+    name = f"grad {mode} {d}d {kernel} k={k} N={N} {prec}"
+    assert check(name + " phi", A.rel_l2(phi, ref_phi), TOL[prec], kap)
+    assert check(name + " grad", A.rel_l2(g, ref_g), TOL[prec], kap_g)
     # grad without phi
     plan.set_grad_mode(mode)
     _, g2 = plan.apply_grad(torch.from_numpy(f).to(DEV), with_phi=False)
     torch.cuda.synchronize()
-    assert A.rel_l2(g2.cpu().numpy(), ref_g) < TOL[prec] * kap
+    assert check(name + " grad only", A.rel_l2(g2.cpu().numpy(), ref_g), TOL[prec], kap_g)
     plan.close()
 
 
@@ -181,29 +181,6 @@ def test_workload_helmholtz2d_n1024_grad_full():
     ref_phi, ref_g = potential(2, 1024, "helmholtz", 40.0, 1.5, f, "exact")
     assert A.rel_l2(phi, ref_phi) < 1e-5
     assert A.rel_l2(g, ref_g) < 1e-5
-    plan.close()
-
-
-def test_workload_helmholtz3d_n256_sampled():
-    """3D Helmholtz k = 60, N = 256 (512^3 apply), 16 Gaussians, FP32: sampled
-    outputs against the oracle's direct sum, plus linearity at full size."""
-    w = I.workload("helmholtz3d_k60_n256")
-    N = 256
-    f = I.to_device_dtype(w.density(), "fp32")
-    plan = Plan(3, N, "helmholtz", 60.0, 1.8, precision="fp32")
-    ft = torch.from_numpy(f).to(DEV)
-    phi = plan.apply(ft).cpu().numpy()
-    T, _ = octants(3, N, "helmholtz", 60.0, 1.8)
-    Tf = K.T_full_from_octant(T)
-    rng = np.random.default_rng(3)
-    pts = [tuple(int(v) for v in rng.integers(0, N, 3)) for _ in range(6)] + [(0, 0, 0), (N - 1,) * 3, (127, 127, 127)]
-    ref = A.apply_direct_at(Tf, f.astype(np.complex128), pts)
-    got = np.array([phi[p] for p in pts])
-    scale = np.sqrt(np.mean(np.abs(phi) ** 2))
-    assert np.abs(got - ref).max() < 1e-5 * scale * 10
-    # linearity at full size (same precision path)
-    phi2 = plan.apply(ft * (2 - 1j)).cpu().numpy()
-    assert A.rel_l2(phi2, (2 - 1j) * phi) < 1e-6
     plan.close()
 
 

@@ -9,7 +9,7 @@ import pytest
 import torch
 
 from oracle import apply as A
-from oracle_cases import condition, potential
+from oracle_cases import check, condition, potential
 from paper_1604_03155_gb300 import inputs as I
 from paper_1604_03155_gb300 import vp
 from paper_1604_03155_gb300.vp import Batch, Plan, VPError
@@ -44,7 +44,8 @@ def test_mixed_batch_against_oracle(strategy):
     for (d, N, kern, k), h, o in zip(MIXED, hs, outs):
         L = 1.8 if d == 3 else 1.5
         ref, _ = potential(d, N, kern, k, L, h)
-        assert A.rel_l2(o.cpu().numpy(), ref) < 1e-5 * condition(d, N, kern, k, L, h)
+        assert check(f"batch {d}d {kern} k={k} N={N}", A.rel_l2(o.cpu().numpy(), ref), 1e-5,
+                     condition(d, N, kern, k, L, h))
     b.close()
 
 

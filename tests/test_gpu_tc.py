@@ -13,8 +13,8 @@ BF16 x 2 3.1e-6 / 1.6e-6 / 5.0e-6, FP16 x 2 8.4e-7 / 5.9e-7 / 9.3e-7,
 BF16 x 3 1.0e-6 / 7.2e-7 / 1.3e-6 (FP32 path 1.8e-7 / 1.0e-7).  FP16 x 2 and
 BF16 x 3 sit near 1e-6 rather than at their split level: there the tensor
 core's FP32 accumulation, not the split, sets the error.  The bars are the
-measured values with a factor of about 3 of margin; all are below the FP32
-requirement of 1e-5.
+measured values with a factor of 2-3 of margin; all are below the FP32
+requirement of 1e-5, and BF16 x 2 is held to that requirement itself.
 """
 import numpy as np
 import pytest
@@ -28,7 +28,7 @@ from paper_1604_03155_gb300.vp import Plan, VPError
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 MODES = ["tc_bf16x2", "tc_fp16x2", "tc_bf16x3"]
-BAR = {"tc_bf16x2": 2e-5, "tc_fp16x2": 3e-6, "tc_bf16x3": 4e-6, "fp32": 1e-6}
+BAR = {"tc_bf16x2": 1e-5, "tc_fp16x2": 3e-6, "tc_bf16x3": 4e-6, "fp32": 1e-6}
 N = 128
 
 
@@ -56,24 +56,16 @@ def test_tc_apply_matches_oracle(case, mode):
     plan.close()
 
 
-def test_tc_full_size_against_fp32_and_sampled_oracle():
+def test_tc_full_size_against_fp32():
     """3D Helmholtz k = 60, N = 256 (2N = 512, the N2 = 32 kernel): each split
-    against the FP32 path on the full grid and against the oracle's direct sum
-    at sampled points."""
-    from oracle import kernel as K
-    from oracle_cases import octants
+    against the FP32 path on the full grid (the oracle comparison of every
+    element is in test_gpu_fullsize.py)."""
     w = I.workload("helmholtz3d_k60_n256")
     Nw = 256
     f = I.to_device_dtype(w.density(), "fp32")
     ft = torch.from_numpy(f).to(DEV)
     plan = Plan(3, Nw, "helmholtz", 60.0, 1.8, precision="fp32")
     ref32 = plan.apply(ft).cpu().numpy()
-    T, _ = octants(3, Nw, "helmholtz", 60.0, 1.8)
-    Tf = K.T_full_from_octant(T)
-    rng = np.random.default_rng(11)
-    pts = [tuple(int(v) for v in rng.integers(0, Nw, 3)) for _ in range(4)] + [(0, 0, 0), (127, 127, 127)]
-    exact = A.apply_direct_at(Tf, f.astype(np.complex128), pts)
-    scale = np.sqrt(np.mean(np.abs(ref32) ** 2))
     for mode in MODES:
         plan.set_precision(mode)
         phi = plan.apply(ft).cpu().numpy()
@@ -81,8 +73,6 @@ def test_tc_full_size_against_fp32_and_sampled_oracle():
         d = A.rel_l2(phi, ref32)
         print(f"N=256 {mode}: rel-L2 vs FP32 path {d:.3e}")
         assert d < BAR[mode]
-        got = np.array([phi[p] for p in pts])
-        assert np.abs(got - exact).max() < 10 * BAR[mode] * scale
     plan.close()
 
 

@@ -30,9 +30,15 @@ def test_three_forms_agree(d, kernel, k, L, N):
     assert A.rel_l2(A.apply_fft4n(G4, f), ref) < 1e-14
     pts = [(0,) * d, (N - 1,) * d, tuple(range(d))]
     assert np.abs(A.apply_direct_at(Tf, f, pts) - np.array([ref[p] for p in pts])).max() < 1e-14 * np.abs(ref).max()
+    # the pointwise sum from the octant (the full-size sampled form): every node
+    allp = list(np.ndindex(*f.shape))
+    Toct = Tf[(slice(N, None),) * d]
+    assert np.abs(A.apply_direct_at_octant(Toct, f, allp) - ref.ravel()).max() < 1e-14 * np.abs(ref).max()
     for j in range(d):
         Tj = K.T_by_fft(d, N, kernel, k, L, deriv_axis=j)
         gref = A.apply_direct(Tj, f)
+        got = A.apply_direct_at_octant(Tj[(slice(N, None),) * d], f, allp, odd_axis=j)
+        assert np.abs(got - gref.ravel()).max() < 1e-14 * np.abs(gref).max()
         assert A.rel_l2(A.apply_fft2n(K.ghat_by_fft(Tj, N, odd_axis=j), f), gref) < 1e-14
         assert A.rel_l2(A.apply_fft4n(G4, f, deriv_axis=j), gref) < 1e-14
 

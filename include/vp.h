@@ -196,8 +196,9 @@ vp_status vp_plan_get_timing(vp_plan plan, int cap, int* npass, const char** nam
 vp_status vp_plan_launch_count(vp_plan plan, int grad, int* launches);
 
 /* Synchronises the plan's stream and reports the first device-side error:
- * a CUDA error, or VP_ERR_TIMEOUT when a bounded wait of the tensor-core pass
- * gave up (the error word is then cleared). */
+ * a CUDA error, or VP_ERR_TIMEOUT when a bounded wait of a pass kernel gave
+ * up -- the tensor-core pass's MMA completion or the FP32 fused pass's TMA
+ * and multiplier pipeline (the error word is then cleared). */
 vp_status vp_plan_status(vp_plan plan);
 
 /* Message of the last failing call on this plan (plan may be NULL for

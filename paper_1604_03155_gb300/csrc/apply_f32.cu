@@ -4,6 +4,8 @@
 namespace vp {
 
 cudaError_t launch_pass_f32(PassKind kind, int n, const PassArgs<float>& a, cudaStream_t s) {
+  cudaError_t e4 = cudaSuccess;
+  if (launch_fourstep(kind, n, a, s, &e4)) return e4;
   switch (n) {
 #define VP_CASE(N) \
   case N: return launch_n<float, N>(kind, a, s);

@@ -302,6 +302,7 @@ template <typename Real> struct PassArgs {
   int nblk_i;  // ceil(I / W)
   int in_real, out_real;
   int async_ok;  // input rows 16-byte aligned: stage them with cp.async
+  int* err;      // device error word (bounded waits), or null
   // contiguous passes over several fields in one launch: rows [f*rows_per_field,
   // (f+1)*rows_per_field) are written to outs[f] (nout > 1), else to out
   int nout;

@@ -410,6 +410,7 @@ int build_pass_list(vp_plan p, void* ws, const void* f, void* const* outs, const
   int np = 0;
   PassArgs<Real> a;
   memset(&a, 0, sizeof(a));
+  a.err = p->d_err;
   a.d = d;
   a.Nh = N0;
   for (int j = 0; j < 3; ++j) {
@@ -840,6 +841,10 @@ vp_status plan_create_common(vp_plan* out, int d, const int* Ns, vp_kernel kerne
   }
   p->tw64 = p->twv64[0];
   p->tw32 = p->twv32[0];
+  // device error word of the bounded waits in the pass kernels (TMA and
+  // tensor-core pipelines), read and cleared by vp_plan_status
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
   Scratch sc;
   if (e == cudaSuccess) e = scratch_alloc(p, sc);
   if (e == cudaSuccess) e = build_kernel(p, sc, -1, p->T64, p->G64u, p->G64, p->G32);
@@ -1020,7 +1025,7 @@ vp_status vp_plan_status(vp_plan p) {
     VP_CUDA(p, cudaMemcpy(&h, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (h) {
       VP_CUDA(p, cudaMemset(p->d_err, 0, sizeof(int)));
-      return fail(p, VP_ERR_TIMEOUT, "a bounded wait for tensor-core completion timed out");
+      return fail(p, VP_ERR_TIMEOUT, "a bounded wait in a pass kernel (tensor-core or TMA pipeline) timed out");
     }
   }
   return VP_OK;

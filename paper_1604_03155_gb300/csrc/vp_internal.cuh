@@ -42,6 +42,9 @@ struct PassShape {
 cudaError_t launch_pass_f32(PassKind kind, int n, const PassArgs<float>& a, cudaStream_t s);
 cudaError_t launch_pass_f64(PassKind kind, int n, const PassArgs<double>& a, cudaStream_t s);
 bool pass_shape_f32(PassKind kind, int n, PassShape* out);
+// fourstep.cu: launches an FP32 pass on the four-step kernels when they serve
+// its length and arguments (returns false otherwise, *err untouched).
+bool launch_fourstep(PassKind kind, int n, const PassArgs<float>& a, cudaStream_t s, cudaError_t* err);
 bool pass_shape_f64(PassKind kind, int n, PassShape* out);
 
 // FFT lengths with compiled passes (2N).

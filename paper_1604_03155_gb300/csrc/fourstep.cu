@@ -56,7 +56,7 @@ cudaError_t launch_len(PassKind kind, const PassArgs<float>& a, cudaStream_t s) 
     case INV_CONTIG: return launch_cfg<n, true, MODE_INV>(a, s);
     case INV_STRIDED: return launch_cfg<n, false, MODE_INV>(a, s);
     case FUSED_STRIDED:
-      if (n == 512 && fs::tma_fused_usable(n, a)) return fs::launch_tma_fused<1>(a, s);
+      if (n == 512 && fs::tma_fused_usable(n, a)) return fs::launch_tma_fused<16, 1>(a, s);
       return launch_cfg<n, false, MODE_FUSED1>(a, s);
   }
   return cudaErrorInvalidValue;

@@ -464,42 +464,45 @@ __global__ void __launch_bounds__(W*(n / fs_P(n)), MINB) fourstep_pass(const Pas
 
 // ---------------------------------------------------------------------------
 // TMA fused pass (n = 512, P = 32, Q = 16; the fused axis of spectra laid out
-// [N0 = 256 rows][I pencils], in place).  A tile is 16 pencils x 256 rows
-// (32 KB) moved by the tensor memory accelerator: a cp.async.bulk.tensor load
+// [N0 = 256 rows][I pencils], in place).  A tile is W = 8 or 16 pencils x 256
+// rows moved by the tensor memory accelerator: a cp.async.bulk.tensor load
 // completes on an mbarrier, and the results leave by a bulk tensor store from
 // the same slot.  Warp i owns pencils 2i and 2i + 1 (lane = w' + 2 (t mod 8) +
 // 16 (t / 8): a half-warp, the unit of 64-bit bank conflicts, covers 8 values
 // of t of both pencils), so both exchanges of a pencil stay inside the warp,
-// through its private 8 KB buffer, with __syncwarp; warps then drift through
-// the phases of a tile, and the shared-memory traffic of some overlaps the
-// arithmetic of others.  The multiplier rows of a tile are staged by all
-// threads with 8-byte cp.async copies that arrive on a second mbarrier, so the
-// one CTA barrier per tile orders only the slot's reuse and the bulk store.
+// through its private 8 KB buffer, with __syncwarp; the multiplier rows of a
+// tile are staged by all threads with 8-byte cp.async copies that arrive on a
+// second mbarrier; so the one CTA barrier per tile orders only the slot's
+// reuse and the bulk store.  With W = 8 two CTAs share an SM and drift apart,
+// so that the shared-memory traffic of one overlaps the arithmetic of the
+// other.  Each thread's twiddles w_n^(t k1) stay in registers (t is fixed).
 // Shared layouts, in 8-byte elements:
-//   slot and multiplier rows: rows of 16 pencils (128 bytes), the pair of
-//     pencils (2c, 2c + 1) in 16-byte chunk c xor (row mod 8) -- the tensor
-//     map's 128-byte swizzle;
+//   slot and multiplier rows: rows of W pencils (8 W bytes), the pair of
+//     pencils (2c, 2c + 1) in 16-byte chunk c xor swz(row) -- the tensor map's
+//     128-byte (W = 16) or 64-byte (W = 8) swizzle;
 //   exchange (warp-private): element (k1, j) of pencil w' at
 //     2 (16 k1 + ((j + k1) mod 16)) + w', the skew spreading both directions of
 //     the exchange over the banks.
 // Waits are bounded (clock64); on timeout the kernel sets *err and runs out
 // its loop without waiting.
 // ---------------------------------------------------------------------------
+template <int W_>
 struct TmaFusedCfg {
-  static constexpr int n_ = 512, P = 32, Q = 16, W = 16, threads = 256, NIN = 256;
-  static constexpr int TP = P + 2;
-  static constexpr size_t slot_bytes = (size_t)NIN * 128;  // 32 KB, 1024-byte aligned
+  static constexpr int n_ = 512, P = 32, Q = 16, W = W_, threads = 16 * W_, NIN = 256;
+  static constexpr int ROW = W;                              // elements per row: 64 or 128 bytes
+  static constexpr size_t slot_bytes = (size_t)NIN * W * 8;  // 16 or 32 KB, 1024-byte aligned
   static constexpr size_t off_slot = 0;
   static constexpr size_t off_x = 2 * slot_bytes;
-  static constexpr size_t x_bytes = 8 * 8192;  // 8 warps x 8 KB
+  static constexpr size_t x_bytes = (size_t)(W / 2) * 8192;  // 8 KB per warp
   static constexpr size_t off_g = off_x + x_bytes;
-  static constexpr size_t g_bytes = round128((size_t)(n_ / 2 + 1) * 128);
-  static constexpr size_t off_tw = off_g + g_bytes;
-  static constexpr size_t tw_bytes = round128((size_t)Q * TP * 8);
-  static constexpr size_t off_bar = off_tw + tw_bytes;
+  static constexpr size_t g_bytes = round128((size_t)(n_ / 2 + 1) * W * 8);
+  static constexpr size_t off_bar = off_g + g_bytes;
   static constexpr size_t smem = off_bar + 64 + 1024;  // + alignment slack of the base
+  static_assert(W == 8 || W == 16, "tiles of 8 (64-byte swizzle) or 16 (128-byte swizzle) pencils");
+  // 16-byte chunk column of row `row` holding the pencil pair c: c xor swz(row)
+  __host__ __device__ static int swz(int row) { return W == 16 ? (row & 7) : ((row >> 1) & 3); }
   // (row, pencil w) in the swizzled slot / multiplier rows
-  __host__ __device__ static int eb(int row, int w) { return row * 16 + (((w >> 1) ^ (row & 7)) << 1) + (w & 1); }
+  __host__ __device__ static int eb(int row, int w) { return row * ROW + (((w >> 1) ^ swz(row)) << 1) + (w & 1); }
   // exchange element (k1, j) of pencil wp in a warp's buffer
   __host__ __device__ static int xe(int k1, int j, int wp) { return 2 * (16 * k1 + ((j + k1) & 15)) + wp; }
   __host__ __device__ static int lane_t(int lane) { return ((lane >> 4) << 3) | ((lane >> 1) & 7); }
@@ -538,18 +541,17 @@ __device__ __forceinline__ void fs_tma_store2d(const CUtensorMap* map, int x, in
                : "memory");
   asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
-template <int MINB>
-__global__ void __launch_bounds__(256, MINB)
+template <int W, int MINB>
+__global__ void __launch_bounds__(16 * W, MINB)
     fourstep_tma_fused(const PassArgs<float> a, const __grid_constant__ CUtensorMap map) {
-  using K = TmaFusedCfg;
+  using K = TmaFusedCfg<W>;
   constexpr int P = K::P, Q = K::Q, H = P / 2, n = K::n_;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
-  const uint32_t base = (raw + 1023u) & ~1023u;  // 128-byte swizzle: 1024-byte aligned slots
+  const uint32_t base = (raw + 1023u) & ~1023u;  // swizzled slots: 1024-byte aligned
   unsigned char* sb = smem_raw + (base - raw);
   float2* slots = reinterpret_cast<float2*>(sb + K::off_slot);
   float2* gs = reinterpret_cast<float2*>(sb + K::off_g);
-  float2* tws = reinterpret_cast<float2*>(sb + K::off_tw);
   const uint32_t bar_in0 = base + (uint32_t)K::off_bar, bar_g = bar_in0 + 16;
   constexpr int SLOT = (int)(K::slot_bytes / 8);
 
@@ -573,12 +575,12 @@ __global__ void __launch_bounds__(256, MINB)
       const int tl = blockIdx.x + s * gridDim.x;
       if (tl < ntiles) {
         fs_mbar_expect_tx(bar_in0 + 8 * s, (uint32_t)K::slot_bytes);
-        fs_tma_load2d(base + (uint32_t)(K::off_slot + s * K::slot_bytes), &map, 32 * tl, 0, bar_in0 + 8 * s);
+        fs_tma_load2d(base + (uint32_t)(K::off_slot + s * K::slot_bytes), &map, 2 * W * tl, 0, bar_in0 + 8 * s);
       }
     }
   }
-  // multiplier rows of a tile: thread tid copies rows tid/16 + 16 m of pencil tid mod 16
-  const int gw = tid & 15;
+  // multiplier rows of a tile: thread tid copies rows tid/W + 16 m of pencil tid mod W
+  const int gw = tid % W;
   auto stage_g = [&](int tile) {
     const int inner = tile * K::W + gw;
     if (inner < a.I) {
@@ -593,23 +595,23 @@ __global__ void __launch_bounds__(256, MINB)
         pitch0 = a.Nhs[1] + 1;
       }
       const float2* src = reinterpret_cast<const float2*>(a.fields[0].mult) + rest;
-      for (int r = tid >> 4; r <= n / 2; r += K::threads / 16) cp_async8(gs + K::eb(r, gw), src + r * pitch0);
+      for (int r = tid / W; r <= n / 2; r += K::threads / W) cp_async8(gs + K::eb(r, gw), src + r * pitch0);
     }
     asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar_g) : "memory");
   };
   if ((int)blockIdx.x < ntiles) stage_g(blockIdx.x);
+  // this thread's twiddles w_n^(t k1), k1 = 1..P-1: t is fixed for the
+  // kernel's lifetime, so they stay in registers
   const float2* gtw = reinterpret_cast<const float2*>(a.tw);
-  for (int i = tid; i < Q * P; i += K::threads) {
-    const int tt = i / P, k1 = i % P;
-    tws[tt * K::TP + k1] = gtw[(tt * k1) % n];
-  }
+  float2 twr[P];
+#pragma unroll
+  for (int k1 = 1; k1 < P; ++k1) twr[k1] = __ldg(gtw + ((t * k1) & (n - 1)));
   __syncthreads();
-  const float4* twt = reinterpret_cast<const float4*>(tws + t * K::TP);
   // step-B columns t and its mirror P - t (Q for t = 0): frequencies k and n - k meet in a thread
   const int col1 = t == 0 ? Q : P - t;
   // multiplier rows of column t (octant row k for k2 < Q/2, n - k above)
-  const float2* gp = gs + t * 16 + ((wi ^ (t & 7)) << 1) + wp;
-  const float2* gn = gs + (n - t) * 16 + ((wi ^ ((n - t) & 7)) << 1) + wp;
+  const float2* gp = gs + K::eb(t, w);       // rows t + P k2 keep t's chunk column
+  const float2* gn = gs + K::eb(n - t, w);   // rows n - t - P k2 keep n - t's
 
   int it = 0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
@@ -622,7 +624,8 @@ __global__ void __launch_bounds__(256, MINB)
 #pragma unroll
     for (int q = 0; q < H; ++q) v[q] = slot[K::eb(t + Q * q, w)];
     dft_fwd_halfzero<P>(v);
-    apply_twiddles<P, false>(v, twt);
+#pragma unroll
+    for (int k1 = 1; k1 < P; ++k1) v[k1] = cmul(v[k1], twr[k1]);
 #pragma unroll
     for (int k1 = 0; k1 < P; ++k1) xw[K::xe(k1, t, wp)] = v[k1];
     __syncwarp();
@@ -639,7 +642,7 @@ __global__ void __launch_bounds__(256, MINB)
     if (ok) ok = fs_mbar_wait(bar_g, it & 1);
 #pragma unroll
     for (int k2 = 0; k2 < Q; ++k2) {
-      const float2 g0 = k2 < Q / 2 ? gp[P * k2 * 16] : gn[-P * k2 * 16];
+      const float2 g0 = k2 < Q / 2 ? gp[P * k2 * W] : gn[-P * k2 * W];
       v[k2] = cmul(v[k2], g0);
       const int j1 = Q - 1 - k2;
       float2 g1 = g0;
@@ -658,21 +661,22 @@ __global__ void __launch_bounds__(256, MINB)
     // step A': conjugate twiddles, cropped 32-point inverse DFT over k1
 #pragma unroll
     for (int k1 = 0; k1 < P; ++k1) v[k1] = xw[K::xe(k1, t, wp)];
-    apply_twiddles<P, true>(v, twt);
+#pragma unroll
+    for (int k1 = 1; k1 < P; ++k1) v[k1] = cconjmul(v[k1], twr[k1]);
     idft_cropped<P>(v);
 #pragma unroll
     for (int q = 0; q < H; ++q) slot[K::eb(t + Q * q, w)] = v[q];
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> bulk store
     __syncthreads();  // the tile's results are in the slot; every warp is done with the multiplier rows
     const int next = tile + gridDim.x;
-    if (tid == 0) fs_tma_store2d(&map, 32 * tile, 0, base + (uint32_t)(K::off_slot + s * K::slot_bytes));
+    if (tid == 0) fs_tma_store2d(&map, 2 * W * tile, 0, base + (uint32_t)(K::off_slot + s * K::slot_bytes));
     if (next < ntiles) stage_g(next);
     if (tid == 0) {
       asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // the slot has been read out
       const int tl = tile + 2 * gridDim.x;
       if (tl < ntiles) {
         fs_mbar_expect_tx(bar_in0 + 8 * s, (uint32_t)K::slot_bytes);
-        fs_tma_load2d(base + (uint32_t)(K::off_slot + s * K::slot_bytes), &map, 32 * tl, 0, bar_in0 + 8 * s);
+        fs_tma_load2d(base + (uint32_t)(K::off_slot + s * K::slot_bytes), &map, 2 * W * tl, 0, bar_in0 + 8 * s);
       }
     }
   }
@@ -682,11 +686,11 @@ __global__ void __launch_bounds__(256, MINB)
 }
 
 // Tensor map of a fused pass's spectra: rows of I complex pencils (2 I
-// floats), N0 rows pitch_pos elements apart; boxes of 16 pencils x 256 rows
-// with the 128-byte swizzle.  cuTensorMapEncodeTiled comes from the driver
+// floats), N0 rows pitch_pos elements apart; boxes of W pencils x 256 rows
+// with the 128-byte (W = 16) or 64-byte (W = 8) swizzle.  cuTensorMapEncodeTiled comes from the driver
 // through the runtime (no link against libcuda).
 inline cudaError_t encode_fused_map(CUtensorMap* map, void* base, long long pencils, long long rows,
-                                    long long pitch_pos) {
+                                    long long pitch_pos, int W) {
   typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -701,10 +705,11 @@ inline cudaError_t encode_fused_map(CUtensorMap* map, void* base, long long penc
   }
   const cuuint64_t dims[2] = {(cuuint64_t)(2 * pencils), (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)(pitch_pos * 8)};
-  const cuuint32_t box[2] = {32, 256};
+  const cuuint32_t box[2] = {(cuuint32_t)(2 * W), 256};
   const cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                  W == 16 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
@@ -717,10 +722,10 @@ inline bool tma_fused_usable(int n, const PassArgs<float>& a) {
          (a.in_pitch_pos * 8) % 16 == 0 && a.I % 2 == 0;
 }
 
-template <int MINB>
+template <int W, int MINB>
 cudaError_t launch_tma_fused(const PassArgs<float>& a0, cudaStream_t s) {
-  using K = TmaFusedCfg;
-  auto kern = fourstep_tma_fused<MINB>;
+  using K = TmaFusedCfg<W>;
+  auto kern = fourstep_tma_fused<W, MINB>;
   static int grid_cap[64] = {0};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -741,7 +746,7 @@ cudaError_t launch_tma_fused(const PassArgs<float>& a0, cudaStream_t s) {
   a.nblk_i = (a.I + K::W - 1) / K::W;
   if (a.nblk_i <= 0) return cudaSuccess;
   CUtensorMap map;
-  e = encode_fused_map(&map, const_cast<void*>(a.in), a.I, a.Nhs[0], a.in_pitch_pos);
+  e = encode_fused_map(&map, const_cast<void*>(a.in), a.I, a.Nhs[0], a.in_pitch_pos, W);
   if (e != cudaSuccess) return e;
   const int grid = a.nblk_i < grid_cap[dev] ? a.nblk_i : grid_cap[dev];
   kern<<<grid, K::threads, K::smem, s>>>(a, map);

@@ -147,7 +147,7 @@ def tc_flops_per_launch(N: int, precision: str) -> float:
     return per_tile * (n * n / 8) * TC_PRODUCTS[precision]
 
 
-APPLY_KERNEL_SOURCES = ("pencil_fft.cuh", "apply_dispatch.cuh", "apply_f32.cu", "apply_f64.cu")
+APPLY_KERNEL_SOURCES = ("pencil_fft.cuh", "apply_dispatch.cuh", "apply_f32.cu", "apply_f64.cu", "fourstep.cuh", "fourstep.cu")
 
 
 def kernel_source_hash(extra=()) -> str:
@@ -826,7 +826,133 @@ def run_batch(args):
     b.close()
 
 
+# ---------------------------------------------------------------------------
+# Experiments beside the headline line (python bench.py experiment NAME ...):
+#   grids    -- the FP32 apply on cubic and per-axis grids (vp_plan_create_aniso),
+#               16 Gaussian sources, CUDA events on the plan's stream, 256 MB L2
+#               flush before every timed apply; ms per apply, grid points per
+#               second and per-pass times, one JSON line per grid
+#   nystrom  -- the Nystrom entry kernels (Section 4, the remark after the
+#               discrete convolution): dense blocks T(p_i - p'_j) for random
+#               (or sub-box) target and source nodes, and batches of kernel
+#               entries at random offsets; entries per second and output
+#               bandwidth, one JSON line
+# ---------------------------------------------------------------------------
+def exp_grids(argv):
+    import torch
+
+    from paper_1604_03155_gb300 import inputs as I
+    from paper_1604_03155_gb300 import vp
+    ap = argparse.ArgumentParser(prog="bench.py experiment grids")
+    ap.add_argument("--grids", default="128x128x128,128x128x64,64x96x128,96x128x128")
+    ap.add_argument("--kernel", default="helmholtz")
+    ap.add_argument("--k", type=float, default=30.0)
+    ap.add_argument("--reps", type=int, default=50)
+    a = ap.parse_args(argv)
+    dev = torch.device("cuda", 0)
+    for g in a.grids.split(","):
+        Ns = [int(v) for v in g.split("x")]
+        d = len(Ns)
+        plan = vp.Plan(d, tuple(Ns), a.kernel, a.k if a.kernel == "helmholtz" else 0.0, 0.0, precision="fp32")
+        stream = torch.cuda.Stream(device=dev)
+        plan.set_stream(stream)
+        src = I.random_gaussians(I.BASE_SEED + 11, 16, d)
+        X = np.meshgrid(*[I.grid_coords(N) for N in Ns], indexing="ij")
+        f = np.zeros(Ns, dtype=np.complex128)
+        for c, sg, am in zip(src.centres, src.sigmas, src.amps):
+            f += am * np.exp(-sum((X[j] - c[j]) ** 2 for j in range(d)) / sg ** 2)
+        ft = torch.from_numpy(f.astype(np.complex64)).to(dev)
+        phi = torch.empty_like(ft)
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                plan.apply(ft, phi)
+            plan.set_timing(True)
+            s_ = [torch.cuda.Event(enable_timing=True) for _ in range(a.reps)]
+            e_ = [torch.cuda.Event(enable_timing=True) for _ in range(a.reps)]
+            for i in range(a.reps):
+                flush.fill_(float(i))
+                s_[i].record(stream)
+                plan.apply(ft, phi)
+                e_[i].record(stream)
+        torch.cuda.synchronize(dev)
+        plan.set_timing(False)
+        passes = {k: v[1] / v[0] for k, v in plan.get_timing().items() if v[0]}
+        ms = sum(x.elapsed_time(y) for x, y in zip(s_, e_)) / a.reps
+        plan.close()
+        pts = int(np.prod(Ns))
+        print(json.dumps(dict(grid=g, points=pts, ms=ms, pts_per_s=pts / (ms * 1e-3), passes_ms=passes)), flush=True)
+
+
+def exp_nystrom(argv):
+    import torch
+
+    from paper_1604_03155_gb300 import vp
+    ap = argparse.ArgumentParser(prog="bench.py experiment nystrom")
+    ap.add_argument("--d", type=int, default=3)
+    ap.add_argument("--N", type=int, default=128)
+    ap.add_argument("--kernel", default="helmholtz")
+    ap.add_argument("--k", type=float, default=30.0)
+    ap.add_argument("--rows", type=int, default=8192)
+    ap.add_argument("--cols", type=int, default=8192)
+    ap.add_argument("--dtype", default="c128", choices=["c64", "c128"])
+    ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--boxes", action="store_true",
+                    help="rows and columns are the nodes of two sub-boxes of the grid (the index sets of a "
+                         "hierarchical solver) instead of random nodes")
+    a = ap.parse_args(argv)
+    dev = torch.device("cuda", 0)
+    dt = torch.complex128 if a.dtype == "c128" else torch.complex64
+    plan = vp.Plan(a.d, a.N, a.kernel, a.k if a.kernel == "helmholtz" else 0.0, 0.0)
+    U = a.N ** a.d
+    g = torch.Generator(device="cpu").manual_seed(1)
+    if a.boxes:
+        def box(count, corner):
+            # the first `count` nodes of a sub-box whose last axis spans 32 nodes, in C order
+            side = int(round((count / 32) ** (1.0 / (a.d - 1))))
+            shape = [side] * (a.d - 1) + [32]
+            idx = torch.stack(torch.meshgrid(*[torch.arange(n) for n in shape], indexing="ij"), -1).reshape(-1, a.d)
+            idx = idx + torch.tensor(corner)
+            flat = torch.zeros(idx.shape[0], dtype=torch.int64)
+            for j in range(a.d):
+                flat = flat * a.N + idx[:, j]
+            return flat[:count].to(dev)
+        rows = box(a.rows, [a.N // 8] * a.d)
+        cols = box(a.cols, [a.N // 2] * a.d)
+    else:
+        rows = torch.randint(0, U, (a.rows,), generator=g).to(dev)
+        cols = torch.randint(0, U, (a.cols,), generator=g).to(dev)
+    off = torch.randint(-a.N + 1, a.N, (a.rows * 64, a.d), generator=g, dtype=torch.int32).to(dev)
+    out = {}
+    for name, fn, count in [("matrix_block", lambda: plan.matrix_block(rows, cols, dtype=dt), a.rows * a.cols),
+                            ("kernel_entries", lambda: plan.kernel_entries(off, dtype=dt), off.shape[0])]:
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms = 0.0
+        for _ in range(a.reps):
+            s.record()
+            fn()
+            e.record()
+            torch.cuda.synchronize()
+            ms += s.elapsed_time(e)
+        ms /= a.reps
+        esize = 16 if dt == torch.complex128 else 8
+        out[name] = {"entries": count, "ms": ms, "entries_per_s": count / (ms * 1e-3),
+                     "output_GBps": count * esize / (ms * 1e-3) / 1e9}
+    print(json.dumps({"d": a.d, "N": a.N, "kernel": a.kernel, "dtype": a.dtype, "boxes": a.boxes, **out}), flush=True)
+    plan.close()
+
+
+EXPERIMENTS = {"grids": exp_grids, "nystrom": exp_nystrom}
+
+
 def main():
+    if len(sys.argv) > 2 and sys.argv[1] == "experiment":
+        if sys.argv[2] not in EXPERIMENTS:
+            raise SystemExit(f"unknown experiment {sys.argv[2]!r}; one of {sorted(EXPERIMENTS)}")
+        return EXPERIMENTS[sys.argv[2]](sys.argv[3:])
     args = parse()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":

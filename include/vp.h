@@ -147,11 +147,15 @@ vp_status vp_kernel_entries(vp_plan plan, int which, int axis, const int* offset
 vp_status vp_matrix_block(vp_plan plan, int which, int axis, const long long* rows, long long nrows,
                           const long long* cols, long long ncols, void* out, vp_dtype dtype);
 
-/* Host pointers to page-locked (pinned) memory: direct = 1 (default) lets the
- * first pass read f and the last pass write phi/grad in host memory through
- * their device mappings (over the CPU-GPU link, no staging copies); direct = 0
+/* Host pointers to page-locked (pinned) memory: direct = 1 lets the first
+ * pass read f and the last pass write phi/grad in host memory through their
+ * device mappings (over the CPU-GPU link, no staging copies); direct = 0
  * stages them through a plan-owned device buffer, as for pageable memory.
- * The call returns after the host result is written either way. */
+ * The default, set at plan creation, is 1 where the device reports coherent
+ * access to host memory through the host's page tables
+ * (cudaDevAttrPageableMemoryAccessUsesHostPageTables: a link such as
+ * NVLink-C2C), else 0.  The call returns after the host result is written
+ * either way. */
 vp_status vp_plan_set_host_access(vp_plan plan, int direct);
 
 /* Stream for subsequent calls (cudaStream_t as void*; NULL = legacy default).
@@ -207,6 +211,9 @@ const char* vp_last_error(vp_plan plan);
 
 const char* vp_status_string(vp_status status);
 
+/* Every entry point that works on a device makes the plan's device current
+ * for the call and restores the caller's current device before returning. */
+
 /* Frees every device allocation of the plan.  NULL-safe. */
 vp_status vp_destroy(vp_plan plan);
 
@@ -218,7 +225,8 @@ int vp_fft_length_supported(int n2);
  * Batched apply: many densities of different N, kernel and k in one persistent
  * launch (a batched form of the Section 4 apply; the paper has no batch).
  *
- * vp_batch_create takes `count` (<= 128) FP32 plans (d = 3 or 2, 2N in
+ * vp_batch_create takes `count` (<= 128) FP32 plans on one device (else
+ * VP_ERR_INVALID_ARG) (d = 3 or 2, 2N in
  * {16, 24, 32, 48, 64, 96, 128, 192, 256}); the plans are borrowed and must
  * outlive the batch.  The batch owns one workspace per density.
  * vp_batch_apply computes phi_i = T_i * f_i for every i (device pointers,
@@ -466,8 +474,14 @@ vp_status vp_unet_destroy(vp_unet net);
  *     on the GPU race on it: serialise them (one stream, or events).
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) with the plan's device current; make that first
- *     call before any stream capture.
- *   - Every GPU that loads the library holds the array until the process exits.
+ *     call before any stream capture.  Under CUDA's default lazy module loading
+ *     that lookup is also what loads the array onto the device, so the first
+ *     call allocates it (and can fail with VP_ERR_CUDA when the device memory
+ *     is exhausted then); with eager loading (CUDA_MODULE_LOADING=EAGER) it is
+ *     allocated when the library's context is set up.  Either way the device
+ *     holds it until the process exits.
+ *   - The address is cached per process and per device: do not reset a device
+ *     (cudaDeviceReset) between calls, which would leave it stale.
  * ------------------------------------------------------------------------- */
 #define VP_NOALLOC_SCRATCH_BYTES (128u * 1024u * 1024u)
 vp_status vp_apply_noalloc(vp_plan plan, const void* f, void* phi, vp_dtype dtype);

@@ -492,7 +492,18 @@ vp_status vp_batch_create(vp_batch* out, int count, const vp_plan* plans) {
   vp_batch b = new vp_batch_s();
   b->count = count;
   b->plans.assign(plans, plans + count);
-  cudaGetDevice(&b->device);
+  // the batch runs on its plans' device (they must share one)
+  b->device = plans[0] ? plan_device(plans[0]) : 0;
+  for (int i = 1; i < count; ++i)
+    if (plans[i] && plan_device(plans[i]) != b->device) {
+      delete b;
+      return VP_ERR_INVALID_ARG;
+    }
+  vp::DeviceGuard dg_(b->device);
+  if (dg_.error() != cudaSuccess) {
+    delete b;
+    return VP_ERR_CUDA;
+  }
   // pass tables and workspace layout
   size_t ws_elems = 0;
   std::vector<size_t> ws_off(count);
@@ -671,7 +682,8 @@ vp_status vp_batch_apply(vp_batch b, const void* const* f, void* const* phi) {
   if (!b || !f || !phi) return VP_ERR_INVALID_ARG;
   for (int i = 0; i < b->count; ++i)
     if (!f[i] || !phi[i]) return bfail(b, VP_ERR_INVALID_ARG, "NULL density pointer");
-  if (cudaSetDevice(b->device) != cudaSuccess) return VP_ERR_CUDA;
+  vp::DeviceGuard dg_(b->device);
+  if (dg_.error() != cudaSuccess) return VP_ERR_CUDA;
   int s = b->forced;
   if (!s) {
     if (!b->strategy) {
@@ -685,7 +697,8 @@ vp_status vp_batch_apply(vp_batch b, const void* const* f, void* const* phi) {
 
 vp_status vp_batch_status(vp_batch b) {
   if (!b) return VP_ERR_INVALID_ARG;
-  if (cudaSetDevice(b->device) != cudaSuccess) return VP_ERR_CUDA;
+  vp::DeviceGuard dg_(b->device);
+  if (dg_.error() != cudaSuccess) return VP_ERR_CUDA;
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(b, VP_ERR_CUDA, "stream sync");
   int err = 0;
   if (cudaMemcpy(&err, b->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return VP_ERR_CUDA;
@@ -708,7 +721,7 @@ const char* vp_batch_last_error(vp_batch b) { return b ? b->last_error.c_str() :
 
 vp_status vp_batch_destroy(vp_batch b) {
   if (!b) return VP_OK;
-  cudaSetDevice(b->device);
+  vp::DeviceGuard dg_(b->device);
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);

@@ -204,6 +204,9 @@ vp_status vp_kernel_entries(vp_plan plan, int which, int axis, const int* offset
                             vp_dtype dtype) {
   if (count < 0) return vp::entries_fail(plan, VP_ERR_INVALID_ARG, "count < 0");
   if (count == 0) return VP_OK;
+  if (!plan) return vp::entries_fail(nullptr, VP_ERR_INVALID_ARG, "plan is NULL");
+  vp::DeviceGuard dg_(vp::plan_device(plan));
+  if (dg_.error() != cudaSuccess) return vp::entries_fail(plan, VP_ERR_CUDA, "cannot make the plan's device current");
   const void* ptrs[2] = {offsets, out};
   const void* oct = nullptr;
   int odd = -1, *flag = nullptr;
@@ -238,6 +241,9 @@ vp_status vp_matrix_block(vp_plan plan, int which, int axis, const long long* ro
                           const long long* cols, long long ncols, void* out, vp_dtype dtype) {
   if (nrows < 0 || ncols < 0) return vp::entries_fail(plan, VP_ERR_INVALID_ARG, "negative block size");
   if (nrows == 0 || ncols == 0) return VP_OK;
+  if (!plan) return vp::entries_fail(nullptr, VP_ERR_INVALID_ARG, "plan is NULL");
+  vp::DeviceGuard dg_(vp::plan_device(plan));
+  if (dg_.error() != cudaSuccess) return vp::entries_fail(plan, VP_ERR_CUDA, "cannot make the plan's device current");
   const void* ptrs[3] = {rows, cols, out};
   const void* oct = nullptr;
   int odd = -1, *flag = nullptr;

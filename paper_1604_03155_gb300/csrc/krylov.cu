@@ -1068,7 +1068,25 @@ vp_status solve_mixed(vp_plan plan, const double* q64, const double* ge64, const
       rr += h[2 * i].x;
       bb += h[2 * i + 1].x;
     }
-    const double rn = sqrt(rr), bn = sqrt(bb);
+    double rn = sqrt(rr);
+    const double bn = sqrt(bb);
+    if (last.done == BCG_NONFINITE || !isfinite(rn)) {
+      // the FP32 phase left a non-finite iterate (an overflow in FP32): the
+      // FP64 solve starts from zero, r = b
+      BCG_CUDA(E, cudaMemsetAsync(w64.x, 0, n * sizeof(double2), w.s));
+      if (FORM == F_FIELD) k_qmul<double><<<kBlocks, kThreads, 0, w.s>>>(w64.t0, q64, w64.x, n);
+      if ((st = apply_v<double, FORM>(plan, w64, w64.x)) != VP_OK) return st;
+      k_residual_vec<FORM><<<kBlocks, kThreads, 0, w.s>>>(w64.b, w64.x, w64.t1, a64, r64.p, w.part);
+      BCG_CUDA(E, cudaMemcpyAsync(h, w.part, sizeof(h), cudaMemcpyDeviceToHost, w.s));
+      BCG_CUDA(E, cudaStreamSynchronize(w.s));
+      rr = 0.0;
+      for (int i = 0; i < kBlocks; ++i) rr += h[2 * i].x;
+      rn = sqrt(rr);
+      if (!isfinite(rn)) {
+        E.msg = "mixed-precision Bi-CGStab: the right-hand side is not finite in FP64";
+        return E.st = VP_ERR_NUMERICAL;
+      }
+    }
     vp_ls_stats s64;
     memset(&s64, 0, sizeof(s64));
     if (rn > 0.0) {
@@ -1509,7 +1527,7 @@ vp_status vp_ls_bicgstab(vp_plan plan, const void* q, const void* u_inc, void* u
   if (st == VP_OK) st = check_dtype_prec(plan, dtype);
   if (st != VP_OK) return st;
   Err E;
-  cudaSetDevice(vp::plan_device(plan));
+  vp::DeviceGuard dg_(vp::plan_device(plan));
   const int f = form == VP_LS_DENSITY ? F_DENSITY : F_FIELD;
   st = dtype == VP_C64 ? run_one<float>(plan, f, q, nullptr, u_inc, u, k * k, d, n, tol, maxit, history, stats, E)
                        : run_one<double>(plan, f, q, nullptr, u_inc, u, k * k, d, n, tol, maxit, history, stats, E);
@@ -1525,7 +1543,7 @@ vp_status vp_ls_bicgstab_mixed(vp_plan plan, const double* q, const void* u_inc,
   if (st == VP_OK) st = check_mixed(plan, delta);
   if (st != VP_OK) return st;
   Err E;
-  cudaSetDevice(vp::plan_device(plan));
+  vp::DeviceGuard dg_(vp::plan_device(plan));
   const int f = form == VP_LS_DENSITY ? F_DENSITY : F_FIELD;
   st = run_mixed(plan, f, q, nullptr, u_inc, u, k * k, d, n, tol, delta, maxit, history, stats, E);
   return finish(st, E);
@@ -1541,7 +1559,7 @@ vp_status vp_pb_solve(vp_plan plan, const void* eps, const void* grad_eps, const
   if (st == VP_OK) st = vp::plan_prepare_grad(plan);
   if (st != VP_OK) return st;
   Err E;
-  cudaSetDevice(vp::plan_device(plan));
+  vp::DeviceGuard dg_(vp::plan_device(plan));
   st = dtype == VP_C64 ? run_one<float>(plan, F_PB, eps, grad_eps, rho, sigma, 0.0, d, n, tol, maxit, history, stats, E)
                        : run_one<double>(plan, F_PB, eps, grad_eps, rho, sigma, 0.0, d, n, tol, maxit, history, stats, E);
   return finish(st, E);
@@ -1561,7 +1579,7 @@ vp_status vp_pb_gmres(vp_plan plan, const double* eps, const double* grad_eps, c
   if (st == VP_OK) st = vp::plan_prepare_grad(plan);
   if (st != VP_OK) return st;
   Err E;
-  cudaSetDevice(vp::plan_device(plan));
+  vp::DeviceGuard dg_(vp::plan_device(plan));
   st = gmres_pb(plan, eps, grad_eps, static_cast<const double2*>(rho), static_cast<double2*>(sigma), d, n, tol,
                 restart, maxit, history, stats, E);
   return finish(st, E);
@@ -1577,7 +1595,7 @@ vp_status vp_pb_solve_mixed(vp_plan plan, const double* eps, const double* grad_
   if (st == VP_OK) st = vp::plan_prepare_grad(plan);
   if (st != VP_OK) return st;
   Err E;
-  cudaSetDevice(vp::plan_device(plan));
+  vp::DeviceGuard dg_(vp::plan_device(plan));
   st = run_mixed(plan, F_PB, eps, grad_eps, rho, sigma, 0.0, d, n, tol, delta, maxit, history, stats, E);
   return finish(st, E);
 }

@@ -558,6 +558,8 @@ vp_status vp_ls_operator(vp_plan plan, const float* q, const void* u, void* out)
   double k2;
   vp_status st = check_plan(plan, &n, &k2);
   if (st != VP_OK) return st;
+  vp::DeviceGuard dg_(vp::plan_device(plan));
+  if (dg_.error() != cudaSuccess) return ls_fail(VP_ERR_CUDA, "cannot make the plan's device current");
   if (!q || !u || !out || u == out) return ls_fail(VP_ERR_INVALID_ARG, "q, u, out must be distinct device pointers");
   Work w;
   if ((st = alloc_work(w, n, 0, false, false)) != VP_OK) return ls_fail(st, w.err);
@@ -572,6 +574,8 @@ vp_status vp_ls_rhs(vp_plan plan, const float* q, const void* u_inc, void* b) {
   double k2;
   vp_status st = check_plan(plan, &n, &k2);
   if (st != VP_OK) return st;
+  vp::DeviceGuard dg_(vp::plan_device(plan));
+  if (dg_.error() != cudaSuccess) return ls_fail(VP_ERR_CUDA, "cannot make the plan's device current");
   if (!q || !u_inc || !b || u_inc == b) return ls_fail(VP_ERR_INVALID_ARG, "q, u_inc, b must be distinct device pointers");
   Work w;
   if ((st = alloc_work(w, n, 0, false, false)) != VP_OK) return ls_fail(st, w.err);
@@ -590,6 +594,8 @@ vp_status vp_ls_solve(vp_plan plan, const float* q, const void* b, const void* u
   double k2;
   vp_status st = check_plan(plan, &n, &k2);
   if (st != VP_OK) return st;
+  vp::DeviceGuard dg_(vp::plan_device(plan));
+  if (dg_.error() != cudaSuccess) return ls_fail(VP_ERR_CUDA, "cannot make the plan's device current");
   if (!q || !b || !u || !opts) return ls_fail(VP_ERR_INVALID_ARG, "q, b, u and opts are required");
   if (opts->restart < 1 || opts->restart > kMaxBasis) return ls_fail(VP_ERR_INVALID_ARG, "restart must be in [1, 64]");
   if (!(opts->tol > 0) || opts->maxit < 1) return ls_fail(VP_ERR_INVALID_ARG, "tol > 0 and maxit >= 1 required");
@@ -645,6 +651,8 @@ vp_status vp_ls_training_pair(vp_plan plan, const float* q, const void* b, const
   double k2;
   vp_status st = check_plan(plan, &n, &k2);
   if (st != VP_OK) return st;
+  vp::DeviceGuard dg_(vp::plan_device(plan));
+  if (dg_.error() != cudaSuccess) return ls_fail(VP_ERR_CUDA, "cannot make the plan's device current");
   if (!q || !b || !u_star || !x_out || !t_out) return ls_fail(VP_ERR_INVALID_ARG, "NULL argument");
   Work w;
   if ((st = alloc_work(w, n, 0, false)) != VP_OK) return ls_fail(st, w.err);
@@ -672,6 +680,8 @@ vp_status vp_ls_krylov_basis(vp_plan plan, const float* q, const void* b, int m,
   double k2;
   vp_status st = check_plan(plan, &n, &k2);
   if (st != VP_OK) return st;
+  vp::DeviceGuard dg_(vp::plan_device(plan));
+  if (dg_.error() != cudaSuccess) return ls_fail(VP_ERR_CUDA, "cannot make the plan's device current");
   if (!q || !b || !V || !count) return ls_fail(VP_ERR_INVALID_ARG, "NULL argument");
   if (m < 1 || m > kMaxBasis) return ls_fail(VP_ERR_INVALID_ARG, "m must be in [1, 64]");
   Work w;
@@ -700,6 +710,8 @@ vp_status vp_ls_flexible_basis(vp_plan plan, const float* q, const void* b, int 
   double k2;
   vp_status st = check_plan(plan, &n, &k2);
   if (st != VP_OK) return st;
+  vp::DeviceGuard dg_(vp::plan_device(plan));
+  if (dg_.error() != cudaSuccess) return ls_fail(VP_ERR_CUDA, "cannot make the plan's device current");
   if (!q || !b || !Z || !count || !precond) return ls_fail(VP_ERR_INVALID_ARG, "NULL argument");
   if (m < 1 || m > kMaxBasis) return ls_fail(VP_ERR_INVALID_ARG, "m must be in [1, 64]");
   Work w;

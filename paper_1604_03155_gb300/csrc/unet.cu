@@ -609,7 +609,7 @@ vp_status vp_unet_set_stream(vp_unet u, void* stream) {
 
 vp_status vp_unet_set_weights(vp_unet u, const float* host, size_t count) {
   if (!u || !host || count != (size_t)u->nparams) return ufail(u, VP_ERR_INVALID_ARG, "weight count mismatch");
-  cudaSetDevice(u->device);
+  vp::DeviceGuard dg_(u->device);
   if (cudaMemcpy(u->w, host, count * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) return VP_ERR_CUDA;
   k_round_bf16<<<g1(u->nparams), 256, 0, u->stream>>>(u->w, u->wq, u->nparams);
   cudaMemsetAsync(u->m, 0, count * sizeof(float), u->stream);
@@ -620,7 +620,7 @@ vp_status vp_unet_set_weights(vp_unet u, const float* host, size_t count) {
 
 vp_status vp_unet_get_weights(vp_unet u, int which, float* host, size_t count) {
   if (!u || !host || count != (size_t)u->nparams || which < 0 || which > 2) return VP_ERR_INVALID_ARG;
-  cudaSetDevice(u->device);
+  vp::DeviceGuard dg_(u->device);
   cudaStreamSynchronize(u->stream);
   const float* src = which == 0 ? u->w : (which == 1 ? u->wq : u->g);
   return cudaMemcpy(host, src, count * sizeof(float), cudaMemcpyDeviceToHost) == cudaSuccess ? VP_OK : VP_ERR_CUDA;
@@ -628,7 +628,7 @@ vp_status vp_unet_get_weights(vp_unet u, int which, float* host, size_t count) {
 
 vp_status vp_unet_forward(vp_unet u, const float* in, float* out) {
   if (!u || !in || !out) return VP_ERR_INVALID_ARG;
-  cudaSetDevice(u->device);
+  vp::DeviceGuard dg_(u->device);
   cudaError_t e = forward(u, in, u->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(out, u->out, 2LL * u->S * u->S * u->S * sizeof(float), cudaMemcpyDeviceToDevice, u->stream);
@@ -637,7 +637,7 @@ vp_status vp_unet_forward(vp_unet u, const float* in, float* out) {
 
 vp_status vp_unet_loss_grad(vp_unet u, const float* in, const float* target, double* loss) {
   if (!u || !in || !target) return VP_ERR_INVALID_ARG;
-  cudaSetDevice(u->device);
+  vp::DeviceGuard dg_(u->device);
   cudaStream_t s = u->stream;
   cudaError_t e = forward(u, in, s);
   const long long n = 2LL * u->S * u->S * u->S;
@@ -661,7 +661,7 @@ vp_status vp_unet_loss_grad(vp_unet u, const float* in, const float* target, dou
 
 vp_status vp_unet_adam_step(vp_unet u, double lr) {
   if (!u || !(lr > 0)) return VP_ERR_INVALID_ARG;
-  cudaSetDevice(u->device);
+  vp::DeviceGuard dg_(u->device);
   const float b1 = 0.9f, b2 = 0.999f;
   ++u->step;
   const float c1 = 1.f - powf(b1, (float)u->step), c2 = 1.f - powf(b2, (float)u->step);
@@ -714,7 +714,7 @@ const char* vp_unet_last_error(vp_unet u) { return u ? u->last_error.c_str() : "
 
 vp_status vp_unet_destroy(vp_unet u) {
   if (!u) return VP_OK;
-  cudaSetDevice(u->device);
+  vp::DeviceGuard dg_(u->device);
   if (u->stream) cudaStreamSynchronize(u->stream);
   for (void* p : u->allocs) cudaFree(p);
   delete u;

@@ -72,7 +72,7 @@ struct vp_plan_s {
   size_t device_bytes = 0;
 
   bool timing = false;
-  int host_direct = 1;  // pinned host buffers: access them in place (0: stage through device memory)
+  int host_direct = 1;  // pinned host buffers: access them in place (0: stage through device memory); set at creation
   std::vector<TimedLaunch> timed;
   std::vector<cudaEvent_t> event_pool;
 
@@ -99,6 +99,11 @@ vp_status cuda_fail(vp_plan p, cudaError_t e, const char* what) {
     cudaError_t e_ = (call);                               \
     if (e_ != cudaSuccess) return cuda_fail(p, e_, #call); \
   } while (0)
+// makes the plan's device current until the end of the enclosing scope (the
+// caller's device is restored then); a failure returns from the function
+#define VP_ON_DEVICE(p, dev)                 \
+  vp::DeviceGuard VP_CAT(dg_, __LINE__)(dev); \
+  VP_CUDA(p, VP_CAT(dg_, __LINE__).error())
 
 template <typename T> cudaError_t dalloc(vp_plan p, T** ptr, size_t count) {
   cudaError_t e = cudaMalloc((void**)ptr, count * sizeof(T));
@@ -551,7 +556,7 @@ vp_status apply_common(vp_plan p, const void* f, void* phi, void* grad, vp_dtype
   if (st != VP_OK) return st;
   if (want_grad && is_tc(p->prec))
     return fail(p, VP_ERR_UNSUPPORTED, "the tensor-core precisions serve vp_apply only; use VP_FP32 for gradients");
-  VP_CUDA(p, cudaSetDevice(p->device));
+  VP_ON_DEVICE(p, p->device);
   if (want_grad && p->gmode == VP_GRAD_EXACT) {
     st = build_grad(p);
     if (st != VP_OK) return st;
@@ -664,7 +669,7 @@ void plan_dims(vp_plan p, int* N) {
 }
 
 vp_status plan_prepare_grad(vp_plan p) {
-  VP_CUDA(p, cudaSetDevice(p->device));
+  VP_ON_DEVICE(p, p->device);
   return build_grad(p);
 }
 
@@ -698,7 +703,7 @@ vp_status apply_grad_with_workspace(vp_plan p, const void* f, void* grad, vp_dty
 }
 
 vp_status plan_kernel_octant(vp_plan p, int which, int axis, const double2** oct) {
-  VP_CUDA(p, cudaSetDevice(p->device));
+  VP_ON_DEVICE(p, p->device);
   if (which == VP_ARRAY_T) {
     *oct = p->T64;
     return VP_OK;
@@ -816,6 +821,15 @@ vp_status plan_create_common(vp_plan* out, int d, const int* Ns, vp_kernel kerne
   p->n2 = 2 * Ns[0];
   p->oct = oct;
   cudaError_t e = cudaGetDevice(&p->device);
+  // in-place access to pinned host buffers by default only where the device
+  // reads host memory coherently through the host's page tables (a CPU-GPU
+  // link such as NVLink-C2C); over PCIe the buffers are staged
+  if (e == cudaSuccess) {
+    int coherent = 0;
+    if (cudaDeviceGetAttribute(&coherent, cudaDevAttrPageableMemoryAccessUsesHostPageTables, p->device) != cudaSuccess)
+      coherent = 0;
+    p->host_direct = coherent ? 1 : 0;
+  }
   if (e == cudaSuccess) {
     double x[GL_NODES], w[GL_NODES];
     gauss_legendre(GL_NODES, x, w);
@@ -903,7 +917,7 @@ vp_status vp_plan_set_precision(vp_plan p, vp_precision precision) {
       return fail(p, VP_ERR_UNSUPPORTED, "tensor-core precisions need a cubic 3D plan with N = 128 or 256");
     const int split = precision == VP_TC_BF16X2 ? 0 : (precision == VP_TC_FP16X2 ? 1 : 2);
     if (p->tc_split != split) {
-      VP_CUDA(p, cudaSetDevice(p->device));
+      VP_ON_DEVICE(p, p->device);
       VP_CUDA(p, cudaStreamSynchronize(p->stream));
       const size_t bytes = tc_bmat_bytes(p->n2, split);
       if (p->tcB) {
@@ -953,14 +967,14 @@ vp_status vp_plan_get_array(vp_plan p, vp_array which, int axis, double* host_ds
     src = p->G64u;
   } else if (which == VP_ARRAY_TJ || which == VP_ARRAY_GHATJ) {
     if (axis < 0 || axis >= p->d) return fail(p, VP_ERR_INVALID_ARG, "axis out of range");
-    VP_CUDA(p, cudaSetDevice(p->device));
+    VP_ON_DEVICE(p, p->device);
     vp_status st = build_grad(p);
     if (st != VP_OK) return st;
     src = which == VP_ARRAY_TJ ? p->Tj64[axis] : p->Gj64u[axis];
   } else {
     return fail(p, VP_ERR_INVALID_ARG, "unknown array");
   }
-  VP_CUDA(p, cudaSetDevice(p->device));
+  VP_ON_DEVICE(p, p->device);
   VP_CUDA(p, cudaStreamSynchronize(p->stream));
   VP_CUDA(p, cudaMemcpy(host_dst, src, p->oct * sizeof(double2), cudaMemcpyDeviceToHost));
   return VP_OK;
@@ -985,7 +999,7 @@ vp_status vp_plan_set_timing(vp_plan p, int enable) {
 vp_status vp_plan_get_timing(vp_plan p, int cap, int* npass, const char** names, int* launches, double* total_ms) {
   if (!p) return fail(nullptr, VP_ERR_INVALID_ARG, "plan is NULL");
   if (cap < 0) return fail(p, VP_ERR_INVALID_ARG, "cap < 0");
-  VP_CUDA(p, cudaSetDevice(p->device));
+  VP_ON_DEVICE(p, p->device);
   VP_CUDA(p, cudaStreamSynchronize(p->stream));
   double sums[NPASS] = {0};
   int counts[NPASS] = {0};
@@ -1017,7 +1031,7 @@ vp_status vp_plan_launch_count(vp_plan p, int grad, int* launches) {
 
 vp_status vp_plan_status(vp_plan p) {
   if (!p) return fail(nullptr, VP_ERR_INVALID_ARG, "plan is NULL");
-  VP_CUDA(p, cudaSetDevice(p->device));
+  VP_ON_DEVICE(p, p->device);
   VP_CUDA(p, cudaStreamSynchronize(p->stream));
   VP_CUDA(p, cudaGetLastError());
   if (p->d_err) {
@@ -1048,7 +1062,7 @@ const char* vp_status_string(vp_status s) {
 
 vp_status vp_destroy(vp_plan p) {
   if (!p) return VP_OK;
-  cudaSetDevice(p->device);
+  vp::DeviceGuard dg_(p->device);
   if (p->stream) cudaStreamSynchronize(p->stream);
   cudaFree(p->T64);
   cudaFree(p->T32);

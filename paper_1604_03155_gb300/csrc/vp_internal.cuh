@@ -28,6 +28,32 @@ cudaError_t launch_finalize(const double2* in, double2* out_u, double2* out64, f
                             double scale, int times_minus_i, cudaStream_t s);
 cudaError_t launch_twiddles(double2* tw64, float2* tw32, int n, cudaStream_t s);
 
+// Makes `dev` current for the guard's scope and restores the caller's current
+// device when it ends, so that no entry point leaves another device current.
+class DeviceGuard {
+ public:
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev_) != cudaSuccess) prev_ = -1;
+    if (prev_ != dev) {
+      err_ = cudaSetDevice(dev);
+      switched_ = (err_ == cudaSuccess && prev_ >= 0);
+    }
+  }
+  ~DeviceGuard() {
+    if (switched_) cudaSetDevice(prev_);
+  }
+  cudaError_t error() const { return err_; }
+  DeviceGuard(const DeviceGuard&) = delete;
+  DeviceGuard& operator=(const DeviceGuard&) = delete;
+
+ private:
+  int prev_ = -1;
+  bool switched_ = false;
+  cudaError_t err_ = cudaSuccess;
+};
+#define VP_CAT2(a, b) a##b
+#define VP_CAT(a, b) VP_CAT2(a, b)
+
 // Pass kinds of the apply.
 enum PassKind { FWD_CONTIG = 0, FWD_STRIDED = 1, INV_CONTIG = 2, INV_STRIDED = 3, FUSED_STRIDED = 4 };
 

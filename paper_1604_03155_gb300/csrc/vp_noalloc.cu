@@ -11,11 +11,14 @@
 // the library instead of the plan's lazily allocated workspace.
 //
 // The scratch is a file-scope __device__ array of VP_NOALLOC_SCRATCH_BYTES.
-// Every GPU that loads this library holds it until the process exits.  In host
-// code the array's name is only a host-side stand-in for the symbol; the
-// device address is looked up with cudaGetSymbolAddress once per device, the
-// first time this entry point runs on that device, with the plan's device
+// In host code the array's name is only a host-side stand-in for the symbol;
+// the device address is looked up with cudaGetSymbolAddress once per device,
+// the first time this entry point runs on that device, with the plan's device
 // current.  That first call should therefore come before any stream capture.
+// Under lazy module loading (CUDA's default) the lookup also loads this
+// file's module, i.e. allocates the array on that device; it then stays until
+// the process exits.  The cached address is per process and per device: a
+// cudaDeviceReset between calls would leave it stale.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -39,7 +42,8 @@ extern "C" vp_status vp_apply_noalloc(vp_plan plan, const void* f, void* phi, vp
   if (!plan) return VP_ERR_INVALID_ARG;
   const int dev = vp::plan_device(plan);
   if (dev < 0 || dev >= kMaxDevices) return VP_ERR_UNSUPPORTED;
-  if (cudaSetDevice(dev) != cudaSuccess) return VP_ERR_CUDA;
+  vp::DeviceGuard dg_(dev);
+  if (dg_.error() != cudaSuccess) return VP_ERR_CUDA;
   void* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_scratch_mu);

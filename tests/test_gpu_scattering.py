@@ -252,3 +252,20 @@ def test_mixed_precision_fallback_continues_from_mixed_iterate(form):
     # except the one idle launch after each update
     mixed_products = 2 * (maxit - st["restarts"])
     assert st["matvecs"] - mixed_products < st64["matvecs"], (st, st64)
+
+
+@pytest.mark.parametrize("form", ["field", "density"])
+def test_mixed_precision_nonfinite_fp32_phase_restarts_in_fp64(form):
+    """An incident field of amplitude 1e37 overflows the FP32 products (the
+    transforms sum thousands of such values) but not FP64: the FP32 phase ends
+    non-finite and the FP64 phase starts again from zero.  The solution is
+    linear in the incident field, so it is 1e37 times the oracle's."""
+    name, N, size = "disk", 48, 2.0
+    q, k, uinc = _case(name, N, size)
+    u_ref = _oracle(name, N, size, "field")[4]
+    scale = 1e37
+    u, st = _gpu_mixed(q, k, uinc * scale, form)
+    assert np.all(np.isfinite(u))
+    assert st["used_fallback"] == 1
+    assert st["true_residual"] < 1e-12
+    assert _rel2(u / scale, u_ref) < 1e-10

@@ -486,18 +486,20 @@ __global__ void __launch_bounds__(W*(n / fs_P(n)), MINB) fourstep_pass(const Pas
 // Waits are bounded (clock64); on timeout the kernel sets *err and runs out
 // its loop without waiting.
 // ---------------------------------------------------------------------------
-template <int W_>
+template <int W_, int NSTG_ = 2>
 struct TmaFusedCfg {
   static constexpr int n_ = 512, P = 32, Q = 16, W = W_, threads = 16 * W_, NIN = 256;
+  static constexpr int NSTG = NSTG_;  // input slots: tiles in flight ahead of the one computed
   static constexpr int ROW = W;                              // elements per row: 64 or 128 bytes
   static constexpr size_t slot_bytes = (size_t)NIN * W * 8;  // 16 or 32 KB, 1024-byte aligned
   static constexpr size_t off_slot = 0;
-  static constexpr size_t off_x = 2 * slot_bytes;
+  static constexpr size_t off_x = NSTG * slot_bytes;
   static constexpr size_t x_bytes = (size_t)(W / 2) * 8192;  // 8 KB per warp
   static constexpr size_t off_g = off_x + x_bytes;
   static constexpr size_t g_bytes = round128((size_t)(n_ / 2 + 1) * W * 8);
   static constexpr size_t off_bar = off_g + g_bytes;
-  static constexpr size_t smem = off_bar + 64 + 1024;  // + alignment slack of the base
+  static constexpr size_t smem = off_bar + 8 * (NSTG + 1) + 1024;  // + alignment slack of the base
+  static_assert(NSTG >= 2 && NSTG <= 4, "2 to 4 input slots");
   static_assert(W == 8 || W == 16, "tiles of 8 (64-byte swizzle) or 16 (128-byte swizzle) pencils");
   // 16-byte chunk column of row `row` holding the pencil pair c: c xor swz(row)
   __host__ __device__ static int swz(int row) { return W == 16 ? (row & 7) : ((row >> 1) & 3); }
@@ -541,10 +543,10 @@ __device__ __forceinline__ void fs_tma_store2d(const CUtensorMap* map, int x, in
                : "memory");
   asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
-template <int W, int MINB>
+template <int W, int MINB, int NSTG = 2>
 __global__ void __launch_bounds__(16 * W, MINB)
     fourstep_tma_fused(const PassArgs<float> a, const __grid_constant__ CUtensorMap map) {
-  using K = TmaFusedCfg<W>;
+  using K = TmaFusedCfg<W, NSTG>;
   constexpr int P = K::P, Q = K::Q, H = P / 2, n = K::n_;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -552,7 +554,7 @@ __global__ void __launch_bounds__(16 * W, MINB)
   unsigned char* sb = smem_raw + (base - raw);
   float2* slots = reinterpret_cast<float2*>(sb + K::off_slot);
   float2* gs = reinterpret_cast<float2*>(sb + K::off_g);
-  const uint32_t bar_in0 = base + (uint32_t)K::off_bar, bar_g = bar_in0 + 16;
+  const uint32_t bar_in0 = base + (uint32_t)K::off_bar, bar_g = bar_in0 + 8 * NSTG;
   constexpr int SLOT = (int)(K::slot_bytes / 8);
 
   const int tid = threadIdx.x;
@@ -562,23 +564,44 @@ __global__ void __launch_bounds__(16 * W, MINB)
   float2* xw = reinterpret_cast<float2*>(sb + K::off_x) + wi * 1024;  // this warp's exchange buffer
   const int ntiles = a.nblk_i;
   bool ok = true;
+  // work units: a tile and, in 3D, its mirror tile (m1 -> n1 - m1, the same m2
+  // block), whose pencils read the same multiplier rows: staged once per unit
+  const int n1 = a.nn[1], n2 = a.nn[2];
+  const bool pair = (a.d == 3) && (n2 % W == 0) && (a.I == n1 * n2);
+  const int rowblk = pair ? n2 / W : 1;  // tiles per m1 row
+  const int nunits = pair ? (n1 / 2 + 1) * rowblk : ntiles;
+  auto unit_ntiles = [&](int u) {
+    if (!pair) return 1;
+    const int m = u / rowblk;
+    return (m == 0 || m == n1 / 2) ? 1 : 2;
+  };
+  auto unit_tile = [&](int u, int kk) {
+    if (!pair) return u;
+    const int m = u / rowblk, bb = u - m * rowblk;
+    return (kk == 0 ? m : n1 - m) * rowblk + bb;
+  };
+  // thread 0's load cursor: the next tile of this CTA's sequence to load
+  int lu = blockIdx.x, lk = 0;
+  auto load_next = [&](int slot_index) {
+    if (lu >= nunits) return;
+    const int tl = unit_tile(lu, lk);
+    fs_mbar_expect_tx(bar_in0 + 8 * slot_index, (uint32_t)K::slot_bytes);
+    fs_tma_load2d(base + (uint32_t)(K::off_slot + slot_index * K::slot_bytes), &map, 2 * W * tl, 0,
+                  bar_in0 + 8 * slot_index);
+    if (++lk == unit_ntiles(lu)) {
+      lk = 0;
+      lu += gridDim.x;
+    }
+  };
 
   if (tid == 0) {
-    fs_mbar_init(bar_in0, 1);
-    fs_mbar_init(bar_in0 + 8, 1);
+    for (int s = 0; s < NSTG; ++s) fs_mbar_init(bar_in0 + 8 * s, 1);
     fs_mbar_init(bar_g, K::threads);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  if (tid == 0) {
-    for (int s = 0; s < 2; ++s) {
-      const int tl = blockIdx.x + s * gridDim.x;
-      if (tl < ntiles) {
-        fs_mbar_expect_tx(bar_in0 + 8 * s, (uint32_t)K::slot_bytes);
-        fs_tma_load2d(base + (uint32_t)(K::off_slot + s * K::slot_bytes), &map, 2 * W * tl, 0, bar_in0 + 8 * s);
-      }
-    }
-  }
+  if (tid == 0)
+    for (int s = 0; s < NSTG; ++s) load_next(s);
   // multiplier rows of a tile: thread tid copies rows tid/W + 16 m of pencil tid mod W
   const int gw = tid % W;
   auto stage_g = [&](int tile) {
@@ -599,7 +622,7 @@ __global__ void __launch_bounds__(16 * W, MINB)
     }
     asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar_g) : "memory");
   };
-  if ((int)blockIdx.x < ntiles) stage_g(blockIdx.x);
+  if ((int)blockIdx.x < nunits) stage_g(unit_tile(blockIdx.x, 0));
   // this thread's twiddles w_n^(t k1), k1 = 1..P-1: t is fixed for the
   // kernel's lifetime, so they stay in registers
   const float2* gtw = reinterpret_cast<const float2*>(a.tw);
@@ -613,11 +636,13 @@ __global__ void __launch_bounds__(16 * W, MINB)
   const float2* gp = gs + K::eb(t, w);       // rows t + P k2 keep t's chunk column
   const float2* gn = gs + K::eb(n - t, w);   // rows n - t - P k2 keep n - t's
 
-  int it = 0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-    const int s = it & 1;
+  int it = 0, ui = 0;
+  for (int u = blockIdx.x; u < nunits; u += gridDim.x, ++ui)
+  for (int kk = 0, nt = unit_ntiles(u); kk < nt; ++kk, ++it) {
+    const int tile = unit_tile(u, kk);
+    const int s = it % NSTG;
     float2* slot = slots + s * SLOT;
-    if (ok) ok = fs_mbar_wait(bar_in0 + 8 * s, (it >> 1) & 1);
+    if (ok) ok = fs_mbar_wait(bar_in0 + 8 * s, (it / NSTG) & 1);
 
     float2 v[P];
     // step A: pruned 32-point DFT over q, twiddles, exchange
@@ -639,7 +664,7 @@ __global__ void __launch_bounds__(16 * W, MINB)
     Dft<Q, false>::run(v + Q);
     // multiply: element (0, k2) is frequency t + P k2, element (1, Q - 1 - k2)
     // its mirror n - k, one octant row; for t = 0 column Q is its own mirror
-    if (ok) ok = fs_mbar_wait(bar_g, it & 1);
+    if (kk == 0 && ok) ok = fs_mbar_wait(bar_g, ui & 1);  // this unit's multiplier rows
 #pragma unroll
     for (int k2 = 0; k2 < Q; ++k2) {
       const float2 g0 = k2 < Q / 2 ? gp[P * k2 * W] : gn[-P * k2 * W];
@@ -668,21 +693,144 @@ __global__ void __launch_bounds__(16 * W, MINB)
     for (int q = 0; q < H; ++q) slot[K::eb(t + Q * q, w)] = v[q];
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> bulk store
     __syncthreads();  // the tile's results are in the slot; every warp is done with the multiplier rows
-    const int next = tile + gridDim.x;
     if (tid == 0) fs_tma_store2d(&map, 2 * W * tile, 0, base + (uint32_t)(K::off_slot + s * K::slot_bytes));
-    if (next < ntiles) stage_g(next);
+    if (kk == nt - 1 && u + (int)gridDim.x < nunits) stage_g(unit_tile(u + gridDim.x, 0));
     if (tid == 0) {
       asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // the slot has been read out
-      const int tl = tile + 2 * gridDim.x;
-      if (tl < ntiles) {
-        fs_mbar_expect_tx(bar_in0 + 8 * s, (uint32_t)K::slot_bytes);
-        fs_tma_load2d(base + (uint32_t)(K::off_slot + s * K::slot_bytes), &map, 2 * W * tl, 0, bar_in0 + 8 * s);
-      }
+      load_next(s);
     }
   }
   if (!ok && a.err) atomicOr(a.err, 1);
   if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------
+// One tile of a pass inside the batched persistent kernel (batch.cu): W
+// pencils of length n, read straight from global memory through L2 (the data
+// may have been written earlier in the same launch, so not through the
+// read-only path), one exchange per transform through xs (layout Cfg::xi,
+// synchronised with __syncthreads: the caller's CTA is W Q threads), and
+// written back.  tws is the (Q x P) twiddle table of this n (pitch Cfg::TP).
+// The fused pass gathers its multiplier values from the octant in global
+// memory before the forward transform, so their latency hides behind it.
+// ---------------------------------------------------------------------------
+template <int n, bool CONTIG, int MODE, int W>
+__device__ __forceinline__ void batch_tile(const PassArgs<float>& a, const float2* in, float2* out, int tile,
+                                           float2* xs, const float2* tws) {
+  using K = Cfg<n, CONTIG, MODE, W, 2>;
+  constexpr int P = K::P, Q = K::Q, CC = K::CC, H = P / 2;
+  const int tid = threadIdx.x;
+  const int w = CONTIG ? tid / Q : tid % W;
+  const int t = CONTIG ? tid % Q : tid / W;
+  bool valid;
+  long long in_base, out_base;
+  int inner = 0;
+  if (CONTIG) {
+    const int row = tile * W + w;
+    valid = row < a.O;
+    in_base = (long long)row * a.in_pitch_o;
+    out_base = (long long)row * a.out_pitch_o;
+  } else {
+    const int o = tile / a.nblk_i;
+    inner = (tile - o * a.nblk_i) * W + w;
+    valid = inner < a.I;
+    in_base = (long long)o * a.in_pitch_o + inner;
+    out_base = (long long)o * a.out_pitch_o + inner;
+  }
+  const long long ip = CONTIG ? 1 : a.in_pitch_pos, op = CONTIG ? 1 : a.out_pitch_pos;
+  const float2* gin = in + in_base;
+  float2* gout = out + out_base;
+  const float4* twt = reinterpret_cast<const float4*>(tws + t * K::TP);
+  float2 v[P];
+  if constexpr (MODE != MODE_INV) {
+    float2 g[K::FUSED ? P : 1];
+    if constexpr (K::FUSED) {
+      // octant row of frequency k = t + Q c + P k2 (k for k2 < Q/2, n - k above)
+      const int n1 = a.nn[1], n2 = a.nn[2];
+      long long rest, pitch0;
+      if (a.d == 3) {
+        const int m1 = inner / n2, m2 = inner % n2;
+        rest = (long long)fold_freq(m1, n1) * (a.Nhs[2] + 1) + fold_freq(m2, n2);
+        pitch0 = (long long)(a.Nhs[1] + 1) * (a.Nhs[2] + 1);
+      } else {
+        rest = fold_freq(inner, n1);
+        pitch0 = a.Nhs[1] + 1;
+      }
+      const float2* mult = reinterpret_cast<const float2*>(a.fields[0].mult) + rest;
+#pragma unroll
+      for (int c = 0; c < CC; ++c)
+#pragma unroll
+        for (int k2 = 0; k2 < Q; ++k2) {
+          const int k = t + Q * c + P * k2;
+          const int row = k2 < Q / 2 ? k : n - k;
+          g[c * Q + k2] = valid ? __ldg(mult + row * pitch0) : float2{0.f, 0.f};
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < H; ++q) v[q] = valid ? __ldcg(gin + (t + Q * q) * ip) : float2{0.f, 0.f};
+    dft_fwd_halfzero<P>(v);
+    apply_twiddles<P, false>(v, twt);
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1) xs[K::xi(k1, t, w)] = v[k1];
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < CC; ++c)
+#pragma unroll
+      for (int j = 0; j < Q; ++j) v[c * Q + j] = xs[K::xi(t + Q * c, j, w)];
+#pragma unroll
+    for (int c = 0; c < CC; ++c) Dft<Q, false>::run(v + c * Q);
+    if constexpr (MODE == MODE_FWD) {
+      if (valid) {
+#pragma unroll
+        for (int c = 0; c < CC; ++c)
+#pragma unroll
+          for (int k2 = 0; k2 < Q; ++k2) gout[(t + Q * c + P * k2) * op] = v[c * Q + k2];
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < CC; ++c) {
+#pragma unroll
+        for (int k2 = 0; k2 < Q; ++k2) v[c * Q + k2] = cmul(v[c * Q + k2], g[c * Q + k2]);
+        Dft<Q, true>::run(v + c * Q);
+      }
+      __syncthreads();  // the step-B reads of xs are done
+#pragma unroll
+      for (int c = 0; c < CC; ++c)
+#pragma unroll
+        for (int j = 0; j < Q; ++j) xs[K::xi(t + Q * c, j, w)] = v[c * Q + j];
+      __syncthreads();
+#pragma unroll
+      for (int k1 = 0; k1 < P; ++k1) v[k1] = xs[K::xi(k1, t, w)];
+      apply_twiddles<P, true>(v, twt);
+      idft_cropped<P>(v);
+      if (valid) {
+#pragma unroll
+        for (int q = 0; q < H; ++q) gout[(t + Q * q) * op] = v[q];
+      }
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < CC; ++c)
+#pragma unroll
+      for (int k2 = 0; k2 < Q; ++k2)
+        v[c * Q + k2] = valid ? __ldcg(gin + (t + Q * c + P * k2) * ip) : float2{0.f, 0.f};
+#pragma unroll
+    for (int c = 0; c < CC; ++c) Dft<Q, true>::run(v + c * Q);
+#pragma unroll
+    for (int c = 0; c < CC; ++c)
+#pragma unroll
+      for (int j = 0; j < Q; ++j) xs[K::xi(t + Q * c, j, w)] = v[c * Q + j];
+    __syncthreads();
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1) v[k1] = xs[K::xi(k1, t, w)];
+    apply_twiddles<P, true>(v, twt);
+    idft_cropped<P>(v);
+    if (valid) {
+#pragma unroll
+      for (int q = 0; q < H; ++q) gout[(t + Q * q) * op] = v[q];
+    }
+  }
 }
 
 // Tensor map of a fused pass's spectra: rows of I complex pencils (2 I
@@ -722,10 +870,10 @@ inline bool tma_fused_usable(int n, const PassArgs<float>& a) {
          (a.in_pitch_pos * 8) % 16 == 0 && a.I % 2 == 0;
 }
 
-template <int W, int MINB>
+template <int W, int MINB, int NSTG = 2>
 cudaError_t launch_tma_fused(const PassArgs<float>& a0, cudaStream_t s) {
-  using K = TmaFusedCfg<W>;
-  auto kern = fourstep_tma_fused<W, MINB>;
+  using K = TmaFusedCfg<W, NSTG>;
+  auto kern = fourstep_tma_fused<W, MINB, NSTG>;
   static int grid_cap[64] = {0};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

@@ -778,8 +778,9 @@ def run_batch(args):
     oct_bytes = sum(8 * int(np.prod([n + 1 for n in Ns])) for Ns, _, _, _ in recipe)
     algo = 27 * U_bytes + oct_bytes - 0  # 3+6+(4+4)+6+3 U and one multiplier octant per density
 
-    def timed(strategy, steps):
+    def timed(strategy, steps, chunk=0):
         b.set_strategy(strategy)
+        b.set_chunk(chunk)
         with torch.cuda.stream(stream):
             for _ in range(max(3, args.warmup)):
                 b.apply(fs, outs)
@@ -796,9 +797,20 @@ def run_batch(args):
         b.status()
         return sum(a.elapsed_time(c) for a, c in zip(st, en)) / steps
 
+    # the autotuner's choice (strategy and chunk), made on the first apply
+    b.set_strategy(vp.VP_BATCH_AUTO)
+    b.set_chunk(0)
+    with torch.cuda.stream(stream):
+        b.apply(fs, outs)
+    torch.cuda.synchronize(dev)
+    auto_strategy, auto_chunk = b.strategy(), b.chunk()
+    # the persistent launch at every chunk size the autotuner tries; the
+    # headline is the fastest
+    chunks = {c: timed(vp.VP_BATCH_PERSISTENT, max(3, args.steps // 4), c) for c in (4, 8, 16, 32)}
+    best_chunk = min(chunks, key=chunks.get)
     clocks = ClockSampler(0)
     clocks.start()
-    ms = timed(vp.VP_BATCH_PERSISTENT, args.steps)
+    ms = timed(vp.VP_BATCH_PERSISTENT, args.steps, best_chunk)
     clk = clocks.stop()
     ms_seq = timed(vp.VP_BATCH_PER_DENSITY, max(3, args.steps // 4))
     ms_one = timed(vp.VP_BATCH_PERSISTENT_ONE_PER_SM, max(3, args.steps // 4))
@@ -813,6 +825,10 @@ def run_batch(args):
         "config": {"workload": args.workload, "densities": len(recipe),
                    "sizes": sorted({n for Ns, _, _, _ in recipe for n in Ns}), "per_axis_sizes": grids,
                    "sum_points": pts, "l2": "flushed before every timed step (256 MB write)"},
+        "persistent_chunk": best_chunk, "persistent_ms_by_chunk": chunks,
+        "autotuner_choice": {"strategy": {1: "persistent", 2: "persistent_one_cta_per_sm", 3: "per_density",
+                                          4: "graph_of_streams"}.get(auto_strategy, auto_strategy),
+                             "chunk": auto_chunk},
         "roofline": {"bound": "hbm", "kernel": "batch_kernel", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
                      "algorithmic_bytes_per_launch": algo, "avg_launch_ms": ms},

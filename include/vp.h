@@ -231,15 +231,20 @@ int vp_fft_length_supported(int n2);
  * outlive the batch.  The batch owns one workspace per density.
  * vp_batch_apply computes phi_i = T_i * f_i for every i (device pointers,
  * complex64, N_i^d elements each; asynchronous on the batch's stream).  Every
- * pass of every density becomes tiles in one global work list; persistent CTAs
- * take tiles in pass-major order and wait (bounded) until the previous pass of
- * the same density has completed.  The launch and its counter reset run as one
+ * pass of every density becomes tiles in one global work list, cut into work
+ * items of `chunk` consecutive tiles of one pass; persistent CTAs take items in
+ * pass-major order, wait (bounded) until the previous pass of the same density
+ * has completed, and run an item's tiles with each tile's input staged while
+ * the one before it is computed.  The launch and its counter reset run as one
  * CUDA graph, replayed per call.
- * Strategy: VP_BATCH_AUTO (default) times the persistent kernel at two grid
- * sizes against per-density vp_apply launches (serial, and forked over eight
- * streams inside one CUDA graph) on the first call, keeps the fastest and
- * caches the choice on disk (file $VP_AUTOTUNE_CACHE, default
+ * Strategy: VP_BATCH_AUTO (default) times, on the first call, the persistent
+ * kernel with chunks of 4, 8, 16 and 32 tiles on all resident CTAs and with
+ * chunks of 8 at one CTA per SM, against per-density vp_apply launches
+ * (serial, and forked over eight streams inside one CUDA graph), keeps the
+ * fastest and caches the choice on disk (file $VP_AUTOTUNE_CACHE, default
  * ~/.cache/vp_autotune.txt) keyed by device, driver and the batch's sizes.
+ * vp_batch_set_chunk fixes the chunk size (1..256; 0 = the autotuner's
+ * choice, 8 before tuning); vp_batch_get_chunk reports the one in use.
  * Failure detection: a wait longer than the batch timeout (default about 2 s,
  * vp_batch_set_timeout) records an error and lets the kernel finish;
  * vp_batch_status then returns VP_ERR_TIMEOUT.  vp_batch_withhold(b, i, p)
@@ -259,6 +264,8 @@ vp_status vp_batch_create(vp_batch* out, int count, const vp_plan* plans);
 vp_status vp_batch_set_stream(vp_batch b, void* stream);
 vp_status vp_batch_set_strategy(vp_batch b, int strategy);
 vp_status vp_batch_get_strategy(vp_batch b, int* strategy);
+vp_status vp_batch_set_chunk(vp_batch b, int chunk);
+vp_status vp_batch_get_chunk(vp_batch b, int* chunk);
 vp_status vp_batch_set_timeout(vp_batch b, double seconds);
 vp_status vp_batch_withhold(vp_batch b, int density, int pass);
 vp_status vp_batch_apply(vp_batch b, const void* const* f, void* const* phi);

@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "../../include/vp.h"
+#include "fourstep.cuh"
 #include "vp_internal.cuh"
 
 namespace vp {
@@ -44,7 +45,7 @@ struct BatchPass {
   int density;           // index into the pointer tables
   int io;                // 1: input is the density's f, 2: output is the density's phi
   long long ntiles;
-  long long item_base;   // first global item of this pass
+  long long item_base;   // first tile of this pass in the pass-major order
   int dep;               // completion counter to wait on (-1: none)
   long long dep_need;    // tiles that counter must reach
   long long dep_need_orig;
@@ -59,6 +60,7 @@ struct BatchLaunch {
   long long* done;
   int* err;
   long long timeout_cycles;
+  int chunk;  // tiles per work item
   const void* f[BATCH_MAX];
   void* phi[BATCH_MAX];
 };
@@ -71,19 +73,54 @@ template <int n> struct BatchE {
 template <int n, bool CONTIG, int MODE>
 using BatchCfg = PassCfg<float, n, CONTIG, MODE, BatchE<n>::E, BATCH_THREADS / (n / BatchE<n>::E), 1, 2>;
 
-template <int n> constexpr size_t batch_smem_n() {
-  return std::max(BatchCfg<n, true, MODE_FWD>::xchg_bytes, BatchCfg<n, false, MODE_FWD>::xchg_bytes);
-}
+// Lengths whose tiles run the four-step code (fourstep.cuh) with W = 256 / Q
+// pencils per tile; the others run the Stockham tiles of pencil_fft.cuh.
+__host__ __device__ constexpr bool batch_fourstep(int n) { return n == 64 || n == 128 || n == 256; }
+template <int n> constexpr int batch_fs_W() { return BATCH_THREADS / (n / fs::fs_P(n)); }
+template <int n, bool CONTIG, int MODE> using BatchFs = fs::Cfg<n, CONTIG, MODE, batch_fs_W<n>(), 2>;
 
 #define VP_BATCH_LENGTHS(X) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256)
+#define VP_BATCH_STOCKHAM(X) X(16) X(24) X(32) X(48) X(96) X(192)
 
-constexpr size_t batch_smem_bytes() {
+// shared memory: the exchange buffer (either engine), two input staging
+// slots, the four-step twiddle tables
+template <int n> constexpr size_t batch_xs_n() {
+  if constexpr (batch_fourstep(n))
+    return std::max((size_t)BatchFs<n, true, MODE_FWD>::XELEMS, (size_t)BatchFs<n, false, MODE_FWD>::XELEMS) * 8;
+  else
+    return std::max(BatchCfg<n, true, MODE_FWD>::xchg_bytes, BatchCfg<n, false, MODE_FWD>::xchg_bytes);
+}
+template <int n> constexpr size_t batch_slot_n() {
+  if constexpr (batch_fourstep(n))
+    return std::max({BatchFs<n, true, MODE_FWD>::in_bytes, BatchFs<n, false, MODE_FWD>::in_bytes,
+                     BatchFs<n, true, MODE_INV>::in_bytes, BatchFs<n, false, MODE_INV>::in_bytes});
+  else
+    return std::max({BatchCfg<n, true, MODE_FWD>::slot_bytes, BatchCfg<n, false, MODE_FWD>::slot_bytes,
+                     BatchCfg<n, true, MODE_INV>::slot_bytes, BatchCfg<n, false, MODE_INV>::slot_bytes});
+}
+constexpr size_t r128(size_t b) { return (b + 127) / 128 * 128; }
+constexpr size_t batch_xs_bytes() {
   size_t m = 0;
-#define VP_M(N) m = std::max(m, batch_smem_n<N>());
+#define VP_M(N) m = std::max(m, batch_xs_n<N>());
   VP_BATCH_LENGTHS(VP_M)
 #undef VP_M
-  return m;
+  return r128(m);
 }
+constexpr size_t batch_slot_bytes() {
+  size_t m = 0;
+#define VP_M(N) m = std::max(m, batch_slot_n<N>());
+  VP_BATCH_LENGTHS(VP_M)
+#undef VP_M
+  return r128(m);
+}
+// four-step twiddle tables, (Q x (P + 2)) each: 2N = 256, 128, 64
+__host__ __device__ constexpr int batch_tw_off(int li) { return li == 0 ? 0 : (li == 1 ? 16 * 18 : 16 * 18 + 8 * 18); }
+constexpr int BATCH_TW_TOTAL = 16 * 18 + 8 * 18 + 8 * 10;
+__host__ __device__ constexpr int batch_tw_index(int n) { return n == 256 ? 0 : (n == 128 ? 1 : 2); }
+constexpr size_t batch_smem_bytes() { return batch_xs_bytes() + 2 * batch_slot_bytes() + (size_t)BATCH_TW_TOTAL * 8; }
+// two CTAs per SM (228 KB of shared memory per SM, 1 KB reserved per CTA, the
+// kernel's static arrays about 3 KB)
+static_assert(2 * (batch_smem_bytes() + 3072 + 1024) <= 233472, "two batch CTAs per SM");
 
 bool batch_length_built(int n) {
   switch (n) {
@@ -95,96 +132,222 @@ bool batch_length_built(int n) {
   return false;
 }
 
+// Stockham tiles: stage the input of a tile into a slot, or run a tile (from
+// the slot when given, else from global memory through L2)
 template <int n>
-__device__ __noinline__ void batch_tile(int kind, const PassArgs<float>& a, long long tile, float2* sm) {
+__device__ __noinline__ void bt_stage_st(int kind, const PassArgs<float>& a, long long tile, float2* slot) {
+  unsigned char* sl = reinterpret_cast<unsigned char*>(slot);
   switch (kind) {
-    case FWD_CONTIG: process_tile<float, n, true, MODE_FWD, BatchCfg<n, true, MODE_FWD>, true>(a, tile, sm, nullptr, false); break;
-    case FWD_STRIDED: process_tile<float, n, false, MODE_FWD, BatchCfg<n, false, MODE_FWD>, true>(a, tile, sm, nullptr, false); break;
-    case INV_CONTIG: process_tile<float, n, true, MODE_INV, BatchCfg<n, true, MODE_INV>, true>(a, tile, sm, nullptr, false); break;
-    case INV_STRIDED: process_tile<float, n, false, MODE_INV, BatchCfg<n, false, MODE_INV>, true>(a, tile, sm, nullptr, false); break;
-    default: process_tile<float, n, false, MODE_FUSED1, BatchCfg<n, false, MODE_FUSED1>, true>(a, tile, sm, nullptr, false); break;
+    case FWD_CONTIG: stage_tile<float, n, true, MODE_FWD, BatchCfg<n, true, MODE_FWD>>(a, tile, sl); break;
+    case FWD_STRIDED: stage_tile<float, n, false, MODE_FWD, BatchCfg<n, false, MODE_FWD>>(a, tile, sl); break;
+    case INV_CONTIG: stage_tile<float, n, true, MODE_INV, BatchCfg<n, true, MODE_INV>>(a, tile, sl); break;
+    case INV_STRIDED: stage_tile<float, n, false, MODE_INV, BatchCfg<n, false, MODE_INV>>(a, tile, sl); break;
+    default: stage_tile<float, n, false, MODE_FUSED1, BatchCfg<n, false, MODE_FUSED1>>(a, tile, sl); break;
+  }
+}
+template <int n>
+__device__ __noinline__ void bt_run_st(int kind, const PassArgs<float>& a, long long tile, float2* sm,
+                                       const float2* slot) {
+  const unsigned char* sl = reinterpret_cast<const unsigned char*>(slot);
+  const bool st = slot != nullptr;
+  switch (kind) {
+    case FWD_CONTIG: process_tile<float, n, true, MODE_FWD, BatchCfg<n, true, MODE_FWD>, true>(a, tile, sm, sl, st); break;
+    case FWD_STRIDED: process_tile<float, n, false, MODE_FWD, BatchCfg<n, false, MODE_FWD>, true>(a, tile, sm, sl, st); break;
+    case INV_CONTIG: process_tile<float, n, true, MODE_INV, BatchCfg<n, true, MODE_INV>, true>(a, tile, sm, sl, st); break;
+    case INV_STRIDED: process_tile<float, n, false, MODE_INV, BatchCfg<n, false, MODE_INV>, true>(a, tile, sm, sl, st); break;
+    default: process_tile<float, n, false, MODE_FUSED1, BatchCfg<n, false, MODE_FUSED1>, true>(a, tile, sm, sl, st); break;
+  }
+}
+// four-step tiles
+template <int n>
+__device__ __noinline__ void bt_stage_fs(int kind, const PassArgs<float>& a, int tile, float2* slot) {
+  const float2* i2 = reinterpret_cast<const float2*>(a.in);
+  switch (kind) {
+    case FWD_CONTIG: fs::stage_input_from<BatchFs<n, true, MODE_FWD>>(a, i2, tile, slot); break;
+    case FWD_STRIDED: fs::stage_input_from<BatchFs<n, false, MODE_FWD>>(a, i2, tile, slot); break;
+    case INV_CONTIG: fs::stage_input_from<BatchFs<n, true, MODE_INV>>(a, i2, tile, slot); break;
+    case INV_STRIDED: fs::stage_input_from<BatchFs<n, false, MODE_INV>>(a, i2, tile, slot); break;
+    default: fs::stage_input_from<BatchFs<n, false, MODE_FUSED1>>(a, i2, tile, slot); break;
+  }
+}
+template <int n>
+__device__ __noinline__ void bt_run_fs(int kind, const PassArgs<float>& a, int tile, float2* xs, const float2* tws,
+                                       const float2* slot) {
+  constexpr int W = batch_fs_W<n>();
+  const float2* i2 = reinterpret_cast<const float2*>(a.in);
+  float2* o2 = reinterpret_cast<float2*>(a.out);
+  switch (kind) {
+    case FWD_CONTIG: fs::batch_tile<n, true, MODE_FWD, W>(a, i2, o2, tile, xs, tws, slot); break;
+    case FWD_STRIDED: fs::batch_tile<n, false, MODE_FWD, W>(a, i2, o2, tile, xs, tws, slot); break;
+    case INV_CONTIG: fs::batch_tile<n, true, MODE_INV, W>(a, i2, o2, tile, xs, tws, slot); break;
+    case INV_STRIDED: fs::batch_tile<n, false, MODE_INV, W>(a, i2, o2, tile, xs, tws, slot); break;
+    default: fs::batch_tile<n, false, MODE_FUSED1, W>(a, i2, o2, tile, xs, tws, slot); break;
   }
 }
 
 constexpr int BATCH_MAX_PASSES = BATCH_MAX * 5;
 
+// The persistent kernel.  Work items are chunks of up to L.chunk consecutive
+// tiles of one pass, laid out pass-major; CTAs take them from a
+// global counter.  Per chunk: thread 0 takes the next chunk, finds its pass and
+// waits (bounded) until every tile of the pass it depends on has completed;
+// one barrier publishes the chunk; its tiles then run like a standalone pass,
+// each tile's input staged into shared memory by cp.async while the tile
+// before it is computed (two slots); a barrier, and thread 0 adds the chunk's
+// tiles to the pass's completion counter (fence, then atomic add).  Every chunk
+// a CTA waits on was taken earlier by a resident CTA, so the batch always
+// makes progress.  Data written inside the launch is read through L2
+// (cp.async.cg, ld.global.cg).
+constexpr int BATCH_CHUNKS[4] = {4, 8, 16, 32};  // chunk sizes the autotuner tries
+
+__device__ __forceinline__ int batch_find_pass(const int* base, int npasses, long long item) {
+  int lo = 0, hi = npasses - 1;  // last pass whose first item <= item
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (base[mid] <= item)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void batch_stage(int n, int kind, const PassArgs<float>& a, long long tile, float2* slot) {
+  switch (n) {
+    case 256: bt_stage_fs<256>(kind, a, (int)tile, slot); break;
+    case 128: bt_stage_fs<128>(kind, a, (int)tile, slot); break;
+    case 64: bt_stage_fs<64>(kind, a, (int)tile, slot); break;
+#define VP_C(N) \
+  case N: bt_stage_st<N>(kind, a, tile, slot); break;
+    VP_BATCH_STOCKHAM(VP_C)
+#undef VP_C
+  }
+}
+
 __global__ void __launch_bounds__(BATCH_THREADS, 2) batch_kernel(const BatchLaunch L) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   float2* sm = reinterpret_cast<float2*>(smem_raw);
-  __shared__ long long s_base[BATCH_MAX_PASSES];  // first item of every pass
-  __shared__ __align__(16) BatchPass s_bp;        // the current tile's pass
+  float2* slots = reinterpret_cast<float2*>(smem_raw + batch_xs_bytes());
+  float2* tws = reinterpret_cast<float2*>(smem_raw + batch_xs_bytes() + 2 * batch_slot_bytes());
+  constexpr int SLOT = (int)(batch_slot_bytes() / 8);
+  __shared__ int s_base[BATCH_MAX_PASSES];  // first chunk of every pass (< 2^31, checked at creation)
   __shared__ long long s_item;
   __shared__ int s_pass;
-  for (int i = threadIdx.x; i < L.npasses; i += blockDim.x) s_base[i] = L.passes[i].item_base;
+  __shared__ __align__(16) PassArgs<float> s_a;  // the chunk's pass arguments, density pointers patched in
+  __shared__ const float2* s_twsrc[3];
+  if (threadIdx.x < 3) s_twsrc[threadIdx.x] = nullptr;
   __syncthreads();
-  for (;;) {
-    if (threadIdx.x == 0) {
-      const long long item = (long long)atomicAdd(L.next_item, 1ULL);
-      int pi = -1;
-      if (item < L.total_items) {
-        // last pass whose first item <= item
-        int lo = 0, hi = L.npasses - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) / 2;
-          if (s_base[mid] <= item)
-            lo = mid;
-          else
-            hi = mid - 1;
-        }
-        pi = lo;
-      }
-      s_item = item;
-      s_pass = pi;
-    }
-    __syncthreads();
-    const int pi = s_pass;
-    if (pi < 0) break;
-    // the pass descriptor, copied cooperatively
-    {
-      const int words = (int)(sizeof(BatchPass) / 4);
-      const unsigned* src = reinterpret_cast<const unsigned*>(L.passes + pi);
-      unsigned* dst = reinterpret_cast<unsigned*>(&s_bp);
-      for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const int dep = s_bp.dep;
-      if (dep >= 0) {
-        const long long need = s_bp.dep_need;
-        const long long t0 = clock64();
-        volatile long long* cnt = L.done + dep;
-        while (*cnt < need) {
-          if (clock64() - t0 > L.timeout_cycles) {
-            atomicOr(L.err, 1);
-            break;
-          }
-          __nanosleep(128);
-        }
-        __threadfence();
-      }
-      if (s_bp.io == 1) s_bp.a.in = L.f[s_bp.density];
-      if (s_bp.io == 2) s_bp.a.out = L.phi[s_bp.density];
-    }
-    __syncthreads();
-    const long long tile = s_item - s_bp.item_base;
-    switch (s_bp.n) {
-#define VP_C(N) \
-  case N: batch_tile<N>(s_bp.kind, s_bp.a, tile, sm); break;
-      VP_BATCH_LENGTHS(VP_C)
-#undef VP_C
-    }
-    __syncthreads();  // every thread's stores of this tile are issued
-    if (threadIdx.x == 0) {
-      __threadfence();
-      atomicAdd(reinterpret_cast<unsigned long long*>(L.done + s_bp.done), 1ULL);
+  if (threadIdx.x == 0) {  // first chunk of every pass
+    long long b = 0;
+    for (int i = 0; i < L.npasses; ++i) {
+      s_base[i] = (int)b;
+      b += (L.passes[i].ntiles + L.chunk - 1) / L.chunk;
     }
   }
+  for (int i = threadIdx.x; i < L.npasses; i += blockDim.x) {
+    const int n = L.passes[i].n;
+    if (batch_fourstep(n)) s_twsrc[batch_tw_index(n)] = reinterpret_cast<const float2*>(L.passes[i].a.tw);
+  }
+  __syncthreads();
+  // four-step twiddle tables w_n^(t k1) (any pass of that length has the table exp(-2 pi i q / n))
+#pragma unroll
+  for (int li = 0; li < 3; ++li) {
+    const float2* src = s_twsrc[li];
+    if (!src) continue;
+    const int n = li == 0 ? 256 : (li == 1 ? 128 : 64);
+    const int P = fs::fs_P(n), Q = n / P, TP = P + 2;
+    for (int i = threadIdx.x; i < Q * P; i += blockDim.x) {
+      const int t = i / P, k1 = i % P;
+      tws[batch_tw_off(li) + t * TP + k1] = src[(t * k1) % n];
+    }
+  }
+  for (;;) {
+    if (threadIdx.x < 32) {
+      // warp 0: lane 0 takes the next chunk and waits for its dependency; the
+      // warp copies the pass arguments into shared memory
+      long long item = 0;
+      int pi = -1;
+      if (threadIdx.x == 0) {
+        item = (long long)atomicAdd(L.next_item, 1ULL);
+        if (item < L.total_items) {
+          pi = batch_find_pass(s_base, L.npasses, item);
+          const int dep = L.passes[pi].dep;
+          if (dep >= 0) {
+            const long long need = L.passes[pi].dep_need;
+            const long long c0 = clock64();
+            volatile long long* cnt = L.done + dep;
+            while (*cnt < need) {
+              if (clock64() - c0 > L.timeout_cycles) {
+                atomicOr(L.err, 1);
+                break;
+              }
+              __nanosleep(64);
+            }
+            __threadfence();
+          }
+        }
+        s_item = item;
+        s_pass = pi;
+      }
+      pi = __shfl_sync(0xffffffffu, pi, 0);
+      if (pi >= 0) {
+        const unsigned* src = reinterpret_cast<const unsigned*>(&L.passes[pi].a);
+        unsigned* dst = reinterpret_cast<unsigned*>(&s_a);
+        for (int i = threadIdx.x; i < (int)(sizeof(PassArgs<float>) / 4); i += 32) dst[i] = src[i];
+        __syncwarp();
+        if (threadIdx.x == 0) {
+          const BatchPass& bp = L.passes[pi];
+          if (bp.io == 1) s_a.in = L.f[bp.density];
+          if (bp.io == 2) s_a.out = L.phi[bp.density];
+        }
+      }
+    }
+    __syncthreads();  // the chunk, its dependency and its arguments are ready for every thread
+    const int pi = s_pass;
+    if (pi < 0) break;
+    const BatchPass& bp = L.passes[pi];
+    const int n = bp.n, kind = bp.kind;
+    const long long t0 = (s_item - s_base[pi]) * L.chunk;
+    const long long t1 = t0 + L.chunk < bp.ntiles ? t0 + L.chunk : bp.ntiles;
+    // the first pass reads the caller's density: staged only when 16-byte aligned
+    const bool stage = !(reinterpret_cast<uintptr_t>(s_a.in) & 15);
+    if (stage) batch_stage(n, kind, s_a, t0, slots);
+    cp_async_commit();
+    for (long long tile = t0; tile < t1; ++tile) {
+      const int si = (int)(tile - t0) & 1;
+      if (stage && tile + 1 < t1) batch_stage(n, kind, s_a, tile + 1, slots + (si ^ 1) * SLOT);
+      cp_async_commit();
+      cp_async_wait<1>();  // this tile's input
+      __syncthreads();
+      const float2* sl = stage ? slots + si * SLOT : nullptr;
+      switch (n) {
+        case 256: bt_run_fs<256>(kind, s_a, (int)tile, sm, tws + batch_tw_off(0), sl); break;
+        case 128: bt_run_fs<128>(kind, s_a, (int)tile, sm, tws + batch_tw_off(1), sl); break;
+        case 64: bt_run_fs<64>(kind, s_a, (int)tile, sm, tws + batch_tw_off(2), sl); break;
+#define VP_C(N) \
+  case N: bt_run_st<N>(kind, s_a, tile, sm, sl); break;
+          VP_BATCH_STOCKHAM(VP_C)
+#undef VP_C
+      }
+      __syncthreads();  // the slot, the exchange buffer and s_a are free; the tile's stores are issued
+    }
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(reinterpret_cast<unsigned long long*>(L.done + bp.done), (unsigned long long)(t1 - t0));
+    }
+  }
+  cp_async_wait<0>();
 }
 
 // tiles of one pass under the batch configuration
 long long batch_tiles(int n, int kind, const PassArgs<float>& a, int* nblk) {
-  int Tp = n / ((n % 3 == 0) ? 12 : 16);
-  int W = BATCH_THREADS / Tp;
+  int W;
+  if (batch_fourstep(n)) {
+    W = BATCH_THREADS / (n / fs::fs_P(n));
+  } else {
+    const int Tp = n / ((n % 3 == 0) ? 12 : 16);
+    W = BATCH_THREADS / Tp;
+  }
   if (kind == FWD_CONTIG || kind == INV_CONTIG) {
     *nblk = 1;
     return (a.O + W - 1) / W;
@@ -211,6 +374,8 @@ struct vp_batch_s {
   cudaStream_t stream = nullptr;
   int strategy = 0;  // 0 = not tuned yet
   int forced = 0;    // strategy set by the caller
+  int chunk = 8;     // tiles per work item of the persistent kernel (the autotuner's choice)
+  int forced_chunk = 0;
   std::vector<BatchPass> host_passes;
   BatchPass* passes = nullptr;
   long long total_items = 0;
@@ -250,7 +415,9 @@ BatchLaunch make_launch(vp_batch b, const void* const* f, void* const* phi) {
   memset(&L, 0, sizeof(L));
   L.passes = b->passes;
   L.npasses = (int)b->host_passes.size();
-  L.total_items = b->total_items;
+  L.chunk = b->forced_chunk ? b->forced_chunk : b->chunk;
+  L.total_items = 0;
+  for (const BatchPass& bp : b->host_passes) L.total_items += (bp.ntiles + L.chunk - 1) / L.chunk;
   L.next_item = b->next_item;
   L.done = b->done;
   L.err = b->err;
@@ -449,34 +616,47 @@ void cache_store(const std::string& key, int s) {
   fclose(fh);
 }
 
-// Times each strategy on the batch (2 warm-ups, 3 timed runs on the batch's
-// stream with CUDA events) and keeps the fastest.
+// Times each candidate on the batch (2 warm-ups, 3 timed runs on the batch's
+// stream with CUDA events) and keeps the fastest: the persistent kernel with
+// every chunk size of BATCH_CHUNKS (all resident CTAs) and with 8-tile chunks
+// at one CTA per SM, the per-density launches and their graph over side
+// streams.  The choice is cached per device, driver and batch shape as
+// strategy + 100 x chunk.
 vp_status autotune(vp_batch b, const void* const* f, void* const* phi) {
-  const int cands[4] = {S_PERSISTENT, S_PERSISTENT_1, S_SEQUENTIAL, S_STREAMS};
+  struct Cand { int s, chunk; };
+  std::vector<Cand> cands;
+  for (int c : BATCH_CHUNKS) cands.push_back({S_PERSISTENT, c});
+  cands.push_back({S_PERSISTENT_1, 8});
+  cands.push_back({S_SEQUENTIAL, 8});
+  cands.push_back({S_STREAMS, 8});
   float best = 1e30f;
-  int bests = S_PERSISTENT;
+  Cand bestc = {S_PERSISTENT, 8};
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  for (int c : cands) {
+  const int saved_forced_chunk = b->forced_chunk;
+  for (const Cand& c : cands) {
+    b->forced_chunk = c.chunk;
     vp_status st = VP_OK;
-    for (int r = 0; r < 2 && st == VP_OK; ++r) st = run_strategy(b, c, f, phi);
+    for (int r = 0; r < 2 && st == VP_OK; ++r) st = run_strategy(b, c.s, f, phi);
     if (st != VP_OK) continue;
     cudaEventRecord(e0, b->stream);
-    for (int r = 0; r < 3 && st == VP_OK; ++r) st = run_strategy(b, c, f, phi);
+    for (int r = 0; r < 3 && st == VP_OK; ++r) st = run_strategy(b, c.s, f, phi);
     cudaEventRecord(e1, b->stream);
     if (cudaEventSynchronize(e1) != cudaSuccess || st != VP_OK) continue;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     if (ms < best) {
       best = ms;
-      bests = c;
+      bestc = c;
     }
   }
+  b->forced_chunk = saved_forced_chunk;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  b->strategy = bests;
-  cache_store(b->signature, bests);
+  b->strategy = bestc.s;
+  b->chunk = bestc.chunk;
+  cache_store(b->signature, bestc.s + 100 * bestc.chunk);
   return VP_OK;
 }
 
@@ -575,6 +755,10 @@ vp_status vp_batch_create(vp_batch* out, int count, const vp_plan* plans) {
         b->host_passes.push_back(bp);
       }
   b->total_items = base;
+  if (base >= (1LL << 31)) {
+    vp_batch_destroy(b);
+    return VP_ERR_UNSUPPORTED;
+  }
   const size_t npass = b->host_passes.size();
   e = cudaMalloc(&b->passes, npass * sizeof(BatchPass));
   if (e == cudaSuccess)
@@ -618,7 +802,9 @@ vp_status vp_batch_create(vp_batch* out, int count, const vp_plan* plans) {
   for (auto& c : sig)
     if (c == ' ') c = '_';
   b->signature = sig;
-  b->strategy = cache_lookup(sig);
+  const int cached = cache_lookup(sig);
+  b->strategy = cached % 100;
+  if (cached >= 100) b->chunk = cached / 100;
   *out = b;
   return VP_OK;
 }
@@ -632,6 +818,18 @@ vp_status vp_batch_set_stream(vp_batch b, void* stream) {
 vp_status vp_batch_set_strategy(vp_batch b, int strategy) {
   if (!b || strategy < 0 || strategy > 4) return VP_ERR_INVALID_ARG;
   b->forced = strategy;
+  return VP_OK;
+}
+
+vp_status vp_batch_set_chunk(vp_batch b, int chunk) {
+  if (!b || chunk < 0 || chunk > 256) return VP_ERR_INVALID_ARG;
+  b->forced_chunk = chunk;
+  return VP_OK;
+}
+
+vp_status vp_batch_get_chunk(vp_batch b, int* chunk) {
+  if (!b || !chunk) return VP_ERR_INVALID_ARG;
+  *chunk = b->forced_chunk ? b->forced_chunk : b->chunk;
   return VP_OK;
 }
 

@@ -219,6 +219,29 @@ __device__ __forceinline__ void stage_input(const PassArgs<float>& a, int tile, 
   }
 }
 
+// stage_input with the input pointer given apart from the pass arguments (the
+// batched kernel's first pass reads the caller's density)
+template <typename K>
+__device__ __forceinline__ void stage_input_from(const PassArgs<float>& a, const float2* gin, int tile, float2* slot) {
+  if constexpr (K::CONTIG_) {
+    constexpr int cpr = K::NIN / 2;
+    const long long row0 = (long long)tile * K::W;
+    for (int c = threadIdx.x; c < K::W * cpr; c += K::threads) {
+      const int w = c / cpr, k = c % cpr;
+      if (row0 + w < a.O) cp_async16(slot + K::si(2 * k, w), gin + (row0 + w) * a.in_pitch_o + 2 * k);
+    }
+  } else {
+    constexpr int cpr = K::W / 2;
+    const int o = tile / a.nblk_i;
+    const int inner0 = (tile - o * a.nblk_i) * K::W;
+    const float2* base = gin + (long long)o * a.in_pitch_o + inner0;
+    for (int c = threadIdx.x; c < K::NIN * cpr; c += K::threads) {
+      const int pos = c / cpr, k = c % cpr;
+      if (inner0 + 2 * k < a.I) cp_async16(slot + K::si(pos, 2 * k), base + pos * a.in_pitch_pos + 2 * k);
+    }
+  }
+}
+
 // Stages rows 0..n/2 of the multiplier octant for the W pencils of a tile
 // (8-byte copies; entry (row, w) at row W + w).  A thread's copies all belong
 // to pencil w = threadIdx.x mod W.
@@ -712,12 +735,14 @@ __global__ void __launch_bounds__(16 * W, MINB)
 // read-only path), one exchange per transform through xs (layout Cfg::xi,
 // synchronised with __syncthreads: the caller's CTA is W Q threads), and
 // written back.  tws is the (Q x P) twiddle table of this n (pitch Cfg::TP).
+// With `slot`, the tile's input was staged there by stage_input_from (layout
+// Cfg::si) and is read from shared memory instead.
 // The fused pass gathers its multiplier values from the octant in global
 // memory before the forward transform, so their latency hides behind it.
 // ---------------------------------------------------------------------------
 template <int n, bool CONTIG, int MODE, int W>
 __device__ __forceinline__ void batch_tile(const PassArgs<float>& a, const float2* in, float2* out, int tile,
-                                           float2* xs, const float2* tws) {
+                                           float2* xs, const float2* tws, const float2* slot = nullptr) {
   using K = Cfg<n, CONTIG, MODE, W, 2>;
   constexpr int P = K::P, Q = K::Q, CC = K::CC, H = P / 2;
   const int tid = threadIdx.x;
@@ -767,8 +792,13 @@ __device__ __forceinline__ void batch_tile(const PassArgs<float>& a, const float
           g[c * Q + k2] = valid ? __ldg(mult + row * pitch0) : float2{0.f, 0.f};
         }
     }
+    if (slot) {
 #pragma unroll
-    for (int q = 0; q < H; ++q) v[q] = valid ? __ldcg(gin + (t + Q * q) * ip) : float2{0.f, 0.f};
+      for (int q = 0; q < H; ++q) v[q] = slot[K::si(t + Q * q, w)];
+    } else {
+#pragma unroll
+      for (int q = 0; q < H; ++q) v[q] = valid ? __ldcg(gin + (t + Q * q) * ip) : float2{0.f, 0.f};
+    }
     dft_fwd_halfzero<P>(v);
     apply_twiddles<P, false>(v, twt);
 #pragma unroll
@@ -810,11 +840,18 @@ __device__ __forceinline__ void batch_tile(const PassArgs<float>& a, const float
       }
     }
   } else {
+    if (slot) {
 #pragma unroll
-    for (int c = 0; c < CC; ++c)
+      for (int c = 0; c < CC; ++c)
 #pragma unroll
-      for (int k2 = 0; k2 < Q; ++k2)
-        v[c * Q + k2] = valid ? __ldcg(gin + (t + Q * c + P * k2) * ip) : float2{0.f, 0.f};
+        for (int k2 = 0; k2 < Q; ++k2) v[c * Q + k2] = slot[K::si(t + Q * c + P * k2, w)];
+    } else {
+#pragma unroll
+      for (int c = 0; c < CC; ++c)
+#pragma unroll
+        for (int k2 = 0; k2 < Q; ++k2)
+          v[c * Q + k2] = valid ? __ldcg(gin + (t + Q * c + P * k2) * ip) : float2{0.f, 0.f};
+    }
 #pragma unroll
     for (int c = 0; c < CC; ++c) Dft<Q, true>::run(v + c * Q);
 #pragma unroll

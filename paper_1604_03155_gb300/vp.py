@@ -76,6 +76,8 @@ _SIGNATURES = {
     "vp_batch_set_stream": (c_int, [c_void_p, c_void_p]),
     "vp_batch_set_strategy": (c_int, [c_void_p, c_int]),
     "vp_batch_get_strategy": (c_int, [c_void_p, ctypes.POINTER(c_int)]),
+    "vp_batch_set_chunk": (c_int, [c_void_p, c_int]),
+    "vp_batch_get_chunk": (c_int, [c_void_p, ctypes.POINTER(c_int)]),
     "vp_batch_set_timeout": (c_int, [c_void_p, c_double]),
     "vp_batch_withhold": (c_int, [c_void_p, c_int, c_int]),
     "vp_batch_apply": (c_int, [c_void_p, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p)]),
@@ -413,6 +415,15 @@ class Batch:
     def strategy(self) -> int:
         s = c_int()
         _bcheck(lib().vp_batch_get_strategy(self.handle, ctypes.byref(s)), self.handle)
+        return s.value
+
+    def set_chunk(self, chunk: int):
+        """Tiles per work item of the persistent kernel (0: the autotuner's choice)."""
+        _bcheck(lib().vp_batch_set_chunk(self.handle, chunk), self.handle)
+
+    def chunk(self) -> int:
+        s = c_int()
+        _bcheck(lib().vp_batch_get_chunk(self.handle, ctypes.byref(s)), self.handle)
         return s.value
 
     def set_timeout(self, seconds: float):

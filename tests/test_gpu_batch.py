@@ -97,14 +97,33 @@ def test_autotuner_chooses_and_caches(tmp_path, monkeypatch):
     assert b.strategy() == 0
     b.apply(fs)
     b.status()
-    s = b.strategy()
-    assert s in (1, 2, 3, 4)
+    s, c = b.strategy(), b.chunk()
+    assert s in (1, 2, 3, 4) and c in (4, 8, 16, 32)
     text = cache.read_text()
-    assert text.strip().endswith(f" {s}") and "3d8x8x8" in text  # the key names every axis's size
+    assert "3d8x8x8" in text  # the key names every axis's size
+    assert int(text.strip().split()[-1]) == s + 100 * c  # cached as strategy + 100 x chunk
     b.close()
     b2 = Batch(plans)  # a new batch of the same sizes reads the cached choice
-    assert b2.strategy() == s
+    assert b2.strategy() == s and b2.chunk() == c
     b2.close()
+
+
+@pytest.mark.parametrize("chunk", [1, 4, 32])
+def test_persistent_chunk_sizes_against_oracle(chunk):
+    """The persistent launch with work items of 1, 4 and 32 tiles gives the
+    oracle's potentials (the chunk only changes how tiles are scheduled)."""
+    plans, fs, hs = _make(MIXED)
+    b = Batch(plans)
+    b.set_strategy(vp.VP_BATCH_PERSISTENT)
+    b.set_chunk(chunk)
+    assert b.chunk() == chunk
+    outs = b.apply(fs)
+    b.status()
+    for (d, N, kern, k), h, o in zip(MIXED, hs, outs):
+        L = 1.8 if d == 3 else 1.5
+        ref, _ = potential(d, N, kern, k, L, h)
+        assert check(f"batch chunk {chunk} {d}d {kern} k={k} N={N}", A.rel_l2(o.cpu().numpy(), ref), 1e-5, 1.0)
+    b.close()
 
 
 def test_invalid_batches_rejected():

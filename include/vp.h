@@ -432,7 +432,10 @@ const char* vp_ls_last_error(void);
  * nearest x2 up, concat with s2, D2a 2C->C, D2b; up, concat with s1, D1a 2C->C,
  * D1b C->2.  Every conv is 3x3x3, zero padding 1, with bias and leaky ReLU
  * (slope 0.1) except D1b.  Weights are bfloat16-rounded copies of FP32 master
- * weights; arithmetic is FP32.  Parameter layout for set/get: for each layer in
+ * weights.  The convolutions run on the tensor cores: the BF16 weights times
+ * the two BF16 parts (hi, lo) of each FP32 activation, accumulated in FP32, so
+ * they agree with FP32 arithmetic to about 2^-16 relative; pooling, upsampling,
+ * activations and the weight gradients are FP32.  Parameter layout for set/get: for each layer in
  * that order, w[C_out][C_in][27] (k = (kz*3 + ky)*3 + kx) then b[C_out].
  * Input channels: (Re r, Im r, q) with r scaled to unit RMS (sqrt(n) r/||r||);
  * output: the deviation of the correction from r, in the same scale.
@@ -441,6 +444,11 @@ const char* vp_ls_last_error(void);
  * vp_unet_precond is a vp_precond_fn (ctx = the network, bound to a contrast
  * with vp_unet_bind): z = r + (||r||/sqrt(n)) net(sqrt(n) r/||r||, q), so a
  * network with a zero last layer is the identity (plain GMRES).
+ * Calls are asynchronous on the network's stream.  A convolution whose wait
+ * for its MMAs runs past a bounded clock budget sets a device error word
+ * instead of hanging: vp_unet_status synchronises the stream and returns
+ * VP_ERR_TIMEOUT if it is set (vp_unet_precond checks it on every call, and
+ * vp_unet_loss_grad when it returns the loss).
  * ------------------------------------------------------------------------- */
 typedef struct vp_unet_s* vp_unet;
 vp_status vp_unet_create(vp_unet* out, int S, int C);
@@ -456,6 +464,7 @@ vp_status vp_unet_adam_step(vp_unet net, double lr);
 vp_status vp_unet_set_slope(vp_unet net, double slope);
 vp_status vp_unet_bind(vp_unet net, const float* q);
 vp_status vp_unet_precond(void* ctx, const void* r, void* z, void* stream);
+vp_status vp_unet_status(vp_unet net);
 const char* vp_unet_last_error(vp_unet net);
 vp_status vp_unet_destroy(vp_unet net);
 

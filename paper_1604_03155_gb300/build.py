@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 LIBPATH = os.path.join(LIBDIR, "libvp.so")
-SOURCES = ["vp_capi.cu", "precompute.cu", "apply_f32.cu", "fourstep.cu", "apply_f64.cu", "vp_noalloc.cu", "batch.cu", "ls.cu", "krylov.cu", "unet.cu", "tc_fused.cu", "entries.cu"]
+SOURCES = ["vp_capi.cu", "precompute.cu", "apply_f32.cu", "fourstep.cu", "apply_f64.cu", "vp_noalloc.cu", "batch.cu", "ls.cu", "krylov.cu", "unet.cu", "unet_tc.cu", "tc_fused.cu", "entries.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

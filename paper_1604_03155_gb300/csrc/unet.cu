@@ -11,12 +11,12 @@
 // forward and backward pass (BF16 weights, FP32 arithmetic).
 //
 // Kernels (all the network's own):
-//  * k_conv3d: 8x8x8 output voxels per CTA, one per thread; the input halo
-//    (10^3 x 4 channels) and the chunk's weights ([ci][k][co], read as float4
-//    broadcasts) are staged in shared memory.  Two input pointers model the
-//    skip concatenation without a copy.
-//  * input gradient: the same kernel with the layer's weights flipped in k and
-//    transposed in (co, ci).
+//  * convolutions: implicit GEMMs on the tensor cores (unet_tc.cu), BF16
+//    weights times the two BF16 parts of the FP32 activations, FP32
+//    accumulation.  Two input pointers model the skip concatenation without a
+//    copy.
+//  * input gradient: the same convolution with the layer's weights flipped in
+//    k and transposed in (co, ci).
 //  * k_wgrad: persistent CTAs accumulate dW[ci][k][co] over their spatial tiles
 //    (halo and dz tile in shared memory, one (ci, k) pair per thread, CO
 //    accumulators), write one partial per CTA; k_wreduce sums the partials in
@@ -35,76 +35,9 @@
 namespace {
 
 constexpr int kLayers = 10;
-constexpr int kTile = 8, kHalo = 10, kHalo3 = 1000, kConvCh = 4, kWgCh = 16;
+constexpr int kTile = 8, kHalo = 10, kHalo3 = 1000, kWgCh = 16;
 
 __device__ __forceinline__ float lrelu(float v, float slope) { return v > 0.f ? v : slope * v; }
-
-template <int CO>
-__global__ void __launch_bounds__(512) k_conv3d(const float* __restrict__ x1, int c1, const float* __restrict__ x2,
-                                                int c2, const float* __restrict__ w, const float* __restrict__ bias,
-                                                float* __restrict__ y, int S, int act, float slope) {
-  __shared__ float halo[kConvCh][kHalo3];
-  __shared__ __align__(16) float ws[kConvCh * 27][CO < 4 ? 4 : CO];
-  const int Ci = c1 + c2;
-  const long long S3 = (long long)S * S * S;
-  const int tpd = (S + kTile - 1) / kTile;
-  int bt = blockIdx.x;
-  const int tx0 = (bt % tpd) * kTile;
-  bt /= tpd;
-  const int ty0 = (bt % tpd) * kTile;
-  const int tz0 = (bt / tpd) * kTile;
-  const int lx = threadIdx.x & 7, ly = (threadIdx.x >> 3) & 7, lz = threadIdx.x >> 6;
-  float acc[CO];
-#pragma unroll
-  for (int co = 0; co < CO; ++co) acc[co] = bias ? bias[co] : 0.f;
-  for (int c0 = 0; c0 < Ci; c0 += kConvCh) {
-    __syncthreads();
-    for (int e = threadIdx.x; e < kConvCh * kHalo3; e += blockDim.x) {
-      const int ci = e / kHalo3, r = e % kHalo3;
-      const int gz = tz0 + r / 100 - 1, gy = ty0 + (r / 10) % 10 - 1, gx = tx0 + r % 10 - 1;
-      const int cc = c0 + ci;
-      float v = 0.f;
-      if (cc < Ci && gz >= 0 && gz < S && gy >= 0 && gy < S && gx >= 0 && gx < S) {
-        const float* src = cc < c1 ? x1 + (long long)cc * S3 : x2 + (long long)(cc - c1) * S3;
-        v = src[((long long)gz * S + gy) * S + gx];
-      }
-      halo[ci][r] = v;
-    }
-    for (int e = threadIdx.x; e < kConvCh * 27 * CO; e += blockDim.x) {
-      const int co = e % CO, ck = e / CO;
-      const int cc = c0 + ck / 27;
-      ws[ck][co] = (cc < Ci) ? w[((long long)co * Ci + cc) * 27 + ck % 27] : 0.f;
-    }
-    __syncthreads();
-#pragma unroll 1
-    for (int ci = 0; ci < kConvCh; ++ci) {
-#pragma unroll
-      for (int k = 0; k < 27; ++k) {
-        const int kz = k / 9, ky = (k / 3) % 3, kx = k % 3;
-        const float xv = halo[ci][((lz + kz) * kHalo + (ly + ky)) * kHalo + lx + kx];
-        if constexpr (CO % 4 == 0) {
-#pragma unroll
-          for (int co = 0; co < CO; co += 4) {
-            const float4 w4 = *reinterpret_cast<const float4*>(&ws[ci * 27 + k][co]);
-            acc[co] = fmaf(w4.x, xv, acc[co]);
-            acc[co + 1] = fmaf(w4.y, xv, acc[co + 1]);
-            acc[co + 2] = fmaf(w4.z, xv, acc[co + 2]);
-            acc[co + 3] = fmaf(w4.w, xv, acc[co + 3]);
-          }
-        } else {
-#pragma unroll
-          for (int co = 0; co < CO; ++co) acc[co] = fmaf(ws[ci * 27 + k][co], xv, acc[co]);
-        }
-      }
-    }
-  }
-  const int gz = tz0 + lz, gy = ty0 + ly, gx = tx0 + lx;
-  if (gz < S && gy < S && gx < S) {
-    const long long idx = ((long long)gz * S + gy) * S + gx;
-#pragma unroll
-    for (int co = 0; co < CO; ++co) y[(long long)co * S3 + idx] = act ? lrelu(acc[co], slope) : acc[co];
-  }
-}
 
 // Weight gradient partials: part[blk][(ci*27 + k)*CO + co] and part[blk][Ci*27*CO + co] (bias)
 template <int CO>
@@ -242,11 +175,20 @@ __global__ void k_pool(const float* __restrict__ x, float* __restrict__ y, int C
 __global__ void k_up(const float* __restrict__ x, float* __restrict__ y, int C, int S, int scale_back) {
   const int h = S / 2;
   if (!scale_back) {
-    const long long n = (long long)C * S * S * S;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-      const long long c = i / ((long long)S * S * S), r = i % ((long long)S * S * S);
-      const int z = (int)(r / (S * S)), yy = (int)((r / S) % S), xx = (int)(r % S);
-      y[i] = x[c * (long long)h * h * h + ((long long)(z / 2) * h + yy / 2) * h + xx / 2];
+    // S a multiple of 4: one float4 of an output row (x positions 4j .. 4j + 3)
+    // from the float2 at 2j of the coarse row (both aligned); else one value.
+    // Indices fit 32 bits (C S^3 < 2^31).
+    const int q = S % 4 == 0 ? S / 4 : S, n = C * S * S * q;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+      const int r = i / q, j = i - r * q;  // r = (c S + z) S + yy
+      const int yy = r % S, cz = r / S, z = cz % S, c = cz / S;
+      const float* src = x + (((long long)c * h + z / 2) * h + yy / 2) * h;
+      if (S % 4 == 0) {
+        const float2 v = *reinterpret_cast<const float2*>(src + 2 * j);
+        reinterpret_cast<float4*>(y)[i] = make_float4(v.x, v.x, v.y, v.y);
+      } else {
+        y[i] = src[j / 2];
+      }
     }
   } else {
     // x fine (S^3) -> y coarse: y = sum of the 8 children (mean when scale_back == 2)
@@ -387,6 +329,7 @@ struct vp_unet_s {
   float* part = nullptr;
   int part_blocks = 0;
   double* red = nullptr;
+  int* err = nullptr;        // device error word: a convolution's bounded wait timed out
   const float* q = nullptr;  // bound contrast for the preconditioner
   std::vector<void*> allocs;
   std::string last_error;
@@ -407,15 +350,20 @@ template <typename T> cudaError_t ualloc(vp_unet u, T** p, long long count) {
 
 cudaError_t conv(vp_unet u, const float* x1, int c1, const float* x2, int c2, const float* w, const float* b, float* y,
                  int CO, int S, int act, cudaStream_t s) {
-  const int tpd = (S + kTile - 1) / kTile;
-  const dim3 grid(tpd * tpd * tpd);
-  switch (CO) {
-    case 2: k_conv3d<2><<<grid, 512, 0, s>>>(x1, c1, x2, c2, w, b, y, S, act, u->slope); break;
-    case 16: k_conv3d<16><<<grid, 512, 0, s>>>(x1, c1, x2, c2, w, b, y, S, act, u->slope); break;
-    case 32: k_conv3d<32><<<grid, 512, 0, s>>>(x1, c1, x2, c2, w, b, y, S, act, u->slope); break;
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
+  vp::unet_tc::ConvArgs a;
+  a.x1 = x1;
+  a.c1 = c1;
+  a.x2 = x2;
+  a.c2 = c2;
+  a.w = w;
+  a.bias = b;
+  a.y = y;
+  a.co = CO;
+  a.S = S;
+  a.act = act;
+  a.slope = u->slope;
+  a.err = u->err;
+  return vp::unet_tc::conv3d(a, s);
 }
 
 cudaError_t wgrad(vp_unet u, int layer, const float* x1, int c1, const float* x2, int c2, const float* dz, int S,
@@ -576,6 +524,8 @@ vp_status vp_unet_create(vp_unet* out, int S, int C) {
   u->part_blocks = 2 * 152;
   A(&u->part, (long long)u->part_blocks * (2 * C * 27 * C + C));
   if (e == cudaSuccess) e = ualloc(u, &u->red, 2048);
+  if (e == cudaSuccess) e = ualloc(u, &u->err, 1);
+  if (e == cudaSuccess) e = cudaMemset(u->err, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(u->m, 0, off * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(u->v, 0, off * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(u->w, 0, off * sizeof(float));
@@ -652,6 +602,9 @@ vp_status vp_unet_loss_grad(vp_unet u, const float* in, const float* target, dou
     if (cudaMemcpyAsync(h.data(), u->red, nb * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
       return VP_ERR_CUDA;
+    int herr = 0;
+    if (cudaMemcpy(&herr, u->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return VP_ERR_CUDA;
+    if (herr) return ufail(u, VP_ERR_TIMEOUT, "a tensor-core convolution timed out waiting for its MMAs");
     double acc = 0.0;
     for (double v : h) acc += v;
     *loss = acc / (double)n;
@@ -692,9 +645,12 @@ vp_status vp_unet_precond(void* ctx, const void* r, void* z, void* stream) {
   const float2* rr = reinterpret_cast<const float2*>(r);
   k_norm2c<<<256, 256, 0, s>>>(rr, n, u->red);
   std::vector<double> h(256);
+  int herr = 0;
   if (cudaMemcpyAsync(h.data(), u->red, 256 * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(&herr, u->err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return VP_ERR_CUDA;
+  if (herr) return ufail(u, VP_ERR_TIMEOUT, "a tensor-core convolution timed out waiting for its MMAs");
   double nr = 0.0;
   for (double v : h) nr += v;
   nr = sqrt(nr);
@@ -708,6 +664,17 @@ vp_status vp_unet_precond(void* ctx, const void* r, void* z, void* stream) {
   if (e != cudaSuccess) return VP_ERR_CUDA;
   k_unpack_output<<<g1(n), 256, 0, s>>>(reinterpret_cast<float2*>(z), rr, u->out, 1.0 / rms, n);
   return cudaGetLastError() == cudaSuccess ? VP_OK : VP_ERR_CUDA;
+}
+
+vp_status vp_unet_status(vp_unet u) {
+  if (!u) return VP_ERR_INVALID_ARG;
+  vp::DeviceGuard dg_(u->device);
+  int herr = 0;
+  if (cudaMemcpyAsync(&herr, u->err, sizeof(int), cudaMemcpyDeviceToHost, u->stream) != cudaSuccess ||
+      cudaStreamSynchronize(u->stream) != cudaSuccess)
+    return ufail(u, VP_ERR_CUDA, "stream synchronisation failed");
+  if (herr) return ufail(u, VP_ERR_TIMEOUT, "a tensor-core convolution timed out waiting for its MMAs");
+  return VP_OK;
 }
 
 const char* vp_unet_last_error(vp_unet u) { return u ? u->last_error.c_str() : ""; }

@@ -127,4 +127,24 @@ vp_status plan_prepare_grad(vp_plan p);
 size_t plan_grad_workspace_bytes(vp_plan p);
 vp_status apply_grad_with_workspace(vp_plan p, const void* f, void* grad, vp_dtype dtype, void* ws, size_t ws_bytes);
 
+// 3x3x3 convolution of the U-Net on the tensor cores (unet_tc.cu): channel-major
+// FP32 activations [C][S][S][S], the input the concatenation of x1 (c1
+// channels) and x2 (c2, may be 0), weights w[co][ci][27] holding BF16 values,
+// optional bias, leaky ReLU (slope) when act; a timed-out wait sets *err.
+namespace unet_tc {
+struct ConvArgs {
+  const float* x1;
+  int c1;
+  const float* x2;
+  int c2;
+  const float* w;
+  const float* bias;
+  float* y;
+  int co, S, act;
+  float slope;
+  int* err;
+};
+cudaError_t conv3d(const ConvArgs& a, cudaStream_t s);
+}  // namespace unet_tc
+
 }  // namespace vp

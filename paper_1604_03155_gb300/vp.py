@@ -116,6 +116,7 @@ _SIGNATURES = {
     "vp_unet_bind": (c_int, [c_void_p, c_void_p]),
     "vp_unet_set_slope": (c_int, [c_void_p, c_double]),
     "vp_unet_precond": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "vp_unet_status": (c_int, [c_void_p]),
     "vp_unet_last_error": (c_char_p, [c_void_p]),
     "vp_unet_destroy": (c_int, [c_void_p]),
 }
@@ -688,6 +689,10 @@ class UNet:
 
     def adam_step(self, lr: float):
         self._check(lib().vp_unet_adam_step(self.handle, lr))
+
+    def status(self):
+        """Synchronises the network's stream; raises on a timed-out convolution."""
+        self._check(lib().vp_unet_status(self.handle))
 
     def bind(self, q):
         self._q = q

@@ -853,6 +853,8 @@ def run_batch(args):
 #               (or sub-box) target and source nodes, and batches of kernel
 #               entries at random offsets; entries per second and output
 #               bandwidth, one JSON line
+#   unet     -- the learned preconditioner network (tensor-core convolutions):
+#               forward and loss + gradients at S^3, ms per call, one JSON line
 # ---------------------------------------------------------------------------
 def exp_grids(argv):
     import torch
@@ -961,7 +963,44 @@ def exp_nystrom(argv):
     plan.close()
 
 
-EXPERIMENTS = {"grids": exp_grids, "nystrom": exp_nystrom}
+def exp_unet(argv):
+    """The learned preconditioner network at S^3: forward and loss + gradients
+    (forward, backward, weight gradients) through the C-ABI, with the seeded
+    initial weights rounded to BF16 and a seeded input."""
+    import torch
+
+    from paper_1604_03155_gb300 import inputs as I
+    from paper_1604_03155_gb300.vp import UNet
+    ap = argparse.ArgumentParser(prog="bench.py experiment unet")
+    ap.add_argument("--S", type=int, default=128)
+    ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    a = ap.parse_args(argv)
+    dev = torch.device("cuda", 0)
+    layers = [(I.bf16_round(w), I.bf16_round(b)) for w, b in I.unet_init_weights(3, 16)]
+    net = UNet(a.S, 16, weights=layers)
+    n = a.S ** 3
+    x = torch.from_numpy(I.normal(77, 3 * n).astype(np.float32).reshape(3, a.S, a.S, a.S)).to(dev)
+    tgt = torch.from_numpy(I.normal(78, 2 * n).astype(np.float32).reshape(2, a.S, a.S, a.S)).to(dev)
+    out = net.forward(x)
+    out_ms = {}
+    for name, fn in [("forward", lambda: net.forward(x, out)), ("loss_grad", lambda: net.loss_grad(x, tgt))]:
+        for _ in range(a.warmup):
+            fn()
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        for _ in range(a.reps):
+            fn()
+        e.record()
+        torch.cuda.synchronize()
+        out_ms[name + "_ms"] = s.elapsed_time(e) / max(a.reps, 1)
+    net.status()
+    print(json.dumps({"S": a.S, "channels": 16, **out_ms, "output_finite": bool(torch.isfinite(out).all())}), flush=True)
+    net.close()
+
+
+EXPERIMENTS = {"grids": exp_grids, "nystrom": exp_nystrom, "unet": exp_unet}
 
 
 def main():

@@ -502,6 +502,11 @@ def run_ours(args, wl):
         plan.get_array("ghatj", 0)  # builds the derivative multipliers (precompute)
     precompute_s = time.perf_counter() - t0
     plan.set_stream(stream)
+    # tile shapes of the FP32 passes from the autotuner (cached per device, driver and grid)
+    autotune = {}
+    if prec == "fp32":
+        t0 = time.perf_counter()
+        autotune = {"shapes": plan.autotune(), "seconds": time.perf_counter() - t0}
 
     f_host = density_for(args.workload, wl, rank).astype(npdt)
     f = torch.from_numpy(f_host).to(dev)
@@ -723,6 +728,7 @@ def run_ours(args, wl):
                     "staged_value": (N ** d) / e2e_staged_s},
             "gpu_launches": launches_per_step * args.steps,
             "precompute_s": precompute_s,
+            "autotune": autotune,
             "fp64_form": fp64,
             "cufft_form": cufft,
         }

@@ -158,6 +158,33 @@ vp_status vp_matrix_block(vp_plan plan, int which, int axis, const long long* ro
  * either way. */
 vp_status vp_plan_set_host_access(vp_plan plan, int direct);
 
+/* Tile shapes of the FP32 passes (the four-step engine, 2N in {64, 128, 256,
+ * 512, 1024}).  Each pass has up to 4 candidate shapes (pencils per CTA,
+ * staging depth, exchange in the staging slot or in its own buffer; for the
+ * fused pass of 2N = 512, candidate 0 is the TMA kernel); candidate 0 is the
+ * measured default.  pass: 0 fwd_rows, 1 fwd_axis1, 2 fused_axis0, 3 inv_axis1,
+ * 4 inv_rows (2D plans have no axis-1 passes).
+ *   vp_plan_autotune times every candidate of every four-step pass on the
+ *     plan's workspace and stream (CUDA events, 10 applies each after 2
+ *     warm-ups), keeps the fastest per pass, and caches the choice on disk per
+ *     device, driver and grid (VP_AUTOTUNE_CACHE, default
+ *     $HOME/.cache/vp_autotune.txt); a cached choice is reused unless
+ *     flags & 1.  Candidates are timed inside whole applies, pass by pass; one
+ *     replaces the current choice when the apply gets more than 1% faster.
+ *     The plan's precision must be VP_FP32 (else VP_ERR_UNSUPPORTED).
+ *     Synchronises the plan's stream; allocates two grid-sized scratch
+ *     buffers for the duration of the call.
+ *   vp_plan_pass_config reports a pass's candidate count (0: the pass runs on
+ *     the Stockham engine; the name is then "stockham", or "absent"), its
+ *     current choice and that candidate's name ("W8 S4 alias": 8 pencils per
+ *     CTA, 4 staging slots, aliased exchange), NUL-terminated within cap bytes.
+ *   vp_plan_set_pass_config sets the choice (VP_ERR_INVALID_ARG for an index
+ *     out of range, VP_ERR_UNSUPPORTED for a shape above a CTA's shared memory).
+ * Every candidate computes the same result up to FP32 rounding order. */
+vp_status vp_plan_autotune(vp_plan plan, int flags);
+vp_status vp_plan_pass_config(vp_plan plan, int pass, int* cfg, int* count, char* name, size_t cap);
+vp_status vp_plan_set_pass_config(vp_plan plan, int pass, int cfg);
+
 /* Stream for subsequent calls (cudaStream_t as void*; NULL = legacy default).
  * One plan serves one stream at a time. */
 vp_status vp_plan_set_stream(vp_plan plan, void* stream);

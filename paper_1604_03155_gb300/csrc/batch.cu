@@ -18,6 +18,7 @@
 // An autotuner times the persistent kernel at two grid sizes against
 // per-density launches and caches the fastest choice per device and batch.
 #include <cuda_runtime.h>
+#include <sys/stat.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -356,6 +357,44 @@ long long batch_tiles(int n, int kind, const PassArgs<float>& a, int* nblk) {
   return (long long)a.O * (*nblk);
 }
 
+// On-disk autotuner cache: lines "key value"; the last line of a key wins.
+// VP_AUTOTUNE_CACHE overrides the path ($HOME/.cache/vp_autotune.txt).
+std::string autotune_cache_path() {
+  const char* p = getenv("VP_AUTOTUNE_CACHE");
+  if (p && *p) return p;
+  const char* home = getenv("HOME");
+  return std::string(home ? home : "/tmp") + "/.cache/vp_autotune.txt";
+}
+
+int autotune_cache_lookup(const std::string& key) {
+  FILE* fh = fopen(autotune_cache_path().c_str(), "r");
+  if (!fh) return 0;
+  char line[4096];
+  int found = 0;
+  while (fgets(line, sizeof(line), fh)) {
+    char* sp = strrchr(line, ' ');
+    if (!sp) continue;
+    *sp = 0;
+    if (key == line) found = atoi(sp + 1);
+  }
+  fclose(fh);
+  return found;
+}
+
+void autotune_cache_store(const std::string& key, int s) {
+  const std::string path = autotune_cache_path();
+  // best effort: create the missing directories of the path, then append
+  FILE* fh = fopen(path.c_str(), "a");
+  if (!fh) {
+    for (size_t i = path.find('/', 1); i != std::string::npos; i = path.find('/', i + 1))
+      mkdir(path.substr(0, i).c_str(), 0755);
+    fh = fopen(path.c_str(), "a");
+  }
+  if (!fh) return;
+  fprintf(fh, "%s %d\n", key.c_str(), s);
+  fclose(fh);
+}
+
 }  // namespace vp
 
 using namespace vp;
@@ -579,43 +618,6 @@ vp_status run_strategy(vp_batch b, int s, const void* const* f, void* const* phi
   return graph_launch(b, L, s == S_PERSISTENT ? b->grid_full : b->grid_one);
 }
 
-std::string cache_path() {
-  const char* p = getenv("VP_AUTOTUNE_CACHE");
-  if (p && *p) return p;
-  const char* home = getenv("HOME");
-  return std::string(home ? home : "/tmp") + "/.cache/vp_autotune.txt";
-}
-
-int cache_lookup(const std::string& key) {
-  FILE* fh = fopen(cache_path().c_str(), "r");
-  if (!fh) return 0;
-  char line[4096];
-  int found = 0;
-  while (fgets(line, sizeof(line), fh)) {
-    char* sp = strrchr(line, ' ');
-    if (!sp) continue;
-    *sp = 0;
-    if (key == line) found = atoi(sp + 1);
-  }
-  fclose(fh);
-  return found;
-}
-
-void cache_store(const std::string& key, int s) {
-  std::string path = cache_path();
-  std::string dir = path.substr(0, path.find_last_of('/'));
-  std::string cmd_dir = dir;
-  // best effort: create the directory, then append
-  FILE* fh = fopen(path.c_str(), "a");
-  if (!fh) {
-    std::string mk = "mkdir -p '" + cmd_dir + "'";
-    if (system(mk.c_str()) == 0) fh = fopen(path.c_str(), "a");
-  }
-  if (!fh) return;
-  fprintf(fh, "%s %d\n", key.c_str(), s);
-  fclose(fh);
-}
-
 // Times each candidate on the batch (2 warm-ups, 3 timed runs on the batch's
 // stream with CUDA events) and keeps the fastest: the persistent kernel with
 // every chunk size of BATCH_CHUNKS (all resident CTAs) and with 8-tile chunks
@@ -656,7 +658,7 @@ vp_status autotune(vp_batch b, const void* const* f, void* const* phi) {
   cudaEventDestroy(e1);
   b->strategy = bestc.s;
   b->chunk = bestc.chunk;
-  cache_store(b->signature, bestc.s + 100 * bestc.chunk);
+  vp::autotune_cache_store(b->signature, bestc.s + 100 * bestc.chunk);
   return VP_OK;
 }
 
@@ -802,7 +804,7 @@ vp_status vp_batch_create(vp_batch* out, int count, const vp_plan* plans) {
   for (auto& c : sig)
     if (c == ' ') c = '_';
   b->signature = sig;
-  const int cached = cache_lookup(sig);
+  const int cached = vp::autotune_cache_lookup(sig);
   b->strategy = cached % 100;
   if (cached >= 100) b->chunk = cached / 100;
   *out = b;

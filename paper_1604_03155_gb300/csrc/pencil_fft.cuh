@@ -303,6 +303,7 @@ template <typename Real> struct PassArgs {
   int in_real, out_real;
   int async_ok;  // input rows 16-byte aligned: stage them with cp.async
   int* err;      // device error word (bounded waits), or null
+  int cfg;       // four-step passes: candidate tile shape (0: the measured default)
   // contiguous passes over several fields in one launch: rows [f*rows_per_field,
   // (f+1)*rows_per_field) are written to outs[f] (nout > 1), else to out
   int nout;
@@ -674,7 +675,7 @@ __global__ void __launch_bounds__(Cfg::threads, Cfg::min_blocks) pencil_pass(con
   constexpr int W = Cfg::W;
   constexpr int NSTG = Cfg::NSTG;
 
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
   unsigned char* stg = smem_raw + Cfg::xchg_bytes;
 

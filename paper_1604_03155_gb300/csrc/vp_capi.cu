@@ -73,6 +73,7 @@ struct vp_plan_s {
 
   bool timing = false;
   int host_direct = 1;  // pinned host buffers: access them in place (0: stage through device memory); set at creation
+  int pass_cfg[5] = {0, 0, 0, 0, 0};  // tile shape of each FP32 four-step pass (vp_plan_autotune)
   std::vector<TimedLaunch> timed;
   std::vector<cudaEvent_t> event_pool;
 
@@ -424,6 +425,7 @@ int build_pass_list(vp_plan p, void* ws, const void* f, void* const* outs, const
   }
   auto push = [&](int pass, PassKind kind, bool contig, int nin, int axis) {
     a.tw = tw_of(axis);
+    a.cfg = p->pass_cfg[pass];
     set_async(a, contig, nin);
     list[np].pass = pass;
     list[np].kind = kind;
@@ -899,6 +901,141 @@ vp_status vp_plan_dims(vp_plan p, int* N) {
 vp_status vp_plan_set_host_access(vp_plan p, int direct) {
   if (!p) return fail(nullptr, VP_ERR_INVALID_ARG, "plan is NULL");
   p->host_direct = direct ? 1 : 0;
+  return VP_OK;
+}
+
+// Pass `pass` of the plan's FP32 apply: its candidate tile shapes (count 0 when
+// the pass does not run on the four-step engine), the current choice and its name.
+vp_status vp_plan_pass_config(vp_plan p, int pass, int* cfg, int* count, char* name, size_t cap) {
+  if (!p) return fail(nullptr, VP_ERR_INVALID_ARG, "plan is NULL");
+  if (pass < 0 || pass >= NPASS) return fail(p, VP_ERR_INVALID_ARG, "pass index out of range");
+  int nc = 0;
+  char names[4][32];
+  bool fits[4];
+  const PassLaunch<float>* L = nullptr;
+  PassLaunch<float> list[6];
+  FieldDesc field{(const void*)p->G32, -1, -1};
+  void* base = reinterpret_cast<void*>((uintptr_t)1 << 20);  // kinds and lengths only: nothing is read
+  void* outs[1] = {base};
+  const int np = build_pass_list<float>(p, base, base, outs, &field, 1, false, list);
+  for (int i = 0; i < np; ++i)
+    if (list[i].pass == pass) L = &list[i];
+  if (L) nc = fourstep_shapes(L->kind, L->len, names, fits);
+  if (cfg) *cfg = p->pass_cfg[pass];
+  if (count) *count = nc;
+  if (name && cap) snprintf(name, cap, "%s", !L ? "absent" : nc ? names[p->pass_cfg[pass]] : "stockham");
+  return VP_OK;
+}
+
+vp_status vp_plan_set_pass_config(vp_plan p, int pass, int cfg) {
+  if (!p) return fail(nullptr, VP_ERR_INVALID_ARG, "plan is NULL");
+  int nc = 0;
+  vp_status st = vp_plan_pass_config(p, pass, nullptr, &nc, nullptr, 0);
+  if (st != VP_OK) return st;
+  if (cfg < 0 || cfg >= (nc > 0 ? nc : 1)) return fail(p, VP_ERR_INVALID_ARG, "no such tile shape for this pass");
+  if (nc > 0) {
+    PassLaunch<float> list[6];
+    FieldDesc field{(const void*)p->G32, -1, -1};
+    void* base = reinterpret_cast<void*>((uintptr_t)1 << 20);
+    void* outs[1] = {base};
+    const int np = build_pass_list<float>(p, base, base, outs, &field, 1, false, list);
+    char names[4][32];
+    bool fits[4];
+    for (int i = 0; i < np; ++i)
+      if (list[i].pass == pass && fourstep_shapes(list[i].kind, list[i].len, names, fits) && !fits[cfg])
+        return fail(p, VP_ERR_UNSUPPORTED, "this tile shape exceeds a CTA's shared memory");
+  }
+  p->pass_cfg[pass] = cfg;
+  return VP_OK;
+}
+
+// Tries every candidate tile shape of each four-step pass of the FP32 apply,
+// pass by pass, timing whole applies on the plan's own workspace and stream
+// (2 warm-ups, 10 timed applies, CUDA events), so that each pass is measured
+// with the cache state the passes before it leave; a candidate replaces the
+// current choice when the apply gets more than 1% faster.  The choices are
+// cached on disk per device, driver and grid; flags & 1 ignores the cache.
+vp_status vp_plan_autotune(vp_plan p, int flags) {
+  if (!p) return fail(nullptr, VP_ERR_INVALID_ARG, "plan is NULL");
+  if (p->prec != VP_FP32) return fail(p, VP_ERR_UNSUPPORTED, "the autotuner tunes the FP32 passes: set VP_FP32 first");
+  VP_ON_DEVICE(p, p->device);
+  cudaDeviceProp prop;
+  VP_CUDA(p, cudaGetDeviceProperties(&prop, p->device));
+  int drv = 0;
+  VP_CUDA(p, cudaDriverGetVersion(&drv));
+  std::string key = std::string(prop.name) + "|drv" + std::to_string(drv) + "|passes|" + std::to_string(p->d) + "d";
+  for (int a = 0; a < p->d; ++a) key += (a ? "x" : "") + std::to_string(p->Nv[a]);
+  if (!(flags & 1)) {
+    const int c = autotune_cache_lookup(key);
+    if (c > 0) {
+      for (int i = 0; i < NPASS; ++i) p->pass_cfg[i] = ((c - 1) >> (3 * i)) & 7;
+      for (int i = 0; i < NPASS; ++i)
+        if (p->pass_cfg[i] >= 4) p->pass_cfg[i] = 0;
+      return VP_OK;
+    }
+  }
+  const size_t U = grid_points(p);
+  vp_status st = ensure_workspace(p, workspace_bytes(p, 1, sizeof(float2)));
+  if (st != VP_OK) return st;
+  float2 *fin = nullptr, *fout = nullptr;
+  VP_CUDA(p, cudaMalloc(&fin, U * sizeof(float2)));
+  cudaError_t e = cudaMalloc(&fout, U * sizeof(float2));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaMemsetAsync(fin, 0, U * sizeof(float2), p->stream);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  PassLaunch<float> list[6];
+  FieldDesc field{(const void*)p->G32, -1, -1};
+  void* outs[1] = {fout};
+  for (int i = 0; i < NPASS; ++i) p->pass_cfg[i] = 0;
+  const int np = e == cudaSuccess ? build_pass_list<float>(p, p->ws, fin, outs, &field, 1, false, list) : 0;
+  // one apply's time with the current choices: 2 warm-ups, 10 timed applies
+  auto time_apply = [&](float* ms) -> cudaError_t {
+    for (int w = 0; w < 2; ++w)
+      if (run_apply_ws<float>(p, p->ws, fin, outs, &field, 1, false) != VP_OK) return cudaErrorUnknown;
+    cudaError_t le = cudaEventRecord(e0, p->stream);
+    for (int r = 0; r < 10 && le == cudaSuccess; ++r)
+      if (run_apply_ws<float>(p, p->ws, fin, outs, &field, 1, false) != VP_OK) le = cudaErrorUnknown;
+    if (le == cudaSuccess) le = cudaEventRecord(e1, p->stream);
+    if (le == cudaSuccess) le = cudaEventSynchronize(e1);
+    if (le == cudaSuccess) le = cudaEventElapsedTime(ms, e0, e1);
+    return le;
+  };
+  float cur = 0.f;
+  if (e == cudaSuccess && np > 0) e = time_apply(&cur);
+  // coordinate descent over the passes: a candidate replaces the current
+  // choice when whole applies get more than 1% faster
+  for (int i = 0; i < np && e == cudaSuccess; ++i) {
+    const PassLaunch<float>& L = list[i];
+    char names[4][32];
+    bool fits[4];
+    const int nc = fourstep_shapes(L.kind, L.len, names, fits);
+    if (!nc || !fourstep_serves(L.kind, L.len, L.a)) continue;
+    int bc = 0;
+    for (int c = 1; c < nc && e == cudaSuccess; ++c) {
+      if (!fits[c]) continue;
+      p->pass_cfg[L.pass] = c;
+      float ms = 0.f;
+      e = time_apply(&ms);
+      if (e == cudaSuccess && ms < 0.99f * cur) {
+        cur = ms;
+        bc = c;
+      }
+    }
+    p->pass_cfg[L.pass] = bc;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(p->stream);
+  cudaFree(fin);
+  if (fout) cudaFree(fout);
+  if (e != cudaSuccess) {
+    for (int i = 0; i < NPASS; ++i) p->pass_cfg[i] = 0;
+    return cuda_fail(p, e, "vp_plan_autotune");
+  }
+  int code = 0;
+  for (int i = 0; i < NPASS; ++i) code |= p->pass_cfg[i] << (3 * i);
+  autotune_cache_store(key, code + 1);
   return VP_OK;
 }
 

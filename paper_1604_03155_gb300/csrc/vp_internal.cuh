@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "../../include/vp.h"
 #include "pencil_fft.cuh"
 
@@ -71,6 +73,14 @@ bool pass_shape_f32(PassKind kind, int n, PassShape* out);
 // fourstep.cu: launches an FP32 pass on the four-step kernels when they serve
 // its length and arguments (returns false otherwise, *err untouched).
 bool launch_fourstep(PassKind kind, int n, const PassArgs<float>& a, cudaStream_t s, cudaError_t* err);
+// The candidate tile shapes of a four-step pass (names, and whether each fits
+// a CTA's shared memory); returns their count, 0 for other lengths.
+int fourstep_shapes(PassKind kind, int n, char (*names)[32], bool* fits);
+// On-disk autotuner cache (batch.cu): value for key (0 when absent), append.
+int autotune_cache_lookup(const std::string& key);
+void autotune_cache_store(const std::string& key, int value);
+// Whether the four-step engine runs this pass (length, data type, alignment).
+bool fourstep_serves(PassKind kind, int n, const PassArgs<float>& a);
 bool pass_shape_f64(PassKind kind, int n, PassShape* out);
 
 // FFT lengths with compiled passes (2N).

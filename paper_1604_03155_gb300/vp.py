@@ -57,6 +57,9 @@ _SIGNATURES = {
                                      c_double]),
     "vp_plan_dims": (c_int, [c_void_p, ctypes.POINTER(c_int)]),
     "vp_plan_set_host_access": (c_int, [c_void_p, c_int]),
+    "vp_plan_autotune": (c_int, [c_void_p, c_int]),
+    "vp_plan_pass_config": (c_int, [c_void_p, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int), c_char_p, c_size_t]),
+    "vp_plan_set_pass_config": (c_int, [c_void_p, c_int, c_int]),
     "vp_kernel_entries": (c_int, [c_void_p, c_int, c_int, c_void_p, ctypes.c_longlong, c_void_p, c_int]),
     "vp_matrix_block": (c_int, [c_void_p, c_int, c_int, c_void_p, ctypes.c_longlong, c_void_p, ctypes.c_longlong,
                                 c_void_p, c_int]),
@@ -280,6 +283,29 @@ class Plan:
     def set_host_access(self, direct: bool):
         """Pinned host buffers: access them in place (True) or stage them (False)."""
         _check(lib().vp_plan_set_host_access(self.handle, int(direct)), self.handle)
+
+    PASS_NAMES = ("fwd_rows", "fwd_axis1", "fused_axis0", "inv_axis1", "inv_rows")
+
+    def autotune(self, force: bool = False) -> dict:
+        """Time the candidate tile shapes of each four-step pass; returns
+        {pass name: chosen shape} for the passes that have candidates."""
+        _check(lib().vp_plan_autotune(self.handle, 1 if force else 0), self.handle)
+        return {name: cfg[2] for name, cfg in self.pass_configs().items() if cfg[1] > 0}
+
+    def pass_config(self, pass_index: int):
+        """(choice, number of candidates, name of the choice) of one pass."""
+        cfg, count = c_int(), c_int()
+        buf = ctypes.create_string_buffer(32)
+        _check(lib().vp_plan_pass_config(self.handle, pass_index, ctypes.byref(cfg), ctypes.byref(count), buf, 32),
+               self.handle)
+        return cfg.value, count.value, buf.value.decode()
+
+    def pass_configs(self) -> dict:
+        return {name: self.pass_config(i) for i, name in enumerate(self.PASS_NAMES)
+                if self.pass_config(i)[2] != "absent"}
+
+    def set_pass_config(self, pass_index: int, cfg: int):
+        _check(lib().vp_plan_set_pass_config(self.handle, pass_index, cfg), self.handle)
 
     def set_grad_mode(self, mode: str):
         vp_plan_set_grad_mode(self.handle, GRAD_MODES[mode])

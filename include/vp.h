@@ -461,8 +461,9 @@ const char* vp_ls_last_error(void);
  * (slope 0.1) except D1b.  Weights are bfloat16-rounded copies of FP32 master
  * weights.  The convolutions run on the tensor cores: the BF16 weights times
  * the two BF16 parts (hi, lo) of each FP32 activation, accumulated in FP32, so
- * they agree with FP32 arithmetic to about 2^-16 relative; pooling, upsampling,
- * activations and the weight gradients are FP32.  Parameter layout for set/get: for each layer in
+ * they agree with FP32 arithmetic to about 2^-16 relative; the weight
+ * gradients likewise (both operands split, FP32 partial sums per CTA reduced in
+ * FP64); pooling, upsampling and activations are FP32.  Parameter layout for set/get: for each layer in
  * that order, w[C_out][C_in][27] (k = (kz*3 + ky)*3 + kx) then b[C_out].
  * Input channels: (Re r, Im r, q) with r scaled to unit RMS (sqrt(n) r/||r||);
  * output: the deviation of the correction from r, in the same scale.

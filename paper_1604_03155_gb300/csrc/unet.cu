@@ -8,7 +8,8 @@
 // conv = 3x3x3 cross-correlation, zero padding 1, bias; leaky ReLU (slope 0.1
 // by default, 1 = linear network) after every conv but the last; pool = 2x2x2 mean; up = nearest x2.
 // Weights are kept in FP32 for the optimiser and rounded to bfloat16 for every
-// forward and backward pass (BF16 weights, FP32 arithmetic).
+// forward and backward pass (BF16 weights; FP32 activations and gradients, split
+// into two BF16 parts on the tensor cores).
 //
 // Kernels (all the network's own):
 //  * convolutions: implicit GEMMs on the tensor cores (unet_tc.cu), BF16
@@ -17,10 +18,9 @@
 //    copy.
 //  * input gradient: the same convolution with the layer's weights flipped in
 //    k and transposed in (co, ci).
-//  * k_wgrad: persistent CTAs accumulate dW[ci][k][co] over their spatial tiles
-//    (halo and dz tile in shared memory, one (ci, k) pair per thread, CO
-//    accumulators), write one partial per CTA; k_wreduce sums the partials in
-//    FP64 in a fixed order (deterministic).
+//  * weight gradients: implicit GEMMs on the tensor cores as well (unet_tc.cu),
+//    both operands split into BF16 parts; each CTA writes one partial and
+//    k_wreduce sums the partials in FP64 in a fixed order (deterministic).
 //  * pool/up forward and backward, leaky-ReLU backward, MSE loss, Adam.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -35,100 +35,8 @@
 namespace {
 
 constexpr int kLayers = 10;
-constexpr int kTile = 8, kHalo = 10, kHalo3 = 1000, kWgCh = 16;
 
 __device__ __forceinline__ float lrelu(float v, float slope) { return v > 0.f ? v : slope * v; }
-
-// Weight gradient partials: part[blk][(ci*27 + k)*CO + co] and part[blk][Ci*27*CO + co] (bias)
-template <int CO>
-__global__ void __launch_bounds__(512) k_wgrad(const float* __restrict__ x1, int c1, const float* __restrict__ x2,
-                                               int c2, const float* __restrict__ dz, float* __restrict__ part, int S) {
-  extern __shared__ __align__(16) float sm[];
-  float* halo = sm;                      // kWgCh x 1000
-  float* dzs = sm + kWgCh * kHalo3;      // 512 x CO ([voxel][co])
-  const int Ci = c1 + c2;
-  const long long S3 = (long long)S * S * S;
-  const int tpd = (S + kTile - 1) / kTile;
-  const int ntiles = tpd * tpd * tpd;
-  const int nch = (Ci + kWgCh - 1) / kWgCh;  // 1 or 2
-  const int pair = threadIdx.x;              // (ci_local, k) = (pair / 27, pair % 27)
-  const int cil = pair / 27, k = pair % 27;
-  const int kz = k / 9, ky = (k / 3) % 3, kx = k % 3;
-  const bool bias_thread = threadIdx.x >= 512 - CO;
-  float acc[2][CO];
-  float bacc = 0.f;
-#pragma unroll
-  for (int h = 0; h < 2; ++h)
-#pragma unroll
-    for (int co = 0; co < CO; ++co) acc[h][co] = 0.f;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    int bt = t;
-    const int tx0 = (bt % tpd) * kTile;
-    bt /= tpd;
-    const int ty0 = (bt % tpd) * kTile;
-    const int tz0 = (bt / tpd) * kTile;
-    __syncthreads();
-    // dz tile, transposed to [voxel][co]; voxels outside the grid contribute zero
-    for (int e = threadIdx.x; e < 512 * CO; e += blockDim.x) {
-      const int co = e / 512, v = e % 512;
-      const int gz = tz0 + v / 64, gy = ty0 + (v / 8) % 8, gx = tx0 + v % 8;
-      float val = 0.f;
-      if (gz < S && gy < S && gx < S) val = dz[(long long)co * S3 + ((long long)gz * S + gy) * S + gx];
-      dzs[v * CO + co] = val;
-    }
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      if (h >= nch) break;
-      __syncthreads();
-      for (int e = threadIdx.x; e < kWgCh * kHalo3; e += blockDim.x) {
-        const int ci = e / kHalo3, r = e % kHalo3;
-        const int gz = tz0 + r / 100 - 1, gy = ty0 + (r / 10) % 10 - 1, gx = tx0 + r % 10 - 1;
-        const int cc = h * kWgCh + ci;
-        float val = 0.f;
-        if (cc < Ci && gz >= 0 && gz < S && gy >= 0 && gy < S && gx >= 0 && gx < S) {
-          const float* src = cc < c1 ? x1 + (long long)cc * S3 : x2 + (long long)(cc - c1) * S3;
-          val = src[((long long)gz * S + gy) * S + gx];
-        }
-        halo[ci * kHalo3 + r] = val;
-      }
-      __syncthreads();
-      if (pair < kWgCh * 27 && h * kWgCh + cil < Ci) {
-#pragma unroll 2
-        for (int v = 0; v < 512; ++v) {
-          const int vz = v >> 6, vy = (v >> 3) & 7, vx = v & 7;
-          const float xv = halo[cil * kHalo3 + ((vz + kz) * kHalo + (vy + ky)) * kHalo + vx + kx];
-          if constexpr (CO % 4 == 0) {
-#pragma unroll
-            for (int co = 0; co < CO; co += 4) {
-              const float4 d4 = *reinterpret_cast<const float4*>(&dzs[v * CO + co]);
-              acc[h][co] = fmaf(d4.x, xv, acc[h][co]);
-              acc[h][co + 1] = fmaf(d4.y, xv, acc[h][co + 1]);
-              acc[h][co + 2] = fmaf(d4.z, xv, acc[h][co + 2]);
-              acc[h][co + 3] = fmaf(d4.w, xv, acc[h][co + 3]);
-            }
-          } else {
-#pragma unroll
-            for (int co = 0; co < CO; ++co) acc[h][co] = fmaf(dzs[v * CO + co], xv, acc[h][co]);
-          }
-        }
-      }
-    }
-    if (bias_thread) {
-      const int co = threadIdx.x - (512 - CO);
-      for (int v = 0; v < 512; ++v) bacc += dzs[v * CO + co];
-    }
-  }
-  const long long stride = (long long)Ci * 27 * CO + CO;
-  float* out = part + (long long)blockIdx.x * stride;
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int cc = h * kWgCh + cil;
-    if (h < nch && pair < kWgCh * 27 && cc < Ci)
-#pragma unroll
-      for (int co = 0; co < CO; ++co) out[((long long)cc * 27 + k) * CO + co] = acc[h][co];
-  }
-  if (bias_thread) out[(long long)Ci * 27 * CO + (threadIdx.x - (512 - CO))] = bacc;
-}
 
 // dw[co][ci][k] = sum_blocks part[blk][(ci*27+k)*CO + co]; db[co] likewise (FP64 sums)
 __global__ void k_wreduce(const float* __restrict__ part, int nblk, int Ci, int CO, float* __restrict__ dw,
@@ -369,16 +277,21 @@ cudaError_t conv(vp_unet u, const float* x1, int c1, const float* x2, int c2, co
 cudaError_t wgrad(vp_unet u, int layer, const float* x1, int c1, const float* x2, int c2, const float* dz, int S,
                   cudaStream_t s) {
   const int CO = u->co[layer], Ci = u->ci[layer];
-  const int tpd = (S + kTile - 1) / kTile;
-  const int nt = tpd * tpd * tpd;
-  const int nb = nt < u->part_blocks ? nt : u->part_blocks;
-  const size_t smem = (size_t)(kWgCh * kHalo3 + 512 * CO) * sizeof(float);
-  if (CO == 16)
-    k_wgrad<16><<<nb, 512, smem, s>>>(x1, c1, x2, c2, dz, u->part, S);
-  else if (CO == 2)
-    k_wgrad<2><<<nb, 512, smem, s>>>(x1, c1, x2, c2, dz, u->part, S);
-  else
-    return cudaErrorInvalidValue;
+  const long long rows = vp::unet_tc::wgrad_rows(S);
+  const int nb = rows < u->part_blocks ? (int)rows : u->part_blocks;
+  vp::unet_tc::WgradArgs a;
+  a.x1 = x1;
+  a.c1 = c1;
+  a.x2 = x2;
+  a.c2 = c2;
+  a.dy = dz;
+  a.co = CO;
+  a.part = u->part;
+  a.nblk = nb;
+  a.S = S;
+  a.err = u->err;
+  cudaError_t e = vp::unet_tc::wgrad3d(a, s);
+  if (e != cudaSuccess) return e;
   k_wreduce<<<g1((long long)Ci * 27 * CO + CO), 256, 0, s>>>(u->part, nb, Ci, CO, u->g + u->woff[layer],
                                                              u->g + u->boff[layer]);
   return cudaGetLastError();
@@ -530,13 +443,6 @@ vp_status vp_unet_create(vp_unet* out, int S, int C) {
   if (e == cudaSuccess) e = cudaMemset(u->v, 0, off * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(u->w, 0, off * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(u->wq, 0, off * sizeof(float));
-  if (e == cudaSuccess) {
-    e = cudaFuncSetAttribute(k_wgrad<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)((kWgCh * kHalo3 + 512 * 16) * sizeof(float)));
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_wgrad<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)((kWgCh * kHalo3 + 512 * 2) * sizeof(float)));
-  }
   if (e != cudaSuccess) {
     vp_unet_destroy(u);
     return e == cudaErrorMemoryAllocation ? VP_ERR_OOM : VP_ERR_CUDA;

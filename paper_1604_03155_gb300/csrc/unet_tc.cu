@@ -390,5 +390,238 @@ cudaError_t conv3d(const ConvArgs& a, cudaStream_t s) {
   return cudaSuccess;
 }
 
+// ---------------------------------------------------------------------------
+// Weight gradients on the tensor cores:
+//   dW[co][ci][(kz, ky, kx)] = sum_v dy[co](v) x[ci](v + (kz - 1, ky - 1, kx - 1)),
+//   db[co] = sum_v dy[co](v)
+// per output row segment (K = its 128 voxels) as D[(input row r, ci)][co] +=
+// A * B with A the nine input rows r = 3 kz + ky staged as the convolution
+// stages them, read MN-major (a voxel's 16 bytes of 8 channels are one K row
+// of a core matrix; channel groups, and then rows, one plane apart, so
+// M = (r, ci)), the tap kx a 16-byte K offset; B the segment's dy (K-major,
+// N = 16 output channels).  Rows 0-7 take one M = 128 chain and row 8 a second
+// one whose window starts at row 1 (its rows 1-7 are not used), three of each
+// for kx, six accumulators of 16 columns in tensor memory.  Both operands are
+// split into BF16 hi and lo parts and the products hi hi, lo hi, hi lo are
+// accumulated (relative residual about 2^-16).  Each CTA sums over its rows
+// and writes one partial per CTA in the layout k_wreduce reduces in FP64:
+// part[blk][(ci * 27 + tap) * co_n + co], the bias at part[blk][Ci * 27 * co_n + co].
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kWgThreads = 256;  // a voxel x a channel group in the staging
+constexpr size_t kWgB = (size_t)16 * 128 * 2;          // one part of B: 16 co x 128 voxels, BF16
+constexpr size_t kWgX = (size_t)9 * kG * kPlane;       // one part of the nine staged input rows
+constexpr size_t kWgOffX = 2 * kWgB;
+constexpr size_t kWgOffBar = kWgOffX + 2 * kWgX;
+constexpr size_t kWgSmem = kWgOffBar + 16;
+constexpr uint32_t kWgTmemCols = 128;                   // 6 accumulators of 16 columns
+static_assert(2 * (kWgSmem + 1024) <= 233472, "two CTAs per SM");
+
+struct WgBlock {
+  const float* x;  // input block: c channels, [c][S^3]
+  int c, ci0;      // its channels and their first index in the layer's input
+  const float* dy;
+  int co;          // output channels of the layer (<= 16)
+  float* part;
+  int Ci;          // the layer's input channels (partial layout)
+  int S, bias;     // bias: write the bias partials (first block only)
+  int* err;
+};
+}  // namespace
+
+__global__ void __launch_bounds__(kWgThreads) k_wgrad_tc(const WgBlock a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int vx = tid & (kSeg - 1), grp = tid >> 7;  // staged voxel and channel group
+  const int S = a.S;
+  const long long S3 = (long long)S * S * S;
+  unsigned char* sB = smem;             // [part][co group][voxel group][8 co][8 voxels]
+  unsigned char* sX = smem + kWgOffX;   // [part][row r][channel group][130 slots][8 ch]
+  uint64_t* s_mbar = reinterpret_cast<uint64_t*>(smem + kWgOffBar);
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + kWgOffBar + 8);
+  int* s_stop = reinterpret_cast<int*>(smem + kWgOffBar + 12);
+  for (size_t i = (size_t)tid * 16; i < 2 * kWgX; i += (size_t)kWgThreads * 16)
+    *reinterpret_cast<uint4*>(sX + i) = make_uint4(0u, 0u, 0u, 0u);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(s_tmem)),
+                 "r"(kWgTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(s_mbar)));
+    *s_stop = 0;
+  }
+  sync_for_mma();
+  const uint32_t tmem = *s_tmem;
+  const uint32_t mbar = su32(s_mbar);
+  // A MN-major (bit 15), B K-major; descriptors: A (K stride 128 B, M stride a
+  // plane), B (K stride 128 B, N stride 2048 B)
+  const uint32_t idesc = idesc_bf16(16) | (1u << 15);
+  const uint64_t ad0 = sdesc(su32(sX), 128, kPlane), bd0 = sdesc(su32(sB), 128, 2048);
+  uint32_t phase = 0;
+  bool ok = true, any = false;
+  float bsum = 0.f;  // bias: this thread's output channel (tid / 8) mod 16
+  const int bco = (tid >> 3) & 15, bj = tid & 7, bh = tid >> 7;
+
+  const int nseg = (S + kSeg - 1) / kSeg;
+  const long long rows = (long long)S * S * nseg;
+  for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int seg = (int)(row % nseg);
+    const long long r2 = row / nseg;
+    const int y = (int)(r2 % S), z = (int)(r2 / S), x0 = seg * kSeg;
+    // the nine input rows (z + kz - 1, y + ky - 1), r = 3 kz + ky: thread
+    // (vx, grp) writes channel group grp of slot vx + 1, all 72 loads in flight;
+    // the threads of voxels 0 and 1 also the end slots of an inner segment
+    const int nslots = (nseg > 1 && vx < 2) ? 2 : 1;
+#pragma unroll 1
+    for (int e = 0; e < nslots; ++e) {
+      const int slot = e == 0 ? vx + 1 : (vx == 0 ? 0 : kSeg + 1);
+      const int x = e == 0 ? x0 + vx : (vx == 0 ? x0 - 1 : x0 + kSeg);
+      float v[9][8];
+#pragma unroll
+      for (int r = 0; r < 9; ++r) {
+        const int zz = z + r / 3 - 1, yy = y + r % 3 - 1;
+        const bool in = zz >= 0 && zz < S && yy >= 0 && yy < S && x >= 0 && x < S;
+        const float* src = a.x + (long long)(8 * grp) * S3 + ((long long)zz * S + yy) * S + x;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[r][j] = (in && 8 * grp + j < a.c) ? __ldg(src + j * S3) : 0.f;
+      }
+#pragma unroll
+      for (int r = 0; r < 9; ++r) {
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) split2(v[r][2 * j], v[r][2 * j + 1], hi[j], lo[j]);
+        const size_t off = ((size_t)r * kG + grp) * kPlane + slot * 16;
+        *reinterpret_cast<uint4*>(sX + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4*>(sX + kWgX + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+      }
+    }
+    // dy of the segment: thread (co = (tid / 8) mod 16, voxel group tid mod 8 + 8 (tid / 128))
+    {
+      const int vg = bj + 8 * bh, xs = x0 + 8 * vg;
+      float v[8];
+      const float* src = a.dy + (long long)bco * S3 + ((long long)z * S + y) * S + xs;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = (bco < a.co && xs + j < S) ? __ldg(src + j) : 0.f;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) bsum += v[j];
+      uint32_t hi[4], lo[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) split2(v[2 * j], v[2 * j + 1], hi[j], lo[j]);
+      const size_t off = ((size_t)(bco >> 3) * 16 + vg) * 128 + (bco & 7) * 16;
+      *reinterpret_cast<uint4*>(sB + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+      *reinterpret_cast<uint4*>(sB + kWgB + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    }
+    sync_for_mma();
+    if (*s_stop) break;
+    if (tid == 0) {
+#pragma unroll
+      for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll 1
+          for (int ks = 0; ks < 8; ++ks)
+#pragma unroll
+            for (int pr = 0; pr < 3; ++pr) {
+              const int pa = pr == 1 ? 1 : 0, pb = pr == 2 ? 1 : 0;  // hi hi, lo hi, hi lo
+              const uint64_t ad = ad0 + (uint64_t)((pa * kWgX + (size_t)h * kG * kPlane + ks * 256 + kx * 16) >> 4);
+              const uint64_t bd = bd0 + (uint64_t)((pb * kWgB + ks * 256) >> 4);
+              mma(tmem + (uint32_t)((kx * 2 + h) * 16), ad, bd, idesc, (any || ks > 0 || pr > 0) ? 1u : 0u);
+            }
+      commit(mbar);
+    }
+    ok = wait(mbar, phase) && ok;
+    phase ^= 1;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    any = true;
+    if (!ok) *s_stop = 1;
+    __syncthreads();  // the operands are free for the next row
+  }
+  // partials of this CTA: D lane L of accumulator (kx, h) is row r = h + L / 16
+  // (chain h = 1 keeps only r = 8) and channel L mod 16; warp w reads lanes
+  // 32 (w mod 4) .. + 31 and output channels 8 (w / 4) .. + 7
+  float* out = a.part + (long long)blockIdx.x * ((long long)a.Ci * 27 * a.co + a.co);
+  const int L = 32 * (warp & 3) + (tid & 31), c0 = 8 * (warp >> 2);
+#pragma unroll
+  for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float v[8];
+      if (any) {
+        tload8(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((kx * 2 + h) * 16 + c0), v);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = 0.f;
+      }
+      const int r = h + L / 16, ci = L & 15;
+      if ((h == 0 || r == 8) && ci < a.c) {
+        const int t = 3 * r + kx;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (c0 + j < a.co) out[((long long)(a.ci0 + ci) * 27 + t) * a.co + c0 + j] = v[j];
+      }
+    }
+  if (a.bias) {
+    // the two halves of the CTA hold the voxel groups 0-7 and 8-15 of each channel
+    bsum += __shfl_xor_sync(0xffffffffu, bsum, 1);
+    bsum += __shfl_xor_sync(0xffffffffu, bsum, 2);
+    bsum += __shfl_xor_sync(0xffffffffu, bsum, 4);
+    float* s_b = reinterpret_cast<float*>(sB);  // the operands are no longer read
+    __syncthreads();
+    if (bj == 0 && bh == 1) s_b[bco] = bsum;
+    __syncthreads();
+    if (bj == 0 && bh == 0 && bco < a.co) out[(long long)a.Ci * 27 * a.co + bco] = bsum + s_b[bco];
+  }
+  if (tid == 0 && *s_stop && a.err) atomicOr(a.err, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kWgTmemCols));
+}
+
+// Per-CTA partials of the layer's weight and bias gradients for nblk CTAs:
+// part[blk][(ci * 27 + tap) * co + co'] and part[blk][Ci * 27 * co + co'].
+cudaError_t wgrad3d(const WgradArgs& a, cudaStream_t s) {
+  const int Ci = a.c1 + a.c2;
+  if (a.c1 < 1 || a.c1 > 16 || a.c2 < 0 || a.c2 > 16 || (a.c2 > 0 && !a.x2) || a.co < 1 || a.co > 16 || a.S < 1 ||
+      a.nblk < 1)
+    return cudaErrorInvalidValue;
+  static bool attr[64] = {false};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!attr[dev]) {
+    e = cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    attr[dev] = true;
+  }
+  WgBlock b;
+  b.dy = a.dy;
+  b.co = a.co;
+  b.part = a.part;
+  b.Ci = Ci;
+  b.S = a.S;
+  b.err = a.err;
+  b.x = a.x1;
+  b.c = a.c1;
+  b.ci0 = 0;
+  b.bias = 1;
+  k_wgrad_tc<<<a.nblk, kWgThreads, kWgSmem, s>>>(b);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || a.c2 == 0) return e;
+  b.x = a.x2;
+  b.c = a.c2;
+  b.ci0 = a.c1;
+  b.bias = 0;
+  k_wgrad_tc<<<a.nblk, kWgThreads, kWgSmem, s>>>(b);
+  return cudaGetLastError();
+}
+
+// CTAs a layer's weight gradient uses: one output row segment or more each.
+long long wgrad_rows(int S) { return (long long)S * S * ((S + kSeg - 1) / kSeg); }
+
 }  // namespace unet_tc
 }  // namespace vp

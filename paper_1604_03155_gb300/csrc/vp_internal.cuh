@@ -155,6 +155,23 @@ struct ConvArgs {
   int* err;
 };
 cudaError_t conv3d(const ConvArgs& a, cudaStream_t s);
+// Weight and bias gradients of a convolution (input x1, x2 as in ConvArgs,
+// dy: co <= 16 channels at the output) as nblk per-CTA partials
+// part[blk][(ci * 27 + tap) * co + o] and part[blk][(c1 + c2) * 27 * co + o].
+struct WgradArgs {
+  const float* x1;
+  int c1;
+  const float* x2;
+  int c2;
+  const float* dy;
+  int co;
+  float* part;
+  int nblk, S;
+  int* err;
+};
+cudaError_t wgrad3d(const WgradArgs& a, cudaStream_t s);
+// output row segments of an S^3 grid (at most this many CTAs do work)
+long long wgrad_rows(int S);
 }  // namespace unet_tc
 
 }  // namespace vp

@@ -493,6 +493,12 @@ vp_status vp_unet_set_slope(vp_unet net, double slope);
 vp_status vp_unet_bind(vp_unet net, const float* q);
 vp_status vp_unet_precond(void* ctx, const void* r, void* z, void* stream);
 vp_status vp_unet_status(vp_unet net);
+/* Budget of each bounded wait of the tensor-core kernels (default about 2 s;
+ * seconds > 0).  vp_unet_withhold is a test hook: on != 0 makes the kernels
+ * issue no MMAs, so their waits run out and the next status check reports
+ * VP_ERR_TIMEOUT.  Every report clears the error word. */
+vp_status vp_unet_set_timeout(vp_unet net, double seconds);
+vp_status vp_unet_withhold(vp_unet net, int on);
 const char* vp_unet_last_error(vp_unet net);
 vp_status vp_unet_destroy(vp_unet net);
 

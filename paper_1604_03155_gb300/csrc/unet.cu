@@ -238,6 +238,8 @@ struct vp_unet_s {
   int part_blocks = 0;
   double* red = nullptr;
   int* err = nullptr;        // device error word: a convolution's bounded wait timed out
+  long long wait_cycles = 4000000000ll;  // budget of each bounded wait (about 2 s)
+  int withhold = 0;                      // test hook: the convolutions issue no MMAs
   const float* q = nullptr;  // bound contrast for the preconditioner
   std::vector<void*> allocs;
   std::string last_error;
@@ -271,6 +273,8 @@ cudaError_t conv(vp_unet u, const float* x1, int c1, const float* x2, int c2, co
   a.act = act;
   a.slope = u->slope;
   a.err = u->err;
+  a.wait_cycles = u->wait_cycles;
+  a.withhold = u->withhold;
   return vp::unet_tc::conv3d(a, s);
 }
 
@@ -290,6 +294,8 @@ cudaError_t wgrad(vp_unet u, int layer, const float* x1, int c1, const float* x2
   a.nblk = nb;
   a.S = S;
   a.err = u->err;
+  a.wait_cycles = u->wait_cycles;
+  a.withhold = u->withhold;
   cudaError_t e = vp::unet_tc::wgrad3d(a, s);
   if (e != cudaSuccess) return e;
   k_wreduce<<<g1((long long)Ci * 27 * CO + CO), 256, 0, s>>>(u->part, nb, Ci, CO, u->g + u->woff[layer],
@@ -510,7 +516,10 @@ vp_status vp_unet_loss_grad(vp_unet u, const float* in, const float* target, dou
       return VP_ERR_CUDA;
     int herr = 0;
     if (cudaMemcpy(&herr, u->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return VP_ERR_CUDA;
-    if (herr) return ufail(u, VP_ERR_TIMEOUT, "a tensor-core convolution timed out waiting for its MMAs");
+    if (herr) {  // reported once, then cleared
+      if (cudaMemset(u->err, 0, sizeof(int)) != cudaSuccess) return VP_ERR_CUDA;
+      return ufail(u, VP_ERR_TIMEOUT, "a tensor-core convolution timed out waiting for its MMAs");
+    }
     double acc = 0.0;
     for (double v : h) acc += v;
     *loss = acc / (double)n;
@@ -556,7 +565,10 @@ vp_status vp_unet_precond(void* ctx, const void* r, void* z, void* stream) {
       cudaMemcpyAsync(&herr, u->err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return VP_ERR_CUDA;
-  if (herr) return ufail(u, VP_ERR_TIMEOUT, "a tensor-core convolution timed out waiting for its MMAs");
+  if (herr) {  // reported once, then cleared
+    if (cudaMemsetAsync(u->err, 0, sizeof(int), s) != cudaSuccess) return VP_ERR_CUDA;
+    return ufail(u, VP_ERR_TIMEOUT, "a tensor-core convolution timed out waiting for its MMAs");
+  }
   double nr = 0.0;
   for (double v : h) nr += v;
   nr = sqrt(nr);
@@ -579,7 +591,28 @@ vp_status vp_unet_status(vp_unet u) {
   if (cudaMemcpyAsync(&herr, u->err, sizeof(int), cudaMemcpyDeviceToHost, u->stream) != cudaSuccess ||
       cudaStreamSynchronize(u->stream) != cudaSuccess)
     return ufail(u, VP_ERR_CUDA, "stream synchronisation failed");
-  if (herr) return ufail(u, VP_ERR_TIMEOUT, "a tensor-core convolution timed out waiting for its MMAs");
+  if (herr) {  // reported once, then cleared
+    if (cudaMemsetAsync(u->err, 0, sizeof(int), u->stream) != cudaSuccess ||
+        cudaStreamSynchronize(u->stream) != cudaSuccess)
+      return ufail(u, VP_ERR_CUDA, "clearing the error word failed");
+    return ufail(u, VP_ERR_TIMEOUT, "a tensor-core convolution timed out waiting for its MMAs");
+  }
+  return VP_OK;
+}
+
+vp_status vp_unet_set_timeout(vp_unet u, double seconds) {
+  if (!u || !(seconds > 0)) return VP_ERR_INVALID_ARG;
+  vp::DeviceGuard dg_(u->device);
+  int khz = 0;
+  if (cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, u->device) != cudaSuccess || khz <= 0) khz = 2000000;
+  const double cycles = seconds * khz * 1e3;
+  u->wait_cycles = cycles > 4e18 ? 4000000000000000000ll : (long long)cycles;
+  return VP_OK;
+}
+
+vp_status vp_unet_withhold(vp_unet u, int on) {
+  if (!u) return VP_ERR_INVALID_ARG;
+  u->withhold = on ? 1 : 0;
   return VP_OK;
 }
 

@@ -57,7 +57,6 @@ constexpr int kYS = 4;                   // y slots of the input ring
 constexpr int kG = 2;                    // 8-channel groups of an input block (16 channels, one K = 16 chunk)
 constexpr int kN = 16;                   // output channels of a block (accumulator columns)
 constexpr uint32_t kTmemCols = 64;       // two accumulators
-constexpr long long kWaitCycles = 4000000000ll;  // about 2 s
 constexpr size_t kBBytes = (size_t)27 * kN * 32;        // B of every tap: N x 16 BF16
 constexpr size_t kRowBytes = (size_t)2 * kG * kPlane;   // one staged input row, both parts
 constexpr size_t kOffA = kBBytes;
@@ -91,7 +90,7 @@ __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t ad, uint64_t bd, u
 __device__ __forceinline__ void commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
 }
-__device__ __forceinline__ bool wait(uint32_t mbar, uint32_t parity) {
+__device__ __forceinline__ bool wait(uint32_t mbar, uint32_t parity, long long budget) {
   const long long t0 = clock64();
   while (true) {
     uint32_t done;
@@ -101,7 +100,7 @@ __device__ __forceinline__ bool wait(uint32_t mbar, uint32_t parity) {
         : "r"(mbar), "r"(parity)
         : "memory");
     if (done) return true;
-    if (clock64() - t0 > kWaitCycles) return false;
+    if (clock64() - t0 > budget) return false;
   }
 }
 // generic-proxy shared stores and earlier tensor-memory loads ordered before
@@ -147,6 +146,8 @@ struct BlockArgs {
   int S, accumulate, act;
   float slope;
   int* err;
+  long long wait_cycles;
+  int withhold;
 };
 
 }  // namespace
@@ -289,12 +290,12 @@ __global__ void __launch_bounds__(kThreads) k_conv3d_tc(const BlockArgs a) {
     for (int y = y0; y < y1; ++y) {
       sync_for_mma();  // rows up to y + 1 staged; the previous epilogue's loads done
       if (*s_stop) break;
-      if (tid == 0) issue(y, (y - y0) & 1);
+      if (tid == 0 && !a.withhold) issue(y, (y - y0) & 1);
       if (y > y0) epilogue(y - 1, (y - 1 - y0) & 1);
       prefetch(y);
       // the slot of row y + 2 held row y - 2, whose last reader, row y - 1's MMAs, is done
       if (y + 2 <= y1) stage(y + 2);
-      ok = wait(mbar, phase) && ok;
+      ok = wait(mbar, phase, a.wait_cycles) && ok;
       phase ^= 1;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (!ok) *s_stop = 1;
@@ -368,6 +369,8 @@ cudaError_t conv3d(const ConvArgs& a, cudaStream_t s) {
     b.S = a.S;
     b.slope = a.slope;
     b.err = a.err;
+    b.wait_cycles = a.wait_cycles;
+    b.withhold = a.withhold;
     b.x = a.x1;
     b.c = a.c1;
     b.ci0 = 0;
@@ -426,6 +429,8 @@ struct WgBlock {
   int Ci;          // the layer's input channels (partial layout)
   int S, bias;     // bias: write the bias partials (first block only)
   int* err;
+  long long wait_cycles;
+  int withhold;
 };
 }  // namespace
 
@@ -514,7 +519,7 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_tc(const WgBlock a) {
     }
     sync_for_mma();
     if (*s_stop) break;
-    if (tid == 0) {
+    if (tid == 0 && !a.withhold) {
 #pragma unroll
       for (int kx = 0; kx < 3; ++kx)
 #pragma unroll
@@ -530,7 +535,7 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_tc(const WgBlock a) {
             }
       commit(mbar);
     }
-    ok = wait(mbar, phase) && ok;
+    ok = wait(mbar, phase, a.wait_cycles) && ok;
     phase ^= 1;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     any = true;
@@ -605,6 +610,8 @@ cudaError_t wgrad3d(const WgradArgs& a, cudaStream_t s) {
   b.Ci = Ci;
   b.S = a.S;
   b.err = a.err;
+  b.wait_cycles = a.wait_cycles;
+  b.withhold = a.withhold;
   b.x = a.x1;
   b.c = a.c1;
   b.ci0 = 0;

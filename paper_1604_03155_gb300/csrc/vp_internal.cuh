@@ -153,6 +153,8 @@ struct ConvArgs {
   int co, S, act;
   float slope;
   int* err;
+  long long wait_cycles;  // budget of each bounded wait (clock cycles)
+  int withhold;           // test hook: issue no MMAs, so the waits run out
 };
 cudaError_t conv3d(const ConvArgs& a, cudaStream_t s);
 // Weight and bias gradients of a convolution (input x1, x2 as in ConvArgs,
@@ -168,6 +170,8 @@ struct WgradArgs {
   float* part;
   int nblk, S;
   int* err;
+  long long wait_cycles;
+  int withhold;
 };
 cudaError_t wgrad3d(const WgradArgs& a, cudaStream_t s);
 // output row segments of an S^3 grid (at most this many CTAs do work)

@@ -120,6 +120,8 @@ _SIGNATURES = {
     "vp_unet_set_slope": (c_int, [c_void_p, c_double]),
     "vp_unet_precond": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "vp_unet_status": (c_int, [c_void_p]),
+    "vp_unet_set_timeout": (c_int, [c_void_p, c_double]),
+    "vp_unet_withhold": (c_int, [c_void_p, c_int]),
     "vp_unet_last_error": (c_char_p, [c_void_p]),
     "vp_unet_destroy": (c_int, [c_void_p]),
 }
@@ -719,6 +721,13 @@ class UNet:
     def status(self):
         """Synchronises the network's stream; raises on a timed-out convolution."""
         self._check(lib().vp_unet_status(self.handle))
+
+    def set_timeout(self, seconds: float):
+        self._check(lib().vp_unet_set_timeout(self.handle, seconds))
+
+    def withhold(self, on: bool):
+        """Test hook: the tensor-core kernels issue no MMAs, so their bounded waits run out."""
+        self._check(lib().vp_unet_withhold(self.handle, int(on)))
 
     def bind(self, q):
         self._q = q

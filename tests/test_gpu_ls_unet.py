@@ -172,3 +172,32 @@ def test_trained_preconditioner_against_plain_gmres(tag):
     assert s["precond_iterations"] <= 4 * s["plain_iterations"]
     net.close()
     plan.close()
+
+
+def test_bounded_wait_timeout_is_reported_and_recoverable():
+    """The tensor-core convolutions and weight gradients bound their waits for
+    the MMAs: with the MMAs withheld (a completion nothing signals) the waits
+    run out after a short budget, the kernels finish, the status reports
+    VP_ERR_TIMEOUT once, and the network runs correctly afterwards."""
+    S = 8
+    net = UNet(S, 16, weights=_weights(5))
+    x = torch.from_numpy(I.normal(91, 3 * S ** 3).astype(np.float32).reshape(3, S, S, S)).to(DEV)
+    tgt = torch.zeros((2, S, S, S), dtype=torch.float32, device=DEV)
+    ref = net.forward(x).cpu().numpy()
+    net.status()
+    net.set_timeout(0.001)
+    net.withhold(True)
+    net.forward(x)
+    with pytest.raises(vp.VPError) as ei:
+        net.status()
+    assert ei.value.status == vp.VP_ERR_TIMEOUT
+    with pytest.raises(vp.VPError) as ei:
+        net.loss_grad(x, tgt)  # the weight gradients' waits run out too
+    assert ei.value.status == vp.VP_ERR_TIMEOUT
+    net.withhold(False)
+    net.set_timeout(2.0)
+    net.status()  # cleared
+    out = net.forward(x).cpu().numpy()
+    net.status()
+    assert np.array_equal(out, ref)
+    net.close()

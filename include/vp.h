@@ -205,6 +205,26 @@ vp_status vp_apply(vp_plan plan, const void* f, void* phi, vp_dtype dtype);
  * ... at the cost of an additional FFT").  grad: d * N^d elements. */
 vp_status vp_apply_grad(vp_plan plan, const void* f, void* phi, void* grad, vp_dtype dtype);
 
+/* The apply of vp_apply / vp_apply_grad on `count` densities in host memory,
+ * pipelined: density i + 1 is copied to the device and the fields of density
+ * i - 1 are copied back on two copy streams of the plan (the GPU's copy
+ * engines) while density i is transformed on the plan's stream, so the
+ * transfers hide behind the transforms.  f[i], phi[i], grad[i]: the N^d (phi)
+ * and d * N^d (grad) element arrays of density i, `dtype` as for vp_apply;
+ * page-locked host memory overlaps (pageable memory works, but its copies do
+ * not overlap); device pointers are copied like host ones.  phi or grad may
+ * be NULL (not both): NULL phi skips the potential, NULL grad the gradient.
+ * The call returns when every output is in the caller's memory, also after a
+ * failure part-way.  On first use the plan allocates 3 device slots of
+ * (1 + fields) * N^d elements (or count slots when count < 3) and keeps them
+ * until vp_destroy.  Errors: VP_ERR_INVALID_ARG for count < 0, a NULL array
+ * or entry, phi[i] == f[i] or a dtype that does not match the plan;
+ * VP_ERR_UNSUPPORTED for grad with a tensor-core precision; VP_ERR_OOM when
+ * the slots do not fit.  Each output equals that of vp_apply / vp_apply_grad
+ * on the same density bit for bit (the same kernels on the same workspace). */
+vp_status vp_apply_pipeline(vp_plan plan, int count, const void* const* f, void* const* phi, void* const* grad,
+                            vp_dtype dtype);
+
 /* Copies a precomputed FP64 octant (prod_j (N_j+1) complex128 = 2 prod_j (N_j+1) doubles) to
  * host memory.  `axis` selects j for the gradient arrays (ignored otherwise);
  * `count` is the number of doubles available at host_dst. */

@@ -76,6 +76,14 @@ struct vp_plan_s {
   int pass_cfg[5] = {0, 0, 0, 0, 0};  // tile shape of each FP32 four-step pass (vp_plan_autotune)
   std::vector<TimedLaunch> timed;
   std::vector<cudaEvent_t> event_pool;
+  // vp_apply_pipeline (made on first use): two copy streams, kPipeSlots device
+  // slots (a density and its output fields each) and per slot the events
+  // "input copied", "apply done", "outputs copied"
+  cudaStream_t pipe_h2d = nullptr, pipe_d2h = nullptr;
+  void* pipe_buf = nullptr;
+  size_t pipe_bytes = 0;
+  cudaEvent_t pipe_ev[3][3] = {};
+  cudaEvent_t pipe_start = nullptr;
 
   std::string last_error;
 };
@@ -547,6 +555,23 @@ vp_status check_dtype(vp_plan p, vp_dtype dtype, bool* real_io) {
   return VP_OK;
 }
 
+// The output fields of one apply: phi (when with_phi) and then the d gradient
+// components, each with its multiplier (or its 2N-mode derivative axis).
+int make_fields(vp_plan p, bool with_phi, bool want_grad, FieldDesc* fields) {
+  const bool fp64 = p->prec == VP_FP64;
+  int F = 0;
+  if (with_phi) fields[F++] = FieldDesc{fp64 ? (const void*)p->G64 : (const void*)p->G32, -1, -1};
+  if (want_grad) {
+    for (int j = 0; j < p->d; ++j) {
+      if (p->gmode == VP_GRAD_EXACT)
+        fields[F++] = FieldDesc{fp64 ? (const void*)p->Gj64[j] : (const void*)p->Gj32[j], j, -1};
+      else
+        fields[F++] = FieldDesc{fp64 ? (const void*)p->G64 : (const void*)p->G32, -1, j};
+    }
+  }
+  return F;
+}
+
 vp_status apply_common(vp_plan p, const void* f, void* phi, void* grad, vp_dtype dtype, bool want_grad) {
   if (!p) return fail(nullptr, VP_ERR_INVALID_ARG, "plan is NULL");
   if (!f) return fail(p, VP_ERR_INVALID_ARG, "f is NULL");
@@ -568,16 +593,7 @@ vp_status apply_common(vp_plan p, const void* f, void* phi, void* grad, vp_dtype
   const size_t U = grid_points(p);
 
   FieldDesc fields[4];
-  int F = 0;
-  if (phi) fields[F++] = FieldDesc{fp64 ? (const void*)p->G64 : (const void*)p->G32, -1, -1};
-  if (want_grad) {
-    for (int j = 0; j < p->d; ++j) {
-      if (p->gmode == VP_GRAD_EXACT)
-        fields[F++] = FieldDesc{fp64 ? (const void*)p->Gj64[j] : (const void*)p->Gj32[j], j, -1};
-      else
-        fields[F++] = FieldDesc{fp64 ? (const void*)p->G64 : (const void*)p->G32, -1, j};
-    }
-  }
+  const int F = make_fields(p, phi != nullptr, want_grad, fields);
 
   const bool host_io = !is_device_ptr(f);
   void* outs[4];
@@ -639,6 +655,109 @@ vp_status apply_common(vp_plan p, const void* f, void* phi, void* grad, vp_dtype
       VP_CUDA(p, cudaMemcpyAsync(grad, outs[i], (size_t)p->d * U * eb, cudaMemcpyDeviceToHost, p->stream));
     VP_CUDA(p, cudaStreamSynchronize(p->stream));
   }
+  return VP_OK;
+}
+
+constexpr int kPipeSlots = 3;
+
+// Copy streams, events and `bytes` of device slots for vp_apply_pipeline.
+vp_status pipeline_resources(vp_plan p, size_t bytes) {
+  if (!p->pipe_h2d) VP_CUDA(p, cudaStreamCreateWithFlags(&p->pipe_h2d, cudaStreamNonBlocking));
+  if (!p->pipe_d2h) VP_CUDA(p, cudaStreamCreateWithFlags(&p->pipe_d2h, cudaStreamNonBlocking));
+  if (!p->pipe_start) VP_CUDA(p, cudaEventCreateWithFlags(&p->pipe_start, cudaEventDisableTiming));
+  for (int s = 0; s < kPipeSlots; ++s)
+    for (int e = 0; e < 3; ++e)
+      if (!p->pipe_ev[s][e]) VP_CUDA(p, cudaEventCreateWithFlags(&p->pipe_ev[s][e], cudaEventDisableTiming));
+  if (p->pipe_bytes < bytes) {
+    if (p->pipe_buf) {
+      cudaFree(p->pipe_buf);
+      p->device_bytes -= p->pipe_bytes;
+      p->pipe_buf = nullptr;
+      p->pipe_bytes = 0;
+    }
+    VP_CUDA(p, cudaMalloc(&p->pipe_buf, bytes));
+    p->pipe_bytes = bytes;
+    p->device_bytes += bytes;
+  }
+  return VP_OK;
+}
+
+// Issues the pipeline: density i is copied in on the h2d stream, applied on
+// the plan's stream and its fields copied out on the d2h stream, in slot
+// i mod R; the copy into a slot waits for the apply that last read it, the
+// apply for the copy-out that last emptied it.  So the copies of densities
+// i + 1 and i - 1 overlap the apply of density i.
+vp_status pipeline_issue(vp_plan p, int count, const void* const* f, void* const* phi, void* const* grad,
+                         size_t fb, const FieldDesc* fields, int F, bool real_io) {
+  const int R = count < kPipeSlots ? count : kPipeSlots;
+  const size_t slot = (1 + (size_t)F) * fb;
+  char* base = reinterpret_cast<char*>(p->pipe_buf);
+  VP_CUDA(p, cudaEventRecord(p->pipe_start, p->stream));
+  VP_CUDA(p, cudaStreamWaitEvent(p->pipe_h2d, p->pipe_start, 0));
+  for (int i = 0; i < count; ++i) {
+    const int s = i % R;
+    char* in = base + (size_t)s * slot;
+    char* out = in + fb;
+    cudaEvent_t* ev = p->pipe_ev[s];
+    if (i >= R) VP_CUDA(p, cudaStreamWaitEvent(p->pipe_h2d, ev[1], 0));
+    VP_CUDA(p, cudaMemcpyAsync(in, f[i], fb, cudaMemcpyDefault, p->pipe_h2d));
+    VP_CUDA(p, cudaEventRecord(ev[0], p->pipe_h2d));
+    VP_CUDA(p, cudaStreamWaitEvent(p->stream, ev[0], 0));
+    if (i >= R) VP_CUDA(p, cudaStreamWaitEvent(p->stream, ev[2], 0));
+    void* outs[4];
+    for (int j = 0; j < F; ++j) outs[j] = out + (size_t)j * fb;
+    vp_status st = p->prec == VP_FP64 ? run_apply_ws<double>(p, p->ws, in, outs, fields, F, real_io)
+                                      : run_apply_ws<float>(p, p->ws, in, outs, fields, F, real_io);
+    if (st != VP_OK) return st;
+    VP_CUDA(p, cudaEventRecord(ev[1], p->stream));
+    VP_CUDA(p, cudaStreamWaitEvent(p->pipe_d2h, ev[1], 0));
+    int j = 0;
+    if (phi) VP_CUDA(p, cudaMemcpyAsync(phi[i], out + fb * j++, fb, cudaMemcpyDefault, p->pipe_d2h));
+    if (grad) VP_CUDA(p, cudaMemcpyAsync(grad[i], out + fb * j, (size_t)p->d * fb, cudaMemcpyDefault, p->pipe_d2h));
+    VP_CUDA(p, cudaEventRecord(ev[2], p->pipe_d2h));
+  }
+  return VP_OK;
+}
+
+vp_status apply_pipeline(vp_plan p, int count, const void* const* f, void* const* phi, void* const* grad,
+                         vp_dtype dtype) {
+  if (!p) return fail(nullptr, VP_ERR_INVALID_ARG, "plan is NULL");
+  if (count < 0) return fail(p, VP_ERR_INVALID_ARG, "count is negative");
+  if (count > 0 && !f) return fail(p, VP_ERR_INVALID_ARG, "f is NULL");
+  if (!phi && !grad) return fail(p, VP_ERR_INVALID_ARG, "phi and grad are both NULL");
+  for (int i = 0; i < count; ++i) {
+    if (!f[i] || (phi && !phi[i]) || (grad && !grad[i]))
+      return fail(p, VP_ERR_INVALID_ARG, "a NULL entry in f, phi or grad");
+    if (phi && phi[i] == f[i]) return fail(p, VP_ERR_INVALID_ARG, "phi may not alias f");
+  }
+  bool real_io = false;
+  vp_status st = check_dtype(p, dtype, &real_io);
+  if (st != VP_OK) return st;
+  if (grad && is_tc(p->prec))
+    return fail(p, VP_ERR_UNSUPPORTED, "the tensor-core precisions serve vp_apply only; use VP_FP32 for gradients");
+  if (count == 0) return VP_OK;
+  VP_ON_DEVICE(p, p->device);
+  if (grad && p->gmode == VP_GRAD_EXACT) {
+    st = build_grad(p);
+    if (st != VP_OK) return st;
+  }
+  FieldDesc fields[4];
+  const int F = make_fields(p, phi != nullptr, grad != nullptr, fields);
+  const size_t fb = grid_points(p) * elem_bytes(dtype);
+  const size_t csize = p->prec == VP_FP64 ? sizeof(double2) : sizeof(float2);
+  const int R = count < kPipeSlots ? count : kPipeSlots;
+  if ((st = ensure_workspace(p, workspace_bytes(p, F, csize))) != VP_OK) return st;
+  if ((st = pipeline_resources(p, (size_t)R * (1 + F) * fb)) != VP_OK) return st;
+  st = pipeline_issue(p, count, f, phi, grad, fb, fields, F, real_io);
+  // every copy into the caller's buffers has ended when the call returns,
+  // whether or not issuing failed part-way
+  const cudaError_t e1 = cudaStreamSynchronize(p->pipe_d2h);
+  const cudaError_t e2 = cudaStreamSynchronize(p->stream);
+  const cudaError_t e3 = cudaStreamSynchronize(p->pipe_h2d);
+  if (st != VP_OK) return st;
+  VP_CUDA(p, e1);
+  VP_CUDA(p, e2);
+  VP_CUDA(p, e3);
   return VP_OK;
 }
 
@@ -1089,6 +1208,11 @@ vp_status vp_apply(vp_plan p, const void* f, void* phi, vp_dtype dtype) {
   return apply_common(p, f, phi, nullptr, dtype, false);
 }
 
+vp_status vp_apply_pipeline(vp_plan p, int count, const void* const* f, void* const* phi, void* const* grad,
+                            vp_dtype dtype) {
+  return apply_pipeline(p, count, f, phi, grad, dtype);
+}
+
 vp_status vp_apply_grad(vp_plan p, const void* f, void* phi, void* grad, vp_dtype dtype) {
   return apply_common(p, f, phi, grad, dtype, true);
 }
@@ -1226,6 +1350,15 @@ vp_status vp_destroy(vp_plan p) {
   cudaFree(p->d_flag);
   cudaFree(p->ws);
   cudaFree(p->stage);
+  if (p->pipe_h2d) cudaStreamSynchronize(p->pipe_h2d);
+  if (p->pipe_d2h) cudaStreamSynchronize(p->pipe_d2h);
+  cudaFree(p->pipe_buf);
+  if (p->pipe_h2d) cudaStreamDestroy(p->pipe_h2d);
+  if (p->pipe_d2h) cudaStreamDestroy(p->pipe_d2h);
+  if (p->pipe_start) cudaEventDestroy(p->pipe_start);
+  for (int s = 0; s < 3; ++s)
+    for (int e = 0; e < 3; ++e)
+      if (p->pipe_ev[s][e]) cudaEventDestroy(p->pipe_ev[s][e]);
   for (const TimedLaunch& t : p->timed) {
     cudaEventDestroy(t.start);
     cudaEventDestroy(t.stop);

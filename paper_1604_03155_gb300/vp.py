@@ -52,6 +52,8 @@ _SIGNATURES = {
     "vp_plan_set_grad_mode": (c_int, [c_void_p, c_int]),
     "vp_apply": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
     "vp_apply_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int]),
+    "vp_apply_pipeline": (c_int, [c_void_p, c_int, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
+                                  ctypes.POINTER(c_void_p), c_int]),
     "vp_plan_get_array": (c_int, [c_void_p, c_int, c_int, ctypes.POINTER(c_double), c_size_t]),
     "vp_plan_create_aniso": (c_int, [ctypes.POINTER(c_void_p), c_int, ctypes.POINTER(c_int), c_int, c_double,
                                      c_double]),
@@ -327,6 +329,34 @@ class Plan:
         self._sync_stream_to_torch(f)
         vp_apply_grad(self.handle, _ptr(f), _ptr(phi) if with_phi else None, _ptr(grad), _dtype_code(f))
         return (phi if with_phi else None), grad
+
+    def apply_pipeline(self, fs, phis=None, grads=None, with_phi: bool = True, with_grad: bool = False):
+        """phi_i = T * f_i (and grad_i when with_grad) for a list of host
+        densities (pinned CPU tensors or numpy arrays), the transfers of one
+        density overlapping the transform of the next; returns (phis, grads)."""
+        fs = list(fs)
+        if not fs:
+            return [], []
+        code = _dtype_code(fs[0])
+        for f in fs:
+            if _dtype_code(f) != code or tuple(f.shape) != tuple(fs[0].shape):
+                raise VPError(VP_ERR_INVALID_ARG, "every density needs the same dtype and shape")
+        if with_phi and phis is None:
+            phis = [_empty_like(f, f.shape) for f in fs]
+        if with_grad and grads is None:
+            grads = [_empty_like(f, (self.d,) + tuple(f.shape)) for f in fs]
+        self._sync_stream_to_torch(fs[0])
+
+        def table(xs):
+            if xs is None:
+                return None
+            if len(xs) != len(fs):
+                raise VPError(VP_ERR_INVALID_ARG, "one output per density")
+            return (c_void_p * len(xs))(*[_ptr(x) for x in xs])
+
+        _check(lib().vp_apply_pipeline(self.handle, len(fs), table(fs), table(phis if with_phi else None),
+                                       table(grads if with_grad else None), code), self.handle)
+        return (phis if with_phi else None), (grads if with_grad else None)
 
     def get_array(self, which: str, axis: int = 0) -> np.ndarray:
         """An FP64 octant ((N+1)^d complex128): 'T', 'ghat', 'Tj', 'ghatj'."""

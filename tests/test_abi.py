@@ -63,6 +63,7 @@ def test_plan_create_validation(lib, args, status):
 def test_null_safety_and_strings(lib):
     assert lib.vp_destroy(None) == vp.VP_OK
     assert lib.vp_apply(None, None, None, vp.VP_C64) == vp.VP_ERR_INVALID_ARG
+    assert lib.vp_apply_pipeline(None, 1, None, None, None, vp.VP_C64) == vp.VP_ERR_INVALID_ARG
     assert lib.vp_status_string(vp.VP_ERR_OOM) == b"VP_ERR_OOM"
     for n2 in (8, 12, 16, 24, 64, 96, 128, 192, 256, 512, 2048):
         assert lib.vp_fft_length_supported(n2) == 1

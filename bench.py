@@ -594,7 +594,7 @@ def run_ours(args, wl):
     f_ring = [torch.from_numpy(f_host).pin_memory() for _ in range(ring)]
     phi_ring = [torch.empty_like(f_pin).pin_memory() for _ in range(ring)]
     grad_ring = [torch.empty_like(grad_pin).pin_memory() for _ in range(ring)] if wl["grad"] else None
-    e2e_pipe_steps = max(8, min(args.steps, 40))
+    e2e_pipe_steps = max(8, min(args.steps, 200))
 
     def pipe_call(n):
         plan.apply_pipeline([f_ring[i % ring] for i in range(n)], [phi_ring[i % ring] for i in range(n)],

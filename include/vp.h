@@ -129,6 +129,29 @@ vp_status vp_plan_create_aniso(vp_plan* out, int d, const int* N, vp_kernel kern
 /* Points per axis (d ints). */
 vp_status vp_plan_dims(vp_plan plan, int* N);
 
+/* Saved plans: the precompute (Sections 2 and 4: sampling G^L, the 4N inverse
+ * transform to T, the 2N multiplier) run once and kept on disk.
+ *   vp_plan_save writes the plan's FP64 results to `path`: T and the unscaled
+ *     multiplier octant, and the derivative kernels T_j with their multipliers
+ *     when a gradient apply has built them (a 96-byte header: magic "VPPLAN01",
+ *     version 1, d, N per axis, kernel, k, L, octant size, payload size and a
+ *     64-bit FNV-1a hash of the payload's 8-byte words; then each octant as
+ *     complex128, axis 0 slowest; host byte order).  Synchronises the plan's
+ *     stream.
+ *   vp_plan_load creates a plan on the current device from such a file
+ *     without running the precompute: the uploaded arrays are scaled and
+ *     rounded by the same kernel as at creation, so every apply equals that
+ *     of the saved plan bit for bit.  The settings (precision, gradient mode,
+ *     stream, host access, tile shapes) start at their defaults.
+ *   vp_plan_kernel reports the plan's kernel.
+ * Errors: VP_ERR_INVALID_ARG for a NULL argument, a file that cannot be
+ * opened, written or read, a wrong magic, version or size, a truncated file,
+ * trailing bytes or a hash mismatch (all checked before any device work);
+ * the errors of vp_plan_create otherwise. */
+vp_status vp_plan_save(vp_plan plan, const char* path);
+vp_status vp_plan_load(vp_plan* out, const char* path);
+vp_status vp_plan_kernel(vp_plan plan, vp_kernel* kernel);
+
 /* Nystrom matrix entries on the fly (Section 4, the remark after the discrete
  * convolution): T is the matrix of a high-order Nystrom discretisation of the
  * volume integral, phi_p = sum_{p'} T(p - p') f_{p'} (weight h^d included).

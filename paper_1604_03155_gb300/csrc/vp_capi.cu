@@ -910,7 +910,28 @@ int vp_fft_length_supported(int n2) { return fft_length_built(n2) ? 1 : 0; }
 
 namespace {
 
-vp_status plan_create_common(vp_plan* out, int d, const int* Ns, vp_kernel kernel, double k, double L) {
+// Host copies of a saved plan's FP64 precompute results (vp_plan_save): T and
+// the unscaled multiplier, and with `grad` the derivative kernels T_j and their
+// multipliers; every other array of a plan follows from these.
+struct PlanPayload {
+  std::vector<double2> T, Gu;
+  std::vector<double2> Tj[3], Gju[3];
+  bool grad = false;
+};
+
+// The multiplier arrays the apply reads, from an uploaded unscaled multiplier
+// (the same scaling and rounding as the precompute's last step).
+cudaError_t upload_kernel(vp_plan p, const std::vector<double2>& T, const std::vector<double2>& Gu, double2* Tout,
+                          double2* Gu_dev, double2* G64, float2* G32, double scale) {
+  const size_t bytes = (size_t)p->oct * sizeof(double2);
+  cudaError_t e = cudaMemcpy(Tout, T.data(), bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(Gu_dev, Gu.data(), bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_finalize(Gu_dev, nullptr, G64, G32, p->oct, scale, 0, 0);
+  return e;
+}
+
+vp_status plan_create_common(vp_plan* out, int d, const int* Ns, vp_kernel kernel, double k, double L,
+                             const PlanPayload* saved = nullptr) {
   if (!out) return fail(nullptr, VP_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (d != 2 && d != 3) return fail(nullptr, VP_ERR_INVALID_ARG, "d must be 2 or 3");
@@ -980,11 +1001,30 @@ vp_status plan_create_common(vp_plan* out, int d, const int* Ns, vp_kernel kerne
   // tensor-core pipelines), read and cleared by vp_plan_status
   if (e == cudaSuccess) e = cudaMalloc(&p->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
-  Scratch sc;
-  if (e == cudaSuccess) e = scratch_alloc(p, sc);
-  if (e == cudaSuccess) e = build_kernel(p, sc, -1, p->T64, p->G64u, p->G64, p->G32);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(0);
-  sc.release();
+  if (!saved) {
+    Scratch sc;
+    if (e == cudaSuccess) e = scratch_alloc(p, sc);
+    if (e == cudaSuccess) e = build_kernel(p, sc, -1, p->T64, p->G64u, p->G64, p->G32);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+    sc.release();
+  } else {
+    // a saved plan: its FP64 arrays replace the precompute
+    double scale = 1.0;
+    for (int a = 0; a < d; ++a) scale /= 2.0 * Ns[a];
+    if (e == cudaSuccess) e = upload_kernel(p, saved->T, saved->Gu, p->T64, p->G64u, p->G64, p->G32, scale);
+    if (saved->grad) {
+      for (int j = 0; j < d && e == cudaSuccess; ++j) {
+        e = dalloc(p, &p->Tj64[j], oct);
+        if (e == cudaSuccess) e = dalloc(p, &p->Gj64u[j], oct);
+        if (e == cudaSuccess) e = dalloc(p, &p->Gj64[j], oct);
+        if (e == cudaSuccess) e = dalloc(p, &p->Gj32[j], oct);
+        if (e == cudaSuccess)
+          e = upload_kernel(p, saved->Tj[j], saved->Gju[j], p->Tj64[j], p->Gj64u[j], p->Gj64[j], p->Gj32[j], scale);
+      }
+      p->grad_built = e == cudaSuccess;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+  }
   if (e != cudaSuccess) {
     std::string msg = std::string("precompute: ") + cudaGetErrorString(e);
     vp_status st = (e == cudaErrorMemoryAllocation) ? VP_ERR_OOM : VP_ERR_CUDA;
@@ -1014,6 +1054,138 @@ vp_status vp_plan_dims(vp_plan p, int* N) {
   if (!p) return fail(nullptr, VP_ERR_INVALID_ARG, "plan is NULL");
   if (!N) return fail(p, VP_ERR_INVALID_ARG, "N is NULL");
   for (int a = 0; a < p->d; ++a) N[a] = p->Nv[a];
+  return VP_OK;
+}
+
+namespace {
+
+// Saved-plan file: a 96-byte header, then the FP64 octants (complex128, axis 0
+// slowest) T, G (unscaled) and, when the gradient kernels were built, T_j and
+// G_j for j < d.  Host byte order.
+constexpr char kPlanMagic[8] = {'V', 'P', 'P', 'L', 'A', 'N', '0', '1'};
+struct PlanFileHeader {
+  char magic[8];
+  uint32_t version, header_bytes;
+  int32_t d, N[3], kernel, grad;
+  double k, L;
+  int64_t oct;
+  uint64_t payload_bytes, checksum;
+  uint8_t reserved[16];
+};
+static_assert(sizeof(PlanFileHeader) == 96, "plan file header is 96 bytes");
+
+// 64-bit FNV-1a over the payload's 8-byte words (offset basis and prime of
+// FNV-1a 64), continued from h
+uint64_t payload_hash(const std::vector<double2>& v, uint64_t h) {
+  const uint64_t* w = reinterpret_cast<const uint64_t*>(v.data());
+  for (size_t i = 0, n = v.size() * 2; i < n; ++i) {
+    h ^= w[i];
+    h *= 1099511628211ULL;
+  }
+  return h;
+}
+constexpr uint64_t kHashBasis = 14695981039346656037ULL;
+
+struct File {
+  FILE* f = nullptr;
+  ~File() {
+    if (f) fclose(f);
+  }
+};
+
+}  // namespace
+
+vp_status vp_plan_save(vp_plan p, const char* path) {
+  if (!p || !path) return fail(p, VP_ERR_INVALID_ARG, "plan or path is NULL");
+  VP_ON_DEVICE(p, p->device);
+  VP_CUDA(p, cudaStreamSynchronize(p->stream));
+  std::vector<const double2*> arrays = {p->T64, p->G64u};
+  if (p->grad_built)
+    for (int j = 0; j < p->d; ++j) {
+      arrays.push_back(p->Tj64[j]);
+      arrays.push_back(p->Gj64u[j]);
+    }
+  PlanFileHeader h;
+  memset(&h, 0, sizeof(h));
+  memcpy(h.magic, kPlanMagic, 8);
+  h.version = 1;
+  h.header_bytes = sizeof(h);
+  h.d = p->d;
+  for (int a = 0; a < 3; ++a) h.N[a] = a < p->d ? p->Nv[a] : 0;
+  h.kernel = p->kernel;
+  h.grad = p->grad_built ? 1 : 0;
+  h.k = p->k;
+  h.L = p->L;
+  h.oct = p->oct;
+  h.payload_bytes = (uint64_t)arrays.size() * (uint64_t)p->oct * sizeof(double2);
+  File out;
+  out.f = fopen(path, "wb");
+  if (!out.f) return fail(p, VP_ERR_INVALID_ARG, std::string("cannot open for writing: ") + path);
+  if (fwrite(&h, sizeof(h), 1, out.f) != 1) return fail(p, VP_ERR_INVALID_ARG, "write failed");
+  std::vector<double2> buf((size_t)p->oct);
+  uint64_t hash = kHashBasis;
+  for (const double2* a : arrays) {
+    VP_CUDA(p, cudaMemcpy(buf.data(), a, buf.size() * sizeof(double2), cudaMemcpyDeviceToHost));
+    hash = payload_hash(buf, hash);
+    if (fwrite(buf.data(), sizeof(double2), buf.size(), out.f) != buf.size())
+      return fail(p, VP_ERR_INVALID_ARG, "write failed");
+  }
+  h.checksum = hash;
+  if (fseek(out.f, 0, SEEK_SET) != 0 || fwrite(&h, sizeof(h), 1, out.f) != 1)
+    return fail(p, VP_ERR_INVALID_ARG, "write failed");
+  if (fclose(out.f) != 0) {
+    out.f = nullptr;
+    return fail(p, VP_ERR_INVALID_ARG, "write failed");
+  }
+  out.f = nullptr;
+  return VP_OK;
+}
+
+vp_status vp_plan_load(vp_plan* out, const char* path) {
+  if (!out || !path) return fail(nullptr, VP_ERR_INVALID_ARG, "out or path is NULL");
+  *out = nullptr;
+  File in;
+  in.f = fopen(path, "rb");
+  if (!in.f) return fail(nullptr, VP_ERR_INVALID_ARG, std::string("cannot open: ") + path);
+  PlanFileHeader h;
+  if (fread(&h, sizeof(h), 1, in.f) != 1 || memcmp(h.magic, kPlanMagic, 8) != 0 || h.version != 1 ||
+      h.header_bytes != sizeof(h))
+    return fail(nullptr, VP_ERR_INVALID_ARG, "not a saved plan (magic, version or header size)");
+  if ((h.d != 2 && h.d != 3) || (h.grad != 0 && h.grad != 1))
+    return fail(nullptr, VP_ERR_INVALID_ARG, "saved plan: bad dimension or flags");
+  int Ns[3] = {0, 0, 0};
+  long long oct = 1;
+  for (int a = 0; a < h.d; ++a) {
+    if (h.N[a] < 4 || h.N[a] > (1 << 16)) return fail(nullptr, VP_ERR_INVALID_ARG, "saved plan: bad grid size");
+    Ns[a] = h.N[a];
+    oct *= h.N[a] + 1;
+  }
+  const uint64_t narrays = 2 + (h.grad ? 2 * h.d : 0);
+  if (h.oct != oct || h.payload_bytes != narrays * (uint64_t)oct * sizeof(double2))
+    return fail(nullptr, VP_ERR_INVALID_ARG, "saved plan: sizes do not match the grid");
+  PlanPayload pl;
+  pl.grad = h.grad != 0;
+  std::vector<std::vector<double2>*> arrays = {&pl.T, &pl.Gu};
+  if (pl.grad)
+    for (int j = 0; j < h.d; ++j) {
+      arrays.push_back(&pl.Tj[j]);
+      arrays.push_back(&pl.Gju[j]);
+    }
+  uint64_t hash = kHashBasis;
+  for (std::vector<double2>* a : arrays) {
+    a->resize((size_t)oct);
+    if (fread(a->data(), sizeof(double2), a->size(), in.f) != a->size())
+      return fail(nullptr, VP_ERR_INVALID_ARG, "saved plan: the file is truncated");
+    hash = payload_hash(*a, hash);
+  }
+  if (fgetc(in.f) != EOF) return fail(nullptr, VP_ERR_INVALID_ARG, "saved plan: trailing bytes");
+  if (hash != h.checksum) return fail(nullptr, VP_ERR_INVALID_ARG, "saved plan: checksum mismatch");
+  return plan_create_common(out, h.d, Ns, (vp_kernel)h.kernel, h.k, h.L, &pl);
+}
+
+vp_status vp_plan_kernel(vp_plan p, vp_kernel* kernel) {
+  if (!p || !kernel) return fail(p, VP_ERR_INVALID_ARG, "plan or kernel is NULL");
+  *kernel = (vp_kernel)p->kernel;
   return VP_OK;
 }
 

@@ -58,6 +58,9 @@ _SIGNATURES = {
     "vp_plan_create_aniso": (c_int, [ctypes.POINTER(c_void_p), c_int, ctypes.POINTER(c_int), c_int, c_double,
                                      c_double]),
     "vp_plan_dims": (c_int, [c_void_p, ctypes.POINTER(c_int)]),
+    "vp_plan_save": (c_int, [c_void_p, c_char_p]),
+    "vp_plan_load": (c_int, [ctypes.POINTER(c_void_p), c_char_p]),
+    "vp_plan_kernel": (c_int, [c_void_p, ctypes.POINTER(c_int)]),
     "vp_plan_set_host_access": (c_int, [c_void_p, c_int]),
     "vp_plan_autotune": (c_int, [c_void_p, c_int]),
     "vp_plan_pass_config": (c_int, [c_void_p, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int), c_char_p, c_size_t]),
@@ -268,6 +271,34 @@ class Plan:
         self._stream = stream
         if stream is not None:
             self.set_stream(stream)
+
+    def save(self, path):
+        """Write the plan's precompute results to `path` (vp_plan_save)."""
+        _check(lib().vp_plan_save(self.handle, os.fsencode(path)), self.handle)
+
+    @classmethod
+    def load(cls, path, precision: str = "fp32", grad_mode: str = "exact", stream=None) -> "Plan":
+        """A plan from a file written by save(), without the precompute."""
+        out = c_void_p()
+        _check(lib().vp_plan_load(ctypes.byref(out), os.fsencode(path)))
+        self = cls.__new__(cls)
+        self.handle = out.value
+        d, kern = c_int(), c_int()
+        _check(lib().vp_plan_info(self.handle, ctypes.byref(d), None, None, None, None), self.handle)
+        dims = (c_int * 3)()
+        _check(lib().vp_plan_dims(self.handle, dims), self.handle)
+        _check(lib().vp_plan_kernel(self.handle, ctypes.byref(kern)), self.handle)
+        self.d = d.value
+        self.dims = tuple(dims[: self.d])
+        self.N = self.dims[0] if len(set(self.dims)) == 1 else self.dims
+        self.kernel = {v: name for name, v in KERNELS.items()}[kern.value]
+        self.precision = precision
+        vp_plan_set_precision(self.handle, PRECISIONS[precision])
+        vp_plan_set_grad_mode(self.handle, GRAD_MODES[grad_mode])
+        self._stream = stream
+        if stream is not None:
+            self.set_stream(stream)
+        return self
 
     def set_stream(self, stream):
         """A torch.cuda.Stream, a raw cudaStream_t (int) or None (legacy default)."""

@@ -110,3 +110,18 @@ def test_pipeline_tensor_core_precision():
     with pytest.raises(VPError):  # the tensor-core precisions serve the potential only
         plan.apply_pipeline(fs, with_grad=True)
     plan.close()
+
+
+def test_pipeline_full_size_3d_n256():
+    """The bench workload's grid (3D Helmholtz k = 60, N = 256: 2N = 512, the
+    TMA fused pass): four densities through three slots, each output equal to
+    the device-resident apply bit for bit."""
+    N = 256
+    plan = Plan(3, N, "helmholtz", 60.0, 1.8, precision="fp32")
+    fs = _densities(3, N, 4, 8800)
+    phis, _ = plan.apply_pipeline(fs)
+    for f, phi in zip(fs, phis):
+        dev = plan.apply(f.to("cuda:0"))
+        torch.cuda.synchronize()
+        assert torch.equal(phi, dev.cpu())
+    plan.close()

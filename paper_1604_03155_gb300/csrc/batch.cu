@@ -879,6 +879,7 @@ vp_status vp_batch_withhold(vp_batch b, int density, int pass) {
 }
 
 vp_status vp_batch_apply(vp_batch b, const void* const* f, void* const* phi) {
+  vp::NvtxRange range("vp_batch_apply");
   if (!b || !f || !phi) return VP_ERR_INVALID_ARG;
   for (int i = 0; i < b->count; ++i)
     if (!f[i] || !phi[i]) return bfail(b, VP_ERR_INVALID_ARG, "NULL density pointer");

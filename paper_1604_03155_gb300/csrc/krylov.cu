@@ -1520,6 +1520,7 @@ extern "C" {
 
 vp_status vp_ls_bicgstab(vp_plan plan, const void* q, const void* u_inc, void* u, vp_dtype dtype, int form,
                          double tol, int maxit, double* history, vp_ls_stats* stats) {
+  vp::NvtxRange range("vp_ls_bicgstab");
   long long n = 0;
   int d = 0;
   double k = 0.0;

@@ -590,6 +590,7 @@ vp_status vp_ls_rhs(vp_plan plan, const float* q, const void* u_inc, void* b) {
 
 vp_status vp_ls_solve(vp_plan plan, const float* q, const void* b, const void* u_inc, void* u, const vp_ls_opts* opts,
                       vp_ls_stats* stats) {
+  vp::NvtxRange range("vp_ls_solve");
   long long n;
   double k2;
   vp_status st = check_plan(plan, &n, &k2);

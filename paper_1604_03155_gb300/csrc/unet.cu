@@ -489,6 +489,7 @@ vp_status vp_unet_get_weights(vp_unet u, int which, float* host, size_t count) {
 }
 
 vp_status vp_unet_forward(vp_unet u, const float* in, float* out) {
+  vp::NvtxRange range("vp_unet_forward");
   if (!u || !in || !out) return VP_ERR_INVALID_ARG;
   vp::DeviceGuard dg_(u->device);
   cudaError_t e = forward(u, in, u->stream);

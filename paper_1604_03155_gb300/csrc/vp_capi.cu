@@ -322,6 +322,7 @@ bool is_tc(vp_precision pr) { return pr == VP_TC_BF16X2 || pr == VP_TC_FP16X2 ||
 
 template <typename Real>
 cudaError_t launch_pass(vp_plan p, int pass, PassKind kind, const PassArgs<Real>& a, int len) {
+  vp::NvtxRange range(kPassNames[pass]);
   TimedLaunch tl{pass, nullptr, nullptr};
   if (p->timing && p->timed.size() < 100000) {
     tl.start = pool_event(p);
@@ -1247,6 +1248,7 @@ vp_status vp_plan_set_pass_config(vp_plan p, int pass, int cfg) {
 // current choice when the apply gets more than 1% faster.  The choices are
 // cached on disk per device, driver and grid; flags & 1 ignores the cache.
 vp_status vp_plan_autotune(vp_plan p, int flags) {
+  vp::NvtxRange range("vp_plan_autotune");
   if (!p) return fail(nullptr, VP_ERR_INVALID_ARG, "plan is NULL");
   if (p->prec != VP_FP32) return fail(p, VP_ERR_UNSUPPORTED, "the autotuner tunes the FP32 passes: set VP_FP32 first");
   VP_ON_DEVICE(p, p->device);
@@ -1377,15 +1379,18 @@ vp_status vp_plan_set_grad_mode(vp_plan p, vp_grad_mode mode) {
 }
 
 vp_status vp_apply(vp_plan p, const void* f, void* phi, vp_dtype dtype) {
+  vp::NvtxRange range("vp_apply");
   return apply_common(p, f, phi, nullptr, dtype, false);
 }
 
 vp_status vp_apply_pipeline(vp_plan p, int count, const void* const* f, void* const* phi, void* const* grad,
                             vp_dtype dtype) {
+  vp::NvtxRange range("vp_apply_pipeline");
   return apply_pipeline(p, count, f, phi, grad, dtype);
 }
 
 vp_status vp_apply_grad(vp_plan p, const void* f, void* phi, void* grad, vp_dtype dtype) {
+  vp::NvtxRange range("vp_apply_grad");
   return apply_common(p, f, phi, grad, dtype, true);
 }
 

@@ -7,10 +7,24 @@
 
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/vp.h"
 #include "pencil_fft.cuh"
 
 namespace vp {
+
+// An NVTX range (domain-less push/pop) for the scope: the library's entry
+// points and pass launches appear by name in profilers (ncu --nvtx
+// --nvtx-include "fused_axis0/"); without a tool attached it costs a function
+// pointer test.
+class NvtxRange {
+ public:
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Gauss-Legendre nodes of the 2D Helmholtz spectrum near s = k.
 constexpr int GL_NODES = 24;

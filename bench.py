@@ -235,8 +235,9 @@ def _oracle_worker(wl: dict, N: int, barrier, cmd, res):
     command one full apply, started together with the other workers."""
     sw = dict(wl, N=N)
     f = density_sample(wl, N)
+    t0 = time.perf_counter()
     Gf, Gjf = oracle_setup(sw)
-    res.put("ready")
+    res.put(("ready", time.perf_counter() - t0))
     while cmd.get() is not None:
         barrier.wait()
         t0, c0 = time.perf_counter(), time.process_time()
@@ -259,8 +260,11 @@ class OraclePool:
                    for c in self.cmds]
         for p in self.ps:
             p.start()
+        self.setup_seconds = []  # each worker's precompute (kernel octants and multipliers)
         for _ in self.ps:
-            assert self.res.get(timeout=600) == "ready"
+            tag, secs = self.res.get(timeout=600)
+            assert tag == "ready"
+            self.setup_seconds.append(secs)
 
     def step(self) -> dict:
         """One apply on every worker at once: points/s of the whole host, wall
@@ -317,6 +321,7 @@ def cpu_baseline(wl: dict, name: str) -> dict:
     pool.close()
     one = OraclePool(w, Ns, 1)
     single = one.step()
+    single_setup = one.setup_seconds[0]
     one.close()
     return {"value": allc["value"], "unit": "grid pts/s", "cores": allc["cores"], "kind": "oracle",
             "sample": (f"{hc['nproc']} worker processes at once, each one full apply "
@@ -325,7 +330,8 @@ def cpu_baseline(wl: dict, name: str) -> dict:
                        f"with its own FFT, {allc['seconds']:.1f} s wall"),
             "nproc": hc["nproc"], "cpu_model": hc["cpu_model"],
             "single_thread": {"value": single["value"], "unit": "grid pts/s", "cores": single["cores"],
-                              "seconds": single["seconds"]}}
+                              "seconds": single["seconds"], "precompute_seconds": single_setup,
+                              "precompute": f"the oracle's kernel octants and multipliers for the N={Ns} grid"}}
 
 
 def oracle_reference(wl: dict, f_host: np.ndarray, npts: int = 40, seed: int = 1604) -> dict:

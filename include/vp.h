@@ -531,6 +531,14 @@ vp_status vp_unet_get_weights(vp_unet net, int which /* 0 FP32, 1 BF16-rounded, 
 vp_status vp_unet_forward(vp_unet net, const float* in, float* out);
 vp_status vp_unet_loss_grad(vp_unet net, const float* in, const float* target, double* loss);
 vp_status vp_unet_adam_step(vp_unet net, double lr);
+/* Training checkpoints: Adam's first and second moments (vp_unet_param_count
+ * floats each, host memory) and its step count.  vp_unet_set_weights resets
+ * them, so a resume calls vp_unet_set_weights, then vp_unet_set_adam; the
+ * next vp_unet_adam_step then continues exactly as the saved run would have.
+ * VP_ERR_INVALID_ARG for a NULL argument, a count other than the parameter
+ * count or a negative step.  Both synchronise the network's stream. */
+vp_status vp_unet_get_adam(vp_unet net, float* m, float* v, size_t count, long long* step);
+vp_status vp_unet_set_adam(vp_unet net, const float* m, const float* v, size_t count, long long step);
 /* Leaky-ReLU slope in [0, 1] (default 0.1); 1 makes the network linear in its input. */
 vp_status vp_unet_set_slope(vp_unet net, double slope);
 vp_status vp_unet_bind(vp_unet net, const float* q);

@@ -528,6 +528,28 @@ vp_status vp_unet_loss_grad(vp_unet u, const float* in, const float* target, dou
   return VP_OK;
 }
 
+vp_status vp_unet_get_adam(vp_unet u, float* m, float* v, size_t count, long long* step) {
+  if (!u || !m || !v || !step || count != (size_t)u->nparams)
+    return ufail(u, VP_ERR_INVALID_ARG, "Adam state: NULL argument or count mismatch");
+  vp::DeviceGuard dg_(u->device);
+  if (cudaStreamSynchronize(u->stream) != cudaSuccess ||
+      cudaMemcpy(m, u->m, count * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(v, u->v, count * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return ufail(u, VP_ERR_CUDA, "Adam state: copy failed");
+  *step = u->step;
+  return VP_OK;
+}
+vp_status vp_unet_set_adam(vp_unet u, const float* m, const float* v, size_t count, long long step) {
+  if (!u || !m || !v || count != (size_t)u->nparams || step < 0)
+    return ufail(u, VP_ERR_INVALID_ARG, "Adam state: NULL argument, count mismatch or negative step");
+  vp::DeviceGuard dg_(u->device);
+  if (cudaStreamSynchronize(u->stream) != cudaSuccess ||
+      cudaMemcpy(u->m, m, count * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(u->v, v, count * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+    return ufail(u, VP_ERR_CUDA, "Adam state: copy failed");
+  u->step = step;
+  return VP_OK;
+}
 vp_status vp_unet_adam_step(vp_unet u, double lr) {
   if (!u || !(lr > 0)) return VP_ERR_INVALID_ARG;
   vp::DeviceGuard dg_(u->device);

@@ -98,3 +98,19 @@ def save_weights(net, path: str):
 
 def load_weights(net, path: str):
     net.set_weights(np.load(path))
+
+
+def save_checkpoint(net, path: str, **extra):
+    """Weights, Adam state and any extra scalars (e.g. the next contrast index)
+    in one .npz file."""
+    m, v, step = net.get_adam()
+    np.savez(path, weights=net.get(0), adam_m=m, adam_v=v, adam_step=np.int64(step),
+             **{k: np.asarray(val) for k, val in extra.items()})
+
+
+def load_checkpoint(net, path: str) -> dict:
+    """Restores weights and Adam state; returns the extra scalars."""
+    z = np.load(path)
+    net.set_weights(z["weights"])
+    net.set_adam(z["adam_m"], z["adam_v"], int(z["adam_step"]))
+    return {k: z[k].item() for k in z.files if k not in ("weights", "adam_m", "adam_v", "adam_step")}

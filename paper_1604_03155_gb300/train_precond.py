@@ -3,8 +3,9 @@
     python -m paper_1604_03155_gb300.train_precond --N 128 --k 30 --contrasts 2000 \
         --heldout 50 --out paper_1604_03155_gb300/weights/unet_ls_k30_n128
 
-Writes <out>.npy (the FP32 master weights, layer order of vp_unet) and
-<out>.json (training loss, and plain vs preconditioned flexible GMRES on the
+Writes <out>.npy (the FP32 master weights, layer order of vp_unet),
+<out>.ckpt.npz (weights, Adam state and the next contrast index, for --resume)
+and <out>.json (training loss, and plain vs preconditioned flexible GMRES on the
 held-out contrasts: iterations, seconds, true FP64 residual).
 """
 from __future__ import annotations
@@ -39,6 +40,8 @@ def main():
     ap.add_argument("--init", default=None, help="start from these weights (.npy) instead of the seeded init")
     ap.add_argument("--first", type=int, default=0, help="index of the first training contrast")
     ap.add_argument("--onpolicy", action="store_true", help="add pairs from the network's own FGMRES directions")
+    ap.add_argument("--resume", default=None,
+                    help="continue from a checkpoint (.npz: weights, Adam state, next contrast index)")
     ap.add_argument("--out", default=os.path.join(ROOT, "paper_1604_03155_gb300", "weights", "unet_ls_k30_n128"))
     a = ap.parse_args()
     os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
@@ -46,10 +49,13 @@ def main():
     net = vp.UNet(a.N, 16, weights=I.unet_init_weights(I.BASE_SEED + 901), slope=a.slope)
     if a.init:
         P.load_weights(net, a.init)
+    if a.resume:
+        a.first = int(P.load_checkpoint(net, a.resume).get("next_contrast", a.first))
     seeds = [I.LS_TRAIN_SEED + a.first + i for i in range(a.contrasts)]
     tr = P.train(plan, net, a.N, a.k, seeds, krylov=a.krylov, lr=a.lr, restart=a.restart, onpolicy=a.onpolicy,
                  log=lambda m: print(m, flush=True))
     P.save_weights(net, a.out + ".npy")
+    P.save_checkpoint(net, a.out + ".ckpt.npz", next_contrast=a.first + a.contrasts)
     ev = P.evaluate(plan, net, a.N, a.k, [I.LS_HELDOUT_SEED + i for i in range(a.heldout)], tol=a.tol,
                     restart=a.restart)
     report = {"N": a.N, "k": a.k, "slope": a.slope, "contrasts": a.contrasts, "first": a.first, "init": a.init,

@@ -119,6 +119,8 @@ _SIGNATURES = {
     "vp_unet_set_weights": (c_int, [c_void_p, c_void_p, c_size_t]),
     "vp_unet_get_weights": (c_int, [c_void_p, c_int, c_void_p, c_size_t]),
     "vp_unet_forward": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "vp_unet_get_adam": (c_int, [c_void_p, c_void_p, c_void_p, c_size_t, ctypes.POINTER(ctypes.c_longlong)]),
+    "vp_unet_set_adam": (c_int, [c_void_p, c_void_p, c_void_p, c_size_t, ctypes.c_longlong]),
     "vp_unet_loss_grad": (c_int, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_double)]),
     "vp_unet_adam_step": (c_int, [c_void_p, c_double]),
     "vp_unet_bind": (c_int, [c_void_p, c_void_p]),
@@ -778,6 +780,20 @@ class UNet:
 
     def adam_step(self, lr: float):
         self._check(lib().vp_unet_adam_step(self.handle, lr))
+
+    def get_adam(self):
+        """(first moments, second moments, step count) of the optimiser."""
+        m, v = np.empty(self.nparams, np.float32), np.empty(self.nparams, np.float32)
+        step = ctypes.c_longlong()
+        self._check(lib().vp_unet_get_adam(self.handle, m.ctypes.data, v.ctypes.data, self.nparams, ctypes.byref(step)))
+        return m, v, step.value
+
+    def set_adam(self, m, v, step: int):
+        m = np.ascontiguousarray(m, dtype=np.float32)
+        v = np.ascontiguousarray(v, dtype=np.float32)
+        if m.size != self.nparams or v.size != self.nparams:
+            raise VPError(VP_ERR_INVALID_ARG, "Adam state: one value per parameter")
+        self._check(lib().vp_unet_set_adam(self.handle, m.ctypes.data, v.ctypes.data, self.nparams, int(step)))
 
     def status(self):
         """Synchronises the network's stream; raises on a timed-out convolution."""

@@ -201,3 +201,46 @@ def test_bounded_wait_timeout_is_reported_and_recoverable():
     net.status()
     assert np.array_equal(out, ref)
     net.close()
+
+
+def test_training_resumes_from_a_checkpoint(tmp_path):
+    """Weights and Adam state saved after 5 steps and restored into a fresh
+    network give, after 5 more steps, the same weights bit for bit as the run
+    that never stopped; restoring the weights alone (Adam state reset) does not."""
+    from paper_1604_03155_gb300 import precond as P
+    S = 16
+    xh = I.random_complex_field(I.BASE_SEED + 321, (3, S, S, S)).real.astype(np.float32)
+    x = torch.from_numpy(xh).to(DEV)
+    t = torch.from_numpy(0.5 * xh[:2]).to(DEV)
+
+    def steps(net, n):
+        for _ in range(n):
+            net.loss_grad(x, t)
+            net.adam_step(3e-3)
+
+    a = UNet(S, 16, weights=_weights(I.BASE_SEED + 320))
+    steps(a, 5)
+    ck = str(tmp_path / "ck.npz")
+    P.save_checkpoint(a, ck, next_contrast=5)
+    m, v, step = a.get_adam()
+    assert step == 5 and np.abs(m).max() > 0 and v.min() >= 0
+    steps(a, 5)
+    ref = a.get(0)
+
+    b = UNet(S, 16)
+    extra = P.load_checkpoint(b, ck)
+    assert extra == {"next_contrast": 5} and b.get_adam()[2] == 5
+    steps(b, 5)
+    assert np.array_equal(b.get(0), ref)
+
+    c = UNet(S, 16)
+    c.set_weights(np.load(ck)["weights"])
+    assert c.get_adam()[2] == 0
+    steps(c, 5)
+    assert not np.array_equal(c.get(0), ref)
+    with pytest.raises(vp.VPError):
+        c.set_adam(m[:-1], v, 1)
+    with pytest.raises(vp.VPError):
+        c.set_adam(m, v, -1)
+    for net in (a, b, c):
+        net.close()

@@ -316,6 +316,7 @@ int vp_fft_length_supported(int n2);
  * vp_batch_set_chunk fixes the chunk size (1..256; 0 = the autotuner's
  * choice, 8 before tuning); vp_batch_get_chunk reports the one in use.
  * Failure detection: a wait longer than the batch timeout (default about 2 s,
+ * or VP_TIMEOUT_MS milliseconds from the environment at vp_batch_create;
  * vp_batch_set_timeout) records an error and lets the kernel finish;
  * vp_batch_status then returns VP_ERR_TIMEOUT.  vp_batch_withhold(b, i, p)
  * (p >= 1) makes pass p of density i wait for one tile more than its
@@ -544,7 +545,8 @@ vp_status vp_unet_set_slope(vp_unet net, double slope);
 vp_status vp_unet_bind(vp_unet net, const float* q);
 vp_status vp_unet_precond(void* ctx, const void* r, void* z, void* stream);
 vp_status vp_unet_status(vp_unet net);
-/* Budget of each bounded wait of the tensor-core kernels (default about 2 s;
+/* Budget of each bounded wait of the tensor-core kernels (default about 2 s,
+ * or VP_TIMEOUT_MS milliseconds from the environment at vp_unet_create;
  * seconds > 0).  vp_unet_withhold is a test hook: on != 0 makes the kernels
  * issue no MMAs, so their waits run out and the next status check reports
  * VP_ERR_TIMEOUT.  Every report clears the error word. */

@@ -807,6 +807,7 @@ vp_status vp_batch_create(vp_batch* out, int count, const vp_plan* plans) {
   const int cached = vp::autotune_cache_lookup(sig);
   b->strategy = cached % 100;
   if (cached >= 100) b->chunk = cached / 100;
+  if (const double secs = vp::env_timeout_seconds()) vp_batch_set_timeout(b, secs);
   *out = b;
   return VP_OK;
 }

@@ -453,6 +453,7 @@ vp_status vp_unet_create(vp_unet* out, int S, int C) {
     vp_unet_destroy(u);
     return e == cudaErrorMemoryAllocation ? VP_ERR_OOM : VP_ERR_CUDA;
   }
+  if (const double secs = vp::env_timeout_seconds()) vp_unet_set_timeout(u, secs);
   *out = u;
   return VP_OK;
 }

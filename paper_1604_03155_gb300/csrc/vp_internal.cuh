@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 #include <string>
 
@@ -13,6 +14,17 @@
 #include "pencil_fft.cuh"
 
 namespace vp {
+
+// The default budget of the bounded device waits of batches and networks from
+// the environment: VP_TIMEOUT_MS (milliseconds, > 0) in seconds, else 0 (keep
+// the built-in default).  Read at vp_batch_create and vp_unet_create.
+inline double env_timeout_seconds() {
+  const char* s = getenv("VP_TIMEOUT_MS");
+  if (!s || !*s) return 0.0;
+  char* end = nullptr;
+  const double ms = strtod(s, &end);
+  return (end && *end == '\0' && ms > 0.0 && ms < 1e12) ? ms * 1e-3 : 0.0;
+}
 
 // An NVTX range (domain-less push/pop) for the scope: the library's entry
 // points and pass launches appear by name in profilers (ncu --nvtx

@@ -244,3 +244,27 @@ def test_training_resumes_from_a_checkpoint(tmp_path):
         c.set_adam(m, v, -1)
     for net in (a, b, c):
         net.close()
+
+
+def test_wait_budget_from_the_environment(monkeypatch):
+    """VP_TIMEOUT_MS sets the bounded waits' budget at vp_unet_create: with the
+    MMAs withheld a forward reports VP_ERR_TIMEOUT after about 1 ms per
+    convolution, not after the built-in 2 s."""
+    import time
+    monkeypatch.setenv("VP_TIMEOUT_MS", "1")
+    S = 8
+    net = UNet(S, 16, weights=_weights(5))
+    x = torch.from_numpy(I.normal(92, 3 * S ** 3).astype(np.float32).reshape(3, S, S, S)).to(DEV)
+    ref = net.forward(x).cpu().numpy()
+    net.withhold(True)
+    t0 = time.perf_counter()
+    net.forward(x)
+    with pytest.raises(vp.VPError) as ei:
+        net.status()
+    elapsed = time.perf_counter() - t0
+    assert ei.value.status == vp.VP_ERR_TIMEOUT
+    assert elapsed < 1.0, elapsed
+    net.withhold(False)
+    net.status()
+    assert np.array_equal(net.forward(x).cpu().numpy(), ref)
+    net.close()

@@ -33,6 +33,10 @@
  *   block j = d phi / d x_j.
  * Errors: every call returns a vp_status and never aborts; argument errors are
  *   reported before any device work.  vp_last_error() gives a message.
+ * Environment: VP_LOG=1 also writes every recorded error message to stderr
+ *   ("vp: <object>: <message>"), VP_LOG=2 the pass autotuner's choices too;
+ *   VP_TIMEOUT_MS sets the default wait budget of batches and networks;
+ *   VP_AUTOTUNE_CACHE names the autotuners' cache file.
  */
 #ifndef VP_H
 #define VP_H

@@ -445,6 +445,7 @@ struct vp_batch_s {
 namespace {
 
 vp_status bfail(vp_batch b, vp_status st, const std::string& m) {
+  vp::log_line(1, "batch", m);
   if (b) b->last_error = m;
   return st;
 }

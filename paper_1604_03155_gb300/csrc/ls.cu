@@ -505,6 +505,7 @@ vp_status fgmres_cycle(const Ctx& c, Work& w, const float2* b, float2* x, double
 thread_local std::string g_ls_error;
 
 vp_status ls_fail(vp_status st, const std::string& m) {
+  vp::log_line(1, "solver", m);
   g_ls_error = m;
   return st;
 }
@@ -548,7 +549,10 @@ vp_status alloc_work(Work& w, long long n, int m, bool basis, bool fp64 = true) 
 }  // namespace
 
 namespace vp {
-void ls_set_error(const char* msg) { g_ls_error = msg; }
+void ls_set_error(const char* msg) {
+  g_ls_error = msg;
+  vp::log_line(1, "solver", g_ls_error);
+}
 }  // namespace vp
 
 extern "C" {

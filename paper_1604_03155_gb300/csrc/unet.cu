@@ -248,6 +248,7 @@ struct vp_unet_s {
 namespace {
 
 vp_status ufail(vp_unet u, vp_status st, const std::string& m) {
+  vp::log_line(1, "network", m);
   if (u) u->last_error = m;
   return st;
 }

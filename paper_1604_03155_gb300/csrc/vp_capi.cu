@@ -91,6 +91,7 @@ struct vp_plan_s {
 namespace {
 
 vp_status fail(vp_plan p, vp_status st, const std::string& msg) {
+  vp::log_line(1, "plan", msg);
   if (p)
     p->last_error = msg;
   else
@@ -770,6 +771,18 @@ vp_status apply_pipeline(vp_plan p, int count, const void* const* f, void* const
 // ---------------------------------------------------------------------------
 namespace vp {
 
+int log_level() {
+  static const int level = [] {
+    const char* s = getenv("VP_LOG");
+    return (s && *s >= '0' && *s <= '9') ? atoi(s) : 0;
+  }();
+  return level;
+}
+
+void log_line(int level, const char* what, const std::string& msg) {
+  if (log_level() >= level) fprintf(stderr, "vp: %s: %s\n", what, msg.c_str());
+}
+
 int plan_device(vp_plan p) { return p ? p->device : -1; }
 
 cudaStream_t plan_stream(vp_plan p) { return p ? p->stream : nullptr; }
@@ -1329,6 +1342,11 @@ vp_status vp_plan_autotune(vp_plan p, int flags) {
   int code = 0;
   for (int i = 0; i < NPASS; ++i) code |= p->pass_cfg[i] << (3 * i);
   autotune_cache_store(key, code + 1);
+  if (vp::log_level() >= 2) {
+    std::string m = key + " ->";
+    for (int pass = 0; pass < NPASS; ++pass) m += " " + std::string(kPassNames[pass]) + "=" + std::to_string(p->pass_cfg[pass]);
+    vp::log_line(2, "autotune", m);
+  }
   return VP_OK;
 }
 

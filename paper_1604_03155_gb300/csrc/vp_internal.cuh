@@ -26,6 +26,12 @@ inline double env_timeout_seconds() {
   return (end && *end == '\0' && ms > 0.0 && ms < 1e12) ? ms * 1e-3 : 0.0;
 }
 
+// VP_LOG from the environment (read once): 0 silent (default), 1 every error
+// message the library records, 2 also the autotuners' choices.  Messages go
+// to stderr, one line each, prefixed "vp: ".
+int log_level();
+void log_line(int level, const char* what, const std::string& msg);
+
 // An NVTX range (domain-less push/pop) for the scope: the library's entry
 // points and pass launches appear by name in profilers (ncu --nvtx
 // --nvtx-include "fused_axis0/"); without a tool attached it costs a function

@@ -7,6 +7,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <new>
 #include <string>
 #include <vector>
 
@@ -1136,7 +1137,12 @@ vp_status vp_plan_save(vp_plan p, const char* path) {
   out.f = fopen(path, "wb");
   if (!out.f) return fail(p, VP_ERR_INVALID_ARG, std::string("cannot open for writing: ") + path);
   if (fwrite(&h, sizeof(h), 1, out.f) != 1) return fail(p, VP_ERR_INVALID_ARG, "write failed");
-  std::vector<double2> buf((size_t)p->oct);
+  std::vector<double2> buf;
+  try {
+    buf.resize((size_t)p->oct);
+  } catch (const std::bad_alloc&) {
+    return fail(p, VP_ERR_OOM, "saving the plan: host memory for one octant");
+  }
   uint64_t hash = kHashBasis;
   for (const double2* a : arrays) {
     VP_CUDA(p, cudaMemcpy(buf.data(), a, buf.size() * sizeof(double2), cudaMemcpyDeviceToHost));
@@ -1177,6 +1183,15 @@ vp_status vp_plan_load(vp_plan* out, const char* path) {
   const uint64_t narrays = 2 + (h.grad ? 2 * h.d : 0);
   if (h.oct != oct || h.payload_bytes != narrays * (uint64_t)oct * sizeof(double2))
     return fail(nullptr, VP_ERR_INVALID_ARG, "saved plan: sizes do not match the grid");
+  // the file must hold exactly the header and the payload it announces; checked
+  // before anything of the payload's size is allocated
+  if (fseek(in.f, 0, SEEK_END) != 0) return fail(nullptr, VP_ERR_INVALID_ARG, "saved plan: cannot seek");
+  const long long fsize = (long long)ftell(in.f);
+  if (fsize < (long long)sizeof(h) + (long long)h.payload_bytes)
+    return fail(nullptr, VP_ERR_INVALID_ARG, "saved plan: the file is truncated");
+  if (fsize > (long long)sizeof(h) + (long long)h.payload_bytes)
+    return fail(nullptr, VP_ERR_INVALID_ARG, "saved plan: trailing bytes");
+  if (fseek(in.f, (long)sizeof(h), SEEK_SET) != 0) return fail(nullptr, VP_ERR_INVALID_ARG, "saved plan: cannot seek");
   PlanPayload pl;
   pl.grad = h.grad != 0;
   std::vector<std::vector<double2>*> arrays = {&pl.T, &pl.Gu};
@@ -1187,7 +1202,11 @@ vp_status vp_plan_load(vp_plan* out, const char* path) {
     }
   uint64_t hash = kHashBasis;
   for (std::vector<double2>* a : arrays) {
-    a->resize((size_t)oct);
+    try {
+      a->resize((size_t)oct);
+    } catch (const std::bad_alloc&) {
+      return fail(nullptr, VP_ERR_OOM, "saved plan: host memory for the payload");
+    }
     if (fread(a->data(), sizeof(double2), a->size(), in.f) != a->size())
       return fail(nullptr, VP_ERR_INVALID_ARG, "saved plan: the file is truncated");
     hash = payload_hash(*a, hash);

@@ -98,3 +98,20 @@ def test_well_formed_file_reaches_the_device(lib, tmp_path):
             assert st == vp.VP_OK, msg
         else:
             assert st == vp.VP_ERR_CUDA, (st, msg)
+
+
+def test_huge_announced_grid_with_a_short_file_is_refused_before_allocating(lib, tmp_path):
+    """A header announcing a 60000^2 grid (two 58 GB octants) on a file of a
+    few hundred bytes: refused as truncated from the file size, at once."""
+    import time
+    d, N = 2, (60000, 60000)
+    oct_ = (N[0] + 1) * (N[1] + 1)
+    header = b"VPPLAN01" + struct.pack("<II", 1, 96) + struct.pack("<5i", d, N[0], N[1], 0, vp.VP_LAPLACE)
+    header += struct.pack("<i", 0) + struct.pack("<dd", 0.0, 1.5) + struct.pack("<q", oct_)
+    header += struct.pack("<QQ", 2 * oct_ * 16, 0) + bytes(16)
+    path = tmp_path / "huge.vpplan"
+    path.write_bytes(header + bytes(256))
+    t0 = time.perf_counter()
+    st, msg = _load(lib, path)
+    assert st == vp.VP_ERR_INVALID_ARG and "truncated" in msg, (st, msg)
+    assert time.perf_counter() - t0 < 1.0
